@@ -1,0 +1,552 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the printed
+Cash-Karp table, Butcher order conditions, closed-form solutions of linear and
+quadratic decay, the Chebyshev stability polynomial of RKC (evaluated with
+numpy's Chebyshev module), the exact Gershgorin bound of a linear chain,
+ideal-gas limits of the rate expressions, conservation laws, and a tight
+scipy reference trajectory.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from numpy.polynomial import chebyshev as C
+
+import oracle
+from paper_1309_2710_gb300 import synth
+from tests import mechs
+
+R_GAS = 8.314462618
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rkck():
+    rows = []
+    with open(os.path.join(GOLDEN, "rkck_table.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append([Fraction(x) for x in line.split()[1:]])
+    a = [r[0] for r in rows]
+    b = [r[1:6] for r in rows]
+    c = [r[6] for r in rows]
+    cs = [r[7] for r in rows]
+    return a, b, c, cs
+
+
+# --------------------------------------------------------------- Table 1 ---
+def test_rkck_table_is_the_printed_table():
+    """Table 1 (T:rkck): every oracle coefficient is the nearest double of the
+    printed rational."""
+    a, b, c, cs = _golden_rkck()
+    oa, ob, oc, ocs = oracle.rkck_table()
+    for i in range(6):
+        assert oa[i] == float(a[i])
+        assert oc[i] == float(c[i])
+        assert ocs[i] == float(cs[i])
+        for j in range(5):
+            assert ob[i, j] == float(b[i][j])
+
+
+def _trees(order):
+    """Rooted trees up to `order` as sorted tuples of children."""
+    by_n = {1: [()]}
+    for n in range(2, order + 1):
+        out = set()
+
+        def parts(remaining, minchild, acc):
+            if remaining == 0:
+                out.add(tuple(sorted(acc)))
+                return
+            for k in range(1, remaining + 1):
+                for t in by_n[k]:
+                    if (k, t) < minchild:
+                        continue
+                    parts(remaining - k, (k, t), acc + [t])
+
+        parts(n - 1, (0, ()), [])
+        by_n[n] = sorted(out)
+    return by_n
+
+
+def _size(t):
+    return 1 + sum(_size(ch) for ch in t)
+
+
+def _gamma(t):
+    g = _size(t)
+    for ch in t:
+        g *= _gamma(ch)
+    return g
+
+
+def _phi(t, A):
+    """Elementary weight vector of tree t for matrix A (exact Fractions)."""
+    s = len(A)
+    v = [Fraction(1)] * s
+    for ch in t:
+        pc = _phi(ch, A)
+        w = [sum(A[i][j] * pc[j] for j in range(s)) for i in range(s)]
+        v = [v[i] * w[i] for i in range(s)]
+    return v
+
+
+def test_rkck_order_conditions_from_oracle_table():
+    """Butcher order conditions: the fifth-order weights satisfy all 17
+    conditions up to order 5 and the embedded weights all 8 up to order 4
+    (checked on the oracle's doubles), and row sums equal the nodes."""
+    oa, ob, oc, ocs = oracle.rkck_table()
+    A = [[Fraction(float(ob[i, j])) if j < i else Fraction(0) for j in range(6)] for i in range(6)]
+    trees = _trees(5)
+    ncond = {4: 0, 5: 0}
+    for n, ts in trees.items():
+        for t in ts:
+            ph = _phi(t, A)
+            lhs5 = sum(Fraction(float(oc[i])) * ph[i] for i in range(6))
+            assert abs(float(lhs5) - 1.0 / _gamma(t)) < 1e-15, (n, t)
+            ncond[5] += 1
+            if n <= 4:
+                lhs4 = sum(Fraction(float(ocs[i])) * ph[i] for i in range(6))
+                assert abs(float(lhs4) - 1.0 / _gamma(t)) < 1e-15, (n, t)
+                ncond[4] += 1
+    assert ncond == {4: 8, 5: 17}
+    for i in range(6):
+        assert abs(sum(ob[i]) - oa[i]) < 1e-15
+    # the embedded solution is not fifth order: some order-5 condition fails
+    bad = 0
+    for t in trees[5]:
+        ph = _phi(t, A)
+        if abs(float(sum(Fraction(float(ocs[i])) * ph[i] for i in range(6))) - 1 / _gamma(t)) > 1e-6:
+            bad += 1
+    assert bad > 0
+
+
+# ----------------------------------------------------------- rate terms ---
+def test_unimolecular_decay_closed_form():
+    """A -> B with equal molar masses: dY_A/dt = -k Y_A, k from Eq. (E:rxn-const)
+    evaluated here with A=3e5, beta=0.7, E=4e4 J/mol at 1234 K."""
+    m = mechs.mech([28.0, 28.0], [dict(reac=[0], prod=[1], A=3e5, beta=0.7, Ea=4e4)])
+    om = oracle.Mech(m)
+    T = 1234.0
+    k = 3e5 * T ** 0.7 * math.exp(-4e4 / (R_GAS * T))
+    for p in (1e4, 101325.0, 2e6):
+        y = np.array([0.3, 0.7])
+        f = oracle.rates(om, T, p, y)
+        assert f[0] == pytest.approx(-k * 0.3, rel=1e-14, abs=0)
+        assert f[1] == pytest.approx(k * 0.3, rel=1e-14, abs=0)
+
+
+def test_third_body_unit_efficiency_is_total_concentration():
+    """With all efficiencies 1, [M] is the total concentration p/(RT) (ideal
+    gas, mol/cm^3), whatever the composition."""
+    W = [2.0, 32.0, 17.0, 17.0, 28.0]
+    base = dict(reac=[0, 1], prod=[2, 3], A=1e12, beta=0.0, Ea=0.0)
+    plain = mechs.mech(W, [base])
+    tb = mechs.mech(W, [dict(base, type=1)], eff_rows=[[1.0] * 5])
+    op, ot = oracle.Mech(plain), oracle.Mech(tb)
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        y = rng.uniform(0.05, 1.0, 5)
+        y /= y.sum()
+        T = rng.uniform(800, 2000)
+        p = rng.uniform(5e4, 2e6)
+        ctot = p / (R_GAS * T) * 1e-6
+        fp = oracle.rates(op, T, p, y)
+        ft = oracle.rates(ot, T, p, y)
+        np.testing.assert_allclose(ft, fp * ctot, rtol=1e-13)
+
+
+def test_falloff_limits():
+    """Lindemann falloff tends to the high-pressure rate when k0[M] >> k_inf and
+    to a third-body rate with k0 when k0[M] << k_inf."""
+    W = [2.0, 32.0, 17.0, 17.0, 28.0]
+    eff = [[1.0, 2.0, 0.5, 1.5, 1.0]]
+    hi = dict(reac=[0, 1], prod=[2, 3], A=1e11, type=2, A0=1e30)
+    lo = dict(reac=[0, 1], prod=[2, 3], A=1e11, type=2, A0=1e-3)
+    plain = oracle.Mech(mechs.mech(W, [dict(reac=[0, 1], prod=[2, 3], A=1e11)]))
+    tb0 = oracle.Mech(mechs.mech(W, [dict(reac=[0, 1], prod=[2, 3], A=1e-3, type=1)], eff))
+    fhi = oracle.Mech(mechs.mech(W, [hi], eff))
+    flo = oracle.Mech(mechs.mech(W, [lo], eff))
+    y = np.array([0.1, 0.3, 0.05, 0.05, 0.5])
+    T, p = 1500.0, 101325.0
+    np.testing.assert_allclose(oracle.rates(fhi, T, p, y), oracle.rates(plain, T, p, y), rtol=1e-9)
+    np.testing.assert_allclose(oracle.rates(flo, T, p, y), oracle.rates(tb0, T, p, y), rtol=1e-9)
+
+
+def test_pressure_order_and_density():
+    """Bimolecular source terms scale with p (one power of density), the
+    third-body ones with p^2; at fixed p and T they scale with the mean molar
+    mass Wbar (ideal gas rho = p Wbar / RT)."""
+    W = [2.0, 32.0, 17.0, 17.0, 28.0]
+    r = dict(reac=[0, 1], prod=[2, 3], A=1e12)
+    om = oracle.Mech(mechs.mech(W, [r]))
+    ot = oracle.Mech(mechs.mech(W, [dict(r, type=1)], [[1, 1, 1, 1, 1]]))
+    y = np.array([0.1, 0.3, 0.05, 0.05, 0.5])
+    T = 1300.0
+    f1 = oracle.rates(om, T, 1e5, y)
+    f2 = oracle.rates(om, T, 3e5, y)
+    np.testing.assert_allclose(f2, 3 * f1, rtol=1e-13)
+    np.testing.assert_allclose(oracle.rates(ot, T, 3e5, y), 9 * oracle.rates(ot, T, 1e5, y), rtol=1e-13)
+    # swap part of the inert diluent (W=28) for a heavier inert (same slot count):
+    # reactant mass fractions fixed, Wbar changes, rates scale with Wbar.
+    W2 = [2.0, 32.0, 17.0, 17.0, 56.0]
+    om2 = oracle.Mech(mechs.mech(W2, [r]))
+    wbar1 = 1.0 / np.sum(y / np.array(W))
+    wbar2 = 1.0 / np.sum(y / np.array(W2))
+    f3 = oracle.rates(om2, T, 1e5, y)
+    np.testing.assert_allclose(f3[:4], f1[:4] * wbar2 / wbar1, rtol=1e-13)
+
+
+def test_quadratic_decay_closed_form_rate():
+    """A + A -> B + B: Omega = k C_A^2 and dC_A/dt = -2 k C_A^2."""
+    W = 30.0
+    om = oracle.Mech(mechs.mech([W, W], [dict(reac=[0, 0], prod=[1, 1], A=2e12)]))
+    T, p = 1000.0, 101325.0
+    y = np.array([0.4, 0.6])
+    rho = p * W / (R_GAS * T) * 1e-6  # all molar masses equal: Wbar = W
+    cA = rho * y[0] / W
+    f = oracle.rates(om, T, p, y)
+    assert f[0] == pytest.approx(W / rho * (-2 * 2e12 * cA * cA), rel=1e-13, abs=0)
+
+
+@pytest.mark.parametrize("name", list(synth.WORKLOADS))
+def test_source_terms_conserve_mass_and_elements(name):
+    """Sum_i dY_i/dt = 0 and sum_i a_ei (dY_i/dt)/W_i = 0 for every element e
+    (each reaction balances atoms), on the synthetic mechanisms."""
+    m = synth.workload_mechanism(name)
+    om = oracle.Mech(m)
+    T, p, Y = synth.workload_states(name, m, cells=6)
+    for c in range(6):
+        f = oracle.rates(om, T[c], p[c], Y[:, c])
+        scale = np.abs(f).sum()
+        assert scale > 0
+        assert abs(f.sum()) < 1e-13 * scale
+        mol = f / m.W
+        for e in range(len(m.elements)):
+            assert abs((m.comp[:, e] * mol).sum()) < 1e-13 * (np.abs(mol) * m.comp[:, e]).sum() + 1e-300
+
+
+# ------------------------------------------------------------------ RKCK ---
+def test_rkck_local_order_on_linear_decay():
+    """One Cash-Karp step on y' = -k y: the fifth-order local error scales as
+    h^6 and the embedded fourth-order one as h^5 (Section 2.2)."""
+    k = 1.0e6
+    om = oracle.Mech(mechs.a_to_b(k))
+    y0 = np.array([1.0, 0.0])
+    e5, e4 = [], []
+    for z in (0.08, 0.04, 0.02):
+        y5, err = oracle.rkck_single(om, 1000.0, 1e5, y0, z / k)
+        exact = math.exp(-z)
+        e5.append(abs(y5[0] - exact))
+        e4.append(abs(y5[0] - err[0] - exact))
+    for i in range(2):
+        assert 2 ** 5.6 < e5[i] / e5[i + 1] < 2 ** 6.4
+        assert 2 ** 4.6 < e4[i] / e4[i + 1] < 2 ** 5.4
+
+
+def test_rkck_step_matches_printed_table_exactly():
+    """On y' = -k y one oracle step multiplies y by the stability function of
+    the printed table, evaluated in exact rational arithmetic."""
+    k = 1.0
+    om = oracle.Mech(mechs.a_to_b(k))
+    for z in (0.01, 0.3, 1.0, 2.5, 3.3):
+        y5, err = oracle.rkck_single(om, 1000.0, 1e5, np.array([1.0, 0.0]), z / k)
+        g5, g4 = _linear_rk_step(Fraction(-z))
+        assert y5[0] == pytest.approx(float(g5), rel=1e-14, abs=1e-15)
+        assert err[0] == pytest.approx(float(g5 - g4), rel=1e-10, abs=1e-16)
+
+
+def _linear_rk_step(z):
+    """Exact one-step factor and embedded factor of the printed table on
+    y' = lambda y, z = h lambda (rational arithmetic on the golden table)."""
+    a, b, c, cs = _golden_rkck()
+    k = []
+    for i in range(6):
+        arg = 1 + sum(b[i][j] * k[j] for j in range(i))
+        k.append(z * arg)
+    y5 = 1 + sum(c[i] * k[i] for i in range(6))
+    y4 = 1 + sum(cs[i] * k[i] for i in range(6))
+    return y5, y4
+
+
+def test_rkck_controller_trace_on_linear_decay():
+    """Hand-worked trace on A -> B: first trial step = dt, error ratio from the
+    exact linear step of the printed table, and the Eq. (E:hnew) rule with the
+    5x/10x limits, for the first attempts."""
+    k = 3.0e7
+    om = oracle.Mech(mechs.a_to_b(k))
+    dt, rtol, atol = 1e-7, 1e-6, 1e-10
+    y = np.array([0.9, 0.1])
+    _, st, tr = oracle.trace_cell(om, 1000.0, 1e5, y, dt, rtol, atol, method=0)
+    assert st == 0
+    t, h = Fraction(0), Fraction(dt)
+    ya, yb = Fraction(0.9), Fraction(0.1)
+    for n in range(min(6, len(tr["h"]))):
+        hh = min(h, Fraction(dt) - t)
+        assert float(hh) == pytest.approx(tr["h"][n], rel=1e-10, abs=0)
+        hh = Fraction(float(tr["h"][n]))
+        z = Fraction(-k) * hh
+        g5, g4 = _linear_rk_step(z)
+        da = (g5 - g4) * ya
+        fa = -k * ya
+        tol_a = rtol * (abs(ya) + abs(hh * fa)) + atol
+        tol_b = rtol * (abs(yb) + abs(hh * (-fa))) + atol
+        errmax = max(abs(float(da)) / float(tol_a), abs(float(da)) / float(tol_b))
+        assert errmax == pytest.approx(tr["err"][n], rel=1e-9, abs=0)
+        errmax = float(tr["err"][n])
+        if errmax <= 1:
+            ya, yb = g5 * ya, yb + (1 - g5) * ya
+            t += hh
+            h = min(5 * hh, Fraction(0.9 * float(hh) * errmax ** -0.2))
+        else:
+            h = max(hh / 10, Fraction(0.9 * float(hh) * errmax ** -0.25))
+
+
+# ------------------------------------------------------------------- RKC ---
+def _cheb_parts(s):
+    """T_s, T_s', T_s'' as numpy Chebyshev series."""
+    ts = np.zeros(s + 1)
+    ts[s] = 1.0
+    return ts, C.chebder(ts, 1), C.chebder(ts, 2)
+
+
+def _stability_poly(s, z):
+    """P_s(z) = a_s + b_s T_s(w0 + w1 z), Section 2.3 (kappa = 2/13)."""
+    w0 = 1 + (2.0 / 13.0) / s ** 2
+    t, d1, d2 = _cheb_parts(s)
+    Td1, Td2 = C.chebval(w0, d1), C.chebval(w0, d2)
+    w1 = Td1 / Td2
+    bs = Td2 / Td1 ** 2
+    a_s = 1 - bs * C.chebval(w0, t)
+    return a_s + bs * C.chebval(w0 + w1 * z, t)
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 7, 16, 40, 100, 250])
+def test_rkc_step_is_chebyshev_stability_polynomial(s):
+    """One s-stage step on y' = -k y multiplies y by P_s(-k h)."""
+    k = 1.0
+    om = oracle.Mech(mechs.a_to_b(k))
+    beta = ((s - 1) ** 2 - 1) / 1.54
+    for frac in (0.0, 0.01, 0.3, 0.77, 1.0):
+        z = -frac * max(beta, 0.5)
+        ys = oracle.rkc_single(om, 1000.0, 1e5, np.array([1.0, 0.0]), -z / k, s)
+        ref = _stability_poly(s, z)
+        assert ys[0] == pytest.approx(ref, abs=2e-13 * s, rel=1e-11)
+        assert ys[0] + ys[1] == pytest.approx(1.0, abs=1e-12)
+
+
+@pytest.mark.parametrize("s", [2, 3, 5, 10, 50, 250])
+def test_rkc_stable_on_stage_rule_interval(s):
+    """|P_s(z)| <= 1 on [-((s-1)^2-1)/1.54, 0], the interval the stage rule
+    s = 1 + sqrt(1 + 1.54 h sigma) allows (Section 2.3)."""
+    k = 1.0
+    om = oracle.Mech(mechs.a_to_b(k))
+    beta = ((s - 1) ** 2 - 1) / 1.54
+    for z in np.linspace(-beta, 0.0, 41):
+        ys = oracle.rkc_single(om, 1000.0, 1e5, np.array([1.0, 0.0]), -z / k, s)
+        assert abs(ys[0]) <= 1.0 + 1e-12
+
+
+def test_rkc_second_order_consistency_of_polynomial():
+    """P_s(z) = 1 + z + z^2/2 + O(z^3): the oracle step on y' = -k y has local
+    error O(h^3)."""
+    om = oracle.Mech(mechs.a_to_b(1.0))
+    for s in (2, 5, 20):
+        errs = []
+        for h in (1e-2, 5e-3, 2.5e-3):
+            ys = oracle.rkc_single(om, 1000.0, 1e5, np.array([1.0, 0.0]), h, s)
+            errs.append(abs(ys[0] - math.exp(-h)))
+        assert 2 ** 2.8 < errs[0] / errs[1] < 2 ** 3.2
+        assert 2 ** 2.8 < errs[1] / errs[2] < 2 ** 3.2
+
+
+@pytest.mark.parametrize("s", [2, 3, 8, 30, 250])
+def test_rkc_first_stage_abscissa(s):
+    """mu~_1 is the first stage abscissa c_1, and the paper fixes
+    c_1 = c_2 / T_2'(w0) with c_2 = w1 T_2''(w0)/T_2'(w0) (Section 2.3).
+    This pins b_1 = b_2."""
+    co = oracle.rkc_coeffs(s)
+    w0 = 1 + (2.0 / 13.0) / s ** 2
+    _, d1s, d2s = _cheb_parts(s)
+    w1 = C.chebval(w0, d1s) / C.chebval(w0, d2s)
+    _, d12, d22 = _cheb_parts(2)
+    c2 = w1 * C.chebval(w0, d22) / C.chebval(w0, d12)
+    c1 = c2 / C.chebval(w0, d12)
+    assert co["w0"] == pytest.approx(w0, rel=1e-15, abs=0)
+    assert co["w1"] == pytest.approx(w1, rel=1e-12, abs=0)
+    assert co["mut"][1] == pytest.approx(c1, rel=1e-12, abs=0)
+    # c_j ~ (j^2 - 1)/(s^2 - 1) for 2 <= j <= s-1, c_s = 1
+    for j in range(2, s):
+        assert co["c"][j] == pytest.approx((j * j - 1) / (s * s - 1), rel=0.05, abs=0.01)
+    assert co["c"][s] == 1.0
+
+
+def test_rkc_second_order_convergence_nonlinear():
+    """Fixed-stage RKC on A + A -> B + B (closed form C_A = C0/(1 + 2 k C0 t))
+    converges with order 2."""
+    W = 30.0
+    kf = 4e11
+    om = oracle.Mech(mechs.mech([W, W], [dict(reac=[0, 0], prod=[1, 1], A=kf)]))
+    T, p = 1000.0, 101325.0
+    rho = p * W / (R_GAS * T) * 1e-6
+    y0 = np.array([0.8, 0.2])
+    c0 = rho * y0[0] / W
+    tend = 2.0 / (2 * kf * c0)
+    exact = c0 / (1 + 2 * kf * c0 * tend) * W / rho
+    errs = []
+    for nsteps in (40, 80, 160):
+        y = y0.copy()
+        for _ in range(nsteps):
+            y = oracle.rkc_single(om, T, p, y, tend / nsteps, 4)
+        errs.append(abs(y[0] - exact))
+    assert 2 ** 1.8 < errs[0] / errs[1] < 2 ** 2.2
+    assert 2 ** 1.8 < errs[1] / errs[2] < 2 ** 2.2
+
+
+def test_gershgorin_on_linear_chain():
+    """A_0 -> A_1 -> ... with rates k_i has Jacobian rows with |-k_i| + |k_{i-1}|:
+    the Gershgorin bound is max_i (k_i + k_{i-1}); the finite-difference
+    Jacobian of a linear f reproduces it to ~sqrt(eps)."""
+    ks = [3e8, 1e9, 2.5e8, 7e9, 1e3]
+    om = oracle.Mech(mechs.chain(ks))
+    exact = max([ks[0]] + [ks[i] + ks[i - 1] for i in range(1, len(ks))] + [ks[-1]])
+    y = np.array([0.3, 0.2, 0.1, 0.25, 0.1, 0.05])
+    sig = oracle.sigma(om, 1500.0, 101325.0, y, 1e-10)
+    assert sig == pytest.approx(exact, rel=1e-6, abs=0)
+
+
+def test_rkc_controller_trace_on_linear_decay():
+    """Hand-worked trace of RKC on A -> B (sigma = k exactly), every attempt to
+    the end of the flow step: initial step from h0 = 1/sigma and Delta_0 (both
+    in closed form), the stage count rule, the step factor P_s(-k h) from numpy
+    Chebyshev, the error estimate, and the step factors (0.8/err^(1/3) first
+    and after a rejection, the predictive form otherwise)."""
+    k = 2.0e8
+    om = oracle.Mech(mechs.a_to_b(k))
+    dt, rtol, atol = 1e-6, 1e-6, 1e-10
+    ya, yb = 0.7, 0.3
+    _, st, tr = oracle.trace_cell(om, 1000.0, 1e5, np.array([ya, yb]), dt, rtol, atol, method=1)
+    assert st == 0
+    sigma = k  # rows of J = [[-k, 0], [k, 0]] both sum to k
+    h0 = 1.0 / sigma
+    # Delta_0 = h0 (f(y + h0 f0) - f0): A component = ya, B component = -ya
+    d0 = math.sqrt(0.5 * ((ya / (atol + rtol * ya)) ** 2 + (ya / (atol + rtol * yb)) ** 2))
+    h = min(0.1 * h0 / math.sqrt(d0), dt)
+    t = 0.0
+    prev = None
+    rejected = False
+    n_att = len(tr["h"])
+    assert n_att > 10
+    for n in range(n_att):
+        hh = min(h, dt - t)
+        assert tr["h"][n] == pytest.approx(hh, rel=1e-9, abs=0)
+        hh = tr["h"][n]
+        s = max(2, int(math.floor(1 + math.sqrt(1 + 1.54 * hh * sigma))))
+        assert tr["s"][n] == s
+        g = _stability_poly(s, -k * hh)
+        na = g * ya
+        nb = yb + (1 - g) * ya
+        fa0, fa1 = -k * ya, -k * na
+        da = 0.8 * (ya - na) + 0.4 * hh * (fa0 + fa1)
+        db = -da
+        ta = atol + rtol * max(abs(ya), abs(na))
+        tb = atol + rtol * max(abs(yb), abs(nb))
+        err = math.sqrt(0.5 * ((da / ta) ** 2 + (db / tb) ** 2))
+        # the estimate cancels terms of size |y|: allow their rounding
+        cancel = 4e-16 * (abs(ya) + abs(na) + abs(hh * fa0)) / min(ta, tb)
+        assert tr["err"][n] == pytest.approx(err, rel=1e-8, abs=cancel)
+        err = tr["err"][n]
+        assert tr["accepted"][n] == (err <= 1.0)
+        if err <= 1.0:
+            if err == 0:
+                fac = 10.0
+            elif prev is None or rejected:
+                fac = 0.8 / err ** (1 / 3)
+            else:
+                fac = 0.8 * (hh / prev[0]) * prev[1] ** (1 / 3) / err ** (2 / 3)
+            prev = (hh, err)
+            rejected = False
+            ya, yb = na, nb
+            t += hh
+        else:
+            fac = 0.8 / err ** (1 / 3)
+            rejected = True
+        h = min(10.0, max(0.1, fac)) * hh
+    assert t == pytest.approx(dt, rel=1e-12, abs=0)
+    assert max(tr["s"]) >= 10  # the stage rule is exercised beyond s = 2
+
+
+# ------------------------------------------------------ whole integrator ---
+def _tiny_mechanism(seed):
+    return synth.make_mechanism(7, 16, ("H", "O"), tb_frac=0.2, fo_frac=0.1, seed=seed)
+
+
+@pytest.mark.parametrize("method", [oracle.RKCK, oracle.RKC])
+def test_integrator_against_tight_scipy_reference(method):
+    """At rtol 1e-6 the integrated state is within a small multiple of the
+    tolerance of a DOP853 trajectory at rtol 1e-13 using the same f."""
+    integrate = pytest.importorskip("scipy.integrate")
+    m = _tiny_mechanism(11)
+    om = oracle.Mech(m)
+    T, p, Y = synth.make_states(m, 4, T_range=(1000, 1600), seed=3)
+    dt, rtol, atol = 1e-6, 1e-6, 1e-10
+    Yn, st, stats, _ = oracle.integrate(om, T, p, Y, dt, rtol, atol, method)
+    assert (st == 0).all()
+    for c in range(4):
+        sol = integrate.solve_ivp(lambda t, y: oracle.rates(om, T[c], p[c], y), (0, dt), Y[:, c],
+                                  method="DOP853", rtol=1e-13, atol=1e-20)
+        ref = sol.y[:, -1]
+        rel = np.abs(Yn[:, c] - ref) / np.maximum(np.abs(ref), atol)
+        assert rel.max() < 50 * rtol, rel.max()
+
+
+@pytest.mark.parametrize("name", ["h2_9sp_rkck", "h2co_13sp_rkc", "ch4_53sp_rkc_mixed"])
+def test_integrator_conserves_mass_and_elements(name):
+    """Runge-Kutta methods keep linear invariants: sum Y = 1 and element totals
+    stay at their initial values up to rounding."""
+    m = synth.workload_mechanism(name)
+    w = synth.WORKLOADS[name]
+    om = oracle.Mech(m)
+    T, p, Y = synth.workload_states(name, m, cells=8)
+    Yn, st, stats, _ = oracle.integrate(om, T, p, Y, w["dt"], w["rtol"], w["atol"], w["method"])
+    assert (st == 0).all()
+    assert (stats[:, 1] > 0).all()
+    np.testing.assert_allclose(Yn.sum(0), 1.0, atol=1e-13)
+    el0 = m.comp.T @ (Y / m.W[:, None])
+    el1 = m.comp.T @ (Yn / m.W[:, None])
+    np.testing.assert_allclose(el1, el0, rtol=1e-12)
+    assert np.abs(Yn - Y).max() > 1e-8  # something happened
+
+
+def test_rkc_fewer_evaluations_when_stiff_and_rkck_when_not():
+    """The qualitative stiffness split of Sections 3.1-3.2: on a stiff linear
+    decay (k dt = 1e4) RKC needs far fewer f evaluations than RKCK; on a
+    nonstiff one (k dt = 0.5) RKCK needs fewer."""
+    for kdt, better in ((1e4, oracle.RKC), (0.5, oracle.RKCK)):
+        om = oracle.Mech(mechs.a_to_b(kdt / 1e-6))
+        Y = np.array([[0.9], [0.1]])
+        nfe = {}
+        for meth in (oracle.RKCK, oracle.RKC):
+            _, st, stats, _ = oracle.integrate(om, [1000.0], [1e5], Y, 1e-6, 1e-6, 1e-10, meth)
+            assert st[0] == 0
+            nfe[meth] = stats[0, 0]
+        other = oracle.RKC if better == oracle.RKCK else oracle.RKCK
+        assert nfe[better] < nfe[other], (kdt, nfe)
+
+
+def test_status_codes():
+    """Step limit -> 1 with the last accepted state kept; non-finite input -> 3."""
+    m = synth.workload_mechanism("h2co_13sp_rkc")
+    om = oracle.Mech(m)
+    T, p, Y = synth.workload_states("h2co_13sp_rkc", m, cells=2)
+    Yn, st, stats, _ = oracle.integrate(om, T, p, Y, 1e-6, 1e-6, 1e-10, oracle.RKC, max_steps=3)
+    assert (st == 1).all()
+    assert (stats[:, 1] + stats[:, 2] == 3).all()
+    np.testing.assert_allclose(Yn.sum(0), 1.0, atol=1e-13)
+    Y2 = Y.copy()
+    Y2[3, 1] = np.nan
+    Yn, st, _, _ = oracle.integrate(om, T, p, Y2, 1e-6, 1e-6, 1e-10, oracle.RKCK)
+    assert st[0] == 0 and st[1] == 3
