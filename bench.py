@@ -1,0 +1,388 @@
+"""Benchmark: cell-ODEs integrated over one flow step per second on GB300.
+
+Default workload: the 13-species / 54-reaction synthetic mechanism, RKC with
+a Gershgorin spectral radius, 262144 cells, dt = 1e-6 s, rtol 1e-6,
+atol 1e-10, FP64. One step = one kin_integrate call over every cell (the
+whole hot path: source terms, RKC stages, spectral radius, error control),
+starting from the same initial state every step (the integrator restarts per
+flow step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kin|reference]
+
+Prints one JSON line. With --impl reference the plain FP64 CPU oracle is
+timed on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1309_2710_gb300 import synth  # noqa: E402
+
+METRIC = "cell-ODEs integrated over Δt per sec per GB300 at rtol 1e-6"
+UNIT = "cell-ODEs/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# FP64 peak derived from the nominal 1.25 TFLOP/s of a GB300: 2 FP64 FMA lanes
+# per SM per clock x 2 flops x 152 SMs x 2070 MHz = 1.259e12 FLOP/s.
+FP64_FMA_LANES_PER_SM = 2
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+# DRAM bytes per launch of the integrate kernel from an ncu capture (see
+# profiles/), valid for the kernel source whose hash is recorded with it.
+TRAFFIC = {}
+
+
+def kernel_hash() -> str:
+    p = os.path.join(ROOT, "paper_1309_2710_gb300", "csrc", "kernels.cu")
+    return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+
+
+# ------------------------------------------------------ algorithmic work ---
+def feval_flops(m) -> int:
+    """FP64 operations of one evaluation of f (an add, multiply or divide is
+    one flop; a fused multiply-add two), counted from the mechanism tables."""
+    nS = m.n_species
+    f = 3 * nS + 1  # Y/W, sum, rho, C
+    for j in range(m.n_reactions):
+        f += int(np.count_nonzero(m.reac[j] >= 0))  # k * prod C
+        if m.rtype[j] == synth.THIRD_BODY:
+            f += 2 * nS + 1
+        elif m.rtype[j] == synth.FALLOFF:
+            f += 2 * nS + 4
+    # stoichiometric sum: one add per net nonzero (a coefficient of 2 adds a multiply)
+    for i in range(nS):
+        for j in range(m.n_reactions):
+            nu = int(np.sum(m.prod[j] == i)) - int(np.sum(m.reac[j] == i))
+            if nu:
+                f += 1 if abs(nu) == 1 else 2
+    f += 2 * nS + 1  # dY/dt = W omega / rho
+    return f
+
+
+def algorithmic_flops(m, method, stats) -> float:
+    """Algorithmic FP64 flops of one call, from per-cell counts
+    (f evaluations, accepted, rejected, spectral-radius estimates)."""
+    nS = m.n_species
+    nfe = stats[:, 0].astype(np.float64)
+    att = (stats[:, 1] + stats[:, 2]).astype(np.float64)
+    nsig = stats[:, 3].astype(np.float64)
+    total = nfe.sum() * feval_flops(m)
+    if method == synth.RKC:
+        stages = nfe - 2 - nsig * nS  # sum of s over attempts
+        total += ((stages - att) * 9 * nS + att * 12 * nS).sum()  # w_1, w_j, error + norm
+        total += (nsig * (3 * nS * nS + 3 * nS)).sum() + 14 * nS * len(nfe)  # sigma, initial step
+    else:
+        total += (att * 66 * nS).sum()  # stage points, y5, error, tolerance
+    return float(total)
+
+
+# ------------------------------------------------------------- clocks ---
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+# ---------------------------------------------------------- CPU oracle ---
+def oracle_rate(name, cells_target_s=10.0, max_cells=None, seed_offset=0):
+    """Time the FP64 oracle on the host cores on a bounded sample of the
+    workload. Returns (cells/s, threads, sample description)."""
+    import oracle
+    w = synth.WORKLOADS[name]
+    m = synth.workload_mechanism(name)
+    om = oracle.Mech(m)
+    total = w["cells"]
+    T, p, Y = synth.workload_states(name, m, seed_offset=seed_offset)
+    probe = min(2048, total)
+    t0 = time.perf_counter()
+    _, _, _, nt = oracle.integrate(om, T[:probe], p[:probe], Y[:, :probe], w["dt"], w["rtol"],
+                                   w["atol"], w["method"])
+    per_cell = (time.perf_counter() - t0) / probe
+    n = int(min(total if max_cells is None else max_cells, max(probe, cells_target_s / per_cell)))
+    t0 = time.perf_counter()
+    _, st, _, nt = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"],
+                                    w["method"])
+    el = time.perf_counter() - t0
+    return n / el, nt, "first %d of the %d cells of %s (same seeds), %.1f s wall" % (n, total, name, el)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    name = args.workload
+    w = synth.WORKLOADS[name]
+    m = synth.workload_mechanism(name)
+    om = oracle.Mech(m)
+    T, p, Y = synth.workload_states(name, m)
+    # bounded per-step sample sized from a probe so K+W steps take ~2 min
+    probe = 1024
+    t0 = time.perf_counter()
+    oracle.integrate(om, T[:probe], p[:probe], Y[:, :probe], w["dt"], w["rtol"], w["atol"], w["method"])
+    per_cell = (time.perf_counter() - t0) / probe
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    n = int(min(w["cells"], max(probe, budget / per_cell)))
+    for _ in range(args.warmup):
+        oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], w["method"])
+    times = []
+    nt = 1
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, _, _, nt = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"],
+                                       w["method"])
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = n * len(times) / tot
+    sample = "first %d of the %d cells per step" % (n, w["cells"])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(name, n),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(name, cells):
+    w = synth.WORKLOADS[name]
+    return {"workload": "%s: %d species / %d reactions, %s %s, %d cells, dt %g s, rtol %g, atol %g"
+                        % (name, w["n_species"], w["n_reactions"],
+                           "RKC (Gershgorin FD)" if w["method"] == synth.RKC else "RKCK",
+                           "FP64" if w["precision"] == synth.FP64 else "mixed FP32/FP64",
+                           cells, w["dt"], w["rtol"], w["atol"]),
+            "cells": cells, "method": "RKC" if w["method"] == synth.RKC else "RKCK",
+            "precision": "fp64" if w["precision"] == synth.FP64 else "mixed",
+            "l2": "flushed between steps (256 MiB write)", "cell_order": "random (as drawn)"}
+
+
+# ------------------------------------------------------------ GPU arm ---
+def run_kin(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1309_2710_gb300 import build as kbuild
+    kbuild.build()
+    from paper_1309_2710_gb300 import kin
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    name = args.workload
+    w = synth.WORKLOADS[name]
+    m = synth.workload_mechanism(name)
+    cells = args.cells or w["cells"]
+    # weak scaling: every rank integrates its own full-size problem (own seeds)
+    T, p, Y0 = synth.workload_states(name, m, cells=cells, seed_offset=1000 * rank)
+    km = kin.Mechanism(m)
+    method, prec = w["method"], w["precision"]
+    Td = torch.as_tensor(T, device=dev)
+    pd = torch.as_tensor(p, device=dev)
+    Y0d = torch.as_tensor(Y0, device=dev).contiguous()
+    Yd = torch.empty_like(Y0d)
+    st = torch.zeros(cells, dtype=torch.uint8, device=dev)
+    sta = torch.zeros((cells, 4), dtype=torch.int32, device=dev)
+    ws = km.workspace(method, prec, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        flush.zero_()
+        Yd.copy_(Y0d)
+        if ev:
+            ev[0].record(stream)
+        kin.integrate(km, Td, pd, Yd, w["dt"], w["rtol"], w["atol"], method, prec,
+                      status=st, stats=sta, workspace=ws, stream=stream)
+        if ev:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms_total = t_start.elapsed_time(t_end)
+    kern_ms = [a.elapsed_time(b) for a, b in evs]
+    tmax = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms_step = float(tmax.item()) / args.steps
+    value = world * cells / (ms_step * 1e-3)
+
+    stats = sta.cpu().numpy()
+    status = st.cpu().numpy()
+    flops = algorithmic_flops(m, method, stats)
+    kavg = sum(kern_ms) / len(kern_ms)
+    achieved = flops / (kavg * 1e-3) / 1e9
+    peak = FP64_FMA_LANES_PER_SM * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
+    tr = TRAFFIC.get(kernel_hash())
+
+    # end to end: host (pinned) buffers through the public API, copies timed
+    e2e = None
+    if not args.no_e2e:
+        Th = torch.as_tensor(T).pin_memory()
+        ph = torch.as_tensor(p).pin_memory()
+        Y0h = torch.as_tensor(Y0).contiguous()
+        Yh = torch.empty_like(Y0h).pin_memory()
+        sth = torch.empty(cells, dtype=torch.uint8).pin_memory()
+        hbuf = kin.host_buffer(km, cells, method, prec, device=dev)
+
+        def e2e_step():
+            # the flow solver hands over its state in host memory every step
+            Yh.copy_(Y0h)
+            kin.integrate_host(km, Th, ph, Yh, w["dt"], w["rtol"], w["atol"], method, prec,
+                               status=sth, buffer=hbuf, stream=stream)
+            stream.synchronize()
+
+        e2e_step()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ne = max(1, min(args.steps, 3))
+        for _ in range(ne):
+            e2e_step()
+        el = time.perf_counter() - t0
+        te = torch.tensor([el], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * cells * ne / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(Th.numel() * 8 + ph.numel() * 8 + Yh.numel() * 8),
+               "d2h_bytes_per_step": int(Yh.numel() * 8 + sth.numel()),
+               "api": "kin_integrate_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, nt, sample = oracle_rate(name, cells_target_s=args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32+f64",
+            "data": "synthetic (seeded generator standing in for the paper's mechanisms and states)",
+            "config": workload_config(name, cells),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                         "frac": achieved / peak, "traffic": tr,
+                         "kernel": "integrate_kernel (FP64 pipe)",
+                         "kernel_ms": kavg, "flops_per_launch": flops},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "cell_status": np.bincount(status, minlength=4).tolist(),
+            "mean_f_evals_per_cell": float(stats[:, 0].mean()),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    km.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["kin", "reference"], default="kin")
+    ap.add_argument("--workload", default="h2co_13sp_rkc", choices=[k for k, v in synth.WORKLOADS.items()
+                                                                   if v["cells"]])
+    ap.add_argument("--cells", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_kin(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

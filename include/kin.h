@@ -1,0 +1,196 @@
+/*
+ * kin.h -- C ABI of the GB300 batched chemical-kinetics integrator.
+ *
+ * The library integrates many independent per-cell kinetics systems
+ * dY/dt = f(T, p, Y) over one operator-split flow step dt. The integration
+ * restarts every call, with internal sub-stepping and no memory between calls
+ * (Niemeyer & Sung, Section 3). Two methods are available:
+ *   KIN_RKCK  Runge-Kutta-Cash-Karp 5(4), Section 2.2, Table 1, Eq. (E:hnew);
+ *   KIN_RKC   second-order Runge-Kutta-Chebyshev, Section 2.3, Eqs.
+ *             (E:rkc0)-(E:rkcs), (E:rmsE). The spectral radius is a Gershgorin
+ *             bound on a finite-difference Jacobian.
+ * f is the species source term of Section 2.1, Eqs. (E:mass), (E:spec-rate),
+ * (E:rxn-rate) and (E:rxn-const), with third-body and Lindemann falloff
+ * reactions. Temperature and pressure are held fixed over the flow step
+ * (no energy equation), so N = n_species.
+ *
+ * Conventions for every entry point:
+ *  - Device pointers are CUDA device memory of the current device; host
+ *    pointers are ordinary host memory. Nothing is retained after a call
+ *    returns except inside a kin_mech.
+ *  - State layout is species-major: Y[i * ldY + c] holds species i of cell c,
+ *    with ldY >= cells.
+ *  - Units: T in K, p in Pa, Y as mass fractions, dt in s, W in g/mol,
+ *    A in cm-mol-s units (given as ln A), Ea in J/mol.
+ *  - Work is enqueued on opts->stream (a cudaStream_t; NULL means the legacy
+ *    default stream). Calls return before the GPU finishes; results, per-cell
+ *    status and statistics are valid after the stream is synchronised.
+ *  - Return value: KIN_OK, or a negative KIN_E* code. kin_last_error() then
+ *    describes the failure (thread-local, valid until the next call on the
+ *    same thread). A failed call enqueues no work.
+ *  - A cell that cannot finish does not fail the call; its status byte says
+ *    why and its Y holds the last accepted state (see KIN_CELL_*).
+ */
+#ifndef KIN_H
+#define KIN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KIN_OK 0
+#define KIN_EINVAL (-1)       /* bad argument: null pointer, size, non-finite or non-positive dt/tol */
+#define KIN_ENOMEM (-2)       /* device or host allocation failed, or workspace too small */
+#define KIN_ECUDA (-3)        /* a CUDA call failed (message has the CUDA error string) */
+#define KIN_EUNSUPPORTED (-4) /* mechanism or option combination not supported */
+
+/* method */
+#define KIN_RKCK 0
+#define KIN_RKC 1
+/* precision: FP64 everywhere, or FP32 rate evaluation (Arrhenius exp and
+ * rate-of-progress products, stoichiometric sum) with FP64 state, stage
+ * accumulation, error norm, step control and spectral-radius bound. */
+#define KIN_FP64 0
+#define KIN_MIXED 1
+
+/* per-cell status */
+#define KIN_CELL_OK 0
+#define KIN_CELL_MAXSTEPS 1  /* attempted-step limit reached */
+#define KIN_CELL_HMIN 2      /* step size fell below 1e-20 * dt */
+#define KIN_CELL_NONFINITE 3 /* f (or the RKC spectral-radius bound) is not finite at
+                                the initial or an accepted state */
+
+/* reaction types */
+#define KIN_RXN_PLAIN 0
+#define KIN_RXN_THIRD_BODY 1 /* Omega = k [M] prod C,   [M] = sum_k eff_k C_k */
+#define KIN_RXN_FALLOFF 2    /* Lindemann: Omega = k_inf Pr/(1+Pr) prod C, Pr = k_0 [M] / k_inf */
+
+/* Host description of an irreversible mechanism. Caller-owned; copied by
+ * kin_create_mechanism. Each reaction has up to two reactants and two products
+ * (index -1 marks an empty slot; a species listed twice has coefficient 2). */
+typedef struct {
+    int32_t n_species;   /* >= 1, <= KIN_MAX_SPECIES */
+    int32_t n_reactions; /* >= 0, <= KIN_MAX_REACTIONS */
+    const double *W;     /* [n_species] molar masses, > 0 */
+    const double *lnA;   /* [n_reactions] ln of the pre-exponential factor */
+    const double *beta;  /* [n_reactions] temperature exponent */
+    const double *Ea;    /* [n_reactions] activation energy, J/mol */
+    const int32_t *reac; /* [n_reactions][2] reactant species or -1 */
+    const int32_t *prod; /* [n_reactions][2] product species or -1 */
+    const int8_t *type;  /* [n_reactions] KIN_RXN_* */
+    const double *eff;   /* [n_rows][n_species] third-body efficiencies, one row
+                            per non-plain reaction in reaction order; may be NULL
+                            when every reaction is plain */
+    const double *lnA0;  /* [n_reactions] low-pressure limit of falloff reactions */
+    const double *beta0; /* (read only where type == KIN_RXN_FALLOFF; the three */
+    const double *Ea0;   /*  may be NULL when there is none) */
+} kin_mech_desc;
+
+#define KIN_MAX_SPECIES 256
+#define KIN_MAX_REACTIONS 8192
+#define KIN_MAX_STAGES 250 /* RKC stage cap */
+
+typedef struct kin_mech kin_mech; /* opaque: device-resident tables */
+
+typedef struct {
+    int32_t method;        /* KIN_RKCK or KIN_RKC */
+    int32_t precision;     /* KIN_FP64 or KIN_MIXED */
+    int32_t max_steps;     /* attempted steps per cell; <= 0 means 100000 */
+    int32_t block_threads; /* threads per block, multiple of 32; 0 = library choice */
+    int32_t blocks_per_sm; /* persistent blocks per SM; 0 = library choice */
+    int32_t reserved;      /* must be 0 */
+    void *stream;          /* cudaStream_t */
+} kin_opts;
+
+/* One independent group of cells ("instance") of a batched call. All pointers
+ * are device pointers with the layouts described above. */
+typedef struct {
+    int64_t cells;     /* >= 0 */
+    const double *T;   /* [cells] */
+    const double *p;   /* [cells] */
+    double *Y;         /* [n_species][ldY], updated in place */
+    int64_t ldY;       /* >= cells */
+    double dt, rtol, atol; /* dt > 0, rtol > 0, atol >= 0, all finite */
+    uint8_t *status;   /* [cells] KIN_CELL_*, or NULL */
+    int32_t *stats;    /* [cells][4]: f evaluations, accepted steps, rejected
+                          steps, spectral-radius estimates; or NULL */
+} kin_instance;
+
+#define KIN_MAX_INSTANCES 128
+
+/* Copy and validate a mechanism, upload its tables to the current device and
+ * precompute the RKC coefficient table there (Section 2.3, s = 2..250).
+ * Synchronous. Errors: KIN_EINVAL (null desc/out, sizes out of range, species
+ * index out of range, W <= 0, non-finite parameter, missing efficiency rows),
+ * KIN_ENOMEM, KIN_ECUDA. */
+int kin_create_mechanism(const kin_mech_desc *desc, kin_mech **out);
+
+/* Free a mechanism. cudaFree waits for outstanding work on the device; do
+ * not destroy a mechanism that a captured CUDA graph still uses. NULL is a
+ * no-op. */
+int kin_destroy(kin_mech *m);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *kin_last_error(void);
+
+/* Bytes of device workspace kin_integrate / kin_integrate_batch need for
+ * `opts` on the current device (independent of the number of cells: the
+ * persistent grid has a fixed number of lanes). Returns < 0 on error. */
+int64_t kin_workspace_bytes(const kin_mech *m, const kin_opts *opts);
+
+/* Integrate `cells` cells of one instance over dt (Sections 2.2/2.3 and the
+ * restart-per-flow-step convention of Section 3). T, p, Y, status, stats
+ * as in kin_instance. workspace: caller-owned device memory of at least
+ * kin_workspace_bytes(m, opts) bytes, 256-byte aligned; it must not be used by
+ * another call that may run concurrently. Errors: KIN_EINVAL, KIN_ENOMEM
+ * (workspace too small), KIN_EUNSUPPORTED, KIN_ECUDA. */
+int kin_integrate(const kin_mech *m, int64_t cells, const double *T, const double *p,
+                  double *Y, int64_t ldY, double dt, double rtol, double atol,
+                  const kin_opts *opts, uint8_t *status, int32_t *stats,
+                  void *workspace, int64_t workspace_bytes);
+
+/* Integrate up to KIN_MAX_INSTANCES instances (each with its own cells, dt and
+ * tolerances) in one persistent launch; lanes take cells from a shared queue,
+ * so uneven instances balance across the GPU. `inst` is a host array that is
+ * copied into the launch parameters, so the call may be captured in a CUDA
+ * graph (the captured graph refers to the same device buffers and workspace).
+ * Errors as kin_integrate. */
+int kin_integrate_batch(const kin_mech *m, int32_t n_instances, const kin_instance *inst,
+                        const kin_opts *opts, void *workspace, int64_t workspace_bytes);
+
+/* Device bytes kin_integrate_host needs for `cells` cells (its staging
+ * copies of T, p, Y, status and stats plus the workspace). < 0 on error. */
+int64_t kin_host_buffer_bytes(const kin_mech *m, const kin_opts *opts, int64_t cells);
+
+/* Host-buffer form of kin_integrate, for callers whose state lives in host
+ * memory: T, p, Y (in/out), status and stats are HOST pointers with the
+ * layouts above (status and stats may be NULL). On opts->stream the call
+ * copies T, p and Y into `device_buffer` (device memory of at least
+ * kin_host_buffer_bytes bytes, 256-byte aligned), integrates there, and copies
+ * Y, status and stats back. Page-locked host memory makes every copy
+ * asynchronous; with pageable memory the copies may block. Host results are
+ * valid after the stream is synchronised. Errors as kin_integrate. */
+int kin_integrate_host(const kin_mech *m, int64_t cells, const double *T, const double *p,
+                       double *Y, int64_t ldY, double dt, double rtol, double atol,
+                       const kin_opts *opts, uint8_t *status, int32_t *stats,
+                       void *device_buffer, int64_t device_bytes);
+
+/* f alone: dYdt[i * ldY + c] = f(T_c, p_c, Y_c)_i (Eqs. (E:mass),
+ * (E:spec-rate), (E:rxn-rate), (E:rxn-const)) in the given precision
+ * (KIN_FP64 or KIN_MIXED), enqueued on `stream`. T, p, Y, dYdt and workspace
+ * are device pointers; dYdt has the layout of Y. The workspace rule is that of
+ * kin_integrate with method KIN_RKC and the same precision. Errors:
+ * KIN_EINVAL, KIN_ENOMEM, KIN_ECUDA. */
+int kin_rates(const kin_mech *m, int64_t cells, const double *T, const double *p,
+              const double *Y, int64_t ldY, double *dYdt, int32_t precision, void *stream,
+              void *workspace, int64_t workspace_bytes);
+
+/* Library version string. */
+const char *kin_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KIN_H */

@@ -47,8 +47,9 @@
  *     gives h = 0.1 h0.
  *
  * Per-cell status codes: 0 ok, 1 step limit reached, 2 step size below hmin,
- * 3 non-finite f at an accepted state (or at the initial state). On 1-3 the
- * cell keeps its last accepted state.
+ * 3 non-finite f at an accepted state (or at the initial state), or a
+ * non-finite spectral-radius bound. On 1-3 the cell keeps its last accepted
+ * state.
  */
 #include <math.h>
 #include <stdint.h>
@@ -475,6 +476,7 @@ static int rkc_cell(orc_f *F, int n, double *y, double dt, double rtol, double a
     sigma = gershgorin(F, n, y, f0, atol, x, fx, rowsum);
     st->nsig++;
     sigma_here = 1;
+    if (!isfinite(sigma)) { free(v); return 3; }
 
     /* initial step, Section 2.3: h0 = 1/sigma, Delta_0 = h0 (f(y0 + h0 f0) - f0),
      * h1 = 0.1 h0 / ||Delta_0||^{1/2} */
@@ -500,6 +502,7 @@ static int rkc_cell(orc_f *F, int n, double *y, double dt, double rtol, double a
             st->nsig++;
             since_sigma = 0;
             sigma_here = 1;
+            if (!isfinite(sigma)) { status = 3; break; }
         }
         if (hh >= dt - t) { hh = dt - t; last = 1; }
         s = rkc_stages(hh, sigma);

@@ -1,0 +1,403 @@
+// abi.cu -- host side of the C ABI declared in include/kin.h: argument
+// validation, mechanism packing and upload, workspace sizing, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "kin_dev.cuh"
+
+using namespace kin;
+
+struct kin_mech {
+    MechDev dev;  // device pointers into `buf`
+    void* buf;
+    int device;
+    int nS, nR, nM;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(KIN_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Device pointer check: the pointer must be device (or managed) memory.
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Grid {
+    int threads, blocks;  // persistent grid
+    int64_t nslots;
+};
+
+int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != m->device) return fail(KIN_EINVAL, "mechanism lives on device %d, current device is %d", m->device, dev);
+    int nsm = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    int threads = o->block_threads > 0 ? o->block_threads : 128;
+    if (threads % 32 != 0 || threads > 128) return fail(KIN_EINVAL, "block_threads must be a multiple of 32 and <= 128");
+    int bps = o->blocks_per_sm;
+    if (bps <= 0) {
+        int occ = 0;
+        e = integrate_occupancy(o->method, o->precision, threads, &occ);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+        bps = std::max(1, std::min(occ, 512 / threads));
+    }
+    if (bps > 64) return fail(KIN_EINVAL, "blocks_per_sm too large");
+    g->threads = threads;
+    g->blocks = nsm * bps;
+    g->nslots = (int64_t)g->blocks * threads;
+    return KIN_OK;
+}
+
+constexpr int64_t HEADER = 256;
+
+int64_t ws_bytes(const kin_mech* m, int precision, int64_t nslots)
+{
+    const int64_t vec = scratch_elems_vec(m->nS) * 8 * nslots;
+    const int64_t rate = scratch_bytes_rate(m->nS, m->nR, precision) * nslots;
+    return HEADER + ((vec + 255) / 256) * 256 + rate;
+}
+
+int check_opts(const kin_opts* o)
+{
+    if (!o) return fail(KIN_EINVAL, "opts is NULL");
+    if (o->method != KIN_RKCK && o->method != KIN_RKC) return fail(KIN_EINVAL, "unknown method %d", o->method);
+    if (o->precision != KIN_FP64 && o->precision != KIN_MIXED)
+        return fail(KIN_EINVAL, "unknown precision %d", o->precision);
+    if (o->reserved != 0) return fail(KIN_EINVAL, "opts.reserved must be 0");
+    return KIN_OK;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* kin_last_error(void) { return g_err; }
+
+const char* kin_version(void) { return "kin 0.1 (sm_103a)"; }
+
+int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
+{
+    g_err[0] = 0;
+    if (!d || !out) return fail(KIN_EINVAL, "desc and out must be non-NULL");
+    *out = nullptr;
+    const int nS = d->n_species, nR = d->n_reactions;
+    if (nS < 1 || nS > KIN_MAX_SPECIES) return fail(KIN_EINVAL, "n_species %d out of range", nS);
+    if (nR < 0 || nR > KIN_MAX_REACTIONS) return fail(KIN_EINVAL, "n_reactions %d out of range", nR);
+    if (!d->W) return fail(KIN_EINVAL, "W is NULL");
+    if (nR > 0 && (!d->lnA || !d->beta || !d->Ea || !d->reac || !d->prod || !d->type))
+        return fail(KIN_EINVAL, "reaction arrays must be non-NULL");
+    for (int i = 0; i < nS; ++i)
+        if (!finite_pos(d->W[i])) return fail(KIN_EINVAL, "W[%d] must be finite and > 0", i);
+
+    std::vector<Rxn> rxn(nR);
+    std::vector<double> EaR(nR), lnA0(nR, 0.0), beta0(nR, 0.0), Ea0R(nR, 0.0);
+    std::vector<std::vector<std::pair<int, double>>> bySp(nS);
+    int nM = 0;
+    for (int j = 0; j < nR; ++j) {
+        const int t = d->type[j];
+        if (t != KIN_RXN_PLAIN && t != KIN_RXN_THIRD_BODY && t != KIN_RXN_FALLOFF)
+            return fail(KIN_EINVAL, "reaction %d: unknown type %d", j, t);
+        if (!std::isfinite(d->lnA[j]) || !std::isfinite(d->beta[j]) || !std::isfinite(d->Ea[j]))
+            return fail(KIN_EINVAL, "reaction %d: non-finite Arrhenius parameter", j);
+        int r[2] = {d->reac[2 * j], d->reac[2 * j + 1]};
+        int q[2] = {d->prod[2 * j], d->prod[2 * j + 1]};
+        for (int k = 0; k < 2; ++k) {
+            if (r[k] < -1 || r[k] >= nS) return fail(KIN_EINVAL, "reaction %d: reactant index %d", j, r[k]);
+            if (q[k] < -1 || q[k] >= nS) return fail(KIN_EINVAL, "reaction %d: product index %d", j, q[k]);
+        }
+        rxn[j] = Rxn{r[0], r[1], t, t != KIN_RXN_PLAIN ? nM : -1};
+        if (t != KIN_RXN_PLAIN) ++nM;
+        EaR[j] = d->Ea[j] / R_GAS;
+        if (t == KIN_RXN_FALLOFF) {
+            if (!d->lnA0 || !d->beta0 || !d->Ea0)
+                return fail(KIN_EINVAL, "falloff reaction %d needs lnA0, beta0, Ea0", j);
+            if (!std::isfinite(d->lnA0[j]) || !std::isfinite(d->beta0[j]) || !std::isfinite(d->Ea0[j]))
+                return fail(KIN_EINVAL, "reaction %d: non-finite low-pressure parameter", j);
+            lnA0[j] = d->lnA0[j];
+            beta0[j] = d->beta0[j];
+            Ea0R[j] = d->Ea0[j] / R_GAS;
+        }
+        // net coefficients nu'' - nu' per species of this reaction
+        int sp[4] = {q[0], q[1], r[0], r[1]};
+        double c[4] = {1, 1, -1, -1};
+        for (int a = 0; a < 4; ++a) {
+            if (sp[a] < 0) continue;
+            auto& v = bySp[sp[a]];
+            if (!v.empty() && v.back().first == j) v.back().second += c[a];
+            else v.push_back({j, c[a]});
+        }
+    }
+    if (nM > 0 && !d->eff) return fail(KIN_EINVAL, "eff is NULL but %d reactions need efficiencies", nM);
+    for (int64_t k = 0; k < (int64_t)nM * nS; ++k)
+        if (!std::isfinite(d->eff[k])) return fail(KIN_EINVAL, "non-finite efficiency");
+    std::vector<int> ptr(nS + 1, 0), crx;
+    std::vector<double> cnu;
+    for (int i = 0; i < nS; ++i) {
+        for (auto& pr : bySp[i])
+            if (pr.second != 0.0) {  // a species on both sides with equal count cancels
+                crx.push_back(pr.first);
+                cnu.push_back(pr.second);
+            }
+        ptr[i + 1] = (int)crx.size();
+    }
+    const int nnz = (int)crx.size();
+
+    // one device buffer, 256-byte aligned sub-arrays
+    std::vector<char> host;
+    auto put = [&](const void* src, size_t bytes) {
+        size_t off = (host.size() + 255) / 256 * 256;
+        host.resize(off + bytes);
+        if (bytes) memcpy(host.data() + off, src, bytes);
+        return off;
+    };
+    std::vector<double> invW(nS);
+    std::vector<float> invW32(nS), nu32(cnu.begin(), cnu.end());
+    for (int i = 0; i < nS; ++i) {
+        invW[i] = 1.0 / d->W[i];
+        invW32[i] = (float)invW[i];
+    }
+    std::vector<float> eff32((size_t)nM * nS);
+    for (size_t k = 0; k < eff32.size(); ++k) eff32[k] = (float)d->eff[k];
+    const size_t oW = put(d->W, 8 * nS), oIW = put(invW.data(), 8 * nS), oIW32 = put(invW32.data(), 4 * nS);
+    const size_t oLA = put(d->lnA, 8 * nR), oB = put(d->beta, 8 * nR), oE = put(EaR.data(), 8 * nR);
+    const size_t oLA0 = put(lnA0.data(), 8 * nR), oB0 = put(beta0.data(), 8 * nR), oE0 = put(Ea0R.data(), 8 * nR);
+    const size_t oRx = put(rxn.data(), sizeof(Rxn) * nR);
+    const size_t oPtr = put(ptr.data(), 4 * (nS + 1)), oCrx = put(crx.data(), 4 * nnz);
+    const size_t oNu = put(cnu.data(), 8 * nnz), oNu32 = put(nu32.data(), 4 * nnz);
+    const size_t oEff = put(d->eff, 8 * (size_t)nM * nS), oEff32 = put(eff32.data(), 4 * (size_t)nM * nS);
+    const size_t oTab = put(nullptr, 0);
+    const size_t tabBytes = sizeof(double) * RKC_TAB_S * RKC_TAB_S * RKC_TAB_W;
+    host.resize(oTab + tabBytes, 0);
+
+    kin_mech* m = new (std::nothrow) kin_mech();
+    if (!m) return fail(KIN_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e != cudaSuccess) { delete m; return cuda_fail(e, "cudaGetDevice"); }
+    e = cudaMalloc(&m->buf, host.size());
+    if (e != cudaSuccess) { delete m; cudaGetLastError(); return fail(KIN_ENOMEM, "cudaMalloc(%zu): %s", host.size(), cudaGetErrorString(e)); }
+    e = cudaMemcpy(m->buf, host.data(), host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(m->buf); delete m; return cuda_fail(e, "cudaMemcpy"); }
+    char* b = (char*)m->buf;
+    MechDev& M = m->dev;
+    M.nS = nS; M.nR = nR; M.nM = nM; M.nnz = nnz;
+    M.W = (const double*)(b + oW); M.invW = (const double*)(b + oIW); M.invW32 = (const float*)(b + oIW32);
+    M.lnA = (const double*)(b + oLA); M.beta = (const double*)(b + oB); M.EaR = (const double*)(b + oE);
+    M.lnA0 = (const double*)(b + oLA0); M.beta0 = (const double*)(b + oB0); M.Ea0R = (const double*)(b + oE0);
+    M.rxn = (const Rxn*)(b + oRx);
+    M.csr_ptr = (const int*)(b + oPtr); M.csr_rxn = (const int*)(b + oCrx);
+    M.csr_nu = (const double*)(b + oNu); M.csr_nu32 = (const float*)(b + oNu32);
+    M.eff = (const double*)(b + oEff); M.eff32 = (const float*)(b + oEff32);
+    M.rkc = (const double*)(b + oTab);
+    m->nS = nS; m->nR = nR; m->nM = nM;
+    e = launch_rkc_table((double*)(b + oTab), 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { cudaFree(m->buf); delete m; return cuda_fail(e, "RKC table"); }
+    *out = m;
+    return KIN_OK;
+}
+
+int kin_destroy(kin_mech* m)
+{
+    g_err[0] = 0;
+    if (!m) return KIN_OK;
+    cudaError_t e = cudaFree(m->buf);
+    delete m;
+    return e == cudaSuccess ? KIN_OK : cuda_fail(e, "cudaFree");
+}
+
+int64_t kin_workspace_bytes(const kin_mech* m, const kin_opts* o)
+{
+    g_err[0] = 0;
+    if (!m) return fail(KIN_EINVAL, "mechanism is NULL");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    Grid g;
+    rc = grid_for(m, o, &g);
+    if (rc) return rc;
+    return ws_bytes(m, o->precision, g.nslots);
+}
+
+int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, const kin_opts* o,
+                        void* ws, int64_t ws_size)
+{
+    g_err[0] = 0;
+    if (!m) return fail(KIN_EINVAL, "mechanism is NULL");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if (n < 1 || n > KIN_MAX_INSTANCES) return fail(KIN_EINVAL, "n_instances %d out of range [1, %d]", n, KIN_MAX_INSTANCES);
+    if (!inst) return fail(KIN_EINVAL, "instances is NULL");
+    // ~10 KB of launch parameters: built on the heap, copied by the launch
+    Launch* Lp = new (std::nothrow) Launch();
+    if (!Lp) return fail(KIN_ENOMEM, "host allocation failed");
+    struct Free { Launch* p; ~Free() { delete p; } } fr{Lp};
+    Launch& P = *Lp;
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const kin_instance& I = inst[i];
+        if (I.cells < 0) return fail(KIN_EINVAL, "instance %d: cells < 0", i);
+        if (!finite_pos(I.dt)) return fail(KIN_EINVAL, "instance %d: dt must be finite and > 0", i);
+        if (!finite_pos(I.rtol)) return fail(KIN_EINVAL, "instance %d: rtol must be finite and > 0", i);
+        if (!std::isfinite(I.atol) || I.atol < 0) return fail(KIN_EINVAL, "instance %d: atol must be finite and >= 0", i);
+        if (I.cells > 0) {
+            if (!I.T || !I.p || !I.Y) return fail(KIN_EINVAL, "instance %d: T, p and Y must be non-NULL", i);
+            if (I.ldY < I.cells) return fail(KIN_EINVAL, "instance %d: ldY < cells", i);
+            if (!is_device_ptr(I.T) || !is_device_ptr(I.p) || !is_device_ptr(I.Y) ||
+                (I.status && !is_device_ptr(I.status)) || (I.stats && !is_device_ptr(I.stats)))
+                return fail(KIN_EINVAL, "instance %d: T, p, Y, status and stats must be device memory", i);
+        }
+        P.start[i] = total;
+        P.inst[i] = InstDev{I.T, I.p, I.Y, I.ldY, I.dt, I.rtol, I.atol, I.status, I.stats};
+        total += I.cells;
+    }
+    P.start[n] = total;
+    if (total == 0) return KIN_OK;
+    Grid g;
+    rc = grid_for(m, o, &g);
+    if (rc) return rc;
+    const int64_t need = ws_bytes(m, o->precision, g.nslots);
+    if (!ws) return fail(KIN_EINVAL, "workspace is NULL");
+    if (((uintptr_t)ws) % 256) return fail(KIN_EINVAL, "workspace must be 256-byte aligned");
+    if (ws_size < need) return fail(KIN_ENOMEM, "workspace has %lld bytes, needs %lld", (long long)ws_size, (long long)need);
+    if (!is_device_ptr(ws)) return fail(KIN_EINVAL, "workspace must be device memory");
+    // never more lanes than cells
+    int blocks = g.blocks;
+    const int64_t want = (total + g.threads - 1) / g.threads;
+    if (want < blocks) blocks = (int)want;
+    const int64_t nslots = (int64_t)blocks * g.threads;
+    P.M = m->dev;
+    P.method = o->method;
+    P.precision = o->precision;
+    P.max_steps = o->max_steps > 0 ? o->max_steps : 100000;
+    P.n_inst = n;
+    P.nslots = nslots;
+    P.total = total;
+    char* base = (char*)ws;
+    P.queue = (unsigned long long*)base;
+    P.vec = (double*)(base + HEADER);
+    const int64_t vecb = scratch_elems_vec(m->nS) * 8 * nslots;
+    P.rarr = base + HEADER + (vecb + 255) / 256 * 256;
+    cudaStream_t st = (cudaStream_t)o->stream;
+    cudaError_t e = cudaMemsetAsync(P.queue, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    e = launch_integrate(P, blocks, g.threads, st);
+    if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
+    return KIN_OK;
+}
+
+int kin_integrate(const kin_mech* m, int64_t cells, const double* T, const double* p, double* Y,
+                  int64_t ldY, double dt, double rtol, double atol, const kin_opts* o,
+                  uint8_t* status, int32_t* stats, void* ws, int64_t ws_size)
+{
+    kin_instance I{cells, T, p, Y, ldY, dt, rtol, atol, status, stats};
+    return kin_integrate_batch(m, 1, &I, o, ws, ws_size);
+}
+
+static int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
+
+int64_t kin_host_buffer_bytes(const kin_mech* m, const kin_opts* o, int64_t cells)
+{
+    g_err[0] = 0;
+    if (cells < 0) return fail(KIN_EINVAL, "cells < 0");
+    int64_t ws = kin_workspace_bytes(m, o);
+    if (ws < 0) return ws;
+    return al256(ws) + 2 * al256(8 * cells) + al256(8 * cells * m->nS) + al256(cells) + al256(16 * cells);
+}
+
+int kin_integrate_host(const kin_mech* m, int64_t cells, const double* T, const double* p, double* Y,
+                       int64_t ldY, double dt, double rtol, double atol, const kin_opts* o,
+                       uint8_t* status, int32_t* stats, void* buf, int64_t bytes)
+{
+    g_err[0] = 0;
+    const int64_t need = kin_host_buffer_bytes(m, o, cells);
+    if (need < 0) return (int)need;
+    if (cells == 0) return KIN_OK;
+    if (!T || !p || !Y) return fail(KIN_EINVAL, "T, p and Y must be non-NULL");
+    if (ldY < cells) return fail(KIN_EINVAL, "ldY < cells");
+    if (!buf || ((uintptr_t)buf) % 256) return fail(KIN_EINVAL, "device_buffer must be non-NULL and 256-byte aligned");
+    if (bytes < need) return fail(KIN_ENOMEM, "device_buffer has %lld bytes, needs %lld", (long long)bytes, (long long)need);
+    if (!is_device_ptr(buf)) return fail(KIN_EINVAL, "device_buffer must be device memory");
+    const int64_t ws = kin_workspace_bytes(m, o);
+    char* b = (char*)buf;
+    int64_t off = al256(ws);
+    double* Td = (double*)(b + off); off += al256(8 * cells);
+    double* pd = (double*)(b + off); off += al256(8 * cells);
+    double* Yd = (double*)(b + off); off += al256(8 * cells * m->nS);
+    uint8_t* sd = (uint8_t*)(b + off); off += al256(cells);
+    int32_t* xd = (int32_t*)(b + off);
+    cudaStream_t st = (cudaStream_t)o->stream;
+    cudaError_t e = cudaMemcpyAsync(Td, T, 8 * cells, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pd, p, 8 * cells, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(Yd, 8 * cells, Y, 8 * ldY, 8 * cells, m->nS, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    int rc = kin_integrate(m, cells, Td, pd, Yd, cells, dt, rtol, atol, o, sd, stats ? xd : nullptr, buf, ws);
+    if (rc) return rc;
+    e = cudaMemcpy2DAsync(Y, 8 * ldY, Yd, 8 * cells, 8 * cells, m->nS, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, sd, cells, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && stats) e = cudaMemcpyAsync(stats, xd, 16 * cells, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    return KIN_OK;
+}
+
+int kin_rates(const kin_mech* m, int64_t cells, const double* T, const double* p, const double* Y,
+              int64_t ldY, double* dYdt, int32_t precision, void* stream, void* ws, int64_t ws_size)
+{
+    g_err[0] = 0;
+    if (!m) return fail(KIN_EINVAL, "mechanism is NULL");
+    if (precision != KIN_FP64 && precision != KIN_MIXED) return fail(KIN_EINVAL, "unknown precision %d", precision);
+    if (cells < 0) return fail(KIN_EINVAL, "cells < 0");
+    if (cells == 0) return KIN_OK;
+    if (!T || !p || !Y || !dYdt) return fail(KIN_EINVAL, "T, p, Y and dYdt must be non-NULL");
+    if (ldY < cells) return fail(KIN_EINVAL, "ldY < cells");
+    if (!is_device_ptr(T) || !is_device_ptr(p) || !is_device_ptr(Y) || !is_device_ptr(dYdt))
+        return fail(KIN_EINVAL, "T, p, Y and dYdt must be device memory");
+    kin_opts o{KIN_RKC, precision, 0, 0, 0, 0, stream};
+    Grid g;
+    int rc = grid_for(m, &o, &g);
+    if (rc) return rc;
+    const int64_t need = ws_bytes(m, precision, g.nslots);
+    if (!ws || ((uintptr_t)ws) % 256) return fail(KIN_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    if (ws_size < need) return fail(KIN_ENOMEM, "workspace has %lld bytes, needs %lld", (long long)ws_size, (long long)need);
+    char* base = (char*)ws;
+    const int64_t vecb = scratch_elems_vec(m->nS) * 8 * g.nslots;
+    void* rarr = base + HEADER + (vecb + 255) / 256 * 256;
+    cudaError_t e = launch_rates(m->dev, cells, T, p, Y, ldY, dYdt, precision, rarr, g.nslots,
+                                 g.blocks, g.threads, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rates launch");
+    return KIN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+"""CPU checks of the C ABI library: it builds, loads, and exports every entry
+point that include/kin.h declares; argument validation that runs before any
+CUDA call rejects bad input. No kernel is launched here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1309_2710_gb300 import build as kbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(kin_\w+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ctypes.CDLL(kbuild.build())
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for required in ("kin_create_mechanism", "kin_integrate", "kin_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header():
+    from paper_1309_2710_gb300 import kin
+    assert set(kin._SIGNATURES) == _declared()
+
+
+def test_create_rejects_null_without_touching_cuda(lib):
+    lib.kin_create_mechanism.restype = ctypes.c_int
+    lib.kin_create_mechanism.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.kin_last_error.restype = ctypes.c_char_p
+    assert lib.kin_create_mechanism(None, None) == -1
+    assert b"non-NULL" in lib.kin_last_error()
+
+
+def test_integrate_rejects_null_mechanism(lib):
+    lib.kin_integrate.restype = ctypes.c_int
+    assert lib.kin_integrate(None, ctypes.c_int64(1), None, None, None, ctypes.c_int64(1),
+                             ctypes.c_double(1e-6), ctypes.c_double(1e-6), ctypes.c_double(1e-10),
+                             None, None, None, None, ctypes.c_int64(0)) == -1
+
+
+def test_version(lib):
+    lib.kin_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.kin_version()

@@ -1,0 +1,257 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs. Sizes span several blocks with ragged tails; the full-size
+13-species workload is checked on sampled cells in the benchmark's launch
+configuration."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1309_2710_gb300 import synth  # noqa: E402
+from tests.parity import compare, rel_err  # noqa: E402
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1309_2710_gb300 import build as kbuild  # noqa: E402
+
+kbuild.build()
+from paper_1309_2710_gb300 import kin  # noqa: E402
+
+DEV = torch.device("cuda:0")
+MECHS = {}
+
+
+def mech(name):
+    if name not in MECHS:
+        m = synth.workload_mechanism(name)
+        MECHS[name] = (m, kin.Mechanism(m), oracle.Mech(m))
+    return MECHS[name]
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV)
+
+
+def run_gpu(km, T, p, Y, dt, rtol, atol, method, precision=kin.FP64, max_steps=20000, ld=None):
+    cells = T.shape[0]
+    ld = cells if ld is None else ld
+    Yd = torch.zeros((Y.shape[0], ld), dtype=torch.float64, device=DEV)
+    Yd[:, :cells] = dev(Y)
+    st = torch.full((cells,), 255, dtype=torch.uint8, device=DEV)
+    sta = torch.zeros((cells, 4), dtype=torch.int32, device=DEV)
+    kin.integrate(km, dev(T), dev(p), Yd, dt, rtol, atol, method, precision, status=st, stats=sta,
+                  max_steps=max_steps)
+    torch.cuda.synchronize()
+    return Yd.cpu().numpy(), st.cpu().numpy(), sta.cpu().numpy()
+
+
+# ------------------------------------------------------------------- f ---
+@pytest.mark.parametrize("name", list(synth.WORKLOADS))
+def test_rates_fp64(name):
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m, cells=333)
+    out = kin.rates(km, dev(T), dev(p), dev(Y)).cpu().numpy()
+    for c in range(0, 333, 7):
+        ref = oracle.rates(om, T[c], p[c], Y[:, c])
+        scale = np.abs(ref).max()
+        assert np.abs(out[:, c] - ref).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("name", list(synth.WORKLOADS))
+def test_rates_mixed(name):
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m, cells=129)
+    out = kin.rates(km, dev(T), dev(p), dev(Y), precision=kin.MIXED).cpu().numpy()
+    worst = 0.0
+    for c in range(129):
+        ref = oracle.rates(om, T[c], p[c], Y[:, c])
+        worst = max(worst, np.abs(out[:, c] - ref).max() / np.abs(ref).max())
+    # FP32 rates: a few ulp of 2^-24 on the largest terms, amplified by the
+    # cancellation in the stoichiometric sum
+    assert worst < 1e-4, worst
+
+
+# ---------------------------------------------------------------- RKCK ---
+def test_rkck_h2_full_workload():
+    """9 species / 38 reactions, RKCK, all 4096 cells of the workload."""
+    name = "h2_9sp_rkck"
+    w = synth.WORKLOADS[name]
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m)
+    Yg, stg, stag = run_gpu(km, T, p, Y, w["dt"], w["rtol"], w["atol"], kin.RKCK)
+    Yo, sto, stao, _ = oracle.integrate(om, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKCK)
+    s = compare(Yg, Yo, stg, sto, stag, stao, w["atol"], w["rtol"])
+    print("rkck h2", s)
+
+
+# ----------------------------------------------------------------- RKC ---
+@pytest.mark.parametrize("cells", [1, 31, 4133])
+def test_rkc_h2co_ragged(cells):
+    name = "h2co_13sp_rkc"
+    w = synth.WORKLOADS[name]
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m, cells=cells, seed_offset=7)
+    Yg, stg, stag = run_gpu(km, T, p, Y, w["dt"], w["rtol"], w["atol"], kin.RKC, ld=cells + 5)
+    Yo, sto, stao, _ = oracle.integrate(om, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKC)
+    s = compare(Yg[:, :cells], Yo, stg, sto, stag, stao, w["atol"], w["rtol"])
+    assert np.all(Yg[:, cells:] == 0.0)  # padding columns untouched
+    print("rkc h2co", cells, s)
+
+
+def test_rkc_h2co_full_size_sampled():
+    """All 262144 cells in one launch (the benchmark's configuration); the
+    oracle recomputes 1536 cells drawn at random."""
+    name = "h2co_13sp_rkc"
+    w = synth.WORKLOADS[name]
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m)
+    Yg, stg, stag = run_gpu(km, T, p, Y, w["dt"], w["rtol"], w["atol"], kin.RKC)
+    idx = np.sort(np.random.default_rng(17).choice(T.shape[0], 1536, replace=False))
+    Yo, sto, stao, _ = oracle.integrate(om, T[idx], p[idx], Y[:, idx], w["dt"], w["rtol"],
+                                        w["atol"], oracle.RKC)
+    s = compare(Yg[:, idx], Yo, stg[idx], sto, stag[idx], stao, w["atol"], w["rtol"])
+    # properties that hold for every cell: mass stays 1, status ok
+    assert (stg == 0).all()
+    assert np.abs(Yg.sum(0) - 1).max() < 1e-12
+    print("rkc h2co full", s)
+
+
+def test_rkc_mixed_ch4_sampled():
+    """53 species / 634 reactions, FP32 rates, FP64 state: within 1e-5 of the
+    FP64 oracle per species (relative to max(|Y|, atol))."""
+    name = "ch4_53sp_rkc_mixed"
+    w = synth.WORKLOADS[name]
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m, cells=2048)
+    Yg, stg, stag = run_gpu(km, T, p, Y, w["dt"], w["rtol"], w["atol"], kin.RKC, kin.MIXED)
+    idx = np.arange(0, 2048, 8)
+    Yo, sto, stao, _ = oracle.integrate(om, T[idx], p[idx], Y[:, idx], w["dt"], w["rtol"],
+                                        w["atol"], oracle.RKC)
+    assert (stg[idx] == sto).all()
+    err = rel_err(Yg[:, idx], Yo, w["atol"]).max()
+    print("mixed ch4 max err", err)
+    assert err <= 1e-5
+
+
+def test_rkc_ch4_fp64_sampled():
+    name = "ch4_53sp_rkc_mixed"
+    w = synth.WORKLOADS[name]
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m, cells=300, seed_offset=3)
+    Yg, stg, stag = run_gpu(km, T, p, Y, w["dt"], w["rtol"], w["atol"], kin.RKC)
+    Yo, sto, stao, _ = oracle.integrate(om, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKC)
+    print("rkc ch4 fp64", compare(Yg, Yo, stg, sto, stag, stao, w["atol"], w["rtol"]))
+
+
+# ------------------------------------------------------------- batched ---
+def _c4_parts(scale):
+    name = "c2h4_111sp_rkc_batched"
+    m, km, om = mech(name)
+    parts, host = [], []
+    for i, (n, dt) in enumerate(synth.batched_instances(name, scale=scale)):
+        T, p, Y = synth.workload_states(name, m, cells=n, seed_offset=100 + i)
+        host.append((T, p, Y, dt))
+        parts.append(kin.Cells(dev(T), dev(p), dev(Y), dt, 1e-6, 1e-10,
+                               torch.zeros(n, dtype=torch.uint8, device=DEV),
+                               torch.zeros((n, 4), dtype=torch.int32, device=DEV)))
+    return m, km, om, parts, host
+
+
+def test_batched_c2h4_reduced():
+    """16 uneven instances of the 111-species mechanism (sizes scaled by
+    1/128) in one launch; every instance's sampled cells against the oracle."""
+    m, km, om, parts, host = _c4_parts(1 / 128)
+    kin.integrate_batch(km, parts, kin.RKC)
+    torch.cuda.synchronize()
+    tot = 0
+    for (T, p, Y, dt), c in zip(host, parts):
+        idx = np.arange(0, T.shape[0], max(1, T.shape[0] // 4))
+        Yo, sto, stao, _ = oracle.integrate(om, T[idx], p[idx], Y[:, idx], dt, 1e-6, 1e-10, oracle.RKC)
+        compare(c.Y.cpu().numpy()[:, idx], Yo, c.status.cpu().numpy()[idx], sto,
+                c.stats.cpu().numpy()[idx], stao, 1e-10, 1e-6, max_div_frac=0.5)
+        tot += len(idx)
+    assert tot >= 32
+
+
+def test_batch_equals_separate_calls():
+    """A cell's result does not depend on which lane or launch integrates it:
+    the batched launch reproduces per-instance launches bit for bit."""
+    name = "h2co_13sp_rkc"
+    m, km, om = mech(name)
+    parts, singles = [], []
+    for i, n in enumerate([100, 7, 2500, 1]):
+        T, p, Y = synth.workload_states(name, m, cells=n, seed_offset=50 + i)
+        dt = [1e-6, 3e-7, 1e-6, 2e-6][i]
+        parts.append(kin.Cells(dev(T), dev(p), dev(Y), dt))
+        Ys = dev(Y)
+        kin.integrate(km, dev(T), dev(p), Ys, dt, 1e-6, 1e-10, kin.RKC)
+        singles.append(Ys)
+    kin.integrate_batch(km, parts, kin.RKC)
+    torch.cuda.synchronize()
+    for c, Ys in zip(parts, singles):
+        assert torch.equal(c.Y, Ys)
+
+
+# ---------------------------------------------------------- edge cases ---
+def test_zero_cells_is_a_noop():
+    m, km, om = mech("h2co_13sp_rkc")
+    Y = torch.ones((m.n_species, 4), dtype=torch.float64, device=DEV)
+    e = torch.empty(0, dtype=torch.float64, device=DEV)
+    kin.integrate(km, e, e, Y, 1e-6, 1e-6, 1e-10, kin.RKC)
+    torch.cuda.synchronize()
+    assert torch.all(Y == 1)
+
+
+def test_step_limit_keeps_last_accepted_state():
+    name = "h2co_13sp_rkc"
+    w = synth.WORKLOADS[name]
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m, cells=70)
+    Yg, stg, stag = run_gpu(km, T, p, Y, w["dt"], w["rtol"], w["atol"], kin.RKC, max_steps=3)
+    Yo, sto, stao, _ = oracle.integrate(om, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKC,
+                                        max_steps=3)
+    assert (stg == kin.CELL_MAXSTEPS).all()
+    compare(Yg, Yo, stg, sto, stag, stao, w["atol"], w["rtol"])
+
+
+@pytest.mark.parametrize("method", [kin.RKCK, kin.RKC])
+def test_nonfinite_cell_is_flagged_alone(method):
+    name = "h2_9sp_rkck"
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m, cells=40)
+    Y[2, 5] = np.nan
+    Yg, stg, stag = run_gpu(km, T, p, Y, 1e-7, 1e-6, 1e-10, method)
+    assert stg[5] == kin.CELL_NONFINITE
+    assert (np.delete(stg, 5) == 0).all()
+    Yo, sto, stao, _ = oracle.integrate(om, T, p, Y, 1e-7, 1e-6, 1e-10, method)
+    keep = np.arange(40) != 5
+    compare(Yg[:, keep], Yo[:, keep], stg[keep], sto[keep], stag[keep], stao[keep], 1e-10, 1e-6)
+
+
+def test_invalid_arguments_raise():
+    m, km, om = mech("h2co_13sp_rkc")
+    T, p, Y = synth.workload_states("h2co_13sp_rkc", m, cells=8)
+    Td, pd, Yd = dev(T), dev(p), dev(Y)
+    with pytest.raises(kin.KinError) as e:
+        kin.integrate(km, Td, pd, Yd, -1e-6, 1e-6, 1e-10)
+    assert e.value.code == kin.KIN_EINVAL
+    with pytest.raises(kin.KinError) as e:
+        kin.integrate(km, Td, pd, Yd, 1e-6, 1e-6, 1e-10,
+                      workspace=torch.empty(1024, dtype=torch.uint8, device=DEV))
+    assert e.value.code == kin.KIN_ENOMEM
+    ws = km.workspace()
+    with pytest.raises(kin.KinError) as e:
+        kin.integrate(km, Td, pd, Yd, 1e-6, 1e-6, 1e-10, workspace=ws[8:])
+    assert e.value.code == kin.KIN_EINVAL
+    # host memory where device memory is required
+    import ctypes
+    h = np.zeros(8)
+    rc = kin.lib().kin_integrate(km.handle, 8, ctypes.c_void_p(h.ctypes.data), kin._ptr(pd),
+                                 kin._ptr(Yd), 8, 1e-6, 1e-6, 1e-10,
+                                 ctypes.byref(kin.Opts(1, 0, 0, 0, 0, 0, None)), None, None,
+                                 kin._ptr(ws), ws.numel())
+    assert rc == kin.KIN_EINVAL
