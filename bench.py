@@ -255,7 +255,7 @@ def run_kin(args):
     Yd = torch.empty_like(Y0d)
     st = torch.zeros(cells, dtype=torch.uint8, device=dev)
     sta = torch.zeros((cells, 4), dtype=torch.int32, device=dev)
-    ws = km.workspace(method, prec, device=dev)
+    ws = km.workspace(method, prec, cells, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 

@@ -135,16 +135,18 @@ int kin_destroy(kin_mech *m);
 /* Message for the last failed call on this thread ("" if none). */
 const char *kin_last_error(void);
 
-/* Bytes of device workspace kin_integrate / kin_integrate_batch need for
- * `opts` on the current device (independent of the number of cells: the
- * persistent grid has a fixed number of lanes). Returns < 0 on error. */
-int64_t kin_workspace_bytes(const kin_mech *m, const kin_opts *opts);
+/* Bytes of device workspace that kin_integrate / kin_integrate_batch (with
+ * `cells` cells in total) or kin_rates (with `cells` cells) need for `opts` on
+ * the current device: per-lane working vectors of the persistent grid plus
+ * per-cell rate constants, f(y0), first-step data and processing order.
+ * Returns < 0 on error. */
+int64_t kin_workspace_bytes(const kin_mech *m, const kin_opts *opts, int64_t cells);
 
 /* Integrate `cells` cells of one instance over dt (Sections 2.2/2.3 and the
  * restart-per-flow-step convention of Section 3). T, p, Y, status, stats
  * as in kin_instance. workspace: caller-owned device memory of at least
- * kin_workspace_bytes(m, opts) bytes, 256-byte aligned; it must not be used by
- * another call that may run concurrently. Errors: KIN_EINVAL, KIN_ENOMEM
+ * kin_workspace_bytes(m, opts, cells) bytes, 256-byte aligned; it must not be
+ * used by another call that may run concurrently. Errors: KIN_EINVAL, KIN_ENOMEM
  * (workspace too small), KIN_EUNSUPPORTED, KIN_ECUDA. */
 int kin_integrate(const kin_mech *m, int64_t cells, const double *T, const double *p,
                   double *Y, int64_t ldY, double dt, double rtol, double atol,
@@ -156,7 +158,8 @@ int kin_integrate(const kin_mech *m, int64_t cells, const double *T, const doubl
  * so uneven instances balance across the GPU. `inst` is a host array that is
  * copied into the launch parameters, so the call may be captured in a CUDA
  * graph (the captured graph refers to the same device buffers and workspace).
- * Errors as kin_integrate. */
+ * The workspace must hold kin_workspace_bytes(m, opts, total cells). Errors
+ * as kin_integrate. */
 int kin_integrate_batch(const kin_mech *m, int32_t n_instances, const kin_instance *inst,
                         const kin_opts *opts, void *workspace, int64_t workspace_bytes);
 
@@ -181,7 +184,7 @@ int kin_integrate_host(const kin_mech *m, int64_t cells, const double *T, const 
  * (E:spec-rate), (E:rxn-rate), (E:rxn-const)) in the given precision
  * (KIN_FP64 or KIN_MIXED), enqueued on `stream`. T, p, Y, dYdt and workspace
  * are device pointers; dYdt has the layout of Y. The workspace rule is that of
- * kin_integrate with method KIN_RKC and the same precision. Errors:
+ * kin_integrate with method KIN_RKC, the same precision and `cells` cells. Errors:
  * KIN_EINVAL, KIN_ENOMEM, KIN_ECUDA. */
 int kin_rates(const kin_mech *m, int64_t cells, const double *T, const double *p,
               const double *Y, int64_t ldY, double *dYdt, int32_t precision, void *stream,

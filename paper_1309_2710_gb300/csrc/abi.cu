@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <climits>
 #include <cstring>
 #include <vector>
 
@@ -79,13 +80,9 @@ int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
     return KIN_OK;
 }
 
-constexpr int64_t HEADER = 256;
-
-int64_t ws_bytes(const kin_mech* m, int precision, int64_t nslots)
+int64_t ws_bytes(const kin_mech* m, int precision, int64_t nslots, int64_t cells)
 {
-    const int64_t vec = scratch_elems_vec(m->nS) * 8 * nslots;
-    const int64_t rate = scratch_bytes_rate(m->nS, m->nR, precision) * nslots;
-    return HEADER + ((vec + 255) / 256) * 256 + rate;
+    return ws_layout(m->dev, precision, nslots, cells).total;
 }
 
 int check_opts(const kin_opts* o)
@@ -125,7 +122,7 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     std::vector<Rxn> rxn(nR);
     std::vector<double> EaR(nR), lnA0(nR, 0.0), beta0(nR, 0.0), Ea0R(nR, 0.0);
     std::vector<std::vector<std::pair<int, double>>> bySp(nS);
-    int nM = 0;
+    int nM = 0, nFO = 0;
     for (int j = 0; j < nR; ++j) {
         const int t = d->type[j];
         if (t != KIN_RXN_PLAIN && t != KIN_RXN_THIRD_BODY && t != KIN_RXN_FALLOFF)
@@ -138,8 +135,10 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
             if (r[k] < -1 || r[k] >= nS) return fail(KIN_EINVAL, "reaction %d: reactant index %d", j, r[k]);
             if (q[k] < -1 || q[k] >= nS) return fail(KIN_EINVAL, "reaction %d: product index %d", j, q[k]);
         }
-        rxn[j] = Rxn{r[0], r[1], t, t != KIN_RXN_PLAIN ? nM : -1};
+        rxn[j] = Rxn{(int16_t)r[0], (int16_t)r[1], (int16_t)t, 0, t != KIN_RXN_PLAIN ? nM : -1,
+                     t == KIN_RXN_FALLOFF ? nFO : -1};
         if (t != KIN_RXN_PLAIN) ++nM;
+        if (t == KIN_RXN_FALLOFF) ++nFO;
         EaR[j] = d->Ea[j] / R_GAS;
         if (t == KIN_RXN_FALLOFF) {
             if (!d->lnA0 || !d->beta0 || !d->Ea0)
@@ -212,7 +211,7 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     if (e != cudaSuccess) { cudaFree(m->buf); delete m; return cuda_fail(e, "cudaMemcpy"); }
     char* b = (char*)m->buf;
     MechDev& M = m->dev;
-    M.nS = nS; M.nR = nR; M.nM = nM; M.nnz = nnz;
+    M.nS = nS; M.nR = nR; M.nM = nM; M.nFO = nFO; M.nnz = nnz;
     M.W = (const double*)(b + oW); M.invW = (const double*)(b + oIW); M.invW32 = (const float*)(b + oIW32);
     M.lnA = (const double*)(b + oLA); M.beta = (const double*)(b + oB); M.EaR = (const double*)(b + oE);
     M.lnA0 = (const double*)(b + oLA0); M.beta0 = (const double*)(b + oB0); M.Ea0R = (const double*)(b + oE0);
@@ -238,16 +237,17 @@ int kin_destroy(kin_mech* m)
     return e == cudaSuccess ? KIN_OK : cuda_fail(e, "cudaFree");
 }
 
-int64_t kin_workspace_bytes(const kin_mech* m, const kin_opts* o)
+int64_t kin_workspace_bytes(const kin_mech* m, const kin_opts* o, int64_t cells)
 {
     g_err[0] = 0;
     if (!m) return fail(KIN_EINVAL, "mechanism is NULL");
+    if (cells < 0) return fail(KIN_EINVAL, "cells < 0");
     int rc = check_opts(o);
     if (rc) return rc;
     Grid g;
     rc = grid_for(m, o, &g);
     if (rc) return rc;
-    return ws_bytes(m, o->precision, g.nslots);
+    return ws_bytes(m, o->precision, g.nslots, cells);
 }
 
 int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, const kin_opts* o,
@@ -287,7 +287,7 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     Grid g;
     rc = grid_for(m, o, &g);
     if (rc) return rc;
-    const int64_t need = ws_bytes(m, o->precision, g.nslots);
+    const int64_t need = ws_bytes(m, o->precision, g.nslots, total);
     if (!ws) return fail(KIN_EINVAL, "workspace is NULL");
     if (((uintptr_t)ws) % 256) return fail(KIN_EINVAL, "workspace must be 256-byte aligned");
     if (ws_size < need) return fail(KIN_ENOMEM, "workspace has %lld bytes, needs %lld", (long long)ws_size, (long long)need);
@@ -305,12 +305,21 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     P.nslots = nslots;
     P.total = total;
     char* base = (char*)ws;
-    P.queue = (unsigned long long*)base;
-    P.vec = (double*)(base + HEADER);
-    const int64_t vecb = scratch_elems_vec(m->nS) * 8 * nslots;
-    P.rarr = base + HEADER + (vecb + 255) / 256 * 256;
+    const WsLayout w = ws_layout(m->dev, o->precision, nslots, total);
+    P.queue = (unsigned long long*)(base + w.header);
+    P.hist = (unsigned*)(base + w.header + 256);
+    P.vec = (double*)(base + w.vec);
+    P.lane_r = base + w.lane_r;
+    P.cell_k = base + w.cell_k;
+    P.cell_f0 = (double*)(base + w.f0);
+    P.cell_sig = (double*)(base + w.sig);
+    P.cell_h = (double*)(base + w.h);
+    P.cell_nfe = (int32_t*)(base + w.nfe);
+    P.cell_st = (uint8_t*)(base + w.st);
+    P.order = (int32_t*)(base + w.order);
+    if (total > INT32_MAX) return fail(KIN_EINVAL, "more than 2^31-1 cells in one call");
     cudaStream_t st = (cudaStream_t)o->stream;
-    cudaError_t e = cudaMemsetAsync(P.queue, 0, sizeof(unsigned long long), st);
+    cudaError_t e = cudaMemsetAsync(base + w.header, 0, 512, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     e = launch_integrate(P, blocks, g.threads, st);
     if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
@@ -331,7 +340,7 @@ int64_t kin_host_buffer_bytes(const kin_mech* m, const kin_opts* o, int64_t cell
 {
     g_err[0] = 0;
     if (cells < 0) return fail(KIN_EINVAL, "cells < 0");
-    int64_t ws = kin_workspace_bytes(m, o);
+    int64_t ws = kin_workspace_bytes(m, o, cells);
     if (ws < 0) return ws;
     return al256(ws) + 2 * al256(8 * cells) + al256(8 * cells * m->nS) + al256(cells) + al256(16 * cells);
 }
@@ -349,7 +358,7 @@ int kin_integrate_host(const kin_mech* m, int64_t cells, const double* T, const 
     if (!buf || ((uintptr_t)buf) % 256) return fail(KIN_EINVAL, "device_buffer must be non-NULL and 256-byte aligned");
     if (bytes < need) return fail(KIN_ENOMEM, "device_buffer has %lld bytes, needs %lld", (long long)bytes, (long long)need);
     if (!is_device_ptr(buf)) return fail(KIN_EINVAL, "device_buffer must be device memory");
-    const int64_t ws = kin_workspace_bytes(m, o);
+    const int64_t ws = kin_workspace_bytes(m, o, cells);
     char* b = (char*)buf;
     int64_t off = al256(ws);
     double* Td = (double*)(b + off); off += al256(8 * cells);
@@ -388,13 +397,11 @@ int kin_rates(const kin_mech* m, int64_t cells, const double* T, const double* p
     Grid g;
     int rc = grid_for(m, &o, &g);
     if (rc) return rc;
-    const int64_t need = ws_bytes(m, precision, g.nslots);
+    const int64_t need = ws_bytes(m, precision, g.nslots, cells);
     if (!ws || ((uintptr_t)ws) % 256) return fail(KIN_EINVAL, "workspace must be non-NULL and 256-byte aligned");
     if (ws_size < need) return fail(KIN_ENOMEM, "workspace has %lld bytes, needs %lld", (long long)ws_size, (long long)need);
-    char* base = (char*)ws;
-    const int64_t vecb = scratch_elems_vec(m->nS) * 8 * g.nslots;
-    void* rarr = base + HEADER + (vecb + 255) / 256 * 256;
-    cudaError_t e = launch_rates(m->dev, cells, T, p, Y, ldY, dYdt, precision, rarr, g.nslots,
+    if (!is_device_ptr(ws)) return fail(KIN_EINVAL, "workspace must be device memory");
+    cudaError_t e = launch_rates(m->dev, cells, T, p, Y, ldY, dYdt, precision, ws, g.nslots,
                                  g.blocks, g.threads, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "rates launch");
     return KIN_OK;

@@ -1,26 +1,31 @@
 // kernels.cu -- sm_103a kernels of the batched kinetics integrator.
 //
-// Design (one GB300, FP64-pipe bound):
-//  * One lane integrates one cell (the cell's whole sub-stepping loop), as in
-//    the paper's thread-per-ODE design (Section 3), but each loop iteration of
-//    a lane performs exactly ONE evaluation of f. The method's control flow
-//    (RKCK stages, RKC stages, finite-difference Jacobian columns, the initial
-//    step probe, accept/reject) is a per-lane state machine around that single
-//    call. Lanes of a warp in different phases or on cells with different
-//    stage counts still execute the expensive part -- f -- together, so warp
-//    divergence costs only the cheap bookkeeping, not whole f evaluations.
-//  * The grid is persistent: lanes pull cells from a global atomic queue
-//    (warp-aggregated), and a lane that finishes its cell immediately takes the
-//    next one. Uneven cells (different step and stage counts) and uneven
-//    instances therefore balance at lane granularity.
-//  * Per-lane arrays (state vectors, rate constants, concentrations, rates of
-//    progress) are element-major in the workspace: coalesced for a warp.
+// Design (one GB300; FP64 runs at 1/64 of the FP32 rate, so the FP64 pipe,
+// not HBM, bounds this path):
+//  * One lane integrates one cell, as in the paper's thread-per-ODE design
+//    (Section 3), but each loop iteration of a lane performs exactly ONE
+//    evaluation of f. The method's control flow (RKCK stages, RKC stages,
+//    finite-difference Jacobian columns, accept/reject) is a per-lane state
+//    machine around that single call, so lanes of a warp in different phases
+//    or on cells with different stage counts still execute f together;
+//    divergence costs only the per-phase bookkeeping.
+//  * A uniform pre-pass (init_kernel) does, for every cell and in lockstep
+//    across the warp, the work every cell needs before its first step: the
+//    rate constants (T is fixed over the flow step), f(y0), and for RKC the
+//    Gershgorin spectral radius and the initial step of Section 2.3. The
+//    initial step predicts a cell's cost (steps ~ dt/h1), so cells are bucket
+//    sorted longest-first before the main kernel: longest-processing-time
+//    order keeps the persistent grid's tail short.
+//  * The main kernel is persistent: lanes pull cells from a warp-aggregated
+//    atomic queue in that order and a lane that finishes its cell takes the
+//    next one immediately.
+//  * Working arrays are element-major in the workspace (coalesced per warp).
 //  * f (Section 2.1): concentrations from the ideal gas law, Omega_j from the
-//    hoisted rate constants (T is fixed over the flow step), third-body and
-//    Lindemann falloff factors, and the stoichiometric sum as a gather over a
-//    species-major CSR of the net coefficients (no scattered read-modify-
-//    write). Template parameter R is the rate arithmetic type: double, or
-//    float for the mixed-precision path (state and control stay double).
+//    stored rate constants, third-body and Lindemann falloff factors, and the
+//    stoichiometric sum as a gather over a species-major CSR of net
+//    coefficients (no scattered read-modify-write). Template parameter R is
+//    the rate arithmetic type: double, or float for the mixed-precision path
+//    (state, stage accumulation, norm and control stay double).
 //  * No tensor cores: the stoichiometric contraction is sparse (about four
 //    nonzeros per reaction).
 #include <cuda_runtime.h>
@@ -36,7 +41,7 @@ namespace kin {
 template <typename T>
 struct Lane {
     T* p;
-    int64_t s;  // stride between elements (= lanes in the grid)
+    int64_t s;  // stride between elements
     __device__ __forceinline__ T& operator[](int i) const { return p[(int64_t)i * s]; }
 };
 
@@ -48,48 +53,60 @@ struct Tab<double> {
     __device__ static const double* eff(const MechDev& M) { return M.eff; }
     __device__ static const double* nu(const MechDev& M) { return M.csr_nu; }
     __device__ static double ex(double a) { return exp(a); }
+    static constexpr double sqrt_u = 1.4901161193847656e-08;  // sqrt(2^-52)
 };
 template <>
 struct Tab<float> {
     __device__ static const float* invW(const MechDev& M) { return M.invW32; }
     __device__ static const float* eff(const MechDev& M) { return M.eff32; }
     __device__ static const float* nu(const MechDev& M) { return M.csr_nu32; }
-    __device__ static float ex(double a) { return expf((float)a); }
+    // exp in FP32 after an exact split a = n ln2 + r formed in FP64, so the
+    // FP32 rounding of a large exponent (|a| ~ 40) does not cost 2e-6
+    // relative accuracy: k = 2^n expf(r) with |r| <= ln2/2.
+    __device__ static float ex(double a)
+    {
+        const double n = rint(a * 1.4426950408889634);
+        const float r = (float)fma(-n, 0.6931471805599453, a);
+        return ldexpf(expf(r), (int)n);
+    }
+    static constexpr double sqrt_u = 3.4526698300124393e-04;  // sqrt(2^-23)
 };
 
 // Rate constants of one cell (Eq. (E:rxn-const)); T is fixed for the call.
-// K_j = exp(ln A_j + beta_j ln T - (Ea_j/R)/T); for falloff reactions KR_j =
-// k_0/k_inf. The exponent is formed in double; the exp runs in R.
+// K_j = exp(ln A_j + beta_j ln T - (Ea_j/R)/T); for falloff reactions
+// KR_fo = k_0/k_inf. The exponent is formed in double; the exp runs in R.
 template <typename R>
 __device__ void rate_constants(const MechDev& M, double T, Lane<R> K, Lane<R> KR)
 {
     const double lnT = log(T), invT = 1.0 / T;
     for (int j = 0; j < M.nR; ++j) {
-        double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
+        const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
         K[j] = Tab<R>::ex(a);
-        if (M.rxn[j].type == KIN_RXN_FALLOFF) {
-            double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
-            KR[j] = Tab<R>::ex(a0 - a);
+        const int fo = M.rxn[j].fo;
+        if (fo >= 0) {
+            const double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
+            KR[fo] = Tab<R>::ex(a0 - a);
         }
     }
 }
 
-// f(x) -> out (Eqs. (E:mass), (E:spec-rate), (E:rxn-rate)). Ctot = p/(R T)
-// in mol/cm^3. C and OM are lane scratch of nS and nR entries.
+// f(x) -> out (Eqs. (E:mass), (E:spec-rate), (E:rxn-rate)). Ctot = p/(R T) in
+// mol/cm^3, invCtot its inverse. C and OM are lane scratch (nS and nR).
 template <typename R>
-__device__ void feval(const MechDev& M, double Ctot, Lane<R> K, Lane<R> KR, Lane<R> C,
-                      Lane<R> OM, Lane<double> x, Lane<double> out)
+__device__ void feval(const MechDev& M, double Ctot, double invCtot, Lane<R> K, Lane<R> KR,
+                      Lane<R> C, Lane<R> OM, Lane<double> x, Lane<double> out)
 {
     const int nS = M.nS, nR = M.nR;
     const R* __restrict__ invW = Tab<R>::invW(M);
     // mixture: S = sum Y/W = 1/Wbar, rho = Ctot Wbar, C_k = rho Y_k / W_k
     R S = R(0);
     for (int i = 0; i < nS; ++i) {
-        R m = (R)x[i] * invW[i];
+        const R m = (R)x[i] * invW[i];
         C[i] = m;
         S += m;
     }
-    const R rho = (R)Ctot / S;
+    const R invS = R(1) / S;
+    const R rho = (R)Ctot * invS;
     for (int i = 0; i < nS; ++i) C[i] = C[i] * rho;
     // rates of progress
     const R* __restrict__ eff = Tab<R>::eff(M);
@@ -105,26 +122,34 @@ __device__ void feval(const MechDev& M, double Ctot, Lane<R> K, Lane<R> KR, Lane
             if (r.type == KIN_RXN_THIRD_BODY) {
                 q *= Mc;
             } else {
-                R Pr = KR[j] * Mc;
+                const R Pr = KR[r.fo] * Mc;
                 q *= Pr / (R(1) + Pr);
             }
         }
         OM[j] = q;
     }
-    // omega_i = sum_j nu_ij Omega_j (gather), dY_i/dt = W_i omega_i / rho
+    // omega_i = sum_j nu_ij Omega_j (gather); dY_i/dt = W_i omega_i / rho
     const R* __restrict__ nu = Tab<R>::nu(M);
-    const double invrho = (double)S / Ctot;
+    const double invrho = (double)S * invCtot;
     for (int i = 0; i < nS; ++i) {
         R w = R(0);
         const int e1 = M.csr_ptr[i + 1];
         for (int e = M.csr_ptr[i]; e < e1; ++e) w += nu[e] * OM[M.csr_rxn[e]];
-        out[i] = (double)w * M.W[i] * invrho;
+        out[i] = (double)w * (M.W[i] * invrho);
     }
 }
 
-// ------------------------------------------------------------ work queue --
-// Warp-aggregated pop of the next global cell index for every active lane
-// that calls it.
+__device__ __forceinline__ int find_inst(const Launch& L, long long g)
+{
+    int lo = 0, hi = L.n_inst - 1;
+    while (lo < hi) {  // largest i with start[i] <= g
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.start[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Warp-aggregated pop of the next queue position for every active lane.
 __device__ __forceinline__ long long pop_cell(unsigned long long* q)
 {
     const unsigned mask = __activemask();
@@ -137,29 +162,177 @@ __device__ __forceinline__ long long pop_cell(unsigned long long* q)
     return (long long)(base + rank);
 }
 
-__device__ __forceinline__ int find_inst(const Launch& L, long long g)
-{
-    int lo = 0, hi = L.n_inst - 1;
-    while (lo < hi) {  // largest i with start[i] <= g
-        int mid = (lo + hi + 1) >> 1;
-        if (L.start[mid] <= g) lo = mid; else hi = mid - 1;
+// Vector slots of a lane's working set.
+enum Vec : int { V_Y = 0, V_F0, V_A, V_B, V_C, V_X, V_FX, V_RS };
+// RKCK reuses slots: F[1..5] = V_A, V_B, V_C, V_FX, V_RS; the stage point is V_X.
+
+template <typename R>
+struct Views {
+    const Launch& L;
+    const MechDev& M;
+    int64_t slot;
+    Lane<R> C, OM;
+    double* vbase;
+    __device__ Views(const Launch& l, int64_t sl) : L(l), M(l.M), slot(sl)
+    {
+        R* rb = reinterpret_cast<R*>(L.lane_r) + sl;
+        C = Lane<R>{rb, L.nslots};
+        OM = Lane<R>{rb + (int64_t)M.nS * L.nslots, L.nslots};
+        vbase = L.vec + sl;
     }
-    return lo;
+    __device__ __forceinline__ Lane<double> V(int v) const
+    {
+        return Lane<double>{vbase + (int64_t)v * M.nS * L.nslots, L.nslots};
+    }
+    __device__ __forceinline__ Lane<R> K(int64_t g) const
+    {
+        return Lane<R>{reinterpret_cast<R*>(L.cell_k) + g, L.total};
+    }
+    __device__ __forceinline__ Lane<R> KR(int64_t g) const
+    {
+        return Lane<R>{reinterpret_cast<R*>(L.cell_k) + (int64_t)M.nR * L.total + g, L.total};
+    }
+    __device__ __forceinline__ Lane<double> F0cell(int64_t g) const
+    {
+        return Lane<double>{L.cell_f0 + g, L.total};
+    }
+};
+
+// Weighted RMS norm, Eq. (E:rmsE), of d with T_i = atol + rtol max(|a|,|b|).
+__device__ __forceinline__ double rms(int n, double rtol, double atol, Lane<double> d,
+                                      Lane<double> a, Lane<double> b)
+{
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double sc = atol + rtol * fmax(fabs(a[i]), fabs(b[i]));
+        const double r = d[i] / sc;
+        acc += r * r;
+    }
+    return sqrt(acc / n);
+}
+
+// ------------------------------------------------------------- pre-pass --
+// For every cell g (grid-stride, uniform across lanes): rate constants, f(y0),
+// and for RKC the Gershgorin bound on the FD Jacobian (Section 2.3) and the
+// initial step h1 = 0.1 h0 / ||Delta_0||^(1/2), h0 = 1/sigma.
+template <int METHOD, typename R>
+__global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launch L)
+{
+    const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= L.nslots) return;
+    Views<R> W(L, slot);
+    const MechDev& M = L.M;
+    const int nS = M.nS;
+    for (int64_t g = slot; g < L.total; g += L.nslots) {
+        const int ii = find_inst(L, g);
+        const InstDev& I = L.inst[ii];
+        const int64_t c = g - L.start[ii];
+        const double T = I.T[c], p = I.p[c];
+        const double Ctot = p * 1e-6 / (R_GAS * T), invCtot = 1.0 / Ctot;
+        Lane<R> K = W.K(g), KR = W.KR(g);
+        rate_constants<R>(M, T, K, KR);
+        Lane<double> Y = W.V(V_Y), F0 = W.F0cell(g), X = W.V(V_X), FX = W.V(V_FX), RS = W.V(V_RS);
+        bool ok = true;
+        for (int i = 0; i < nS; ++i) {
+            const double y = I.Y[(int64_t)i * I.ldY + c];
+            Y[i] = y;
+            X[i] = y;
+            RS[i] = 0.0;
+        }
+        feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, Y, F0);
+        for (int i = 0; i < nS; ++i) ok &= isfinite(F0[i]);
+        uint8_t st = ok ? 0 : KIN_CELL_NONFINITE;
+        double sigma = 0.0, h = I.dt;
+        int nfe = 1;
+        if (METHOD == KIN_RKC && ok) {
+            for (int k = 0; k < nS; ++k) {  // Gershgorin columns
+                const double eps = Tab<R>::sqrt_u * fmax(fabs(Y[k]), I.atol);
+                X[k] = Y[k] + eps;
+                feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, X, FX);
+                const double ie = 1.0 / eps;
+                for (int i = 0; i < nS; ++i) RS[i] += fabs((FX[i] - F0[i]) * ie);
+                X[k] = Y[k];
+            }
+            for (int i = 0; i < nS; ++i) sigma = fmax(sigma, RS[i]);
+            nfe += nS;
+            if (!isfinite(sigma)) {
+                st = KIN_CELL_NONFINITE;
+            } else {
+                double h0 = sigma > 0.0 ? 1.0 / sigma : I.dt;
+                if (h0 > I.dt) h0 = I.dt;
+                for (int i = 0; i < nS; ++i) X[i] = Y[i] + h0 * F0[i];
+                feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, X, FX);
+                nfe++;
+                for (int i = 0; i < nS; ++i) X[i] = h0 * (FX[i] - F0[i]);  // Delta_0
+                const double e0 = rms(nS, I.rtol, I.atol, X, Y, Y);
+                if (!isfinite(e0)) h = 0.1 * h0;
+                else h = e0 > 0.0 ? 0.1 * h0 / sqrt(e0) : I.dt;
+                if (h > I.dt) h = I.dt;
+                if (h < 1e-20 * I.dt) st = KIN_CELL_HMIN;
+            }
+        }
+        L.cell_sig[g] = sigma;
+        L.cell_h[g] = h;
+        L.cell_nfe[g] = nfe;
+        L.cell_st[g] = st;
+    }
+}
+
+// ----------------------------------------------- longest-first ordering --
+// Predicted cost of a cell: steps ~ dt/h1 (RKC). Bucket b >= 1 grows with
+// log2(1 + dt/h1) in quarter octaves; cells already finished go to bucket 0.
+__device__ __forceinline__ int cost_bucket(const Launch& L, int64_t g)
+{
+    if (L.cell_st[g] != 0) return 0;
+    const int ii = find_inst(L, g);
+    const double r = L.inst[ii].dt / L.cell_h[g];
+    const int b = 1 + (int)(4.0f * log2f(1.0f + (float)r));
+    return b < 1 ? 1 : (b > NBUCKET - 1 ? NBUCKET - 1 : b);
+}
+
+__global__ void bucket_count_kernel(const __grid_constant__ Launch L)
+{
+    __shared__ unsigned h[NBUCKET];
+    for (int i = threadIdx.x; i < NBUCKET; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L.total;
+         g += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[cost_bucket(L, g)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < NBUCKET; i += blockDim.x)
+        if (h[i]) atomicAdd(&L.hist[i], h[i]);
+}
+
+// Exclusive scan in descending bucket order: the costliest bucket first.
+__global__ void bucket_scan_kernel(unsigned* hist)
+{
+    if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (int b = NBUCKET - 1; b >= 0; --b) {
+            const unsigned n = hist[b];
+            hist[b] = run;
+            run += n;
+        }
+    }
+}
+
+__global__ void bucket_scatter_kernel(const __grid_constant__ Launch L)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < L.total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned pos = atomicAdd(&L.hist[cost_bucket(L, g)], 1u);
+        L.order[pos] = (int32_t)g;
+    }
 }
 
 // ------------------------------------------------------------ integrator --
 enum Phase : int {
-    PH_F0 = 0,   // f at the current accepted state -> F0
-    PH_SIG,      // f at Y + eps_k e_k (Gershgorin column k) -> FX
-    PH_PROBE,    // RKC initial step probe f(Y + h0 F0) -> FX
-    PH_STAGE,    // RKC: f(w_{j-1}) -> FJ, then w_j
+    PH_F0 = 0,   // RKCK: f at the current accepted state -> F0
+    PH_SIG,      // RKC: f at Y + eps_k e_k (Gershgorin column k) -> FX
+    PH_STAGE,    // RKC: f(w_{j-1}) -> FX, then w_j
     PH_FINAL,    // RKC: f(w_s) -> FX, error estimate and control
-    PH_K,        // RKCK: f at stage point -> F[st]
+    PH_K,        // RKCK: f at a stage point -> F[st]
 };
-
-// Vector slots of the lane's working set.
-enum Vec : int { V_Y = 0, V_F0, V_A, V_B, V_C, V_X, V_FX, V_RS };
-// RKCK reuses slots: F[1..5] = V_A, V_B, V_C, V_FX, V_RS; the stage point is V_X.
 
 __constant__ double CK_B[6][5] = {
     {0, 0, 0, 0, 0},
@@ -177,83 +350,85 @@ __constant__ double CK_E[6] = {37.0 / 378.0 - 2825.0 / 27648.0, 0.0, 250.0 / 621
 __device__ __forceinline__ int ck_slot(int st)
 {
     // F[0] lives in V_F0; F[1..5] in the slots listed above
-    const int map[6] = {V_F0, V_A, V_B, V_C, V_FX, V_RS};
-    return map[st];
+    return st == 0 ? V_F0 : (st <= 3 ? V_A + st - 1 : (st == 4 ? V_FX : V_RS));
 }
 
 struct LaneState {
-    long long cell;  // local index within the instance
+    long long g;     // global cell index
+    long long cell;  // index within the instance
     int inst;
     int phase, st, j, s, col;
     int attempts, nacc, nrej, nsig, nfe;
     int since_sigma;
-    bool initial, last, last_rejected, have_prev, sigma_here;
+    bool last, last_rejected, have_prev, sigma_here;
     int iw1, iw2;  // RKC: slots of w_{j-1}, w_{j-2}
-    double t, dt, h, hh, h0, hprev, errprev, sigma, eps, rtol, atol, Ctot;
+    double t, dt, h, hh, hprev, cprev, sigma, eps, rtol, atol, Ctot, invCtot;
     int in_v, out_v;  // vectors read and written by the next f evaluation
 };
 
 template <int METHOD, typename R>
 struct Integrator {
+    Views<R> W;
     const Launch& L;
     const MechDev& M;
-    int64_t slot;
-    Lane<R> K, KR, C, OM;
-    double* vbase;
+    Lane<R> K, KR;
 
-    __device__ Integrator(const Launch& l, int64_t sl) : L(l), M(l.M), slot(sl)
-    {
-        R* rb = reinterpret_cast<R*>(L.rarr) + sl;
-        const int64_t s = L.nslots;
-        K = Lane<R>{rb, s};
-        KR = Lane<R>{rb + (int64_t)M.nR * s, s};
-        C = Lane<R>{rb + (int64_t)2 * M.nR * s, s};
-        OM = Lane<R>{rb + (int64_t)(2 * M.nR + M.nS) * s, s};
-        vbase = L.vec + sl;
-    }
-    __device__ __forceinline__ Lane<double> V(int v) const
-    {
-        return Lane<double>{vbase + (int64_t)v * M.nS * L.nslots, L.nslots};
-    }
+    __device__ Integrator(const Launch& l, int64_t sl) : W(l, sl), L(l), M(l.M) {}
+    __device__ __forceinline__ Lane<double> V(int v) const { return W.V(v); }
 
     // ---------------------------------------------------------- cell I/O --
+    // Take the next cell; returns false when the queue is exhausted. A cell
+    // whose fate the pre-pass already decided is finished here directly.
     __device__ bool load_next(LaneState& S)
     {
-        const long long g = pop_cell(L.queue);
-        if (g >= L.total) return false;
-        const int i = find_inst(L, g);
-        const InstDev& I = L.inst[i];
-        S.inst = i;
-        S.cell = g - L.start[i];
-        const double T = I.T[S.cell], p = I.p[S.cell];
-        Lane<double> Y = V(V_Y);
-        for (int k = 0; k < M.nS; ++k) Y[k] = I.Y[(int64_t)k * I.ldY + S.cell];
-        rate_constants<R>(M, T, K, KR);
-        S.Ctot = p * 1e-6 / (R_GAS * T);
-        S.dt = I.dt;
-        S.rtol = I.rtol;
-        S.atol = I.atol;
-        S.t = 0.0;
-        S.h = I.dt;
-        S.attempts = S.nacc = S.nrej = S.nsig = S.nfe = 0;
-        S.since_sigma = 0;
-        S.initial = true;
-        S.last = false;
-        S.last_rejected = false;
-        S.have_prev = false;
-        S.sigma_here = false;
-        S.hprev = S.errprev = S.sigma = 0.0;
-        S.phase = PH_F0;
-        S.in_v = V_Y;
-        S.out_v = V_F0;
-        return true;
+        for (;;) {
+            const long long q = pop_cell(L.queue);
+            if (q >= L.total) return false;
+            const long long g = (METHOD == KIN_RKC) ? (long long)L.order[q] : q;
+            const int i = find_inst(L, g);
+            const InstDev& I = L.inst[i];
+            S.g = g;
+            S.inst = i;
+            S.cell = g - L.start[i];
+            S.attempts = S.nacc = S.nrej = 0;
+            S.nsig = METHOD == KIN_RKC ? 1 : 0;
+            S.nfe = L.cell_nfe[g];
+            const uint8_t pre = L.cell_st[g];
+            if (pre != 0) {  // Y stays as given
+                finish_stats(S, pre);
+                continue;
+            }
+            const double T = I.T[S.cell], p = I.p[S.cell];
+            S.Ctot = p * 1e-6 / (R_GAS * T);
+            S.invCtot = 1.0 / S.Ctot;
+            K = W.K(g);
+            KR = W.KR(g);
+            Lane<double> Y = V(V_Y), F0 = V(V_F0), F0c = W.F0cell(g);
+            for (int k = 0; k < M.nS; ++k) {
+                Y[k] = I.Y[(int64_t)k * I.ldY + S.cell];
+                F0[k] = F0c[k];
+            }
+            S.dt = I.dt;
+            S.rtol = I.rtol;
+            S.atol = I.atol;
+            S.t = 0.0;
+            S.h = L.cell_h[g];
+            S.sigma = L.cell_sig[g];
+            S.since_sigma = 0;
+            S.last = false;
+            S.last_rejected = false;
+            S.have_prev = false;
+            S.sigma_here = true;
+            S.hprev = S.cprev = 0.0;
+            const int code = METHOD == KIN_RKC ? rkc_begin_step(S) : rkck_begin_attempt(S);
+            if (code < 0) return true;
+            store(S, code);
+        }
     }
 
-    __device__ void store(const LaneState& S, int code)
+    __device__ void finish_stats(const LaneState& S, int code)
     {
         const InstDev& I = L.inst[S.inst];
-        Lane<double> Y = V(V_Y);
-        for (int k = 0; k < M.nS; ++k) I.Y[(int64_t)k * I.ldY + S.cell] = Y[k];
         if (I.status) I.status[S.cell] = (uint8_t)code;
         if (I.stats) {
             int32_t* st = I.stats + 4 * S.cell;
@@ -264,28 +439,15 @@ struct Integrator {
         }
     }
 
-    // ----------------------------------------------------- shared pieces --
-    __device__ bool finite_vec(int v) const
+    __device__ void store(const LaneState& S, int code)
     {
-        Lane<double> a = V(v);
-        bool ok = true;
-        for (int i = 0; i < M.nS; ++i) ok &= isfinite(a[i]);
-        return ok;
+        const InstDev& I = L.inst[S.inst];
+        Lane<double> Y = V(V_Y);
+        for (int k = 0; k < M.nS; ++k) I.Y[(int64_t)k * I.ldY + S.cell] = Y[k];
+        finish_stats(S, code);
     }
 
-    // Weighted RMS norm, Eq. (E:rmsE), of d with T_i = atol + rtol max(|a|,|b|).
-    __device__ double rms(const LaneState& S, Lane<double> d, Lane<double> a, Lane<double> b) const
-    {
-        double acc = 0.0;
-        for (int i = 0; i < M.nS; ++i) {
-            double sc = S.atol + S.rtol * fmax(fabs(a[i]), fabs(b[i]));
-            double r = d[i] / sc;
-            acc += r * r;
-        }
-        return sqrt(acc / M.nS);
-    }
-
-    // Start a Gershgorin estimate: X = Y + eps_0 e_0, RS = 0.
+    // Start a Gershgorin estimate at Y: X = Y + eps_0 e_0, RS = 0.
     __device__ void sigma_begin(LaneState& S)
     {
         Lane<double> Y = V(V_Y), X = V(V_X), RS = V(V_RS);
@@ -294,27 +456,22 @@ struct Integrator {
             RS[i] = 0.0;
         }
         S.col = 0;
-        S.eps = sqrt_u() * fmax(fabs(Y[0]), S.atol);
+        S.eps = Tab<R>::sqrt_u * fmax(fabs(Y[0]), S.atol);
         X[0] = Y[0] + S.eps;
         S.phase = PH_SIG;
         S.in_v = V_X;
         S.out_v = V_FX;
-    }
-    __device__ static double sqrt_u()
-    {
-        // sqrt of the unit roundoff of the rate arithmetic type
-        return sizeof(R) == 8 ? 1.4901161193847656e-08 : 3.4526698300124393e-04;
     }
 
     // Post-processing of one Gershgorin column. Returns true when sigma is done.
     __device__ bool sigma_column(LaneState& S)
     {
         Lane<double> Y = V(V_Y), X = V(V_X), RS = V(V_RS), FX = V(V_FX), F0 = V(V_F0);
-        const double e = S.eps;
-        for (int i = 0; i < M.nS; ++i) RS[i] += fabs((FX[i] - F0[i]) / e);
+        const double ie = 1.0 / S.eps;
+        for (int i = 0; i < M.nS; ++i) RS[i] += fabs((FX[i] - F0[i]) * ie);
         X[S.col] = Y[S.col];
         if (++S.col < M.nS) {
-            S.eps = sqrt_u() * fmax(fabs(Y[S.col]), S.atol);
+            S.eps = Tab<R>::sqrt_u * fmax(fabs(Y[S.col]), S.atol);
             X[S.col] = Y[S.col] + S.eps;
             return false;
         }
@@ -333,9 +490,8 @@ struct Integrator {
         return M.rkc + ((int64_t)s * RKC_TAB_S + j) * RKC_TAB_W;
     }
 
-    // Choose the next attempt (or a spectral-radius refresh) after an
-    // accepted/rejected step or the initial step. Returns a finish code >= 0
-    // if the cell must stop, else -1.
+    // Choose the next attempt (or a spectral-radius refresh). Returns a
+    // finish code >= 0 if the cell must stop, else -1.
     __device__ int rkc_begin_step(LaneState& S)
     {
         if (S.attempts >= L.max_steps) return KIN_CELL_MAXSTEPS;
@@ -349,7 +505,7 @@ struct Integrator {
             hh = S.dt - S.t;
             S.last = true;
         }
-        double sr = floor(1.0 + sqrt(1.0 + 1.54 * hh * S.sigma));
+        const double sr = floor(1.0 + sqrt(1.0 + 1.54 * hh * S.sigma));
         int s;
         if (sr < 2.0) {
             s = 2;
@@ -377,41 +533,7 @@ struct Integrator {
 
     __device__ int rkc_post(LaneState& S)
     {
-        switch (S.phase) {
-        case PH_F0: {
-            if (!finite_vec(V_F0)) return KIN_CELL_NONFINITE;
-            sigma_begin(S);
-            return -1;
-        }
-        case PH_SIG: {
-            if (!sigma_column(S)) return -1;
-            if (!isfinite(S.sigma)) return KIN_CELL_NONFINITE;
-            if (!S.initial) return rkc_begin_step(S);
-            // initial step: h0 = 1/sigma, probe f(y + h0 f0)
-            double h0 = S.sigma > 0.0 ? 1.0 / S.sigma : S.dt;
-            if (h0 > S.dt) h0 = S.dt;
-            S.h0 = h0;
-            Lane<double> Y = V(V_Y), F0 = V(V_F0), X = V(V_X);
-            for (int i = 0; i < M.nS; ++i) X[i] = Y[i] + h0 * F0[i];
-            S.phase = PH_PROBE;
-            S.in_v = V_X;
-            S.out_v = V_FX;
-            return -1;
-        }
-        case PH_PROBE: {
-            Lane<double> Y = V(V_Y), F0 = V(V_F0), FX = V(V_FX), D = V(V_X);
-            for (int i = 0; i < M.nS; ++i) D[i] = S.h0 * (FX[i] - F0[i]);
-            const double e0 = rms(S, D, Y, Y);
-            double h;
-            if (!isfinite(e0)) h = 0.1 * S.h0;
-            else h = e0 > 0.0 ? 0.1 * S.h0 / sqrt(e0) : S.dt;
-            if (h > S.dt) h = S.dt;
-            if (h < 1e-20 * S.dt) return KIN_CELL_HMIN;
-            S.h = h;
-            S.initial = false;
-            return rkc_begin_step(S);
-        }
-        case PH_STAGE: {
+        if (S.phase == PH_STAGE) {
             // FX = f(w_{j-1}); w_j = (1-mu-nu) y + mu w_{j-1} + nu w_{j-2}
             //                       + mu~ h f_{j-1} + gamma~ h f_0
             const double* c = coef(S.s, S.j);
@@ -429,56 +551,59 @@ struct Integrator {
             else S.j++;
             return -1;
         }
-        case PH_FINAL: {
-            // error estimate (Section 2.3) and step control
-            Lane<double> Y = V(V_Y), F0 = V(V_F0), WS = V(S.iw1), FX = V(V_FX);
-            double acc = 0.0;
-            const double hh = S.hh;
-            for (int i = 0; i < M.nS; ++i) {
-                double d = 0.8 * (Y[i] - WS[i]) + 0.4 * hh * (F0[i] + FX[i]);
-                double sc = S.atol + S.rtol * fmax(fabs(Y[i]), fabs(WS[i]));
-                double r = d / sc;
-                acc += r * r;
-            }
-            const double err = sqrt(acc / M.nS);
-            S.attempts++;
-            if (err <= 1.0) {
-                S.nacc++;
-                double fac;
-                if (err == 0.0) fac = 10.0;
-                else if (S.have_prev && !S.last_rejected && S.errprev > 0.0)
-                    fac = 0.8 * (hh / S.hprev) * cbrt(S.errprev) / pow(err, 2.0 / 3.0);
-                else fac = 0.8 / cbrt(err);
-                fac = fmin(10.0, fmax(0.1, fac));
-                for (int i = 0; i < M.nS; ++i) {
-                    Y[i] = WS[i];
-                    F0[i] = FX[i];
-                }
-                if (S.last) {
-                    S.t = S.dt;
-                    return KIN_CELL_OK;
-                }
-                S.t += hh;  // err <= 1 implies f(w_s) is finite
-                S.have_prev = true;
-                S.hprev = hh;
-                S.errprev = err;
-                S.last_rejected = false;
-                S.sigma_here = false;
-                S.since_sigma++;
-                S.h = fac * hh;
-            } else {
-                S.nrej++;
-                double fac = isfinite(err) ? 0.8 / cbrt(err) : 0.1;
-                if (fac < 0.1) fac = 0.1;
-                S.last_rejected = true;
-                S.h = fac * hh;
-                if (S.h < 1e-20 * S.dt) return KIN_CELL_HMIN;
-            }
+        if (S.phase == PH_SIG) {
+            if (!sigma_column(S)) return -1;
+            if (!isfinite(S.sigma)) return KIN_CELL_NONFINITE;
             return rkc_begin_step(S);
         }
-        default:
-            return KIN_CELL_NONFINITE;
+        // PH_FINAL: error estimate (Section 2.3) and step control
+        Lane<double> Y = V(V_Y), F0 = V(V_F0), WS = V(S.iw1), FX = V(V_FX);
+        double acc = 0.0;
+        const double hh = S.hh;
+        for (int i = 0; i < M.nS; ++i) {
+            const double d = 0.8 * (Y[i] - WS[i]) + 0.4 * hh * (F0[i] + FX[i]);
+            const double sc = S.atol + S.rtol * fmax(fabs(Y[i]), fabs(WS[i]));
+            const double r = d / sc;
+            acc += r * r;
         }
+        const double err = sqrt(acc / M.nS);
+        S.attempts++;
+        if (err <= 1.0) {
+            S.nacc++;
+            // err^(1/3) once; err^(2/3) = (err^(1/3))^2; the previous step's
+            // err^(1/3) is kept for the predictive factor.
+            const double c3 = cbrt(err);
+            double fac;
+            if (err == 0.0) fac = 10.0;
+            else if (S.have_prev && !S.last_rejected && S.cprev > 0.0)
+                fac = 0.8 * (hh / S.hprev) * S.cprev / (c3 * c3);
+            else fac = 0.8 / c3;
+            fac = fmin(10.0, fmax(0.1, fac));
+            for (int i = 0; i < M.nS; ++i) {
+                Y[i] = WS[i];
+                F0[i] = FX[i];
+            }
+            if (S.last) {
+                S.t = S.dt;
+                return KIN_CELL_OK;
+            }
+            S.t += hh;  // err <= 1 implies f(w_s) is finite
+            S.have_prev = true;
+            S.hprev = hh;
+            S.cprev = c3;
+            S.last_rejected = false;
+            S.sigma_here = false;
+            S.since_sigma++;
+            S.h = fac * hh;
+        } else {
+            S.nrej++;
+            double fac = isfinite(err) ? 0.8 / cbrt(err) : 0.1;
+            if (fac < 0.1) fac = 0.1;
+            S.last_rejected = true;
+            S.h = fac * hh;
+            if (S.h < 1e-20 * S.dt) return KIN_CELL_HMIN;
+        }
+        return rkc_begin_step(S);
     }
 
     // ------------------------------------------------------------ RKCK ---
@@ -517,7 +642,6 @@ struct Integrator {
             if (!finite_vec(V_F0)) return KIN_CELL_NONFINITE;
             return rkck_begin_attempt(S);
         }
-        // PH_K
         if (S.st < 5) {
             rkck_stage_point(S, S.st + 1);
             return -1;
@@ -547,7 +671,7 @@ struct Integrator {
                 return KIN_CELL_OK;
             }
             S.t += hh;
-            double hn = errmax == 0.0 ? 5.0 * hh : 0.9 * hh * pow(errmax, -0.2);
+            const double hn = errmax == 0.0 ? 5.0 * hh : 0.9 * hh * pow(errmax, -0.2);
             S.h = fmin(hn, 5.0 * hh);
             S.phase = PH_F0;
             S.in_v = V_Y;
@@ -555,10 +679,18 @@ struct Integrator {
             return -1;
         }
         S.nrej++;
-        double hn = isfinite(errmax) ? 0.9 * hh * pow(errmax, -0.25) : 0.1 * hh;
+        const double hn = isfinite(errmax) ? 0.9 * hh * pow(errmax, -0.25) : 0.1 * hh;
         S.h = fmax(hn, 0.1 * hh);
         if (S.h < 1e-20 * S.dt) return KIN_CELL_HMIN;
         return rkck_begin_attempt(S);
+    }
+
+    __device__ bool finite_vec(int v) const
+    {
+        Lane<double> a = V(v);
+        bool ok = true;
+        for (int i = 0; i < M.nS; ++i) ok &= isfinite(a[i]);
+        return ok;
     }
 
     // --------------------------------------------------------- main loop --
@@ -567,7 +699,7 @@ struct Integrator {
         LaneState S;
         if (!load_next(S)) return;
         for (;;) {
-            feval<R>(M, S.Ctot, K, KR, C, OM, V(S.in_v), V(S.out_v));
+            feval<R>(M, S.Ctot, S.invCtot, K, KR, W.C, W.OM, V(S.in_v), V(S.out_v));
             S.nfe++;
             const int code = METHOD == KIN_RKC ? rkc_post(S) : rkck_post(S);
             if (code >= 0) {
@@ -591,19 +723,19 @@ __global__ void __launch_bounds__(128) integrate_kernel(const __grid_constant__ 
 template <typename R>
 __global__ void rates_kernel(MechDev M, int64_t cells, const double* __restrict__ T,
                              const double* __restrict__ p, const double* Y, int64_t ldY,
-                             double* dYdt, void* rarr, int64_t nslots)
+                             double* dYdt, void* lane_r, void* cell_k, int64_t nslots)
 {
     const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= nslots) return;
-    R* rb = reinterpret_cast<R*>(rarr) + slot;
-    Lane<R> K{rb, nslots}, KR{rb + (int64_t)M.nR * nslots, nslots},
-        C{rb + (int64_t)2 * M.nR * nslots, nslots},
-        OM{rb + (int64_t)(2 * M.nR + M.nS) * nslots, nslots};
+    R* rb = reinterpret_cast<R*>(lane_r) + slot;
+    Lane<R> C{rb, nslots}, OM{rb + (int64_t)M.nS * nslots, nslots};
     for (int64_t c = slot; c < cells; c += nslots) {
+        Lane<R> K{reinterpret_cast<R*>(cell_k) + c, cells};
+        Lane<R> KR{reinterpret_cast<R*>(cell_k) + (int64_t)M.nR * cells + c, cells};
         rate_constants<R>(M, T[c], K, KR);
         const double Ctot = p[c] * 1e-6 / (R_GAS * T[c]);
-        feval<R>(M, Ctot, K, KR, C, OM, Lane<double>{const_cast<double*>(Y) + c, ldY},
-                 Lane<double>{dYdt + c, ldY});
+        feval<R>(M, Ctot, 1.0 / Ctot, K, KR, C, OM,
+                 Lane<double>{const_cast<double*>(Y) + c, ldY}, Lane<double>{dYdt + c, ldY});
     }
 }
 
@@ -618,27 +750,25 @@ __global__ void rkc_table_kernel(double* tab)
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < 2 || s > SMAX) return;
     const double w0 = 1.0 + (2.0 / 13.0) / ((double)s * s);
-    // first pass: T', T'' at j = s for w1
     double t0 = 1.0, t1 = w0, d0 = 0.0, d1 = 1.0, e0 = 0.0, e1 = 0.0;
     for (int j = 2; j <= s; ++j) {
-        double t2 = 2.0 * w0 * t1 - t0;
-        double d2 = 2.0 * t1 + 2.0 * w0 * d1 - d0;
-        double e2 = 4.0 * d1 + 2.0 * w0 * e1 - e0;
+        const double t2 = 2.0 * w0 * t1 - t0;
+        const double d2 = 2.0 * t1 + 2.0 * w0 * d1 - d0;
+        const double e2 = 4.0 * d1 + 2.0 * w0 * e1 - e0;
         t0 = t1; t1 = t2; d0 = d1; d1 = d2; e0 = e1; e1 = e2;
     }
     const double w1 = d1 / e1;
-    // second pass: coefficients
     t0 = 1.0; t1 = w0; d0 = 0.0; d1 = 1.0; e0 = 0.0; e1 = 0.0;
     const double b2 = 4.0 / (16.0 * w0 * w0);  // T_2''/T_2'^2 = 4 / (4 w0)^2
-    double bjm2 = b2, bjm1 = b2;  // b_0, b_1
-    double ajm1 = 1.0 - b2 * w0;  // a_1 = 1 - b_1 T_1(w0)
+    double bjm2 = b2, bjm1 = b2;                // b_0, b_1
+    double ajm1 = 1.0 - b2 * w0;                // a_1 = 1 - b_1 T_1(w0)
     double* row1 = tab + ((int64_t)s * RKC_TAB_S + 1) * RKC_TAB_W;
     row1[0] = row1[1] = row1[3] = row1[4] = 0.0;
     row1[2] = b2 * w1;
     for (int j = 2; j <= s; ++j) {
-        double t2 = 2.0 * w0 * t1 - t0;
-        double d2 = 2.0 * t1 + 2.0 * w0 * d1 - d0;
-        double e2 = 4.0 * d1 + 2.0 * w0 * e1 - e0;
+        const double t2 = 2.0 * w0 * t1 - t0;
+        const double d2 = 2.0 * t1 + 2.0 * w0 * d1 - d0;
+        const double e2 = 4.0 * d1 + 2.0 * w0 * e1 - e0;
         const double bj = e2 / (d2 * d2);
         const double mu = 2.0 * bj * w0 / bjm1;
         const double nu = -bj / bjm2;
@@ -658,28 +788,49 @@ __global__ void rkc_table_kernel(double* tab)
 }
 
 // -------------------------------------------------------- host launchers --
-int64_t scratch_elems_vec(int nS) { return (int64_t)NVEC * nS; }
+static int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
 
-int64_t scratch_bytes_rate(int nS, int nR, int precision)
+WsLayout ws_layout(const MechDev& M, int precision, int64_t nslots, int64_t cells)
 {
-    const int64_t n = (int64_t)3 * nR + nS;
-    return n * (precision == KIN_MIXED ? 4 : 8);
+    const int64_t rb = precision == KIN_MIXED ? 4 : 8;
+    WsLayout w;
+    int64_t off = 0;
+    w.header = off;  off += 4096;
+    w.vec = off;     off += al256((int64_t)NVEC * M.nS * 8 * nslots);
+    w.lane_r = off;  off += al256((int64_t)(M.nS + M.nR) * rb * nslots);
+    w.cell_k = off;  off += al256((int64_t)(M.nR + M.nFO) * rb * cells);
+    w.f0 = off;      off += al256((int64_t)M.nS * 8 * cells);
+    w.sig = off;     off += al256(8 * cells);
+    w.h = off;       off += al256(8 * cells);
+    w.nfe = off;     off += al256(4 * cells);
+    w.st = off;      off += al256(cells);
+    w.order = off;   off += al256(4 * cells);
+    w.total = off;
+    return w;
 }
 
 template <int METHOD, typename R>
-static cudaError_t launch_one(const Launch& L, int blocks, int threads, cudaStream_t st)
+static cudaError_t launch_all(Launch& L, int blocks, int threads, cudaStream_t st)
 {
+    init_kernel<METHOD, R><<<blocks, threads, 0, st>>>(L);
+    if (METHOD == KIN_RKC) {
+        const int64_t nb = (L.total + 255) / 256;
+        const int sb = (int)(nb < 1024 ? nb : 1024);
+        bucket_count_kernel<<<sb, 256, 0, st>>>(L);
+        bucket_scan_kernel<<<1, 32, 0, st>>>(L.hist);
+        bucket_scatter_kernel<<<sb, 256, 0, st>>>(L);
+    }
     integrate_kernel<METHOD, R><<<blocks, threads, 0, st>>>(L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_integrate(const Launch& L, int blocks, int threads, cudaStream_t st)
+cudaError_t launch_integrate(Launch& L, int blocks, int threads, cudaStream_t st)
 {
     if (L.method == KIN_RKCK)
-        return L.precision == KIN_MIXED ? launch_one<KIN_RKCK, float>(L, blocks, threads, st)
-                                        : launch_one<KIN_RKCK, double>(L, blocks, threads, st);
-    return L.precision == KIN_MIXED ? launch_one<KIN_RKC, float>(L, blocks, threads, st)
-                                    : launch_one<KIN_RKC, double>(L, blocks, threads, st);
+        return L.precision == KIN_MIXED ? launch_all<KIN_RKCK, float>(L, blocks, threads, st)
+                                        : launch_all<KIN_RKCK, double>(L, blocks, threads, st);
+    return L.precision == KIN_MIXED ? launch_all<KIN_RKC, float>(L, blocks, threads, st)
+                                    : launch_all<KIN_RKC, double>(L, blocks, threads, st);
 }
 
 cudaError_t integrate_occupancy(int method, int precision, int threads, int* bps)
@@ -694,13 +845,17 @@ cudaError_t integrate_occupancy(int method, int precision, int threads, int* bps
 }
 
 cudaError_t launch_rates(const MechDev& M, int64_t cells, const double* T, const double* p,
-                         const double* Y, int64_t ldY, double* dYdt, int precision, void* rarr,
+                         const double* Y, int64_t ldY, double* dYdt, int precision, void* ws,
                          int64_t nslots, int blocks, int threads, cudaStream_t st)
 {
+    const WsLayout w = ws_layout(M, precision, nslots, cells);
+    char* b = (char*)ws;
     if (precision == KIN_MIXED)
-        rates_kernel<float><<<blocks, threads, 0, st>>>(M, cells, T, p, Y, ldY, dYdt, rarr, nslots);
+        rates_kernel<float><<<blocks, threads, 0, st>>>(M, cells, T, p, Y, ldY, dYdt, b + w.lane_r,
+                                                        b + w.cell_k, nslots);
     else
-        rates_kernel<double><<<blocks, threads, 0, st>>>(M, cells, T, p, Y, ldY, dYdt, rarr, nslots);
+        rates_kernel<double><<<blocks, threads, 0, st>>>(M, cells, T, p, Y, ldY, dYdt, b + w.lane_r,
+                                                         b + w.cell_k, nslots);
     return cudaGetLastError();
 }
 

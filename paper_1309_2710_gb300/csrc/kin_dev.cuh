@@ -1,10 +1,9 @@
 // kin_dev.cuh -- device-side data layout shared by the kernels and the host ABI.
 //
-// Mechanism tables live in one device allocation owned by kin_mech. Per-lane
-// working arrays live in the caller's workspace, laid out element-major
-// ([element][lane]) so that the 32 lanes of a warp touching element e of
-// their own cells hit 32 consecutive words (coalesced), whatever the
-// mechanism size.
+// Mechanism tables live in one device allocation owned by kin_mech. Working
+// arrays live in the caller's workspace, laid out element-major
+// ([element][lane] or [element][cell]) so that the 32 lanes of a warp touching
+// element e of their own cells hit consecutive words.
 #pragma once
 #include <cstdint>
 
@@ -16,16 +15,19 @@ constexpr double R_GAS = 8.314462618;  // J/(mol K)
 constexpr int SMAX = KIN_MAX_STAGES;
 constexpr int RKC_TAB_S = SMAX + 1;    // rows s = 0..250 (2..250 used)
 constexpr int RKC_TAB_W = 5;           // mu, nu, mu~, gamma~, 1 - mu - nu
+constexpr int NBUCKET = 64;            // cost buckets of the longest-first order
 
-// Per-reaction descriptor: reactant slots, type, efficiency row.
+// Per-reaction descriptor (16 bytes).
 struct Rxn {
-    int r0, r1;  // reactant species or -1
-    int type;    // KIN_RXN_*
-    int row;     // efficiency row or -1
+    int16_t r0, r1;  // reactant species or -1
+    int16_t type;    // KIN_RXN_*
+    int16_t pad;
+    int32_t row;     // efficiency row or -1
+    int32_t fo;      // falloff ordinal or -1
 };
 
 struct MechDev {
-    int nS, nR, nM, nnz;
+    int nS, nR, nM, nFO, nnz;
     const double* W;       // [nS]
     const double* invW;    // [nS]
     const float* invW32;   // [nS]
@@ -56,28 +58,42 @@ struct InstDev {
     int32_t* stats;
 };
 
-// Number of FP64 working vectors of nS entries each, per lane.
+// FP64 working vectors of nS entries per lane.
 constexpr int NVEC = 8;
 
 struct Launch {
     MechDev M;
     int method, precision, max_steps, n_inst;
-    int64_t nslots;                 // lanes in the persistent grid
-    unsigned long long* queue;      // next global cell index
-    double* vec;                    // [NVEC * nS][nslots]
-    void* rarr;                     // [2 nR + nS + nR][nslots] of the rate type
+    int64_t nslots;                 // lanes of the persistent grid
     int64_t total;                  // cells over all instances
+    unsigned long long* queue;      // next position in `order`
+    unsigned* hist;                 // [NBUCKET] counts, then cursors
+    // per lane
+    double* vec;                    // [NVEC * nS][nslots]
+    void* lane_r;                   // C [nS], Omega [nR] of the rate type: [nS + nR][nslots]
+    // per cell (global cell index g over all instances)
+    void* cell_k;                   // k_j [nR][total], then k0/kinf [nFO][total], rate type
+    double* cell_f0;                // f(y0) [nS][total]
+    double* cell_sig;               // RKC spectral radius at y0 [total]
+    double* cell_h;                 // first trial step [total]
+    int32_t* cell_nfe;              // f evaluations spent before the main kernel [total]
+    uint8_t* cell_st;               // 0, or a final status decided before the main kernel
+    int32_t* order;                 // processing order (longest predicted first) [total]
     int64_t start[KIN_MAX_INSTANCES + 1];  // prefix sums of instance cells
     InstDev inst[KIN_MAX_INSTANCES];
 };
 
+// Workspace layout for `cells` cells and `nslots` lanes.
+struct WsLayout {
+    int64_t header, vec, lane_r, cell_k, f0, sig, h, nfe, st, order, total;
+};
+WsLayout ws_layout(const MechDev& M, int precision, int64_t nslots, int64_t cells);
+
 // Host-side helpers implemented in kernels.cu.
-int64_t scratch_elems_vec(int nS);
-int64_t scratch_bytes_rate(int nS, int nR, int precision);
-cudaError_t launch_integrate(const Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_integrate(Launch& L, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_rates(const MechDev& M, int64_t cells, const double* T, const double* p,
-                         const double* Y, int64_t ldY, double* dYdt, int precision,
-                         void* rarr, int64_t nslots, int blocks, int threads, cudaStream_t st);
+                         const double* Y, int64_t ldY, double* dYdt, int precision, void* ws,
+                         int64_t nslots, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_rkc_table(double* tab, cudaStream_t st);
 cudaError_t integrate_occupancy(int method, int precision, int threads, int* blocks_per_sm);
 

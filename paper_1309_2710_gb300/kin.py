@@ -56,7 +56,7 @@ _SIGNATURES = {
     "kin_create_mechanism": (ctypes.c_int, [ctypes.POINTER(MechDesc), ctypes.POINTER(ctypes.c_void_p)]),
     "kin_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "kin_last_error": (ctypes.c_char_p, []),
-    "kin_workspace_bytes": (ctypes.c_int64, [ctypes.c_void_p, ctypes.POINTER(Opts)]),
+    "kin_workspace_bytes": (ctypes.c_int64, [ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.c_int64]),
     "kin_integrate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.POINTER(Opts), ctypes.c_void_p,
@@ -151,16 +151,17 @@ class Mechanism:
         except Exception:
             pass
 
-    def workspace_bytes(self, method=RKC, precision=FP64, block_threads=0, blocks_per_sm=0) -> int:
+    def workspace_bytes(self, method=RKC, precision=FP64, cells=0, block_threads=0,
+                        blocks_per_sm=0) -> int:
         o = Opts(method, precision, 0, block_threads, blocks_per_sm, 0, None)
-        n = lib().kin_workspace_bytes(self.handle, ctypes.byref(o))
+        n = lib().kin_workspace_bytes(self.handle, ctypes.byref(o), int(cells))
         if n < 0:
             _check(int(n))
         return int(n)
 
-    def workspace(self, method=RKC, precision=FP64, block_threads=0, blocks_per_sm=0,
+    def workspace(self, method=RKC, precision=FP64, cells=0, block_threads=0, blocks_per_sm=0,
                   device=None) -> torch.Tensor:
-        n = self.workspace_bytes(method, precision, block_threads, blocks_per_sm)
+        n = self.workspace_bytes(method, precision, cells, block_threads, blocks_per_sm)
         return torch.empty(n, dtype=torch.uint8, device=device or torch.device("cuda"))
 
 
@@ -195,7 +196,7 @@ def integrate(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP
     """Integrate every cell over dt in place (kin_integrate)."""
     cells, ld = _check_state(mech, T, p, Y)
     if workspace is None:
-        workspace = mech.workspace(method, precision, block_threads, blocks_per_sm, Y.device)
+        workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm, Y.device)
     o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, 0, _stream_handle(stream))
     _check(lib().kin_integrate(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), ld, float(dt),
                                float(rtol), float(atol), ctypes.byref(o), _ptr(status),
@@ -220,7 +221,9 @@ def integrate_batch(mech: Mechanism, parts: Sequence[Cells], method=RKC, precisi
         raise ValueError("1..%d instances per launch" % MAX_INSTANCES)
     arr = make_instances(mech, parts)
     if workspace is None:
-        workspace = mech.workspace(method, precision, block_threads, blocks_per_sm, parts[0].Y.device)
+        cells = sum(int(c.T.numel()) for c in parts)
+        workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm,
+                                   parts[0].Y.device)
     o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, 0, _stream_handle(stream))
     _check(lib().kin_integrate_batch(mech.handle, len(parts), arr, ctypes.byref(o),
                                      _ptr(workspace), workspace.numel()))
@@ -232,7 +235,7 @@ def rates(mech: Mechanism, T, p, Y, precision=FP64, out=None, workspace=None, st
     if out is None:
         out = torch.empty_strided(Y.shape, Y.stride(), dtype=Y.dtype, device=Y.device)
     if workspace is None:
-        workspace = mech.workspace(RKC, precision, device=Y.device)
+        workspace = mech.workspace(RKC, precision, cells, device=Y.device)
     _check(lib().kin_rates(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(out),
                            precision, _stream_handle(stream), _ptr(workspace), workspace.numel()))
     return out
