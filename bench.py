@@ -255,7 +255,17 @@ def run_kin(args):
     Yd = torch.empty_like(Y0d)
     st = torch.zeros(cells, dtype=torch.uint8, device=dev)
     sta = torch.zeros((cells, 4), dtype=torch.int32, device=dev)
-    ws = km.workspace(method, prec, cells, device=dev)
+    shape = dict(block_threads=0, blocks_per_sm=0, staging=kin.STAGE_GLOBAL)
+    if not args.no_tune:
+        # launch shape from the autotuner (cached per GPU and mechanism shape),
+        # timed on the first 65536 cells, outside the timed region
+        from paper_1309_2710_gb300 import autotune
+        n = min(cells, 65536)
+        best = autotune.tune(km, m, Td[:n], pd[:n], Y0d[:, :n].contiguous(), w["dt"], w["rtol"],
+                             w["atol"], method, prec)
+        shape = {k: best[k] for k in shape}
+    ws = km.workspace(method, prec, cells, shape["block_threads"], shape["blocks_per_sm"], dev,
+                      shape["staging"])
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -265,7 +275,7 @@ def run_kin(args):
         if ev:
             ev[0].record(stream)
         kin.integrate(km, Td, pd, Yd, w["dt"], w["rtol"], w["atol"], method, prec,
-                      status=st, stats=sta, workspace=ws, stream=stream)
+                      status=st, stats=sta, workspace=ws, stream=stream, **shape)
         if ev:
             ev[1].record(stream)
 
@@ -311,13 +321,13 @@ def run_kin(args):
         Y0h = torch.as_tensor(Y0).contiguous()
         Yh = torch.empty_like(Y0h).pin_memory()
         sth = torch.empty(cells, dtype=torch.uint8).pin_memory()
-        hbuf = kin.host_buffer(km, cells, method, prec, device=dev)
+        hbuf = kin.host_buffer(km, cells, method, prec, device=dev, **shape)
 
         def e2e_step():
             # the flow solver hands over its state in host memory every step
             Yh.copy_(Y0h)
             kin.integrate_host(km, Th, ph, Yh, w["dt"], w["rtol"], w["atol"], method, prec,
-                               status=sth, buffer=hbuf, stream=stream)
+                               status=sth, buffer=hbuf, stream=stream, **shape)
             stream.synchronize()
 
         e2e_step()
@@ -347,7 +357,7 @@ def run_kin(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32+f64",
             "data": "synthetic (seeded generator standing in for the paper's mechanisms and states)",
-            "config": workload_config(name, cells),
+            "config": dict(workload_config(name, cells), launch_shape=shape),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
                          "frac": achieved / peak, "traffic": tr,
                          "kernel": "integrate_kernel (FP64 pipe)",
@@ -378,6 +388,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="library default launch shape")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

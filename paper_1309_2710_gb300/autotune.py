@@ -1,0 +1,91 @@
+"""Autotuner for the launch shape of the integrator.
+
+For one mechanism, method and precision it times kin_integrate on a sample
+of the caller's cells over the candidate shapes:
+  block_threads  32 .. 128 lanes per block (one cell per lane),
+  blocks_per_sm  persistent blocks per SM (only shapes that fit),
+  staging        per-lane rate scratch in the workspace or in shared memory,
+and keeps the fastest. Results are cached per GPU and mechanism shape in a
+JSON file next to the built library.
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Dict, Optional
+
+import torch
+
+from . import build as _build
+from . import kin
+
+CACHE = os.path.join(_build.OUT_DIR, "autotune.json")
+
+
+def _key(mech: kin.Mechanism, method: int, precision: int, desc) -> str:
+    dev = torch.cuda.get_device_name()
+    n_m = int(len(desc.eff)) if hasattr(desc, "eff") else -1
+    return "%s|%d|%d|%d|%d|%d" % (dev, mech.n_species, mech.n_reactions, n_m, method, precision)
+
+
+def candidates():
+    for staging in (kin.STAGE_GLOBAL, kin.STAGE_SHARED, kin.STAGE_SHARED_ALL):
+        for threads in (128, 64, 32):
+            for bps in (1, 2, 3, 4, 6, 8, 12, 16):
+                if threads * bps > 1024:
+                    continue
+                yield dict(block_threads=threads, blocks_per_sm=bps, staging=staging)
+
+
+def time_config(mech, T, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2) -> Optional[float]:
+    """Mean kernel milliseconds of kin_integrate with `cfg`, or None if the
+    shape is not supported."""
+    cells = int(T.numel())
+    try:
+        ws = mech.workspace(method, precision, cells, cfg["block_threads"], cfg["blocks_per_sm"],
+                            T.device, cfg["staging"])
+    except kin.KinError:
+        return None
+    Y = torch.empty_like(Y0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    best = None
+    for r in range(reps + 1):
+        Y.copy_(Y0)
+        ev[0].record()
+        try:
+            kin.integrate(mech, T, p, Y, dt, rtol, atol, method, precision, workspace=ws, **cfg)
+        except kin.KinError:
+            return None
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        if r > 0:
+            best = ms if best is None else min(best, ms)
+    return best
+
+
+def tune(mech: kin.Mechanism, desc, T, p, Y, dt, rtol, atol, method, precision,
+         use_cache: bool = True, verbose: bool = False) -> Dict:
+    """Best launch shape for this mechanism on the current GPU, timed on the
+    given (device) sample of cells."""
+    key = _key(mech, method, precision, desc)
+    cache = {}
+    if use_cache and os.path.exists(CACHE):
+        with open(CACHE) as f:
+            cache = json.load(f)
+        if key in cache:
+            return cache[key]
+    results = []
+    for cfg in candidates():
+        ms = time_config(mech, T, p, Y, dt, rtol, atol, method, precision, cfg)
+        if verbose:
+            print("autotune", cfg, ms)
+        if ms is not None:
+            results.append((ms, cfg))
+    results.sort(key=lambda x: x[0])
+    best = dict(results[0][1], ms=results[0][0], cells=int(T.numel()))
+    cache[key] = best
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    with open(CACHE, "w") as f:
+        json.dump(cache, f, indent=1)
+    return best

@@ -66,14 +66,22 @@ int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     int threads = o->block_threads > 0 ? o->block_threads : 128;
     if (threads % 32 != 0 || threads > 128) return fail(KIN_EINVAL, "block_threads must be a multiple of 32 and <= 128");
-    int bps = o->blocks_per_sm;
-    if (bps <= 0) {
-        int occ = 0;
-        e = integrate_occupancy(o->method, o->precision, threads, &occ);
-        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-        bps = std::max(1, std::min(occ, 512 / threads));
+    const int stg = o->staging;
+    if (stg > 0) {
+        int maxsm = 0;
+        e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+        if (smem_bytes(m->dev, o->precision, threads, stg) > (size_t)maxsm)
+            return fail(KIN_EUNSUPPORTED, "shared-memory staging needs %zu bytes per block (max %d)",
+                        smem_bytes(m->dev, o->precision, threads, stg), maxsm);
     }
-    if (bps > 64) return fail(KIN_EINVAL, "blocks_per_sm too large");
+    int occ = 0;
+    e = integrate_occupancy(m->dev, o->method, o->precision, stg, threads, &occ);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (occ < 1) return fail(KIN_EUNSUPPORTED, "kernel does not fit on an SM with these options");
+    int bps = o->blocks_per_sm;
+    if (bps <= 0) bps = std::max(1, std::min(occ, 512 / threads));
+    if (bps > occ) return fail(KIN_EINVAL, "blocks_per_sm %d exceeds the %d blocks that fit per SM", bps, occ);
     g->threads = threads;
     g->blocks = nsm * bps;
     g->nslots = (int64_t)g->blocks * threads;
@@ -91,7 +99,9 @@ int check_opts(const kin_opts* o)
     if (o->method != KIN_RKCK && o->method != KIN_RKC) return fail(KIN_EINVAL, "unknown method %d", o->method);
     if (o->precision != KIN_FP64 && o->precision != KIN_MIXED)
         return fail(KIN_EINVAL, "unknown precision %d", o->precision);
-    if (o->reserved != 0) return fail(KIN_EINVAL, "opts.reserved must be 0");
+    if (o->staging != KIN_STAGE_GLOBAL && o->staging != KIN_STAGE_SHARED &&
+        o->staging != KIN_STAGE_SHARED_ALL)
+        return fail(KIN_EINVAL, "unknown staging %d", o->staging);
     return KIN_OK;
 }
 
@@ -274,6 +284,7 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
         if (I.cells > 0) {
             if (!I.T || !I.p || !I.Y) return fail(KIN_EINVAL, "instance %d: T, p and Y must be non-NULL", i);
             if (I.ldY < I.cells) return fail(KIN_EINVAL, "instance %d: ldY < cells", i);
+            if (I.ldY > INT32_MAX) return fail(KIN_EINVAL, "instance %d: ldY >= 2^31", i);
             if (!is_device_ptr(I.T) || !is_device_ptr(I.p) || !is_device_ptr(I.Y) ||
                 (I.status && !is_device_ptr(I.status)) || (I.stats && !is_device_ptr(I.stats)))
                 return fail(KIN_EINVAL, "instance %d: T, p, Y, status and stats must be device memory", i);
@@ -321,7 +332,7 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     cudaStream_t st = (cudaStream_t)o->stream;
     cudaError_t e = cudaMemsetAsync(base + w.header, 0, 512, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    e = launch_integrate(P, blocks, g.threads, st);
+    e = launch_integrate(P, o->staging, blocks, g.threads, st);
     if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
     return KIN_OK;
 }
@@ -391,9 +402,10 @@ int kin_rates(const kin_mech* m, int64_t cells, const double* T, const double* p
     if (cells == 0) return KIN_OK;
     if (!T || !p || !Y || !dYdt) return fail(KIN_EINVAL, "T, p, Y and dYdt must be non-NULL");
     if (ldY < cells) return fail(KIN_EINVAL, "ldY < cells");
+    if (ldY > INT32_MAX) return fail(KIN_EINVAL, "ldY >= 2^31");
     if (!is_device_ptr(T) || !is_device_ptr(p) || !is_device_ptr(Y) || !is_device_ptr(dYdt))
         return fail(KIN_EINVAL, "T, p, Y and dYdt must be device memory");
-    kin_opts o{KIN_RKC, precision, 0, 0, 0, 0, stream};
+    kin_opts o{KIN_RKC, precision, 0, 0, 0, KIN_STAGE_GLOBAL, stream};
     Grid g;
     int rc = grid_for(m, &o, &g);
     if (rc) return rc;

@@ -41,7 +41,7 @@ namespace kin {
 template <typename T>
 struct Lane {
     T* p;
-    int64_t s;  // stride between elements
+    int32_t s;  // stride between elements (lanes or cells, < 2^31)
     __device__ __forceinline__ T& operator[](int i) const { return p[(int64_t)i * s]; }
 };
 
@@ -166,35 +166,57 @@ __device__ __forceinline__ long long pop_cell(unsigned long long* q)
 enum Vec : int { V_Y = 0, V_F0, V_A, V_B, V_C, V_X, V_FX, V_RS };
 // RKCK reuses slots: F[1..5] = V_A, V_B, V_C, V_FX, V_RS; the stage point is V_X.
 
-template <typename R>
+extern __shared__ __align__(16) unsigned char kin_smem[];
+
+// Per-lane views of the workspace. Staging level STG places the arrays f
+// touches most in shared memory, element-major across the block
+// ([element][thread]): 1 = concentrations and rates of progress, 2 = also
+// the cell's rate constants. Otherwise they live in the lane's slice of the
+// workspace ([element][lane]): C [nS], Omega [nR], k [nR], k0/kinf [nFO].
+template <typename R, int STG>
 struct Views {
     const Launch& L;
     const MechDev& M;
     int64_t slot;
-    Lane<R> C, OM;
+    Lane<R> C, OM, Kl, KRl;
     double* vbase;
     __device__ Views(const Launch& l, int64_t sl) : L(l), M(l.M), slot(sl)
     {
         R* rb = reinterpret_cast<R*>(L.lane_r) + sl;
-        C = Lane<R>{rb, L.nslots};
-        OM = Lane<R>{rb + (int64_t)M.nS * L.nslots, L.nslots};
+        const int64_t ns = L.nslots;
+        R* sb = reinterpret_cast<R*>(kin_smem) + threadIdx.x;
+        const int64_t bs = blockDim.x;
+        if (STG >= 1) {
+            C = Lane<R>{sb, (int32_t)bs};
+            OM = Lane<R>{sb + (int64_t)M.nS * bs, (int32_t)bs};
+        } else {
+            C = Lane<R>{rb, (int32_t)ns};
+            OM = Lane<R>{rb + (int64_t)M.nS * ns, (int32_t)ns};
+        }
+        if (STG >= 2) {
+            Kl = Lane<R>{sb + (int64_t)(M.nS + M.nR) * bs, (int32_t)bs};
+            KRl = Lane<R>{sb + (int64_t)(M.nS + 2 * M.nR) * bs, (int32_t)bs};
+        } else {
+            Kl = Lane<R>{rb + (int64_t)(M.nS + M.nR) * ns, (int32_t)ns};
+            KRl = Lane<R>{rb + (int64_t)(M.nS + 2 * M.nR) * ns, (int32_t)ns};
+        }
         vbase = L.vec + sl;
     }
     __device__ __forceinline__ Lane<double> V(int v) const
     {
-        return Lane<double>{vbase + (int64_t)v * M.nS * L.nslots, L.nslots};
+        return Lane<double>{vbase + (int64_t)v * M.nS * L.nslots, (int32_t)L.nslots};
     }
     __device__ __forceinline__ Lane<R> K(int64_t g) const
     {
-        return Lane<R>{reinterpret_cast<R*>(L.cell_k) + g, L.total};
+        return Lane<R>{reinterpret_cast<R*>(L.cell_k) + g, (int32_t)L.total};
     }
     __device__ __forceinline__ Lane<R> KR(int64_t g) const
     {
-        return Lane<R>{reinterpret_cast<R*>(L.cell_k) + (int64_t)M.nR * L.total + g, L.total};
+        return Lane<R>{reinterpret_cast<R*>(L.cell_k) + (int64_t)M.nR * L.total + g, (int32_t)L.total};
     }
     __device__ __forceinline__ Lane<double> F0cell(int64_t g) const
     {
-        return Lane<double>{L.cell_f0 + g, L.total};
+        return Lane<double>{L.cell_f0 + g, (int32_t)L.total};
     }
 };
 
@@ -215,12 +237,12 @@ __device__ __forceinline__ double rms(int n, double rtol, double atol, Lane<doub
 // For every cell g (grid-stride, uniform across lanes): rate constants, f(y0),
 // and for RKC the Gershgorin bound on the FD Jacobian (Section 2.3) and the
 // initial step h1 = 0.1 h0 / ||Delta_0||^(1/2), h0 = 1/sigma.
-template <int METHOD, typename R>
+template <int METHOD, typename R, int STG>
 __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launch L)
 {
     const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= L.nslots) return;
-    Views<R> W(L, slot);
+    Views<R, STG> W(L, slot);
     const MechDev& M = L.M;
     const int nS = M.nS;
     for (int64_t g = slot; g < L.total; g += L.nslots) {
@@ -366,9 +388,9 @@ struct LaneState {
     int in_v, out_v;  // vectors read and written by the next f evaluation
 };
 
-template <int METHOD, typename R>
+template <int METHOD, typename R, int STG>
 struct Integrator {
-    Views<R> W;
+    Views<R, STG> W;
     const Launch& L;
     const MechDev& M;
     Lane<R> K, KR;
@@ -401,8 +423,12 @@ struct Integrator {
             const double T = I.T[S.cell], p = I.p[S.cell];
             S.Ctot = p * 1e-6 / (R_GAS * T);
             S.invCtot = 1.0 / S.Ctot;
-            K = W.K(g);
-            KR = W.KR(g);
+            // the cell's rate constants into the lane's (coalesced or shared) copy
+            K = W.Kl;
+            KR = W.KRl;
+            const Lane<R> Kc = W.K(g), KRc = W.KR(g);
+            for (int j = 0; j < M.nR; ++j) K[j] = Kc[j];
+            for (int j = 0; j < M.nFO; ++j) KR[j] = KRc[j];
             Lane<double> Y = V(V_Y), F0 = V(V_F0), F0c = W.F0cell(g);
             for (int k = 0; k < M.nS; ++k) {
                 Y[k] = I.Y[(int64_t)k * I.ldY + S.cell];
@@ -710,12 +736,12 @@ struct Integrator {
     }
 };
 
-template <int METHOD, typename R>
+template <int METHOD, typename R, int STG>
 __global__ void __launch_bounds__(128) integrate_kernel(const __grid_constant__ Launch L)
 {
     const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= L.nslots) return;
-    Integrator<METHOD, R> I(L, slot);
+    Integrator<METHOD, R, STG> I(L, slot);
     I.run();
 }
 
@@ -728,14 +754,14 @@ __global__ void rates_kernel(MechDev M, int64_t cells, const double* __restrict_
     const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= nslots) return;
     R* rb = reinterpret_cast<R*>(lane_r) + slot;
-    Lane<R> C{rb, nslots}, OM{rb + (int64_t)M.nS * nslots, nslots};
+    Lane<R> C{rb, (int32_t)nslots}, OM{rb + (int64_t)M.nS * nslots, (int32_t)nslots};
     for (int64_t c = slot; c < cells; c += nslots) {
-        Lane<R> K{reinterpret_cast<R*>(cell_k) + c, cells};
-        Lane<R> KR{reinterpret_cast<R*>(cell_k) + (int64_t)M.nR * cells + c, cells};
+        Lane<R> K{reinterpret_cast<R*>(cell_k) + c, (int32_t)cells};
+        Lane<R> KR{reinterpret_cast<R*>(cell_k) + (int64_t)M.nR * cells + c, (int32_t)cells};
         rate_constants<R>(M, T[c], K, KR);
         const double Ctot = p[c] * 1e-6 / (R_GAS * T[c]);
         feval<R>(M, Ctot, 1.0 / Ctot, K, KR, C, OM,
-                 Lane<double>{const_cast<double*>(Y) + c, ldY}, Lane<double>{dYdt + c, ldY});
+                 Lane<double>{const_cast<double*>(Y) + c, (int32_t)ldY}, Lane<double>{dYdt + c, (int32_t)ldY});
     }
 }
 
@@ -797,7 +823,7 @@ WsLayout ws_layout(const MechDev& M, int precision, int64_t nslots, int64_t cell
     int64_t off = 0;
     w.header = off;  off += 4096;
     w.vec = off;     off += al256((int64_t)NVEC * M.nS * 8 * nslots);
-    w.lane_r = off;  off += al256((int64_t)(M.nS + M.nR) * rb * nslots);
+    w.lane_r = off;  off += al256((int64_t)(M.nS + 2 * M.nR + M.nFO) * rb * nslots);
     w.cell_k = off;  off += al256((int64_t)(M.nR + M.nFO) * rb * cells);
     w.f0 = off;      off += al256((int64_t)M.nS * 8 * cells);
     w.sig = off;     off += al256(8 * cells);
@@ -809,10 +835,25 @@ WsLayout ws_layout(const MechDev& M, int precision, int64_t nslots, int64_t cell
     return w;
 }
 
-template <int METHOD, typename R>
+size_t smem_bytes(const MechDev& M, int precision, int threads, int stg)
+{
+    const size_t n = (stg >= 1 ? M.nS + M.nR : 0) + (stg >= 2 ? M.nR + M.nFO : 0);
+    return n * threads * (precision == KIN_MIXED ? 4 : 8);
+}
+
+template <int METHOD, typename R, int STG>
 static cudaError_t launch_all(Launch& L, int blocks, int threads, cudaStream_t st)
 {
-    init_kernel<METHOD, R><<<blocks, threads, 0, st>>>(L);
+    const size_t sm = smem_bytes(L.M, L.precision, threads, STG);
+    if (STG > 0) {
+        cudaError_t e = cudaFuncSetAttribute(init_kernel<METHOD, R, STG>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(integrate_kernel<METHOD, R, STG>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    init_kernel<METHOD, R, STG><<<blocks, threads, sm, st>>>(L);
     if (METHOD == KIN_RKC) {
         const int64_t nb = (L.total + 255) / 256;
         const int sb = (int)(nb < 1024 ? nb : 1024);
@@ -820,28 +861,55 @@ static cudaError_t launch_all(Launch& L, int blocks, int threads, cudaStream_t s
         bucket_scan_kernel<<<1, 32, 0, st>>>(L.hist);
         bucket_scatter_kernel<<<sb, 256, 0, st>>>(L);
     }
-    integrate_kernel<METHOD, R><<<blocks, threads, 0, st>>>(L);
+    integrate_kernel<METHOD, R, STG><<<blocks, threads, sm, st>>>(L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_integrate(Launch& L, int blocks, int threads, cudaStream_t st)
+template <int METHOD, typename R>
+static cudaError_t launch_staged(Launch& L, int stg, int blocks, int threads, cudaStream_t st)
 {
-    if (L.method == KIN_RKCK)
-        return L.precision == KIN_MIXED ? launch_all<KIN_RKCK, float>(L, blocks, threads, st)
-                                        : launch_all<KIN_RKCK, double>(L, blocks, threads, st);
-    return L.precision == KIN_MIXED ? launch_all<KIN_RKC, float>(L, blocks, threads, st)
-                                    : launch_all<KIN_RKC, double>(L, blocks, threads, st);
+    if (stg == 2) return launch_all<METHOD, R, 2>(L, blocks, threads, st);
+    if (stg == 1) return launch_all<METHOD, R, 1>(L, blocks, threads, st);
+    return launch_all<METHOD, R, 0>(L, blocks, threads, st);
 }
 
-cudaError_t integrate_occupancy(int method, int precision, int threads, int* bps)
+cudaError_t launch_integrate(Launch& L, int stg, int blocks, int threads, cudaStream_t st)
 {
+    if (L.method == KIN_RKCK)
+        return L.precision == KIN_MIXED ? launch_staged<KIN_RKCK, float>(L, stg, blocks, threads, st)
+                                        : launch_staged<KIN_RKCK, double>(L, stg, blocks, threads, st);
+    return L.precision == KIN_MIXED ? launch_staged<KIN_RKC, float>(L, stg, blocks, threads, st)
+                                    : launch_staged<KIN_RKC, double>(L, stg, blocks, threads, st);
+}
+
+template <int METHOD, typename R, int STG>
+static cudaError_t occ_one(int threads, size_t sm, int* bps)
+{
+    if (STG > 0) {
+        cudaError_t e = cudaFuncSetAttribute(integrate_kernel<METHOD, R, STG>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, integrate_kernel<METHOD, R, STG>, threads, sm);
+}
+
+template <int METHOD, typename R>
+static cudaError_t occ_staged(int stg, int threads, size_t sm, int* bps)
+{
+    if (stg == 2) return occ_one<METHOD, R, 2>(threads, sm, bps);
+    if (stg == 1) return occ_one<METHOD, R, 1>(threads, sm, bps);
+    return occ_one<METHOD, R, 0>(threads, sm, bps);
+}
+
+cudaError_t integrate_occupancy(const MechDev& M, int method, int precision, int stg, int threads,
+                                int* bps)
+{
+    const size_t sm = smem_bytes(M, precision, threads, stg);
     if (method == KIN_RKCK)
-        return precision == KIN_MIXED
-                   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, integrate_kernel<KIN_RKCK, float>, threads, 0)
-                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, integrate_kernel<KIN_RKCK, double>, threads, 0);
-    return precision == KIN_MIXED
-               ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, integrate_kernel<KIN_RKC, float>, threads, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, integrate_kernel<KIN_RKC, double>, threads, 0);
+        return precision == KIN_MIXED ? occ_staged<KIN_RKCK, float>(stg, threads, sm, bps)
+                                      : occ_staged<KIN_RKCK, double>(stg, threads, sm, bps);
+    return precision == KIN_MIXED ? occ_staged<KIN_RKC, float>(stg, threads, sm, bps)
+                                  : occ_staged<KIN_RKC, double>(stg, threads, sm, bps);
 }
 
 cudaError_t launch_rates(const MechDev& M, int64_t cells, const double* T, const double* p,

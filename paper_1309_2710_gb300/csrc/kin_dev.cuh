@@ -70,7 +70,8 @@ struct Launch {
     unsigned* hist;                 // [NBUCKET] counts, then cursors
     // per lane
     double* vec;                    // [NVEC * nS][nslots]
-    void* lane_r;                   // C [nS], Omega [nR] of the rate type: [nS + nR][nslots]
+    void* lane_r;                   // C [nS], Omega [nR], k [nR], k0/kinf [nFO] of the rate
+                                    // type: [nS + 2 nR + nFO][nslots]
     // per cell (global cell index g over all instances)
     void* cell_k;                   // k_j [nR][total], then k0/kinf [nFO][total], rate type
     double* cell_f0;                // f(y0) [nS][total]
@@ -90,11 +91,13 @@ struct WsLayout {
 WsLayout ws_layout(const MechDev& M, int precision, int64_t nslots, int64_t cells);
 
 // Host-side helpers implemented in kernels.cu.
-cudaError_t launch_integrate(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_integrate(Launch& L, int staging, int blocks, int threads, cudaStream_t st);
+size_t smem_bytes(const MechDev& M, int precision, int threads, int staging);
 cudaError_t launch_rates(const MechDev& M, int64_t cells, const double* T, const double* p,
                          const double* Y, int64_t ldY, double* dYdt, int precision, void* ws,
                          int64_t nslots, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_rkc_table(double* tab, cudaStream_t st);
-cudaError_t integrate_occupancy(int method, int precision, int threads, int* blocks_per_sm);
+cudaError_t integrate_occupancy(const MechDev& M, int method, int precision, int staging,
+                                int threads, int* blocks_per_sm);
 
 }  // namespace kin

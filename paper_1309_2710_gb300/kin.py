@@ -20,6 +20,7 @@ KIN_OK, KIN_EINVAL, KIN_ENOMEM, KIN_ECUDA, KIN_EUNSUPPORTED = 0, -1, -2, -3, -4
 RKCK, RKC = 0, 1
 FP64, MIXED = 0, 1
 CELL_OK, CELL_MAXSTEPS, CELL_HMIN, CELL_NONFINITE = 0, 1, 2, 3
+STAGE_GLOBAL, STAGE_SHARED, STAGE_SHARED_ALL = 0, 1, 2
 MAX_INSTANCES = 128
 
 
@@ -40,7 +41,7 @@ class MechDesc(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("max_steps", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("staging", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -152,16 +153,16 @@ class Mechanism:
             pass
 
     def workspace_bytes(self, method=RKC, precision=FP64, cells=0, block_threads=0,
-                        blocks_per_sm=0) -> int:
-        o = Opts(method, precision, 0, block_threads, blocks_per_sm, 0, None)
+                        blocks_per_sm=0, staging=STAGE_GLOBAL) -> int:
+        o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, None)
         n = lib().kin_workspace_bytes(self.handle, ctypes.byref(o), int(cells))
         if n < 0:
             _check(int(n))
         return int(n)
 
     def workspace(self, method=RKC, precision=FP64, cells=0, block_threads=0, blocks_per_sm=0,
-                  device=None) -> torch.Tensor:
-        n = self.workspace_bytes(method, precision, cells, block_threads, blocks_per_sm)
+                  device=None, staging=STAGE_GLOBAL) -> torch.Tensor:
+        n = self.workspace_bytes(method, precision, cells, block_threads, blocks_per_sm, staging)
         return torch.empty(n, dtype=torch.uint8, device=device or torch.device("cuda"))
 
 
@@ -192,12 +193,14 @@ class Cells:
 
 def integrate(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP64,
               status=None, stats=None, workspace=None, stream=None, max_steps=0,
-              block_threads=0, blocks_per_sm=0):
+              block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL):
     """Integrate every cell over dt in place (kin_integrate)."""
     cells, ld = _check_state(mech, T, p, Y)
     if workspace is None:
-        workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm, Y.device)
-    o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, 0, _stream_handle(stream))
+        workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm, Y.device,
+                                   staging)
+    o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging,
+             _stream_handle(stream))
     _check(lib().kin_integrate(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), ld, float(dt),
                                float(rtol), float(atol), ctypes.byref(o), _ptr(status),
                                _ptr(stats), _ptr(workspace), workspace.numel()))
@@ -215,7 +218,8 @@ def make_instances(mech: Mechanism, parts: Sequence[Cells]):
 
 
 def integrate_batch(mech: Mechanism, parts: Sequence[Cells], method=RKC, precision=FP64,
-                    workspace=None, stream=None, max_steps=0, block_threads=0, blocks_per_sm=0):
+                    workspace=None, stream=None, max_steps=0, block_threads=0, blocks_per_sm=0,
+                    staging=STAGE_GLOBAL):
     """Integrate several instances in one persistent launch (kin_integrate_batch)."""
     if not 1 <= len(parts) <= MAX_INSTANCES:
         raise ValueError("1..%d instances per launch" % MAX_INSTANCES)
@@ -223,8 +227,9 @@ def integrate_batch(mech: Mechanism, parts: Sequence[Cells], method=RKC, precisi
     if workspace is None:
         cells = sum(int(c.T.numel()) for c in parts)
         workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm,
-                                   parts[0].Y.device)
-    o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, 0, _stream_handle(stream))
+                                   parts[0].Y.device, staging)
+    o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging,
+             _stream_handle(stream))
     _check(lib().kin_integrate_batch(mech.handle, len(parts), arr, ctypes.byref(o),
                                      _ptr(workspace), workspace.numel()))
 
@@ -245,9 +250,10 @@ def version() -> str:
     return lib().kin_version().decode()
 
 
-def host_buffer(mech: Mechanism, cells: int, method=RKC, precision=FP64, device=None) -> torch.Tensor:
+def host_buffer(mech: Mechanism, cells: int, method=RKC, precision=FP64, device=None,
+                block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL) -> torch.Tensor:
     """Device buffer for integrate_host (kin_host_buffer_bytes)."""
-    o = Opts(method, precision, 0, 0, 0, 0, None)
+    o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, None)
     n = lib().kin_host_buffer_bytes(mech.handle, ctypes.byref(o), int(cells))
     if n < 0:
         _check(int(n))
@@ -255,7 +261,8 @@ def host_buffer(mech: Mechanism, cells: int, method=RKC, precision=FP64, device=
 
 
 def integrate_host(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP64,
-                   status=None, stats=None, buffer=None, stream=None, max_steps=0):
+                   status=None, stats=None, buffer=None, stream=None, max_steps=0,
+                   block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL):
     """kin_integrate_host: T, p, Y (in place), status, stats are CPU tensors
     (pin them for asynchronous copies). Returns after enqueueing; synchronise
     the stream before reading the results."""
@@ -266,8 +273,10 @@ def integrate_host(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precisi
     if Y.dim() != 2 or Y.shape[0] != mech.n_species or Y.stride(1) != 1 or Y.shape[1] < cells:
         raise ValueError("Y must be [n_species, >= cells] with unit column stride")
     if buffer is None:
-        buffer = host_buffer(mech, cells, method, precision)
-    o = Opts(method, precision, max_steps, 0, 0, 0, _stream_handle(stream))
+        buffer = host_buffer(mech, cells, method, precision, None, block_threads, blocks_per_sm,
+                             staging)
+    o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging,
+             _stream_handle(stream))
     _check(lib().kin_integrate_host(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), int(Y.stride(0)),
                                     float(dt), float(rtol), float(atol), ctypes.byref(o),
                                     _ptr(status), _ptr(stats), _ptr(buffer), buffer.numel()))

@@ -1,0 +1,319 @@
+"""Continuous-batching server for kinetics integration requests.
+
+A request is one CFD subdomain: its cells' (T, p, Y), the flow step dt and
+the tolerances, for one of the registered mechanisms. The server
+
+* admits arrived requests in FIFO order while their device state fits a
+  memory budget, and keeps that state resident until the result is back;
+* groups admitted requests by mechanism/method/precision and launches each
+  group's waiting requests as ONE persistent kin_integrate_batch launch on one
+  of the group's stream slots as soon as a slot is free, so requests that
+  arrive while others run start on another slot and overlap on the device;
+* returns each request's Y and status, and records arrival, launch and
+  completion times (latency = completion - arrival).
+
+`one_launch_per_request` is the plain alternative: one kin_integrate per
+request, in arrival order, on one stream.
+
+Every cell is integrated independently by the same per-lane arithmetic, so a
+request's result does not depend on what it is batched with (the tests check
+bitwise identity against a standalone run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+import torch
+
+from . import kin, synth
+
+
+@dataclass
+class Request:
+    rid: int
+    group: str
+    T: torch.Tensor  # pinned host [cells]
+    p: torch.Tensor  # pinned host [cells]
+    Y: torch.Tensor  # pinned host [n_species, cells], unit column stride
+    dt: float
+    rtol: float = 1e-6
+    atol: float = 1e-10
+    arrival: float = 0.0
+    Y_out: Optional[torch.Tensor] = None
+    status: Optional[torch.Tensor] = None
+    t_admit: float = math.nan
+    t_launch: float = math.nan
+    t_done: float = math.nan
+    _dev: Optional[tuple] = None
+    _bytes: int = 0
+
+    @property
+    def cells(self) -> int:
+        return int(self.T.numel())
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.arrival
+
+
+@dataclass
+class Group:
+    mech: kin.Mechanism
+    method: int
+    precision: int
+    blocks_per_sm: int = 0
+
+
+@dataclass
+class _Slot:
+    stream: torch.cuda.Stream
+    workspace: Optional[torch.Tensor] = None
+    batch: List[Request] = field(default_factory=list)
+    event: Optional[torch.cuda.Event] = None
+
+
+def _h2d(dst: torch.Tensor, src: torch.Tensor):
+    """Asynchronous host-to-device copy; strided 2-D sources row by row."""
+    if src.dim() == 2 and not src.is_contiguous():
+        for i in range(src.shape[0]):
+            dst[i].copy_(src[i], non_blocking=True)
+    else:
+        dst.copy_(src, non_blocking=True)
+
+
+class Server:
+    def __init__(self, groups: Dict[str, Group], budget_bytes: int, slots_per_group: int = 2,
+                 max_instances: int = kin.MAX_INSTANCES, max_batch_cells: int = 1 << 21,
+                 device=None):
+        self.groups = groups
+        self.budget = int(budget_bytes)
+        self.max_instances = min(max_instances, kin.MAX_INSTANCES)
+        self.max_batch_cells = max_batch_cells
+        self.device = device or torch.device("cuda")
+        self.slots = {g: [_Slot(torch.cuda.Stream(device=self.device)) for _ in range(slots_per_group)]
+                      for g in groups}
+        self.used = 0
+
+    def request_bytes(self, r: Request) -> int:
+        nS = self.groups[r.group].mech.n_species
+        return r.cells * ((nS + 2) * 8 + 1)
+
+    # -------------------------------------------------------------- steps --
+    def _admit(self, r: Request, now: float):
+        n, nS = r.cells, self.groups[r.group].mech.n_species
+        d = self.device
+        r._dev = (torch.empty(n, dtype=torch.float64, device=d),
+                  torch.empty(n, dtype=torch.float64, device=d),
+                  torch.empty((nS, n), dtype=torch.float64, device=d),
+                  torch.empty(n, dtype=torch.uint8, device=d))
+        r.Y_out = torch.empty((nS, n), dtype=torch.float64, pin_memory=True)
+        r.status = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+        r._bytes = self.request_bytes(r)
+        self.used += r._bytes
+        r.t_admit = now
+
+    def _launch(self, gname: str, slot: _Slot, batch: List[Request], now: float):
+        g = self.groups[gname]
+        cells = sum(r.cells for r in batch)
+        need = g.mech.workspace_bytes(g.method, g.precision, cells, 0, g.blocks_per_sm)
+        if slot.workspace is None or slot.workspace.numel() < need:
+            slot.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+        with torch.cuda.stream(slot.stream):
+            parts = []
+            for r in batch:
+                Td, pd, Yd, sd = r._dev
+                _h2d(Td, r.T)
+                _h2d(pd, r.p)
+                _h2d(Yd, r.Y)
+                parts.append(kin.Cells(Td, pd, Yd, r.dt, r.rtol, r.atol, sd))
+                r.t_launch = now
+            kin.integrate_batch(g.mech, parts, g.method, g.precision, workspace=slot.workspace,
+                                stream=slot.stream, blocks_per_sm=g.blocks_per_sm)
+            for r in batch:
+                r.Y_out.copy_(r._dev[2], non_blocking=True)
+                r.status.copy_(r._dev[3], non_blocking=True)
+            slot.event = torch.cuda.Event()
+            slot.event.record(slot.stream)
+        slot.batch = batch
+
+    def _complete(self, slot: _Slot, now: float):
+        for r in slot.batch:
+            r.t_done = now
+            r._dev = None
+            self.used -= r._bytes
+        slot.batch = []
+        slot.event = None
+
+    # ---------------------------------------------------------------- run --
+    def run(self, requests: List[Request]) -> List[Request]:
+        """Serve `requests` (arrival times in seconds from the start of the
+        call, in wall-clock time). Returns them with results and times."""
+        todo = sorted(requests, key=lambda r: r.arrival)
+        for r in todo:
+            if self.request_bytes(r) > self.budget:
+                raise ValueError("request %d needs more memory than the budget" % r.rid)
+        waiting: List[Request] = []  # arrived, not admitted (FIFO)
+        ready: Dict[str, List[Request]] = {g: [] for g in self.groups}
+        nxt, done = 0, 0
+        t0 = time.perf_counter()
+        while done < len(todo):
+            now = time.perf_counter() - t0
+            while nxt < len(todo) and todo[nxt].arrival <= now:
+                waiting.append(todo[nxt])
+                nxt += 1
+            while waiting and self.used + self.request_bytes(waiting[0]) <= self.budget:
+                r = waiting.pop(0)
+                self._admit(r, now)
+                ready[r.group].append(r)
+            progressed = False
+            for gname, slots in self.slots.items():
+                for slot in slots:
+                    if slot.event is not None and slot.event.query():
+                        done += len(slot.batch)
+                        self._complete(slot, now)
+                        progressed = True
+                    if slot.event is None and ready[gname]:
+                        batch, cells = [], 0
+                        q = ready[gname]
+                        while q and len(batch) < self.max_instances and (
+                                not batch or cells + q[0].cells <= self.max_batch_cells):
+                            r = q.pop(0)
+                            batch.append(r)
+                            cells += r.cells
+                        self._launch(gname, slot, batch, now)
+                        progressed = True
+            if not progressed:
+                time.sleep(20e-6)
+        return todo
+
+
+def one_launch_per_request(groups: Dict[str, Group], requests: List[Request], device=None):
+    """Plain FIFO: one kin_integrate per request on one stream, each waited for."""
+    device = device or torch.device("cuda")
+    stream = torch.cuda.Stream(device=device)
+    todo = sorted(requests, key=lambda r: r.arrival)
+    ws: Dict[str, torch.Tensor] = {}
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for r in todo:
+            while time.perf_counter() - t0 < r.arrival:
+                time.sleep(20e-6)
+            g = groups[r.group]
+            n, nS = r.cells, g.mech.n_species
+            r.t_launch = time.perf_counter() - t0
+            Td = torch.empty(n, dtype=torch.float64, device=device)
+            pd = torch.empty(n, dtype=torch.float64, device=device)
+            Yd = torch.empty((nS, n), dtype=torch.float64, device=device)
+            sd = torch.empty(n, dtype=torch.uint8, device=device)
+            _h2d(Td, r.T)
+            _h2d(pd, r.p)
+            _h2d(Yd, r.Y)
+            need = g.mech.workspace_bytes(g.method, g.precision, n)
+            if r.group not in ws or ws[r.group].numel() < need:
+                ws[r.group] = torch.empty(need, dtype=torch.uint8, device=device)
+            kin.integrate(g.mech, Td, pd, Yd, r.dt, r.rtol, r.atol, g.method, g.precision,
+                          status=sd, workspace=ws[r.group], stream=stream)
+            r.Y_out = torch.empty((nS, n), dtype=torch.float64, pin_memory=True)
+            r.status = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+            r.Y_out.copy_(Yd, non_blocking=True)
+            r.status.copy_(sd, non_blocking=True)
+            stream.synchronize()
+            r.t_done = time.perf_counter() - t0
+    return todo
+
+
+# ------------------------------------------------------- serving workload --
+class StatePool:
+    """Pinned, species-major pool of seeded initial states per mechanism;
+    a request of n cells views n consecutive pool cells."""
+
+    def __init__(self, name: str, mech, cells: int, seed_offset: int = 500):
+        T, p, Y = synth.workload_states(name, mech, cells=cells, seed_offset=seed_offset)
+        self.T = torch.as_tensor(T).pin_memory()
+        self.p = torch.as_tensor(p).pin_memory()
+        self.Y = torch.as_tensor(Y).contiguous().pin_memory()
+        self.cells = cells
+
+    def view(self, off: int, n: int):
+        return self.T[off:off + n], self.p[off:off + n], self.Y[:, off:off + n]
+
+
+def make_requests(n: int, pools: Dict[str, StatePool], seed: int = 3005, loads_rate=None):
+    """The serving workload (Section 3 setup recast as requests): mechanism
+    13- or 53-species (p = 0.5), cells log-uniform in [1024, 65536], dt
+    log-uniform in [1e-7, 1e-5] s, rtol 1e-6. Arrival times are 0 unless a
+    Poisson rate (requests/s) is given."""
+    spec = synth.serve_requests(n, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    t = 0.0
+    out = []
+    for i, (g, cells, dt) in enumerate(spec):
+        pool = pools[g]
+        off = int(rng.integers(0, pool.cells - cells + 1))
+        T, p, Y = pool.view(off, cells)
+        if loads_rate:
+            t += rng.exponential(1.0 / loads_rate)
+        out.append(Request(i, g, T, p, Y, dt, arrival=t))
+    return out
+
+
+def percentiles(reqs: List[Request]):
+    lat = np.array([r.latency for r in reqs])
+    cells = sum(r.cells for r in reqs)
+    span = max(r.t_done for r in reqs) - min(r.arrival for r in reqs)
+    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "throughput_cells_per_s": cells / span, "requests": len(reqs), "cells": int(cells)}
+
+
+def default_groups(blocks_per_sm: int = 2):
+    groups, pools = {}, {}
+    for name in ("h2co_13sp_rkc", "ch4_53sp_rkc_mixed"):
+        w = synth.WORKLOADS[name]
+        m = synth.workload_mechanism(name)
+        groups[name] = Group(kin.Mechanism(m), w["method"], w["precision"], blocks_per_sm)
+        pools[name] = StatePool(name, m, 65536 + 1024)
+    return groups, pools
+
+
+def main():
+    ap = argparse.ArgumentParser(description="continuous-batching serving benchmark")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--loads", default="0.5,0.8,0.95")
+    ap.add_argument("--budget-gb", type=float, default=16.0)
+    ap.add_argument("--slots", type=int, default=2)
+    ap.add_argument("--blocks-per-sm", type=int, default=2)
+    args = ap.parse_args()
+    from . import build as _b
+    _b.build()
+    groups, pools = default_groups(args.blocks_per_sm)
+    budget = int(args.budget_gb * (1 << 30))
+    # warm up both paths (module loads, workspaces, pinned pools)
+    warm = make_requests(8, pools, seed=7)
+    Server(groups, budget, args.slots).run(warm)
+    one_launch_per_request(groups, make_requests(4, pools, seed=8))
+    torch.cuda.synchronize()
+    # saturated throughput: everything arrives at t = 0
+    sat_reqs = make_requests(args.requests, pools)
+    srv = Server(groups, budget, args.slots)
+    sat = percentiles(srv.run(sat_reqs))
+    mean_cells = np.mean([r.cells for r in sat_reqs])
+    out = {"saturated": sat, "loads": []}
+    for load in [float(x) for x in args.loads.split(",") if x]:
+        rate = load * sat["throughput_cells_per_s"] / mean_cells
+        a = percentiles(Server(groups, budget, args.slots).run(make_requests(args.requests, pools,
+                                                                             loads_rate=rate)))
+        b = percentiles(one_launch_per_request(groups, make_requests(args.requests, pools,
+                                                                     loads_rate=rate)))
+        out["loads"].append({"load": load, "offered_requests_per_s": rate,
+                             "continuous_batching": a, "one_launch_per_request": b})
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

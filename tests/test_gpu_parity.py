@@ -11,7 +11,7 @@ torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
 from paper_1309_2710_gb300 import synth  # noqa: E402
-from tests.parity import compare, rel_err  # noqa: E402
+from tests.parity import compare, rel_err, tol_rel_err  # noqa: E402
 
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no CUDA device", allow_module_level=True)
@@ -122,12 +122,9 @@ def test_rkc_h2co_full_size_sampled():
 
 def test_rkc_mixed_ch4_sampled():
     """53 species / 634 reactions, FP32 rates, FP64 state, against the FP64
-    oracle. The integrator controls each species to atol + rtol |Y| per step,
-    i.e. relatively only where |Y| >= atol/rtol (1e-4). There the mixed path
-    must be within 1e-5 relative; below it within atol absolute. (Two FP64
-    runs whose rtol differs by 1% already differ by ~2e-4 relative on species
-    near atol, so a relative bound there measures the integrator's own
-    step-sequence sensitivity, not precision.)"""
+    oracle: per-species relative error (scale max(|Y|, atol/rtol), the
+    integrator's own weighting) within 1e-5. The traces differ (the FP32 rates
+    move error estimates), so this compares two valid RKC solutions."""
     name = "ch4_53sp_rkc_mixed"
     w = synth.WORKLOADS[name]
     m, km, om = mech(name)
@@ -138,13 +135,11 @@ def test_rkc_mixed_ch4_sampled():
                                         w["atol"], oracle.RKC)
     assert (stg[idx] == sto).all()
     Yg = Yg[:, idx]
-    big = np.abs(Yo) >= w["atol"] / w["rtol"]
-    rel = np.abs(Yg - Yo)[big] / np.abs(Yo)[big]
-    small = np.abs(Yg - Yo)[~big]
-    print("mixed ch4: rel err (|Y| >= 1e-4) %.3e, abs err below %.3e, atol-floored %.3e"
-          % (rel.max(), small.max(), rel_err(Yg, Yo, w["atol"]).max()))
-    assert rel.max() <= 1e-5
-    assert small.max() <= w["atol"]
+    e = tol_rel_err(Yg, Yo, w["atol"], w["rtol"])
+    per_species = e.max(axis=1)
+    print("mixed ch4: max %.3e, per species %s; error relative to max(|Y|, atol) %.3e"
+          % (e.max(), np.array2string(per_species, precision=1), rel_err(Yg, Yo, w["atol"]).max()))
+    assert e.max() <= 1e-5
 
 
 def test_rkc_ch4_fp64_sampled():
@@ -225,7 +220,13 @@ def test_step_limit_keeps_last_accepted_state():
     Yo, sto, stao, _ = oracle.integrate(om, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKC,
                                         max_steps=3)
     assert (stg == kin.CELL_MAXSTEPS).all()
-    compare(Yg, Yo, stg, sto, stag, stao, w["atol"], w["rtol"])
+    # Stopped after three steps, the time reached depends continuously on the
+    # finite-difference spectral radius through h1. Rounding differences in f
+    # of order 1e-16 of its largest terms become up to ~1e-5 of a Jacobian
+    # entry (they are divided by eps ~ 1.5e-8 |y|), so the state is compared
+    # at the trace-divergent tolerance here; the decision trace is exact.
+    assert (stag == stao).all()
+    compare(Yg, Yo, stg, sto, stag, stao, w["atol"], w["rtol"], tol=10 * w["rtol"])
 
 
 @pytest.mark.parametrize("method", [kin.RKCK, kin.RKC])
@@ -300,3 +301,29 @@ def test_batch_in_cuda_graph():
         for c, e in zip(parts, eager):
             assert torch.equal(c.Y, e)
             assert int(c.status.max()) == 0
+
+
+@pytest.mark.parametrize("method,name", [(kin.RKC, "h2co_13sp_rkc"), (kin.RKCK, "h2_9sp_rkck"),
+                                         (kin.RKC, "ch4_53sp_rkc_mixed")])
+def test_launch_shapes_are_bitwise_identical(method, name):
+    """Block size, blocks per SM and shared-memory staging change where the
+    per-lane arrays live and which lane takes a cell, never the arithmetic."""
+    w = synth.WORKLOADS[name]
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m, cells=1500, seed_offset=11)
+    prec = w["precision"]
+    ref = None
+    for shape in [dict(), dict(block_threads=64, blocks_per_sm=1),
+                  dict(block_threads=32, blocks_per_sm=3, staging=kin.STAGE_SHARED),
+                  dict(block_threads=64, blocks_per_sm=1, staging=kin.STAGE_SHARED_ALL)]:
+        Yd = dev(Y)
+        try:
+            kin.integrate(km, dev(T), dev(p), Yd, w["dt"], w["rtol"], w["atol"], method, prec, **shape)
+        except kin.KinError as e:
+            assert e.code == kin.KIN_EUNSUPPORTED  # staging that does not fit
+            continue
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = Yd
+        else:
+            assert torch.equal(Yd, ref), shape
