@@ -255,7 +255,7 @@ def run_kin(args):
     Yd = torch.empty_like(Y0d)
     st = torch.zeros(cells, dtype=torch.uint8, device=dev)
     sta = torch.zeros((cells, 4), dtype=torch.int32, device=dev)
-    shape = dict(block_threads=0, blocks_per_sm=0, staging=kin.STAGE_GLOBAL)
+    shape = dict(block_threads=0, blocks_per_sm=0, staging=kin.STAGE_GLOBAL, occupancy=kin.OCC_DEFAULT)
     if not args.no_tune:
         # launch shape from the autotuner (cached per GPU and mechanism shape),
         # timed on the first 65536 cells, outside the timed region

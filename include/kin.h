@@ -60,6 +60,10 @@ extern "C" {
 #define KIN_STAGE_SHARED 1     /* concentrations and rates of progress in shared memory */
 #define KIN_STAGE_SHARED_ALL 2 /* ... and the cell's rate constants too */
 
+/* kernel register budget */
+#define KIN_OCC_DEFAULT 0
+#define KIN_OCC_HIGH 1
+
 /* per-cell status */
 #define KIN_CELL_OK 0
 #define KIN_CELL_MAXSTEPS 1  /* attempted-step limit reached */
@@ -104,11 +108,15 @@ typedef struct {
     int32_t precision;     /* KIN_FP64 or KIN_MIXED */
     int32_t max_steps;     /* attempted steps per cell; <= 0 means 100000 */
     int32_t block_threads; /* threads per block, multiple of 32; 0 = library choice */
-    int32_t blocks_per_sm; /* persistent blocks per SM; 0 = as many as fit (<= 512 threads/SM) */
+    int32_t blocks_per_sm; /* persistent blocks per SM; 0 = as many as fit (<= 512 threads per
+                              SM, 768 with KIN_OCC_HIGH) */
     int32_t staging;       /* KIN_STAGE_*: where f's per-lane arrays live. Shared staging
                               needs (n_species + n_reactions) [+ n_reactions + n_falloff
                               for SHARED_ALL] x block_threads elements of the rate type
                               per block; KIN_EUNSUPPORTED if that does not fit */
+    int32_t occupancy;     /* KIN_OCC_DEFAULT: kernel built for up to 16 resident warps per
+                              SM; KIN_OCC_HIGH: built with a register cap for 24 */
+    int32_t reserved;      /* must be 0 */
     void *stream;          /* cudaStream_t */
 } kin_opts;
 

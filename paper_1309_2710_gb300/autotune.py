@@ -29,12 +29,13 @@ def _key(mech: kin.Mechanism, method: int, precision: int, desc) -> str:
 
 
 def candidates():
-    for staging in (kin.STAGE_GLOBAL, kin.STAGE_SHARED, kin.STAGE_SHARED_ALL):
-        for threads in (128, 64, 32):
-            for bps in (1, 2, 3, 4, 6, 8, 12, 16):
-                if threads * bps > 1024:
-                    continue
-                yield dict(block_threads=threads, blocks_per_sm=bps, staging=staging)
+    for occupancy in (kin.OCC_DEFAULT, kin.OCC_HIGH):
+        for staging in (kin.STAGE_GLOBAL, kin.STAGE_SHARED, kin.STAGE_SHARED_ALL):
+            for threads in (128, 64, 32):
+                for lanes in (256, 384, 512, 640, 768):
+                    bps = lanes // threads
+                    yield dict(block_threads=threads, blocks_per_sm=bps, staging=staging,
+                               occupancy=occupancy)
 
 
 def time_config(mech, T, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2) -> Optional[float]:
@@ -43,7 +44,7 @@ def time_config(mech, T, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2) 
     cells = int(T.numel())
     try:
         ws = mech.workspace(method, precision, cells, cfg["block_threads"], cfg["blocks_per_sm"],
-                            T.device, cfg["staging"])
+                            T.device, cfg["staging"], cfg["occupancy"])
     except kin.KinError:
         return None
     Y = torch.empty_like(Y0)

@@ -76,11 +76,11 @@ int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
                         smem_bytes(m->dev, o->precision, threads, stg), maxsm);
     }
     int occ = 0;
-    e = integrate_occupancy(m->dev, o->method, o->precision, stg, threads, &occ);
+    e = integrate_occupancy(m->dev, o->method, o->precision, stg, o->occupancy, threads, &occ);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (occ < 1) return fail(KIN_EUNSUPPORTED, "kernel does not fit on an SM with these options");
     int bps = o->blocks_per_sm;
-    if (bps <= 0) bps = std::max(1, std::min(occ, 512 / threads));
+    if (bps <= 0) bps = std::max(1, std::min(occ, (o->occupancy ? 768 : 512) / threads));
     if (bps > occ) return fail(KIN_EINVAL, "blocks_per_sm %d exceeds the %d blocks that fit per SM", bps, occ);
     g->threads = threads;
     g->blocks = nsm * bps;
@@ -102,12 +102,24 @@ int check_opts(const kin_opts* o)
     if (o->staging != KIN_STAGE_GLOBAL && o->staging != KIN_STAGE_SHARED &&
         o->staging != KIN_STAGE_SHARED_ALL)
         return fail(KIN_EINVAL, "unknown staging %d", o->staging);
+    if (o->occupancy != KIN_OCC_DEFAULT && o->occupancy != KIN_OCC_HIGH)
+        return fail(KIN_EINVAL, "unknown occupancy %d", o->occupancy);
+    if (o->reserved != 0) return fail(KIN_EINVAL, "opts.reserved must be 0");
     return KIN_OK;
 }
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 }  // namespace
+
+int kin::set_last_error(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
 
 extern "C" {
 
@@ -332,7 +344,7 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     cudaStream_t st = (cudaStream_t)o->stream;
     cudaError_t e = cudaMemsetAsync(base + w.header, 0, 512, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    e = launch_integrate(P, o->staging, blocks, g.threads, st);
+    e = launch_integrate(P, o->staging, o->occupancy, blocks, g.threads, st);
     if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
     return KIN_OK;
 }
@@ -405,7 +417,7 @@ int kin_rates(const kin_mech* m, int64_t cells, const double* T, const double* p
     if (ldY > INT32_MAX) return fail(KIN_EINVAL, "ldY >= 2^31");
     if (!is_device_ptr(T) || !is_device_ptr(p) || !is_device_ptr(Y) || !is_device_ptr(dYdt))
         return fail(KIN_EINVAL, "T, p, Y and dYdt must be device memory");
-    kin_opts o{KIN_RKC, precision, 0, 0, 0, KIN_STAGE_GLOBAL, stream};
+    kin_opts o{KIN_RKC, precision, 0, 0, 0, KIN_STAGE_GLOBAL, KIN_OCC_DEFAULT, 0, stream};
     Grid g;
     int rc = grid_for(m, &o, &g);
     if (rc) return rc;

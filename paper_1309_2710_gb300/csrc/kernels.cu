@@ -1,316 +1,10 @@
-// kernels.cu -- sm_103a kernels of the batched kinetics integrator.
-//
-// Design (one GB300; FP64 runs at 1/64 of the FP32 rate, so the FP64 pipe,
-// not HBM, bounds this path):
-//  * One lane integrates one cell, as in the paper's thread-per-ODE design
-//    (Section 3), but each loop iteration of a lane performs exactly ONE
-//    evaluation of f. The method's control flow (RKCK stages, RKC stages,
-//    finite-difference Jacobian columns, accept/reject) is a per-lane state
-//    machine around that single call, so lanes of a warp in different phases
-//    or on cells with different stage counts still execute f together;
-//    divergence costs only the per-phase bookkeeping.
-//  * A uniform pre-pass (init_kernel) does, for every cell and in lockstep
-//    across the warp, the work every cell needs before its first step: the
-//    rate constants (T is fixed over the flow step), f(y0), and for RKC the
-//    Gershgorin spectral radius and the initial step of Section 2.3. The
-//    initial step predicts a cell's cost (steps ~ dt/h1), so cells are bucket
-//    sorted longest-first before the main kernel: longest-processing-time
-//    order keeps the persistent grid's tail short.
-//  * The main kernel is persistent: lanes pull cells from a warp-aggregated
-//    atomic queue in that order and a lane that finishes its cell takes the
-//    next one immediately.
-//  * Working arrays are element-major in the workspace (coalesced per warp).
-//  * f (Section 2.1): concentrations from the ideal gas law, Omega_j from the
-//    stored rate constants, third-body and Lindemann falloff factors, and the
-//    stoichiometric sum as a gather over a species-major CSR of net
-//    coefficients (no scattered read-modify-write). Template parameter R is
-//    the rate arithmetic type: double, or float for the mixed-precision path
-//    (state, stage accumulation, norm and control stay double).
-//  * No tensor cores: the stoichiometric contraction is sparse (about four
-//    nonzeros per reaction).
-#include <cuda_runtime.h>
-
-#include <cmath>
-#include <cstdint>
-
-#include "kin_dev.cuh"
+// kernels.cu -- non-template kernels and host launchers of the integrator:
+// the f-alone kernel, the RKC coefficient table, the longest-first bucket
+// sort, workspace layout, and dispatch to the per-method/precision
+// instantiations (inst_*.cu).
+#include "kernels.cuh"
 
 namespace kin {
-
-// ---------------------------------------------------------------- helpers --
-template <typename T>
-struct Lane {
-    T* p;
-    int32_t s;  // stride between elements (lanes or cells, < 2^31)
-    __device__ __forceinline__ T& operator[](int i) const { return p[(int64_t)i * s]; }
-};
-
-template <typename R>
-struct Tab;
-template <>
-struct Tab<double> {
-    __device__ static const double* invW(const MechDev& M) { return M.invW; }
-    __device__ static const double* eff(const MechDev& M) { return M.eff; }
-    __device__ static const double* nu(const MechDev& M) { return M.csr_nu; }
-    __device__ static double ex(double a) { return exp(a); }
-    static constexpr double sqrt_u = 1.4901161193847656e-08;  // sqrt(2^-52)
-};
-template <>
-struct Tab<float> {
-    __device__ static const float* invW(const MechDev& M) { return M.invW32; }
-    __device__ static const float* eff(const MechDev& M) { return M.eff32; }
-    __device__ static const float* nu(const MechDev& M) { return M.csr_nu32; }
-    // exp in FP32 after an exact split a = n ln2 + r formed in FP64, so the
-    // FP32 rounding of a large exponent (|a| ~ 40) does not cost 2e-6
-    // relative accuracy: k = 2^n expf(r) with |r| <= ln2/2.
-    __device__ static float ex(double a)
-    {
-        const double n = rint(a * 1.4426950408889634);
-        const float r = (float)fma(-n, 0.6931471805599453, a);
-        return ldexpf(expf(r), (int)n);
-    }
-    static constexpr double sqrt_u = 3.4526698300124393e-04;  // sqrt(2^-23)
-};
-
-// Rate constants of one cell (Eq. (E:rxn-const)); T is fixed for the call.
-// K_j = exp(ln A_j + beta_j ln T - (Ea_j/R)/T); for falloff reactions
-// KR_fo = k_0/k_inf. The exponent is formed in double; the exp runs in R.
-template <typename R>
-__device__ void rate_constants(const MechDev& M, double T, Lane<R> K, Lane<R> KR)
-{
-    const double lnT = log(T), invT = 1.0 / T;
-    for (int j = 0; j < M.nR; ++j) {
-        const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
-        K[j] = Tab<R>::ex(a);
-        const int fo = M.rxn[j].fo;
-        if (fo >= 0) {
-            const double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
-            KR[fo] = Tab<R>::ex(a0 - a);
-        }
-    }
-}
-
-// f(x) -> out (Eqs. (E:mass), (E:spec-rate), (E:rxn-rate)). Ctot = p/(R T) in
-// mol/cm^3, invCtot its inverse. C and OM are lane scratch (nS and nR).
-template <typename R>
-__device__ void feval(const MechDev& M, double Ctot, double invCtot, Lane<R> K, Lane<R> KR,
-                      Lane<R> C, Lane<R> OM, Lane<double> x, Lane<double> out)
-{
-    const int nS = M.nS, nR = M.nR;
-    const R* __restrict__ invW = Tab<R>::invW(M);
-    // mixture: S = sum Y/W = 1/Wbar, rho = Ctot Wbar, C_k = rho Y_k / W_k
-    R S = R(0);
-    for (int i = 0; i < nS; ++i) {
-        const R m = (R)x[i] * invW[i];
-        C[i] = m;
-        S += m;
-    }
-    const R invS = R(1) / S;
-    const R rho = (R)Ctot * invS;
-    for (int i = 0; i < nS; ++i) C[i] = C[i] * rho;
-    // rates of progress
-    const R* __restrict__ eff = Tab<R>::eff(M);
-    for (int j = 0; j < nR; ++j) {
-        const Rxn r = M.rxn[j];
-        R q = K[j];
-        if (r.r0 >= 0) q *= C[r.r0];
-        if (r.r1 >= 0) q *= C[r.r1];
-        if (r.type != KIN_RXN_PLAIN) {
-            const R* a = eff + (int64_t)r.row * nS;
-            R Mc = R(0);
-            for (int i = 0; i < nS; ++i) Mc += a[i] * C[i];
-            if (r.type == KIN_RXN_THIRD_BODY) {
-                q *= Mc;
-            } else {
-                const R Pr = KR[r.fo] * Mc;
-                q *= Pr / (R(1) + Pr);
-            }
-        }
-        OM[j] = q;
-    }
-    // omega_i = sum_j nu_ij Omega_j (gather); dY_i/dt = W_i omega_i / rho
-    const R* __restrict__ nu = Tab<R>::nu(M);
-    const double invrho = (double)S * invCtot;
-    for (int i = 0; i < nS; ++i) {
-        R w = R(0);
-        const int e1 = M.csr_ptr[i + 1];
-        for (int e = M.csr_ptr[i]; e < e1; ++e) w += nu[e] * OM[M.csr_rxn[e]];
-        out[i] = (double)w * (M.W[i] * invrho);
-    }
-}
-
-__device__ __forceinline__ int find_inst(const Launch& L, long long g)
-{
-    int lo = 0, hi = L.n_inst - 1;
-    while (lo < hi) {  // largest i with start[i] <= g
-        const int mid = (lo + hi + 1) >> 1;
-        if (L.start[mid] <= g) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Warp-aggregated pop of the next queue position for every active lane.
-__device__ __forceinline__ long long pop_cell(unsigned long long* q)
-{
-    const unsigned mask = __activemask();
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    const int rank = __popc(mask & ((1u << lane) - 1u));
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(q, (unsigned long long)__popc(mask));
-    base = __shfl_sync(mask, base, leader);
-    return (long long)(base + rank);
-}
-
-// Vector slots of a lane's working set.
-enum Vec : int { V_Y = 0, V_F0, V_A, V_B, V_C, V_X, V_FX, V_RS };
-// RKCK reuses slots: F[1..5] = V_A, V_B, V_C, V_FX, V_RS; the stage point is V_X.
-
-extern __shared__ __align__(16) unsigned char kin_smem[];
-
-// Per-lane views of the workspace. Staging level STG places the arrays f
-// touches most in shared memory, element-major across the block
-// ([element][thread]): 1 = concentrations and rates of progress, 2 = also
-// the cell's rate constants. Otherwise they live in the lane's slice of the
-// workspace ([element][lane]): C [nS], Omega [nR], k [nR], k0/kinf [nFO].
-template <typename R, int STG>
-struct Views {
-    const Launch& L;
-    const MechDev& M;
-    int64_t slot;
-    Lane<R> C, OM, Kl, KRl;
-    double* vbase;
-    __device__ Views(const Launch& l, int64_t sl) : L(l), M(l.M), slot(sl)
-    {
-        R* rb = reinterpret_cast<R*>(L.lane_r) + sl;
-        const int64_t ns = L.nslots;
-        R* sb = reinterpret_cast<R*>(kin_smem) + threadIdx.x;
-        const int64_t bs = blockDim.x;
-        if (STG >= 1) {
-            C = Lane<R>{sb, (int32_t)bs};
-            OM = Lane<R>{sb + (int64_t)M.nS * bs, (int32_t)bs};
-        } else {
-            C = Lane<R>{rb, (int32_t)ns};
-            OM = Lane<R>{rb + (int64_t)M.nS * ns, (int32_t)ns};
-        }
-        if (STG >= 2) {
-            Kl = Lane<R>{sb + (int64_t)(M.nS + M.nR) * bs, (int32_t)bs};
-            KRl = Lane<R>{sb + (int64_t)(M.nS + 2 * M.nR) * bs, (int32_t)bs};
-        } else {
-            Kl = Lane<R>{rb + (int64_t)(M.nS + M.nR) * ns, (int32_t)ns};
-            KRl = Lane<R>{rb + (int64_t)(M.nS + 2 * M.nR) * ns, (int32_t)ns};
-        }
-        vbase = L.vec + sl;
-    }
-    __device__ __forceinline__ Lane<double> V(int v) const
-    {
-        return Lane<double>{vbase + (int64_t)v * M.nS * L.nslots, (int32_t)L.nslots};
-    }
-    __device__ __forceinline__ Lane<R> K(int64_t g) const
-    {
-        return Lane<R>{reinterpret_cast<R*>(L.cell_k) + g, (int32_t)L.total};
-    }
-    __device__ __forceinline__ Lane<R> KR(int64_t g) const
-    {
-        return Lane<R>{reinterpret_cast<R*>(L.cell_k) + (int64_t)M.nR * L.total + g, (int32_t)L.total};
-    }
-    __device__ __forceinline__ Lane<double> F0cell(int64_t g) const
-    {
-        return Lane<double>{L.cell_f0 + g, (int32_t)L.total};
-    }
-};
-
-// Weighted RMS norm, Eq. (E:rmsE), of d with T_i = atol + rtol max(|a|,|b|).
-__device__ __forceinline__ double rms(int n, double rtol, double atol, Lane<double> d,
-                                      Lane<double> a, Lane<double> b)
-{
-    double acc = 0.0;
-    for (int i = 0; i < n; ++i) {
-        const double sc = atol + rtol * fmax(fabs(a[i]), fabs(b[i]));
-        const double r = d[i] / sc;
-        acc += r * r;
-    }
-    return sqrt(acc / n);
-}
-
-// ------------------------------------------------------------- pre-pass --
-// For every cell g (grid-stride, uniform across lanes): rate constants, f(y0),
-// and for RKC the Gershgorin bound on the FD Jacobian (Section 2.3) and the
-// initial step h1 = 0.1 h0 / ||Delta_0||^(1/2), h0 = 1/sigma.
-template <int METHOD, typename R, int STG>
-__global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launch L)
-{
-    const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= L.nslots) return;
-    Views<R, STG> W(L, slot);
-    const MechDev& M = L.M;
-    const int nS = M.nS;
-    for (int64_t g = slot; g < L.total; g += L.nslots) {
-        const int ii = find_inst(L, g);
-        const InstDev& I = L.inst[ii];
-        const int64_t c = g - L.start[ii];
-        const double T = I.T[c], p = I.p[c];
-        const double Ctot = p * 1e-6 / (R_GAS * T), invCtot = 1.0 / Ctot;
-        Lane<R> K = W.K(g), KR = W.KR(g);
-        rate_constants<R>(M, T, K, KR);
-        Lane<double> Y = W.V(V_Y), F0 = W.F0cell(g), X = W.V(V_X), FX = W.V(V_FX), RS = W.V(V_RS);
-        bool ok = true;
-        for (int i = 0; i < nS; ++i) {
-            const double y = I.Y[(int64_t)i * I.ldY + c];
-            Y[i] = y;
-            X[i] = y;
-            RS[i] = 0.0;
-        }
-        feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, Y, F0);
-        for (int i = 0; i < nS; ++i) ok &= isfinite(F0[i]);
-        uint8_t st = ok ? 0 : KIN_CELL_NONFINITE;
-        double sigma = 0.0, h = I.dt;
-        int nfe = 1;
-        if (METHOD == KIN_RKC && ok) {
-            for (int k = 0; k < nS; ++k) {  // Gershgorin columns
-                const double eps = Tab<R>::sqrt_u * fmax(fabs(Y[k]), I.atol);
-                X[k] = Y[k] + eps;
-                feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, X, FX);
-                const double ie = 1.0 / eps;
-                for (int i = 0; i < nS; ++i) RS[i] += fabs((FX[i] - F0[i]) * ie);
-                X[k] = Y[k];
-            }
-            for (int i = 0; i < nS; ++i) sigma = fmax(sigma, RS[i]);
-            nfe += nS;
-            if (!isfinite(sigma)) {
-                st = KIN_CELL_NONFINITE;
-            } else {
-                double h0 = sigma > 0.0 ? 1.0 / sigma : I.dt;
-                if (h0 > I.dt) h0 = I.dt;
-                for (int i = 0; i < nS; ++i) X[i] = Y[i] + h0 * F0[i];
-                feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, X, FX);
-                nfe++;
-                for (int i = 0; i < nS; ++i) X[i] = h0 * (FX[i] - F0[i]);  // Delta_0
-                const double e0 = rms(nS, I.rtol, I.atol, X, Y, Y);
-                if (!isfinite(e0)) h = 0.1 * h0;
-                else h = e0 > 0.0 ? 0.1 * h0 / sqrt(e0) : I.dt;
-                if (h > I.dt) h = I.dt;
-                if (h < 1e-20 * I.dt) st = KIN_CELL_HMIN;
-            }
-        }
-        L.cell_sig[g] = sigma;
-        L.cell_h[g] = h;
-        L.cell_nfe[g] = nfe;
-        L.cell_st[g] = st;
-    }
-}
-
-// ----------------------------------------------- longest-first ordering --
-// Predicted cost of a cell: steps ~ dt/h1 (RKC). Bucket b >= 1 grows with
-// log2(1 + dt/h1) in quarter octaves; cells already finished go to bucket 0.
-__device__ __forceinline__ int cost_bucket(const Launch& L, int64_t g)
-{
-    if (L.cell_st[g] != 0) return 0;
-    const int ii = find_inst(L, g);
-    const double r = L.inst[ii].dt / L.cell_h[g];
-    const int b = 1 + (int)(4.0f * log2f(1.0f + (float)r));
-    return b < 1 ? 1 : (b > NBUCKET - 1 ? NBUCKET - 1 : b);
-}
 
 __global__ void bucket_count_kernel(const __grid_constant__ Launch L)
 {
@@ -345,404 +39,6 @@ __global__ void bucket_scatter_kernel(const __grid_constant__ Launch L)
         const unsigned pos = atomicAdd(&L.hist[cost_bucket(L, g)], 1u);
         L.order[pos] = (int32_t)g;
     }
-}
-
-// ------------------------------------------------------------ integrator --
-enum Phase : int {
-    PH_F0 = 0,   // RKCK: f at the current accepted state -> F0
-    PH_SIG,      // RKC: f at Y + eps_k e_k (Gershgorin column k) -> FX
-    PH_STAGE,    // RKC: f(w_{j-1}) -> FX, then w_j
-    PH_FINAL,    // RKC: f(w_s) -> FX, error estimate and control
-    PH_K,        // RKCK: f at a stage point -> F[st]
-};
-
-__constant__ double CK_B[6][5] = {
-    {0, 0, 0, 0, 0},
-    {1.0 / 5.0, 0, 0, 0, 0},
-    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0},
-    {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0, 0},
-    {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0},
-    {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0}};
-// fifth-order weights c_i and error weights c_i - c*_i (Table 1)
-__constant__ double CK_C[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
-__constant__ double CK_E[6] = {37.0 / 378.0 - 2825.0 / 27648.0, 0.0, 250.0 / 621.0 - 18575.0 / 48384.0,
-                               125.0 / 594.0 - 13525.0 / 55296.0, -277.0 / 14336.0,
-                               512.0 / 1771.0 - 1.0 / 4.0};
-
-__device__ __forceinline__ int ck_slot(int st)
-{
-    // F[0] lives in V_F0; F[1..5] in the slots listed above
-    return st == 0 ? V_F0 : (st <= 3 ? V_A + st - 1 : (st == 4 ? V_FX : V_RS));
-}
-
-struct LaneState {
-    long long g;     // global cell index
-    long long cell;  // index within the instance
-    int inst;
-    int phase, st, j, s, col;
-    int attempts, nacc, nrej, nsig, nfe;
-    int since_sigma;
-    bool last, last_rejected, have_prev, sigma_here;
-    int iw1, iw2;  // RKC: slots of w_{j-1}, w_{j-2}
-    double t, dt, h, hh, hprev, cprev, sigma, eps, rtol, atol, Ctot, invCtot;
-    int in_v, out_v;  // vectors read and written by the next f evaluation
-};
-
-template <int METHOD, typename R, int STG>
-struct Integrator {
-    Views<R, STG> W;
-    const Launch& L;
-    const MechDev& M;
-    Lane<R> K, KR;
-
-    __device__ Integrator(const Launch& l, int64_t sl) : W(l, sl), L(l), M(l.M) {}
-    __device__ __forceinline__ Lane<double> V(int v) const { return W.V(v); }
-
-    // ---------------------------------------------------------- cell I/O --
-    // Take the next cell; returns false when the queue is exhausted. A cell
-    // whose fate the pre-pass already decided is finished here directly.
-    __device__ bool load_next(LaneState& S)
-    {
-        for (;;) {
-            const long long q = pop_cell(L.queue);
-            if (q >= L.total) return false;
-            const long long g = (METHOD == KIN_RKC) ? (long long)L.order[q] : q;
-            const int i = find_inst(L, g);
-            const InstDev& I = L.inst[i];
-            S.g = g;
-            S.inst = i;
-            S.cell = g - L.start[i];
-            S.attempts = S.nacc = S.nrej = 0;
-            S.nsig = METHOD == KIN_RKC ? 1 : 0;
-            S.nfe = L.cell_nfe[g];
-            const uint8_t pre = L.cell_st[g];
-            if (pre != 0) {  // Y stays as given
-                finish_stats(S, pre);
-                continue;
-            }
-            const double T = I.T[S.cell], p = I.p[S.cell];
-            S.Ctot = p * 1e-6 / (R_GAS * T);
-            S.invCtot = 1.0 / S.Ctot;
-            // the cell's rate constants into the lane's (coalesced or shared) copy
-            K = W.Kl;
-            KR = W.KRl;
-            const Lane<R> Kc = W.K(g), KRc = W.KR(g);
-            for (int j = 0; j < M.nR; ++j) K[j] = Kc[j];
-            for (int j = 0; j < M.nFO; ++j) KR[j] = KRc[j];
-            Lane<double> Y = V(V_Y), F0 = V(V_F0), F0c = W.F0cell(g);
-            for (int k = 0; k < M.nS; ++k) {
-                Y[k] = I.Y[(int64_t)k * I.ldY + S.cell];
-                F0[k] = F0c[k];
-            }
-            S.dt = I.dt;
-            S.rtol = I.rtol;
-            S.atol = I.atol;
-            S.t = 0.0;
-            S.h = L.cell_h[g];
-            S.sigma = L.cell_sig[g];
-            S.since_sigma = 0;
-            S.last = false;
-            S.last_rejected = false;
-            S.have_prev = false;
-            S.sigma_here = true;
-            S.hprev = S.cprev = 0.0;
-            const int code = METHOD == KIN_RKC ? rkc_begin_step(S) : rkck_begin_attempt(S);
-            if (code < 0) return true;
-            store(S, code);
-        }
-    }
-
-    __device__ void finish_stats(const LaneState& S, int code)
-    {
-        const InstDev& I = L.inst[S.inst];
-        if (I.status) I.status[S.cell] = (uint8_t)code;
-        if (I.stats) {
-            int32_t* st = I.stats + 4 * S.cell;
-            st[0] = S.nfe;
-            st[1] = S.nacc;
-            st[2] = S.nrej;
-            st[3] = S.nsig;
-        }
-    }
-
-    __device__ void store(const LaneState& S, int code)
-    {
-        const InstDev& I = L.inst[S.inst];
-        Lane<double> Y = V(V_Y);
-        for (int k = 0; k < M.nS; ++k) I.Y[(int64_t)k * I.ldY + S.cell] = Y[k];
-        finish_stats(S, code);
-    }
-
-    // Start a Gershgorin estimate at Y: X = Y + eps_0 e_0, RS = 0.
-    __device__ void sigma_begin(LaneState& S)
-    {
-        Lane<double> Y = V(V_Y), X = V(V_X), RS = V(V_RS);
-        for (int i = 0; i < M.nS; ++i) {
-            X[i] = Y[i];
-            RS[i] = 0.0;
-        }
-        S.col = 0;
-        S.eps = Tab<R>::sqrt_u * fmax(fabs(Y[0]), S.atol);
-        X[0] = Y[0] + S.eps;
-        S.phase = PH_SIG;
-        S.in_v = V_X;
-        S.out_v = V_FX;
-    }
-
-    // Post-processing of one Gershgorin column. Returns true when sigma is done.
-    __device__ bool sigma_column(LaneState& S)
-    {
-        Lane<double> Y = V(V_Y), X = V(V_X), RS = V(V_RS), FX = V(V_FX), F0 = V(V_F0);
-        const double ie = 1.0 / S.eps;
-        for (int i = 0; i < M.nS; ++i) RS[i] += fabs((FX[i] - F0[i]) * ie);
-        X[S.col] = Y[S.col];
-        if (++S.col < M.nS) {
-            S.eps = Tab<R>::sqrt_u * fmax(fabs(Y[S.col]), S.atol);
-            X[S.col] = Y[S.col] + S.eps;
-            return false;
-        }
-        double sg = 0.0;
-        for (int i = 0; i < M.nS; ++i) sg = fmax(sg, RS[i]);
-        S.sigma = sg;
-        S.nsig++;
-        S.since_sigma = 0;
-        S.sigma_here = true;
-        return true;
-    }
-
-    // ------------------------------------------------------------- RKC ---
-    __device__ const double* coef(int s, int j) const
-    {
-        return M.rkc + ((int64_t)s * RKC_TAB_S + j) * RKC_TAB_W;
-    }
-
-    // Choose the next attempt (or a spectral-radius refresh). Returns a
-    // finish code >= 0 if the cell must stop, else -1.
-    __device__ int rkc_begin_step(LaneState& S)
-    {
-        if (S.attempts >= L.max_steps) return KIN_CELL_MAXSTEPS;
-        if (S.since_sigma >= 25 || (S.last_rejected && !S.sigma_here)) {
-            sigma_begin(S);
-            return -1;
-        }
-        double hh = S.h;
-        S.last = false;
-        if (hh >= S.dt - S.t) {
-            hh = S.dt - S.t;
-            S.last = true;
-        }
-        const double sr = floor(1.0 + sqrt(1.0 + 1.54 * hh * S.sigma));
-        int s;
-        if (sr < 2.0) {
-            s = 2;
-        } else if (sr > (double)SMAX) {
-            s = SMAX;
-            hh = ((SMAX - 1.0) * (SMAX - 1.0) - 1.0) / (1.54 * S.sigma);
-            S.last = false;
-        } else {
-            s = (int)sr;
-        }
-        S.hh = hh;
-        S.s = s;
-        // w_1 = y + mu~_1 h f_0 into slot A; w_0 = y stays in V_Y
-        const double m1 = coef(s, 1)[2] * hh;
-        Lane<double> Y = V(V_Y), F0 = V(V_F0), A = V(V_A);
-        for (int i = 0; i < M.nS; ++i) A[i] = Y[i] + m1 * F0[i];
-        S.iw1 = V_A;
-        S.iw2 = V_Y;
-        S.j = 2;
-        S.phase = PH_STAGE;
-        S.in_v = V_A;
-        S.out_v = V_FX;
-        return -1;
-    }
-
-    __device__ int rkc_post(LaneState& S)
-    {
-        if (S.phase == PH_STAGE) {
-            // FX = f(w_{j-1}); w_j = (1-mu-nu) y + mu w_{j-1} + nu w_{j-2}
-            //                       + mu~ h f_{j-1} + gamma~ h f_0
-            const double* c = coef(S.s, S.j);
-            const double mu = c[0], nu = c[1], mt = c[2] * S.hh, gt = c[3] * S.hh, c0 = c[4];
-            const int nw = (S.iw1 == V_A) ? V_B : (S.iw1 == V_B ? V_C : V_A);
-            Lane<double> Y = V(V_Y), F0 = V(V_F0), W1 = V(S.iw1), W2 = V(S.iw2), FJ = V(V_FX),
-                         WN = V(nw);
-            for (int i = 0; i < M.nS; ++i)
-                WN[i] = c0 * Y[i] + mu * W1[i] + nu * W2[i] + mt * FJ[i] + gt * F0[i];
-            S.iw2 = S.iw1;
-            S.iw1 = nw;
-            S.in_v = nw;
-            S.out_v = V_FX;
-            if (S.j == S.s) S.phase = PH_FINAL;
-            else S.j++;
-            return -1;
-        }
-        if (S.phase == PH_SIG) {
-            if (!sigma_column(S)) return -1;
-            if (!isfinite(S.sigma)) return KIN_CELL_NONFINITE;
-            return rkc_begin_step(S);
-        }
-        // PH_FINAL: error estimate (Section 2.3) and step control
-        Lane<double> Y = V(V_Y), F0 = V(V_F0), WS = V(S.iw1), FX = V(V_FX);
-        double acc = 0.0;
-        const double hh = S.hh;
-        for (int i = 0; i < M.nS; ++i) {
-            const double d = 0.8 * (Y[i] - WS[i]) + 0.4 * hh * (F0[i] + FX[i]);
-            const double sc = S.atol + S.rtol * fmax(fabs(Y[i]), fabs(WS[i]));
-            const double r = d / sc;
-            acc += r * r;
-        }
-        const double err = sqrt(acc / M.nS);
-        S.attempts++;
-        if (err <= 1.0) {
-            S.nacc++;
-            // err^(1/3) once; err^(2/3) = (err^(1/3))^2; the previous step's
-            // err^(1/3) is kept for the predictive factor.
-            const double c3 = cbrt(err);
-            double fac;
-            if (err == 0.0) fac = 10.0;
-            else if (S.have_prev && !S.last_rejected && S.cprev > 0.0)
-                fac = 0.8 * (hh / S.hprev) * S.cprev / (c3 * c3);
-            else fac = 0.8 / c3;
-            fac = fmin(10.0, fmax(0.1, fac));
-            for (int i = 0; i < M.nS; ++i) {
-                Y[i] = WS[i];
-                F0[i] = FX[i];
-            }
-            if (S.last) {
-                S.t = S.dt;
-                return KIN_CELL_OK;
-            }
-            S.t += hh;  // err <= 1 implies f(w_s) is finite
-            S.have_prev = true;
-            S.hprev = hh;
-            S.cprev = c3;
-            S.last_rejected = false;
-            S.sigma_here = false;
-            S.since_sigma++;
-            S.h = fac * hh;
-        } else {
-            S.nrej++;
-            double fac = isfinite(err) ? 0.8 / cbrt(err) : 0.1;
-            if (fac < 0.1) fac = 0.1;
-            S.last_rejected = true;
-            S.h = fac * hh;
-            if (S.h < 1e-20 * S.dt) return KIN_CELL_HMIN;
-        }
-        return rkc_begin_step(S);
-    }
-
-    // ------------------------------------------------------------ RKCK ---
-    // Form stage point st (1..5): X = Y + hh sum_{l<st} b_{st,l} F_l.
-    __device__ void rkck_stage_point(LaneState& S, int st)
-    {
-        Lane<double> Y = V(V_Y), X = V(V_X);
-        for (int i = 0; i < M.nS; ++i) {
-            double acc = 0.0;
-            for (int l = 0; l < st; ++l) acc += CK_B[st][l] * V(ck_slot(l))[i];
-            X[i] = Y[i] + S.hh * acc;
-        }
-        S.st = st;
-        S.phase = PH_K;
-        S.in_v = V_X;
-        S.out_v = ck_slot(st);
-    }
-
-    __device__ int rkck_begin_attempt(LaneState& S)
-    {
-        if (S.attempts >= L.max_steps) return KIN_CELL_MAXSTEPS;
-        double hh = S.h;
-        S.last = false;
-        if (hh >= S.dt - S.t) {
-            hh = S.dt - S.t;
-            S.last = true;
-        }
-        S.hh = hh;
-        rkck_stage_point(S, 1);
-        return -1;
-    }
-
-    __device__ int rkck_post(LaneState& S)
-    {
-        if (S.phase == PH_F0) {
-            if (!finite_vec(V_F0)) return KIN_CELL_NONFINITE;
-            return rkck_begin_attempt(S);
-        }
-        if (S.st < 5) {
-            rkck_stage_point(S, S.st + 1);
-            return -1;
-        }
-        // all six derivatives known: y5, error, errmax (Section 2.2)
-        Lane<double> Y = V(V_Y), F0 = V(V_F0), X = V(V_X);
-        const double hh = S.hh;
-        double errmax = 0.0;
-        for (int i = 0; i < M.nS; ++i) {
-            double s5 = 0.0, e = 0.0;
-            for (int l = 0; l < 6; ++l) {
-                const double f = V(ck_slot(l))[i];
-                s5 += CK_C[l] * f;
-                e += CK_E[l] * f;
-            }
-            X[i] = Y[i] + hh * s5;
-            const double tol = S.rtol * (fabs(Y[i]) + fabs(hh * F0[i])) + S.atol;
-            const double r = fabs(hh * e) / tol;
-            if (!(r <= errmax)) errmax = r;
-        }
-        S.attempts++;
-        if (errmax <= 1.0) {
-            S.nacc++;
-            for (int i = 0; i < M.nS; ++i) Y[i] = X[i];
-            if (S.last) {
-                S.t = S.dt;
-                return KIN_CELL_OK;
-            }
-            S.t += hh;
-            const double hn = errmax == 0.0 ? 5.0 * hh : 0.9 * hh * pow(errmax, -0.2);
-            S.h = fmin(hn, 5.0 * hh);
-            S.phase = PH_F0;
-            S.in_v = V_Y;
-            S.out_v = V_F0;
-            return -1;
-        }
-        S.nrej++;
-        const double hn = isfinite(errmax) ? 0.9 * hh * pow(errmax, -0.25) : 0.1 * hh;
-        S.h = fmax(hn, 0.1 * hh);
-        if (S.h < 1e-20 * S.dt) return KIN_CELL_HMIN;
-        return rkck_begin_attempt(S);
-    }
-
-    __device__ bool finite_vec(int v) const
-    {
-        Lane<double> a = V(v);
-        bool ok = true;
-        for (int i = 0; i < M.nS; ++i) ok &= isfinite(a[i]);
-        return ok;
-    }
-
-    // --------------------------------------------------------- main loop --
-    __device__ void run()
-    {
-        LaneState S;
-        if (!load_next(S)) return;
-        for (;;) {
-            feval<R>(M, S.Ctot, S.invCtot, K, KR, W.C, W.OM, V(S.in_v), V(S.out_v));
-            S.nfe++;
-            const int code = METHOD == KIN_RKC ? rkc_post(S) : rkck_post(S);
-            if (code >= 0) {
-                store(S, code);
-                if (!load_next(S)) return;
-            }
-        }
-    }
-};
-
-template <int METHOD, typename R, int STG>
-__global__ void __launch_bounds__(128) integrate_kernel(const __grid_constant__ Launch L)
-{
-    const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= L.nslots) return;
-    Integrator<METHOD, R, STG> I(L, slot);
-    I.run();
 }
 
 // ------------------------------------------------------------- f alone ---
@@ -841,75 +137,34 @@ size_t smem_bytes(const MechDev& M, int precision, int threads, int stg)
     return n * threads * (precision == KIN_MIXED ? 4 : 8);
 }
 
-template <int METHOD, typename R, int STG>
-static cudaError_t launch_all(Launch& L, int blocks, int threads, cudaStream_t st)
-{
-    const size_t sm = smem_bytes(L.M, L.precision, threads, STG);
-    if (STG > 0) {
-        cudaError_t e = cudaFuncSetAttribute(init_kernel<METHOD, R, STG>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(integrate_kernel<METHOD, R, STG>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-    }
-    init_kernel<METHOD, R, STG><<<blocks, threads, sm, st>>>(L);
-    if (METHOD == KIN_RKC) {
-        const int64_t nb = (L.total + 255) / 256;
-        const int sb = (int)(nb < 1024 ? nb : 1024);
-        bucket_count_kernel<<<sb, 256, 0, st>>>(L);
-        bucket_scan_kernel<<<1, 32, 0, st>>>(L.hist);
-        bucket_scatter_kernel<<<sb, 256, 0, st>>>(L);
-    }
-    integrate_kernel<METHOD, R, STG><<<blocks, threads, sm, st>>>(L);
-    return cudaGetLastError();
-}
-
-template <int METHOD, typename R>
-static cudaError_t launch_staged(Launch& L, int stg, int blocks, int threads, cudaStream_t st)
-{
-    if (stg == 2) return launch_all<METHOD, R, 2>(L, blocks, threads, st);
-    if (stg == 1) return launch_all<METHOD, R, 1>(L, blocks, threads, st);
-    return launch_all<METHOD, R, 0>(L, blocks, threads, st);
-}
-
-cudaError_t launch_integrate(Launch& L, int stg, int blocks, int threads, cudaStream_t st)
+cudaError_t launch_integrate(Launch& L, int stg, int occ, int blocks, int threads, cudaStream_t st)
 {
     if (L.method == KIN_RKCK)
-        return L.precision == KIN_MIXED ? launch_staged<KIN_RKCK, float>(L, stg, blocks, threads, st)
-                                        : launch_staged<KIN_RKCK, double>(L, stg, blocks, threads, st);
-    return L.precision == KIN_MIXED ? launch_staged<KIN_RKC, float>(L, stg, blocks, threads, st)
-                                    : launch_staged<KIN_RKC, double>(L, stg, blocks, threads, st);
+        return L.precision == KIN_MIXED ? launch_rkck_f32(L, stg, occ, blocks, threads, st)
+                                        : launch_rkck_f64(L, stg, occ, blocks, threads, st);
+    return L.precision == KIN_MIXED ? launch_rkc_f32(L, stg, occ, blocks, threads, st)
+                                    : launch_rkc_f64(L, stg, occ, blocks, threads, st);
 }
 
-template <int METHOD, typename R, int STG>
-static cudaError_t occ_one(int threads, size_t sm, int* bps)
-{
-    if (STG > 0) {
-        cudaError_t e = cudaFuncSetAttribute(integrate_kernel<METHOD, R, STG>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, integrate_kernel<METHOD, R, STG>, threads, sm);
-}
-
-template <int METHOD, typename R>
-static cudaError_t occ_staged(int stg, int threads, size_t sm, int* bps)
-{
-    if (stg == 2) return occ_one<METHOD, R, 2>(threads, sm, bps);
-    if (stg == 1) return occ_one<METHOD, R, 1>(threads, sm, bps);
-    return occ_one<METHOD, R, 0>(threads, sm, bps);
-}
-
-cudaError_t integrate_occupancy(const MechDev& M, int method, int precision, int stg, int threads,
-                                int* bps)
+cudaError_t integrate_occupancy(const MechDev& M, int method, int precision, int stg, int occ,
+                                int threads, int* bps)
 {
     const size_t sm = smem_bytes(M, precision, threads, stg);
     if (method == KIN_RKCK)
-        return precision == KIN_MIXED ? occ_staged<KIN_RKCK, float>(stg, threads, sm, bps)
-                                      : occ_staged<KIN_RKCK, double>(stg, threads, sm, bps);
-    return precision == KIN_MIXED ? occ_staged<KIN_RKC, float>(stg, threads, sm, bps)
-                                  : occ_staged<KIN_RKC, double>(stg, threads, sm, bps);
+        return precision == KIN_MIXED ? occ_rkck_f32(stg, occ, threads, sm, bps)
+                                      : occ_rkck_f64(stg, occ, threads, sm, bps);
+    return precision == KIN_MIXED ? occ_rkc_f32(stg, occ, threads, sm, bps)
+                                  : occ_rkc_f64(stg, occ, threads, sm, bps);
+}
+
+cudaError_t launch_sort(Launch& L, cudaStream_t st)
+{
+    const int64_t nb = (L.total + 255) / 256;
+    const int sb = (int)(nb < 1024 ? nb : 1024);
+    bucket_count_kernel<<<sb, 256, 0, st>>>(L);
+    bucket_scan_kernel<<<1, 32, 0, st>>>(L.hist);
+    bucket_scatter_kernel<<<sb, 256, 0, st>>>(L);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rates(const MechDev& M, int64_t cells, const double* T, const double* p,

@@ -91,13 +91,28 @@ struct WsLayout {
 WsLayout ws_layout(const MechDev& M, int precision, int64_t nslots, int64_t cells);
 
 // Host-side helpers implemented in kernels.cu.
-cudaError_t launch_integrate(Launch& L, int staging, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_integrate(Launch& L, int staging, int occupancy, int blocks, int threads,
+                             cudaStream_t st);
 size_t smem_bytes(const MechDev& M, int precision, int threads, int staging);
 cudaError_t launch_rates(const MechDev& M, int64_t cells, const double* T, const double* p,
                          const double* Y, int64_t ldY, double* dYdt, int precision, void* ws,
                          int64_t nslots, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_rkc_table(double* tab, cudaStream_t st);
+// Per method/precision instantiations (inst_*.cu) and the bucket sort.
+cudaError_t launch_rkc_f64(Launch& L, int stg, int occ, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_rkc_f32(Launch& L, int stg, int occ, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_rkck_f64(Launch& L, int stg, int occ, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_rkck_f32(Launch& L, int stg, int occ, int blocks, int threads, cudaStream_t st);
+cudaError_t occ_rkc_f64(int stg, int occ, int threads, size_t sm, int* bps);
+cudaError_t occ_rkc_f32(int stg, int occ, int threads, size_t sm, int* bps);
+cudaError_t occ_rkck_f64(int stg, int occ, int threads, size_t sm, int* bps);
+cudaError_t occ_rkck_f32(int stg, int occ, int threads, size_t sm, int* bps);
+cudaError_t launch_sort(Launch& L, cudaStream_t st);
+
+// Record `code` and a printf-style message as the calling thread's last
+// error (kin_last_error); returns `code`.
+int set_last_error(int code, const char* fmt, ...);
 cudaError_t integrate_occupancy(const MechDev& M, int method, int precision, int staging,
-                                int threads, int* blocks_per_sm);
+                                int occupancy, int threads, int* blocks_per_sm);
 
 }  // namespace kin

@@ -21,6 +21,7 @@ RKCK, RKC = 0, 1
 FP64, MIXED = 0, 1
 CELL_OK, CELL_MAXSTEPS, CELL_HMIN, CELL_NONFINITE = 0, 1, 2, 3
 STAGE_GLOBAL, STAGE_SHARED, STAGE_SHARED_ALL = 0, 1, 2
+OCC_DEFAULT, OCC_HIGH = 0, 1
 MAX_INSTANCES = 128
 
 
@@ -42,6 +43,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("max_steps", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("staging", ctypes.c_int32),
+                ("occupancy", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -153,16 +155,17 @@ class Mechanism:
             pass
 
     def workspace_bytes(self, method=RKC, precision=FP64, cells=0, block_threads=0,
-                        blocks_per_sm=0, staging=STAGE_GLOBAL) -> int:
-        o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, None)
+                        blocks_per_sm=0, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT) -> int:
+        o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, 0, None)
         n = lib().kin_workspace_bytes(self.handle, ctypes.byref(o), int(cells))
         if n < 0:
             _check(int(n))
         return int(n)
 
     def workspace(self, method=RKC, precision=FP64, cells=0, block_threads=0, blocks_per_sm=0,
-                  device=None, staging=STAGE_GLOBAL) -> torch.Tensor:
-        n = self.workspace_bytes(method, precision, cells, block_threads, blocks_per_sm, staging)
+                  device=None, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT) -> torch.Tensor:
+        n = self.workspace_bytes(method, precision, cells, block_threads, blocks_per_sm, staging,
+                                 occupancy)
         return torch.empty(n, dtype=torch.uint8, device=device or torch.device("cuda"))
 
 
@@ -193,13 +196,13 @@ class Cells:
 
 def integrate(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP64,
               status=None, stats=None, workspace=None, stream=None, max_steps=0,
-              block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL):
+              block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT):
     """Integrate every cell over dt in place (kin_integrate)."""
     cells, ld = _check_state(mech, T, p, Y)
     if workspace is None:
         workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm, Y.device,
-                                   staging)
-    o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging,
+                                   staging, occupancy)
+    o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging, occupancy, 0,
              _stream_handle(stream))
     _check(lib().kin_integrate(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), ld, float(dt),
                                float(rtol), float(atol), ctypes.byref(o), _ptr(status),
@@ -219,7 +222,7 @@ def make_instances(mech: Mechanism, parts: Sequence[Cells]):
 
 def integrate_batch(mech: Mechanism, parts: Sequence[Cells], method=RKC, precision=FP64,
                     workspace=None, stream=None, max_steps=0, block_threads=0, blocks_per_sm=0,
-                    staging=STAGE_GLOBAL):
+                    staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT):
     """Integrate several instances in one persistent launch (kin_integrate_batch)."""
     if not 1 <= len(parts) <= MAX_INSTANCES:
         raise ValueError("1..%d instances per launch" % MAX_INSTANCES)
@@ -227,8 +230,8 @@ def integrate_batch(mech: Mechanism, parts: Sequence[Cells], method=RKC, precisi
     if workspace is None:
         cells = sum(int(c.T.numel()) for c in parts)
         workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm,
-                                   parts[0].Y.device, staging)
-    o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging,
+                                   parts[0].Y.device, staging, occupancy)
+    o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging, occupancy, 0,
              _stream_handle(stream))
     _check(lib().kin_integrate_batch(mech.handle, len(parts), arr, ctypes.byref(o),
                                      _ptr(workspace), workspace.numel()))
@@ -251,9 +254,10 @@ def version() -> str:
 
 
 def host_buffer(mech: Mechanism, cells: int, method=RKC, precision=FP64, device=None,
-                block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL) -> torch.Tensor:
+                block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL,
+                occupancy=OCC_DEFAULT) -> torch.Tensor:
     """Device buffer for integrate_host (kin_host_buffer_bytes)."""
-    o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, None)
+    o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, 0, None)
     n = lib().kin_host_buffer_bytes(mech.handle, ctypes.byref(o), int(cells))
     if n < 0:
         _check(int(n))
@@ -262,7 +266,7 @@ def host_buffer(mech: Mechanism, cells: int, method=RKC, precision=FP64, device=
 
 def integrate_host(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP64,
                    status=None, stats=None, buffer=None, stream=None, max_steps=0,
-                   block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL):
+                   block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT):
     """kin_integrate_host: T, p, Y (in place), status, stats are CPU tensors
     (pin them for asynchronous copies). Returns after enqueueing; synchronise
     the stream before reading the results."""
@@ -274,8 +278,8 @@ def integrate_host(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precisi
         raise ValueError("Y must be [n_species, >= cells] with unit column stride")
     if buffer is None:
         buffer = host_buffer(mech, cells, method, precision, None, block_threads, blocks_per_sm,
-                             staging)
-    o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging,
+                             staging, occupancy)
+    o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging, occupancy, 0,
              _stream_handle(stream))
     _check(lib().kin_integrate_host(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), int(Y.stride(0)),
                                     float(dt), float(rtol), float(atol), ctypes.byref(o),

@@ -263,7 +263,7 @@ def test_invalid_arguments_raise():
     h = np.zeros(8)
     rc = kin.lib().kin_integrate(km.handle, 8, ctypes.c_void_p(h.ctypes.data), kin._ptr(pd),
                                  kin._ptr(Yd), 8, 1e-6, 1e-6, 1e-10,
-                                 ctypes.byref(kin.Opts(1, 0, 0, 0, 0, 0, None)), None, None,
+                                 ctypes.byref(kin.Opts(1, 0, 0, 0, 0, 0, 0, 0, None)), None, None,
                                  kin._ptr(ws), ws.numel())
     assert rc == kin.KIN_EINVAL
 
@@ -314,13 +314,13 @@ def test_launch_shapes_are_bitwise_identical(method, name):
     prec = w["precision"]
     ref = None
     for shape in [dict(), dict(block_threads=64, blocks_per_sm=1),
-                  dict(block_threads=32, blocks_per_sm=3, staging=kin.STAGE_SHARED),
+                  dict(block_threads=32, blocks_per_sm=1, staging=kin.STAGE_SHARED),
                   dict(block_threads=64, blocks_per_sm=1, staging=kin.STAGE_SHARED_ALL)]:
         Yd = dev(Y)
         try:
             kin.integrate(km, dev(T), dev(p), Yd, w["dt"], w["rtol"], w["atol"], method, prec, **shape)
         except kin.KinError as e:
-            assert e.code == kin.KIN_EUNSUPPORTED  # staging that does not fit
+            assert e.code == kin.KIN_EUNSUPPORTED  # staging that does not fit in shared memory
             continue
         torch.cuda.synchronize()
         if ref is None:
