@@ -265,7 +265,7 @@ def run_kin(args):
                              w["atol"], method, prec)
         shape = {k: best[k] for k in shape}
     ws = km.workspace(method, prec, cells, shape["block_threads"], shape["blocks_per_sm"], dev,
-                      shape["staging"])
+                      shape["staging"], shape["occupancy"])
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
