@@ -196,6 +196,33 @@ int kin_integrate_host(const kin_mech *m, int64_t cells, const double *T, const 
                        const kin_opts *opts, uint8_t *status, int32_t *stats,
                        void *device_buffer, int64_t device_bytes);
 
+/* Size of the fixed device array behind kin_integrate_noalloc (64 MiB). */
+#define KIN_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/* kin_integrate for callers that cannot allocate device memory when they
+ * integrate (for example a flow solver whose own memory manager owns the
+ * device, or code running where allocation is not allowed). Same arguments,
+ * meaning and errors as kin_integrate, minus the workspace: the working memory
+ * comes from a fixed array of KIN_NOALLOC_SCRATCH_BYTES that the library
+ * reserves on every device where it is loaded and keeps until the process
+ * exits. The call itself allocates nothing.
+ *  - The first call on a device looks up that array's device address (with
+ *    the device current); make that first call before any stream capture.
+ *  - The array is shared by all calls on a device and keeps the last call's
+ *    contents; each call clears what must start at zero. Calls that overlap
+ *    on the GPU (on different streams, or from different threads) race on it:
+ *    serialise them.
+ *  - The working memory grows with the cell count: a call fits when
+ *    kin_workspace_bytes(m, opts with blocks_per_sm = 1, cells) is at most
+ *    KIN_NOALLOC_SCRATCH_BYTES (for a 13-species / 54-reaction mechanism in
+ *    FP64 on a 152-SM GPU, about 57,000 cells). A call that does not fit fails
+ *    with KIN_ENOMEM and launches nothing. Fewer persistent blocks per SM
+ *    than requested are used when that makes the call fit.
+ * The paper has no counterpart of this entry point. */
+int kin_integrate_noalloc(const kin_mech *m, int64_t cells, const double *T, const double *p,
+                          double *Y, int64_t ldY, double dt, double rtol, double atol,
+                          const kin_opts *opts, uint8_t *status, int32_t *stats);
+
 /* f alone: dYdt[i * ldY + c] = f(T_c, p_c, Y_c)_i (Eqs. (E:mass),
  * (E:spec-rate), (E:rxn-rate), (E:rxn-const)) in the given precision
  * (KIN_FP64 or KIN_MIXED), enqueued on `stream`. T, p, Y, dYdt and workspace

@@ -70,6 +70,10 @@ _SIGNATURES = {
                                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "kin_version": (ctypes.c_char_p, []),
+    "kin_integrate_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.POINTER(Opts), ctypes.c_void_p, ctypes.c_void_p]),
     "kin_host_buffer_bytes": (ctypes.c_int64, [ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.c_int64]),
     "kin_integrate_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
