@@ -36,9 +36,12 @@ METRIC = "cell-ODEs integrated over Δt per sec per GB300 at rtol 1e-6"
 UNIT = "cell-ODEs/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# FP64 peak derived from the nominal 1.25 TFLOP/s of a GB300: 2 FP64 FMA lanes
-# per SM per clock x 2 flops x 152 SMs x 2070 MHz = 1.259e12 FLOP/s.
-FP64_FMA_LANES_PER_SM = 2
+# The FP64 pipe binds this path. From the nominal 1.25 TFLOP/s of a GB300:
+# 2 FP64 lanes per SM per clock x 152 SMs x 2070 MHz = 629.3 G lane-ops/s
+# (1258.6 GFLOP/s counting an FMA as 2 flops). Every FP64 add, multiply,
+# divide or FMA occupies one lane-op of that pipe, so the roofline is stated
+# in FP64 operations; the flop-based fraction is reported beside it.
+FP64_LANES_PER_SM = 2
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
@@ -72,6 +75,43 @@ def feval_flops(m) -> int:
                 f += 1 if abs(nu) == 1 else 2
     f += 2 * nS + 1  # dY/dt = W omega / rho
     return f
+
+
+def feval_ops(m) -> int:
+    """FP64 operations of one evaluation of f in its minimal fused form
+    (an FMA, add, multiply or divide is one operation)."""
+    nS = m.n_species
+    o = 3 * nS + 1  # Y/W, sum, rho, C
+    for j in range(m.n_reactions):
+        o += int(np.count_nonzero(m.reac[j] >= 0))
+        if m.rtype[j] == synth.THIRD_BODY:
+            o += nS + 1  # [M] as nS fused multiply-adds, times [M]
+        elif m.rtype[j] == synth.FALLOFF:
+            o += nS + 4  # [M], Pr, 1 + Pr, Pr/(1+Pr), times
+    for i in range(nS):
+        for j in range(m.n_reactions):
+            if int(np.sum(m.prod[j] == i)) != int(np.sum(m.reac[j] == i)):
+                o += 1  # one fused multiply-add per net nonzero
+    o += 2 * nS + 1
+    return o
+
+
+def algorithmic_ops(m, method, stats) -> float:
+    """Algorithmic FP64 operations of one call from the per-cell counts."""
+    nS = m.n_species
+    nfe = stats[:, 0].astype(np.float64)
+    att = (stats[:, 1] + stats[:, 2]).astype(np.float64)
+    nsig = stats[:, 3].astype(np.float64)
+    total = nfe.sum() * feval_ops(m)
+    if method == synth.RKC:
+        stages = nfe - 2 - nsig * nS
+        # w_j: 5 nS per stage after the first; per attempt w_1 (nS) and the
+        # error estimate and norm (7 nS)
+        total += ((stages - att) * 5 * nS + att * 8 * nS).sum()
+        total += (nsig * 3 * nS * nS).sum() + 6 * nS * len(nfe)  # sigma, initial step
+    else:
+        total += (att * 38 * nS).sum()  # stage points (20 nS), y5, error, tolerance
+    return float(total)
 
 
 def algorithmic_flops(m, method, stats) -> float:
@@ -256,13 +296,14 @@ def run_kin(args):
     st = torch.zeros(cells, dtype=torch.uint8, device=dev)
     sta = torch.zeros((cells, 4), dtype=torch.int32, device=dev)
     shape = dict(block_threads=0, blocks_per_sm=0, staging=kin.STAGE_GLOBAL, occupancy=kin.OCC_DEFAULT)
-    if not args.no_tune:
-        # launch shape from the autotuner (cached per GPU and mechanism shape),
-        # timed on the first 65536 cells, outside the timed region
+    if args.shape:
+        bt, bps, stg, occ = (int(x) for x in args.shape.split(","))
+        shape = dict(block_threads=bt, blocks_per_sm=bps, staging=stg, occupancy=occ)
+    elif not args.no_tune:
+        # launch shape from the autotuner (cached per GPU, mechanism shape and
+        # cell count), timed on this workload outside the timed region
         from paper_1309_2710_gb300 import autotune
-        n = min(cells, 65536)
-        best = autotune.tune(km, m, Td[:n], pd[:n], Y0d[:, :n].contiguous(), w["dt"], w["rtol"],
-                             w["atol"], method, prec)
+        best = autotune.tune(km, m, Td, pd, Y0d, w["dt"], w["rtol"], w["atol"], method, prec)
         shape = {k: best[k] for k in shape}
     ws = km.workspace(method, prec, cells, shape["block_threads"], shape["blocks_per_sm"], dev,
                       shape["staging"], shape["occupancy"])
@@ -308,9 +349,11 @@ def run_kin(args):
     stats = sta.cpu().numpy()
     status = st.cpu().numpy()
     flops = algorithmic_flops(m, method, stats)
+    ops = algorithmic_ops(m, method, stats)
     kavg = sum(kern_ms) / len(kern_ms)
-    achieved = flops / (kavg * 1e-3) / 1e9
-    peak = FP64_FMA_LANES_PER_SM * 2 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
+    achieved = ops / (kavg * 1e-3) / 1e9
+    peak = FP64_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
+    flop_rate = flops / (kavg * 1e-3) / 1e9
     tr = TRAFFIC.get(kernel_hash())
 
     # end to end: host (pinned) buffers through the public API, copies timed
@@ -358,10 +401,12 @@ def run_kin(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32+f64",
             "data": "synthetic (seeded generator standing in for the paper's mechanisms and states)",
             "config": dict(workload_config(name, cells), launch_shape=shape),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                         "frac": achieved / peak, "traffic": tr,
-                         "kernel": "integrate_kernel (FP64 pipe)",
-                         "kernel_ms": kavg, "flops_per_launch": flops},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "G FP64 lane-ops/s", "frac": achieved / peak, "traffic": tr,
+                         "kernel": "kin_integrate launch (init_kernel + sort + integrate_kernel)",
+                         "peak_basis": "derived: 2 FP64 lanes/SM/clk x 152 SMs x 2070 MHz",
+                         "kernel_ms": kavg, "ops_per_launch": ops, "flops_per_launch": flops,
+                         "gflops": flop_rate, "flop_frac": flop_rate / (2 * peak)},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,
@@ -373,6 +418,78 @@ def run_kin(args):
     if world > 1:
         dist.destroy_process_group()
     km.close()
+    return 0
+
+
+# ------------------------------------------------------- batched mode ---
+def run_batched(args):
+    """The 16-instance 111-species workload: one persistent launch over all
+    instances (replayed from a CUDA graph) against 16 separate launches."""
+    import torch
+    from paper_1309_2710_gb300 import build as kbuild
+    kbuild.build()
+    from paper_1309_2710_gb300 import kin
+    name = "c2h4_111sp_rkc_batched"
+    w = synth.WORKLOADS[name]
+    m = synth.workload_mechanism(name)
+    km = kin.Mechanism(m)
+    prec = synth.MIXED if args.precision == "mixed" else synth.FP64
+    dev = torch.device("cuda")
+    inst = synth.batched_instances(name, scale=args.scale)
+    parts, Y0s = [], []
+    for i, (n, dt) in enumerate(inst):
+        T, p, Y = synth.workload_states(name, m, cells=n, seed_offset=100 + i)
+        Yd = torch.as_tensor(Y, device=dev).contiguous()
+        Y0s.append(Yd.clone())
+        parts.append(kin.Cells(torch.as_tensor(T, device=dev), torch.as_tensor(p, device=dev), Yd, dt,
+                               w["rtol"], w["atol"], torch.zeros(n, dtype=torch.uint8, device=dev),
+                               torch.zeros((n, 4), dtype=torch.int32, device=dev)))
+    total = sum(n for n, _ in inst)
+    ws = km.workspace(kin.RKC, prec, total, device=dev)
+    ws1 = km.workspace(kin.RKC, prec, max(n for n, _ in inst), device=dev)
+    stream = torch.cuda.Stream()
+
+    def reset():
+        for c, y0 in zip(parts, Y0s):
+            c.Y.copy_(y0)
+
+    def separate():
+        for c in parts:
+            kin.integrate(km, c.T, c.p, c.Y, c.dt, c.rtol, c.atol, kin.RKC, prec, status=c.status,
+                          stats=c.stats, workspace=ws1, stream=stream)
+
+    with torch.cuda.stream(stream):
+        reset()
+        kin.integrate_batch(km, parts, kin.RKC, prec, workspace=ws, stream=stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        kin.integrate_batch(km, parts, kin.RKC, prec, workspace=ws)
+    out = {}
+    for label, fn in (("persistent_graph", g.replay), ("separate_launches", separate)):
+        for _ in range(args.warmup):
+            with torch.cuda.stream(stream):
+                reset()
+                fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                reset()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = torch.cat([c.status for c in parts]).cpu().numpy()
+        out[label] = {"ms": float(np.median(ms)), "cells_per_s": total / (np.median(ms) * 1e-3),
+                      "status": np.bincount(st, minlength=4).tolist()}
+    nfe = torch.cat([c.stats[:, 0] for c in parts]).double().mean().item()
+    print(json.dumps({"mode": "batched", "workload": name, "instances": len(inst), "cells": total,
+                      "scale": args.scale, "precision": args.precision, "mean_f_evals": nfe,
+                      "sizes": [n for n, _ in inst], **out,
+                      "speedup": out["separate_launches"]["ms"] / out["persistent_graph"]["ms"]}))
     return 0
 
 
@@ -389,7 +506,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shape")
+    ap.add_argument("--shape", default="", help="block_threads,blocks_per_sm,staging,occupancy "
+                                                "(skips the autotuner)")
+    ap.add_argument("--mode", choices=["headline", "batched"], default="headline")
+    ap.add_argument("--scale", type=float, default=1.0, help="batched mode: instance size scale")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="batched mode: rate precision")
     args = ap.parse_args()
+    if args.mode == "batched":
+        return run_batched(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_kin(args)

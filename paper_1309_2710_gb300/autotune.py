@@ -28,11 +28,12 @@ def _key(mech: kin.Mechanism, method: int, precision: int, desc) -> str:
     return "%s|%d|%d|%d|%d|%d" % (dev, mech.n_species, mech.n_reactions, n_m, method, precision)
 
 
-def candidates():
+def candidates(full: bool = False):
+    """Launch shapes to try; `full` adds more block sizes and lane counts."""
     for occupancy in (kin.OCC_DEFAULT, kin.OCC_HIGH):
         for staging in (kin.STAGE_GLOBAL, kin.STAGE_SHARED, kin.STAGE_SHARED_ALL):
-            for threads in (128, 64, 32):
-                for lanes in (256, 384, 512, 640, 768):
+            for threads in ((128, 64, 32) if full else (128, 32)):
+                for lanes in ((256, 384, 512, 640, 768) if full else (384, 512, 768)):
                     bps = lanes // threads
                     yield dict(block_threads=threads, blocks_per_sm=bps, staging=staging,
                                occupancy=occupancy)
@@ -66,10 +67,11 @@ def time_config(mech, T, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2) 
 
 
 def tune(mech: kin.Mechanism, desc, T, p, Y, dt, rtol, atol, method, precision,
-         use_cache: bool = True, verbose: bool = False) -> Dict:
+         use_cache: bool = True, verbose: bool = False, full: bool = False, reps: int = 1) -> Dict:
     """Best launch shape for this mechanism on the current GPU, timed on the
-    given (device) sample of cells."""
-    key = _key(mech, method, precision, desc)
+    given (device) cells: pass the cells of a representative call, since the
+    persistent grid's tail depends on the cell count."""
+    key = _key(mech, method, precision, desc) + "|%d" % int(T.numel())
     cache = {}
     if use_cache and os.path.exists(CACHE):
         with open(CACHE) as f:
@@ -77,8 +79,8 @@ def tune(mech: kin.Mechanism, desc, T, p, Y, dt, rtol, atol, method, precision,
         if key in cache:
             return cache[key]
     results = []
-    for cfg in candidates():
-        ms = time_config(mech, T, p, Y, dt, rtol, atol, method, precision, cfg)
+    for cfg in candidates(full):
+        ms = time_config(mech, T, p, Y, dt, rtol, atol, method, precision, cfg, reps)
         if verbose:
             print("autotune", cfg, ms)
         if ms is not None:
