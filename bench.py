@@ -190,6 +190,13 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------- CPU oracle ---
+def oracle_method(w):
+    """The oracle's method code for a workload (2 = RKC with power sigma)."""
+    if w["method"] == synth.RKCK:
+        return 0
+    return 2 if w["sigma"] == synth.POWER else 1
+
+
 def oracle_rate(name, cells_target_s=10.0, max_cells=None, seed_offset=0):
     """Time the FP64 oracle on the host cores on a bounded sample of the
     workload. Returns (cells/s, threads, sample description)."""
@@ -201,13 +208,13 @@ def oracle_rate(name, cells_target_s=10.0, max_cells=None, seed_offset=0):
     T, p, Y = synth.workload_states(name, m, seed_offset=seed_offset)
     probe = min(2048, total)
     t0 = time.perf_counter()
+    meth = oracle_method(w)
     _, _, _, nt = oracle.integrate(om, T[:probe], p[:probe], Y[:, :probe], w["dt"], w["rtol"],
-                                   w["atol"], w["method"])
+                                   w["atol"], meth)
     per_cell = (time.perf_counter() - t0) / probe
     n = int(min(total if max_cells is None else max_cells, max(probe, cells_target_s / per_cell)))
     t0 = time.perf_counter()
-    _, st, _, nt = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"],
-                                    w["method"])
+    _, st, _, nt = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], meth)
     el = time.perf_counter() - t0
     return n / el, nt, "first %d of the %d cells of %s (same seeds), %.1f s wall" % (n, total, name, el)
 
@@ -225,18 +232,18 @@ def run_reference(args):
     # bounded per-step sample sized from a probe so K+W steps take ~2 min
     probe = 1024
     t0 = time.perf_counter()
-    oracle.integrate(om, T[:probe], p[:probe], Y[:, :probe], w["dt"], w["rtol"], w["atol"], w["method"])
+    meth = oracle_method(w)
+    oracle.integrate(om, T[:probe], p[:probe], Y[:, :probe], w["dt"], w["rtol"], w["atol"], meth)
     per_cell = (time.perf_counter() - t0) / probe
     budget = 120.0 / max(1, args.steps + args.warmup)
     n = int(min(w["cells"], max(probe, budget / per_cell)))
     for _ in range(args.warmup):
-        oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], w["method"])
+        oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], meth)
     times = []
     nt = 1
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        _, _, _, nt = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"],
-                                       w["method"])
+        _, _, _, nt = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], meth)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = n * len(times) / tot
@@ -253,11 +260,13 @@ def run_reference(args):
     return 0
 
 
-def workload_config(name, cells):
+def workload_config(name, cells, sigma=None):
     w = synth.WORKLOADS[name]
+    sigma = w["sigma"] if sigma is None else sigma
+    rkc = "RKC (%s sigma)" % ("power-method" if sigma == synth.POWER else "Gershgorin FD")
     return {"workload": "%s: %d species / %d reactions, %s %s, %d cells, dt %g s, rtol %g, atol %g"
                         % (name, w["n_species"], w["n_reactions"],
-                           "RKC (Gershgorin FD)" if w["method"] == synth.RKC else "RKCK",
+                           rkc if w["method"] == synth.RKC else "RKCK",
                            "FP64" if w["precision"] == synth.FP64 else "mixed FP32/FP64",
                            cells, w["dt"], w["rtol"], w["atol"]),
             "cells": cells, "method": "RKC" if w["method"] == synth.RKC else "RKCK",
@@ -289,6 +298,8 @@ def run_kin(args):
     T, p, Y0 = synth.workload_states(name, m, cells=cells, seed_offset=1000 * rank)
     km = kin.Mechanism(m)
     method, prec = w["method"], w["precision"]
+    sigma = w["sigma"] if args.sigma == "default" else (synth.POWER if args.sigma == "power"
+                                                         else synth.GERSHGORIN)
     Td = torch.as_tensor(T, device=dev)
     pd = torch.as_tensor(p, device=dev)
     Y0d = torch.as_tensor(Y0, device=dev).contiguous()
@@ -303,10 +314,11 @@ def run_kin(args):
         # launch shape from the autotuner (cached per GPU, mechanism shape and
         # cell count), timed on this workload outside the timed region
         from paper_1309_2710_gb300 import autotune
-        best = autotune.tune(km, m, Td, pd, Y0d, w["dt"], w["rtol"], w["atol"], method, prec)
+        best = autotune.tune(km, m, Td, pd, Y0d, w["dt"], w["rtol"], w["atol"], method, prec,
+                             sigma=sigma)
         shape = {k: best[k] for k in shape}
     ws = km.workspace(method, prec, cells, shape["block_threads"], shape["blocks_per_sm"], dev,
-                      shape["staging"], shape["occupancy"])
+                      shape["staging"], shape["occupancy"], sigma)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -316,7 +328,7 @@ def run_kin(args):
         if ev:
             ev[0].record(stream)
         kin.integrate(km, Td, pd, Yd, w["dt"], w["rtol"], w["atol"], method, prec,
-                      status=st, stats=sta, workspace=ws, stream=stream, **shape)
+                      status=st, stats=sta, workspace=ws, stream=stream, sigma=sigma, **shape)
         if ev:
             ev[1].record(stream)
 
@@ -364,13 +376,13 @@ def run_kin(args):
         Y0h = torch.as_tensor(Y0).contiguous()
         Yh = torch.empty_like(Y0h).pin_memory()
         sth = torch.empty(cells, dtype=torch.uint8).pin_memory()
-        hbuf = kin.host_buffer(km, cells, method, prec, device=dev, **shape)
+        hbuf = kin.host_buffer(km, cells, method, prec, device=dev, sigma=sigma, **shape)
 
         def e2e_step():
             # the flow solver hands over its state in host memory every step
             Yh.copy_(Y0h)
             kin.integrate_host(km, Th, ph, Yh, w["dt"], w["rtol"], w["atol"], method, prec,
-                               status=sth, buffer=hbuf, stream=stream, **shape)
+                               status=sth, buffer=hbuf, stream=stream, sigma=sigma, **shape)
             stream.synchronize()
 
         e2e_step()
@@ -400,7 +412,7 @@ def run_kin(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32+f64",
             "data": "synthetic (seeded generator standing in for the paper's mechanisms and states)",
-            "config": dict(workload_config(name, cells), launch_shape=shape),
+            "config": dict(workload_config(name, cells, sigma), launch_shape=shape),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "G FP64 lane-ops/s", "frac": achieved / peak, "traffic": tr,
                          "kernel": "kin_integrate launch (init_kernel + sort + integrate_kernel)",
@@ -445,8 +457,10 @@ def run_batched(args):
                                w["rtol"], w["atol"], torch.zeros(n, dtype=torch.uint8, device=dev),
                                torch.zeros((n, 4), dtype=torch.int32, device=dev)))
     total = sum(n for n, _ in inst)
-    ws = km.workspace(kin.RKC, prec, total, device=dev)
-    ws1 = km.workspace(kin.RKC, prec, max(n for n, _ in inst), device=dev)
+    sigma = w["sigma"] if args.sigma == "default" else (synth.POWER if args.sigma == "power"
+                                                         else synth.GERSHGORIN)
+    ws = km.workspace(kin.RKC, prec, total, device=dev, sigma=sigma)
+    ws1 = km.workspace(kin.RKC, prec, max(n for n, _ in inst), device=dev, sigma=sigma)
     stream = torch.cuda.Stream()
 
     def reset():
@@ -456,15 +470,15 @@ def run_batched(args):
     def separate():
         for c in parts:
             kin.integrate(km, c.T, c.p, c.Y, c.dt, c.rtol, c.atol, kin.RKC, prec, status=c.status,
-                          stats=c.stats, workspace=ws1, stream=stream)
+                          stats=c.stats, workspace=ws1, stream=stream, sigma=sigma)
 
     with torch.cuda.stream(stream):
         reset()
-        kin.integrate_batch(km, parts, kin.RKC, prec, workspace=ws, stream=stream)
+        kin.integrate_batch(km, parts, kin.RKC, prec, workspace=ws, stream=stream, sigma=sigma)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
-        kin.integrate_batch(km, parts, kin.RKC, prec, workspace=ws)
+        kin.integrate_batch(km, parts, kin.RKC, prec, workspace=ws, sigma=sigma)
     out = {}
     for label, fn in (("persistent_graph", g.replay), ("separate_launches", separate)):
         for _ in range(args.warmup):
@@ -488,6 +502,7 @@ def run_batched(args):
     nfe = torch.cat([c.stats[:, 0] for c in parts]).double().mean().item()
     print(json.dumps({"mode": "batched", "workload": name, "instances": len(inst), "cells": total,
                       "scale": args.scale, "precision": args.precision, "mean_f_evals": nfe,
+                      "sigma": "power" if sigma == synth.POWER else "gershgorin",
                       "sizes": [n for n, _ in inst], **out,
                       "speedup": out["separate_launches"]["ms"] / out["persistent_graph"]["ms"]}))
     return 0
@@ -509,6 +524,8 @@ def main():
     ap.add_argument("--shape", default="", help="block_threads,blocks_per_sm,staging,occupancy "
                                                 "(skips the autotuner)")
     ap.add_argument("--mode", choices=["headline", "batched"], default="headline")
+    ap.add_argument("--sigma", choices=["default", "gershgorin", "power"], default="default",
+                    help="RKC spectral-radius estimator (default: the workload's)")
     ap.add_argument("--scale", type=float, default=1.0, help="batched mode: instance size scale")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="batched mode: rate precision")

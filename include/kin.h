@@ -8,7 +8,8 @@
  *   KIN_RKCK  Runge-Kutta-Cash-Karp 5(4), Section 2.2, Table 1, Eq. (E:hnew);
  *   KIN_RKC   second-order Runge-Kutta-Chebyshev, Section 2.3, Eqs.
  *             (E:rkc0)-(E:rkcs), (E:rmsE). The spectral radius is a Gershgorin
- *             bound on a finite-difference Jacobian.
+ *             bound on a finite-difference Jacobian or, as in the paper, a
+ *             nonlinear power method (kin_opts.sigma).
  * f is the species source term of Section 2.1, Eqs. (E:mass), (E:spec-rate),
  * (E:rxn-rate) and (E:rxn-const), with third-body and Lindemann falloff
  * reactions. Temperature and pressure are held fixed over the flow step
@@ -59,6 +60,10 @@ extern "C" {
 #define KIN_STAGE_GLOBAL 0     /* every per-lane array in the workspace */
 #define KIN_STAGE_SHARED 1     /* concentrations and rates of progress in shared memory */
 #define KIN_STAGE_SHARED_ALL 2 /* ... and the cell's rate constants too */
+
+/* RKC spectral-radius estimator */
+#define KIN_SIGMA_GERSHGORIN 0
+#define KIN_SIGMA_POWER 1
 
 /* kernel register budget */
 #define KIN_OCC_DEFAULT 0
@@ -116,7 +121,10 @@ typedef struct {
                               per block; KIN_EUNSUPPORTED if that does not fit */
     int32_t occupancy;     /* KIN_OCC_DEFAULT: kernel built for up to 16 resident warps per
                               SM; KIN_OCC_HIGH: built with a register cap for 24 */
-    int32_t reserved;      /* must be 0 */
+    int32_t sigma;         /* RKC spectral radius: KIN_SIGMA_GERSHGORIN (Gershgorin bound on a
+                              finite-difference Jacobian, n_species f evaluations) or
+                              KIN_SIGMA_POWER (nonlinear power method with warm start, the
+                              paper's choice, end of Section 2.3); ignored for RKCK */
     void *stream;          /* cudaStream_t */
 } kin_opts;
 

@@ -19,7 +19,7 @@ _OUT = os.path.join(_HERE, "_build", "libkin_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-RKCK, RKC = 0, 1
+RKCK, RKC, RKC_POWER = 0, 1, 2  # method: RKC_POWER = RKC with the power-method sigma
 
 
 def compile_source(src: str, out: str) -> str:
@@ -83,6 +83,9 @@ def bind(path: str) -> ctypes.CDLL:
                                  ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int] + [ctypes.c_void_p] * 5
+    L.orc_sigma_power.restype = ctypes.c_double
+    L.orc_sigma_power.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.orc_has_openmp.restype = ctypes.c_int
     return L
 
@@ -153,6 +156,17 @@ def rkc_coeffs(s: int):
 def sigma(om: Mech, T: float, p: float, y, atol: float) -> float:
     y = _f64(y)
     return float(lib().orc_sigma(om.ptr, float(T), float(p), _ptr(y), float(atol)))
+
+
+def sigma_power(om: Mech, T: float, p: float, y, v0=None):
+    """Power-method spectral radius at y. Returns (sigma, direction, f evals)."""
+    y = _f64(y)
+    v = np.array(v0 if v0 is not None else np.zeros_like(y), dtype=np.float64)
+    it = ctypes.c_int32(0)
+    if v0 is None:
+        v[:] = rates(om, T, p, y)
+    sig = lib().orc_sigma_power(om.ptr, float(T), float(p), _ptr(y), _ptr(v), ctypes.byref(it))
+    return float(sig), v, it.value
 
 
 def rkck_single(om: Mech, T, p, y, h):

@@ -38,6 +38,9 @@
  *     accepted steps since the last estimate, and after a rejection when the
  *     last estimate was made at an earlier point (re-estimating at the same
  *     point gives the same bound).
+ *   - Spectral radius: the Gershgorin bound (below), or the nonlinear power
+ *     method (power_sigma) that the paper used; both are re-estimated on the
+ *     same schedule.
  *   - Gershgorin: sigma = max_i sum_k |J_ik| with
  *     J_ik = (f_i(y + eps_k e_k) - f_i(y)) / eps_k,
  *     eps_k = sqrt(2^-52) * max(|y_k|, atol).
@@ -436,6 +439,70 @@ static double gershgorin(orc_f *F, int n, const double *y, const double *f0, dou
     return sigma;
 }
 
+/* Nonlinear power method for the spectral radius (the paper's choice, end of
+ * Section 2.3): repeated finite-difference products w = f(y + v) - f(y) ~ J v
+ * with v rescaled to length dyn = sqrt(u) ||y||_2 (sqrt(u) if y = 0), starting
+ * from the warm-start direction v (the previous estimate's eigenvector; f(y)
+ * at the first estimate; all ones if that is zero). The estimate ||w||/dyn is
+ * accepted once two successive values agree to 1 % (at most 20 products) and
+ * returned with a 20 % margin, since the iteration approaches |lambda_max|
+ * from below. v is left holding the new direction. *iters receives the
+ * number of f evaluations. */
+static double power_sigma(orc_f *F, int n, const double *y, const double *f0, double *v,
+                          double *z, double *fz, int *iters)
+{
+    const double sqrt_u = sqrt(ldexp(1.0, -52));
+    double ynorm = 0.0, vnorm = 0.0, dyn, sig = 0.0, prev = 0.0;
+    int i, k;
+    for (i = 0; i < n; i++) ynorm += y[i] * y[i];
+    ynorm = sqrt(ynorm);
+    dyn = ynorm > 0.0 ? sqrt_u * ynorm : sqrt_u;
+    for (i = 0; i < n; i++) vnorm += v[i] * v[i];
+    vnorm = sqrt(vnorm);
+    if (!(vnorm > 0.0) || !isfinite(vnorm)) {
+        for (i = 0; i < n; i++) v[i] = 1.0;
+        vnorm = sqrt((double)n);
+    }
+    for (i = 0; i < n; i++) v[i] *= dyn / vnorm;
+    *iters = 0;
+    for (k = 1; k <= 20; k++) {
+        double wnorm = 0.0;
+        for (i = 0; i < n; i++) z[i] = y[i] + v[i];
+        feval(F, z, fz);
+        (*iters)++;
+        for (i = 0; i < n; i++) {
+            fz[i] -= f0[i];
+            wnorm += fz[i] * fz[i];
+        }
+        wnorm = sqrt(wnorm);
+        sig = wnorm / dyn;
+        if (!(wnorm > 0.0) || !isfinite(wnorm)) break;
+        for (i = 0; i < n; i++) v[i] = fz[i] * (dyn / wnorm);
+        if (k >= 2 && fabs(sig - prev) <= 0.01 * sig) break;
+        prev = sig;
+    }
+    return 1.2 * sig;
+}
+
+double orc_sigma_power(const void *mp, double T, double p, const double *y, double *v,
+                       int32_t *iters)
+{
+    const orc_mech *m = (const orc_mech *)mp;
+    int n = m->nS, it = 0;
+    double *k = (double *)xmalloc(sizeof(double) * 2 * m->nR);
+    double *work = (double *)xmalloc(sizeof(double) * (2 * n + m->nR));
+    double *w = (double *)xmalloc(sizeof(double) * 3 * n);
+    orc_f F;
+    double sigma;
+    orc_rate_constants(m, T, k, k + m->nR);
+    F.m = m; F.T = T; F.p = p; F.k = k; F.k0 = k + m->nR; F.work = work; F.nfe = 0;
+    feval(&F, y, w);
+    sigma = power_sigma(&F, n, y, w, v, w + n, w + 2 * n, &it);
+    *iters = it;
+    free(k); free(work); free(w);
+    return sigma;
+}
+
 double orc_sigma(const void *mp, double T, double p, const double *y, double atol)
 {
     const orc_mech *m = (const orc_mech *)mp;
@@ -461,19 +528,30 @@ static int rkc_stages(double h, double sigma)
     return (int)s;
 }
 
-static int rkc_cell(orc_f *F, int n, double *y, double dt, double rtol, double atol,
-                    int max_steps, orc_stats *st)
+/* sigma by the selected estimator: 1 Gershgorin on the FD Jacobian,
+ * 2 nonlinear power method with warm start in ev */
+static double estimate_sigma(orc_f *F, int n, int est, const double *y, const double *f0,
+                             double atol, double *x, double *fx, double *rowsum, double *ev)
 {
-    double *v = (double *)xmalloc(sizeof(double) * n * 9);
+    int it;
+    if (est == 2) return power_sigma(F, n, y, f0, ev, x, fx, &it);
+    return gershgorin(F, n, y, f0, atol, x, fx, rowsum);
+}
+
+static int rkc_cell(orc_f *F, int n, double *y, double dt, double rtol, double atol,
+                    int max_steps, orc_stats *st, int est)
+{
+    double *v = (double *)xmalloc(sizeof(double) * n * 10);
     double *f0 = v, *x = v + n, *fx = v + 2 * n, *ys = v + 3 * n, *d = v + 4 * n;
-    double *wk = v + 5 * n, *rowsum = v + 8 * n;
+    double *wk = v + 5 * n, *rowsum = v + 8 * n, *ev = v + 9 * n;
     double t = 0.0, hmin = 1e-20 * dt, sigma, h, h0, e0, err_prev = 0.0, h_prev = 0.0;
     int i, status = 0, attempts = 0, since_sigma = 0, sigma_here, last_rejected = 0;
     int have_prev = 0;
 
     feval(F, y, f0);
     if (!all_finite(n, f0)) { free(v); return 3; }
-    sigma = gershgorin(F, n, y, f0, atol, x, fx, rowsum);
+    memcpy(ev, f0, sizeof(double) * n); /* first power-method direction */
+    sigma = estimate_sigma(F, n, est, y, f0, atol, x, fx, rowsum, ev);
     st->nsig++;
     sigma_here = 1;
     if (!isfinite(sigma)) { free(v); return 3; }
@@ -498,7 +576,7 @@ static int rkc_cell(orc_f *F, int n, double *y, double dt, double rtol, double a
         int s, last = 0;
         if (attempts >= max_steps) { status = 1; break; }
         if (since_sigma >= 25 || (last_rejected && !sigma_here)) {
-            sigma = gershgorin(F, n, y, f0, atol, x, fx, rowsum);
+            sigma = estimate_sigma(F, n, est, y, f0, atol, x, fx, rowsum, ev);
             st->nsig++;
             since_sigma = 0;
             sigma_here = 1;
@@ -586,7 +664,8 @@ void orc_rkc_single(const void *mp, double T, double p, const double *y, double 
 }
 
 /* Integrate `cells` independent cells over dt. Y is species-major,
- * Y[i * ldY + cell]; it is updated in place. method 0 = RKCK, 1 = RKC.
+ * Y[i * ldY + cell]; it is updated in place. method 0 = RKCK, 1 = RKC with
+ * the Gershgorin spectral radius, 2 = RKC with the power-method one.
  * Per-cell outputs (any may be NULL): status, and stats[cell] =
  * {f evaluations, accepted steps, rejected steps, sigma estimates}.
  * Returns the number of threads used.
@@ -617,7 +696,7 @@ int orc_integrate(const void *mp, int64_t cells, const double *Tc, const double 
         if (method == 0)
             st = rkck_cell(&F, n, y, dt, rtol, atol, max_steps, &S);
         else
-            st = rkc_cell(&F, n, y, dt, rtol, atol, max_steps, &S);
+            st = rkc_cell(&F, n, y, dt, rtol, atol, max_steps, &S, method);
         for (i = 0; i < n; i++) Y[(int64_t)i * ldY + c] = y[i];
         if (status) status[c] = (uint8_t)st;
         if (stats) {
@@ -647,7 +726,7 @@ int orc_trace_cell(const void *mp, double T, double p, double *y, double dt, dou
     orc_rate_constants(m, T, k, k + m->nR);
     F.m = m; F.T = T; F.p = p; F.k = k; F.k0 = k + m->nR; F.work = work; F.nfe = 0;
     st = method == 0 ? rkck_cell(&F, n, y, dt, rtol, atol, max_steps, &S)
-                     : rkc_cell(&F, n, y, dt, rtol, atol, max_steps, &S);
+                     : rkc_cell(&F, n, y, dt, rtol, atol, max_steps, &S, method);
     *len = S.len;
     free(k); free(work);
     return st;

@@ -39,13 +39,14 @@ def candidates(full: bool = False):
                                occupancy=occupancy)
 
 
-def time_config(mech, T, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2) -> Optional[float]:
+def time_config(mech, T, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2,
+                sigma=kin.SIGMA_GERSHGORIN) -> Optional[float]:
     """Mean kernel milliseconds of kin_integrate with `cfg`, or None if the
     shape is not supported."""
     cells = int(T.numel())
     try:
         ws = mech.workspace(method, precision, cells, cfg["block_threads"], cfg["blocks_per_sm"],
-                            T.device, cfg["staging"], cfg["occupancy"])
+                            T.device, cfg["staging"], cfg["occupancy"], sigma)
     except kin.KinError:
         return None
     Y = torch.empty_like(Y0)
@@ -55,7 +56,8 @@ def time_config(mech, T, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2) 
         Y.copy_(Y0)
         ev[0].record()
         try:
-            kin.integrate(mech, T, p, Y, dt, rtol, atol, method, precision, workspace=ws, **cfg)
+            kin.integrate(mech, T, p, Y, dt, rtol, atol, method, precision, workspace=ws,
+                          sigma=sigma, **cfg)
         except kin.KinError:
             return None
         ev[1].record()
@@ -67,11 +69,12 @@ def time_config(mech, T, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2) 
 
 
 def tune(mech: kin.Mechanism, desc, T, p, Y, dt, rtol, atol, method, precision,
-         use_cache: bool = True, verbose: bool = False, full: bool = False, reps: int = 1) -> Dict:
+         use_cache: bool = True, verbose: bool = False, full: bool = False, reps: int = 1,
+         sigma: int = kin.SIGMA_GERSHGORIN) -> Dict:
     """Best launch shape for this mechanism on the current GPU, timed on the
     given (device) cells: pass the cells of a representative call, since the
     persistent grid's tail depends on the cell count."""
-    key = _key(mech, method, precision, desc) + "|%d" % int(T.numel())
+    key = _key(mech, method, precision, desc) + "|%d|%d" % (int(T.numel()), sigma)
     cache = {}
     if use_cache and os.path.exists(CACHE):
         with open(CACHE) as f:
@@ -80,7 +83,7 @@ def tune(mech: kin.Mechanism, desc, T, p, Y, dt, rtol, atol, method, precision,
             return cache[key]
     results = []
     for cfg in candidates(full):
-        ms = time_config(mech, T, p, Y, dt, rtol, atol, method, precision, cfg, reps)
+        ms = time_config(mech, T, p, Y, dt, rtol, atol, method, precision, cfg, reps, sigma)
         if verbose:
             print("autotune", cfg, ms)
         if ms is not None:

@@ -88,9 +88,10 @@ int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
     return KIN_OK;
 }
 
-int64_t ws_bytes(const kin_mech* m, int precision, int64_t nslots, int64_t cells)
+int64_t ws_bytes(const kin_mech* m, const kin_opts* o, int64_t nslots, int64_t cells)
 {
-    return ws_layout(m->dev, precision, nslots, cells).total;
+    const int sig = o->method == KIN_RKC ? o->sigma : KIN_SIGMA_GERSHGORIN;
+    return ws_layout(m->dev, o->precision, sig, nslots, cells).total;
 }
 
 int check_opts(const kin_opts* o)
@@ -104,7 +105,8 @@ int check_opts(const kin_opts* o)
         return fail(KIN_EINVAL, "unknown staging %d", o->staging);
     if (o->occupancy != KIN_OCC_DEFAULT && o->occupancy != KIN_OCC_HIGH)
         return fail(KIN_EINVAL, "unknown occupancy %d", o->occupancy);
-    if (o->reserved != 0) return fail(KIN_EINVAL, "opts.reserved must be 0");
+    if (o->sigma != KIN_SIGMA_GERSHGORIN && o->sigma != KIN_SIGMA_POWER)
+        return fail(KIN_EINVAL, "unknown sigma estimator %d", o->sigma);
     return KIN_OK;
 }
 
@@ -269,7 +271,7 @@ int64_t kin_workspace_bytes(const kin_mech* m, const kin_opts* o, int64_t cells)
     Grid g;
     rc = grid_for(m, o, &g);
     if (rc) return rc;
-    return ws_bytes(m, o->precision, g.nslots, cells);
+    return ws_bytes(m, o, g.nslots, cells);
 }
 
 int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, const kin_opts* o,
@@ -310,7 +312,7 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     Grid g;
     rc = grid_for(m, o, &g);
     if (rc) return rc;
-    const int64_t need = ws_bytes(m, o->precision, g.nslots, total);
+    const int64_t need = ws_bytes(m, o, g.nslots, total);
     if (!ws) return fail(KIN_EINVAL, "workspace is NULL");
     if (((uintptr_t)ws) % 256) return fail(KIN_EINVAL, "workspace must be 256-byte aligned");
     if (ws_size < need) return fail(KIN_ENOMEM, "workspace has %lld bytes, needs %lld", (long long)ws_size, (long long)need);
@@ -328,7 +330,10 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     P.nslots = nslots;
     P.total = total;
     char* base = (char*)ws;
-    const WsLayout w = ws_layout(m->dev, o->precision, nslots, total);
+    const int sig = o->method == KIN_RKC ? o->sigma : KIN_SIGMA_GERSHGORIN;
+    const WsLayout w = ws_layout(m->dev, o->precision, sig, nslots, total);
+    P.sigma_method = sig;
+    P.cell_ev = sig == KIN_SIGMA_POWER ? (double*)(base + w.ev) : nullptr;
     P.queue = (unsigned long long*)(base + w.header);
     P.hist = (unsigned*)(base + w.header + 256);
     P.vec = (double*)(base + w.vec);
@@ -421,7 +426,7 @@ int kin_rates(const kin_mech* m, int64_t cells, const double* T, const double* p
     Grid g;
     int rc = grid_for(m, &o, &g);
     if (rc) return rc;
-    const int64_t need = ws_bytes(m, precision, g.nslots, cells);
+    const int64_t need = ws_bytes(m, &o, g.nslots, cells);
     if (!ws || ((uintptr_t)ws) % 256) return fail(KIN_EINVAL, "workspace must be non-NULL and 256-byte aligned");
     if (ws_size < need) return fail(KIN_ENOMEM, "workspace has %lld bytes, needs %lld", (long long)ws_size, (long long)need);
     if (!is_device_ptr(ws)) return fail(KIN_EINVAL, "workspace must be device memory");

@@ -112,7 +112,8 @@ __global__ void rkc_table_kernel(double* tab)
 // -------------------------------------------------------- host launchers --
 static int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
 
-WsLayout ws_layout(const MechDev& M, int precision, int64_t nslots, int64_t cells)
+WsLayout ws_layout(const MechDev& M, int precision, int sigma_method, int64_t nslots,
+                   int64_t cells)
 {
     const int64_t rb = precision == KIN_MIXED ? 4 : 8;
     WsLayout w;
@@ -122,6 +123,7 @@ WsLayout ws_layout(const MechDev& M, int precision, int64_t nslots, int64_t cell
     w.lane_r = off;  off += al256((int64_t)(M.nS + 2 * M.nR + M.nFO) * rb * nslots);
     w.cell_k = off;  off += al256((int64_t)(M.nR + M.nFO) * rb * cells);
     w.f0 = off;      off += al256((int64_t)M.nS * 8 * cells);
+    w.ev = off;      off += sigma_method == KIN_SIGMA_POWER ? al256((int64_t)M.nS * 8 * cells) : 0;
     w.sig = off;     off += al256(8 * cells);
     w.h = off;       off += al256(8 * cells);
     w.nfe = off;     off += al256(4 * cells);
@@ -171,7 +173,7 @@ cudaError_t launch_rates(const MechDev& M, int64_t cells, const double* T, const
                          const double* Y, int64_t ldY, double* dYdt, int precision, void* ws,
                          int64_t nslots, int blocks, int threads, cudaStream_t st)
 {
-    const WsLayout w = ws_layout(M, precision, nslots, cells);
+    const WsLayout w = ws_layout(M, precision, KIN_SIGMA_GERSHGORIN, nslots, cells);
     char* b = (char*)ws;
     if (precision == KIN_MIXED)
         rates_kernel<float><<<blocks, threads, 0, st>>>(M, cells, T, p, Y, ldY, dYdt, b + w.lane_r,

@@ -238,6 +238,10 @@ struct Views {
     {
         return Lane<R>{reinterpret_cast<R*>(L.cell_k) + (int64_t)M.nR * L.total + g, (int32_t)L.total};
     }
+    __device__ __forceinline__ Lane<double> EVcell(int64_t g) const
+    {
+        return Lane<double>{L.cell_ev + g, (int32_t)L.total};
+    }
     __device__ __forceinline__ Lane<double> F0cell(int64_t g) const
     {
         return Lane<double>{L.cell_f0 + g, (int32_t)L.total};
@@ -255,6 +259,66 @@ __device__ __forceinline__ double rms(int n, double rtol, double atol, Lane<doub
         acc += r * r;
     }
     return sqrt(acc / n);
+}
+
+// ------------------------------------------------- power-method sigma ---
+// Nonlinear power method (the paper's spectral-radius estimator, end of
+// Section 2.3): w = f(y + v) - f(y) ~ J v with v rescaled to length
+// dyn = sqrt(u) ||y||_2, warm-started from the previous estimate's direction
+// (f(y0) at the first estimate, all ones if that is zero); stop when two
+// successive ||w||/dyn agree to 1 % or after 20 products; sigma = 1.2 x the
+// last value (the iteration approaches |lambda_max| from below).
+struct PowerState {
+    int k;
+    double prev, dyn, sig;
+};
+
+template <typename R>
+__device__ void power_begin(int nS, Lane<double> Y, Lane<double> EV, Lane<double> X, PowerState& P)
+{
+    double yn = 0.0, vn = 0.0;
+    for (int i = 0; i < nS; ++i) {
+        yn += Y[i] * Y[i];
+        vn += EV[i] * EV[i];
+    }
+    yn = sqrt(yn);
+    P.dyn = yn > 0.0 ? Tab<R>::sqrt_u * yn : Tab<R>::sqrt_u;
+    vn = sqrt(vn);
+    if (!(vn > 0.0) || !isfinite(vn)) {
+        for (int i = 0; i < nS; ++i) EV[i] = 1.0;
+        vn = sqrt((double)nS);
+    }
+    const double sc = P.dyn / vn;
+    for (int i = 0; i < nS; ++i) {
+        EV[i] = EV[i] * sc;
+        X[i] = Y[i] + EV[i];
+    }
+    P.k = 1;
+    P.prev = 0.0;
+    P.sig = 0.0;
+}
+
+// FX holds f(Y + EV). Updates EV; returns true when the estimate is final
+// (then sigma = 1.2 P.sig); otherwise X is set to the next point Y + EV.
+__device__ __forceinline__ bool power_post(int nS, Lane<double> Y, Lane<double> F0, Lane<double> EV,
+                           Lane<double> X, Lane<double> FX, PowerState& P)
+{
+    double wn = 0.0;
+    for (int i = 0; i < nS; ++i) {
+        const double w = FX[i] - F0[i];
+        FX[i] = w;
+        wn += w * w;
+    }
+    wn = sqrt(wn);
+    P.sig = wn / P.dyn;
+    if (!(wn > 0.0) || !isfinite(wn)) return true;
+    const double sc = P.dyn / wn;
+    for (int i = 0; i < nS; ++i) EV[i] = FX[i] * sc;
+    if (P.k >= 2 && fabs(P.sig - P.prev) <= 0.01 * P.sig) return true;
+    P.prev = P.sig;
+    if (++P.k > 20) return true;
+    for (int i = 0; i < nS; ++i) X[i] = Y[i] + EV[i];
+    return false;
 }
 
 // ------------------------------------------------------------- pre-pass --
@@ -290,7 +354,18 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
         uint8_t st = ok ? 0 : KIN_CELL_NONFINITE;
         double sigma = 0.0, h = I.dt;
         int nfe = 1;
-        if (METHOD == KIN_RKC && ok) {
+        if (METHOD == KIN_RKC && ok && L.sigma_method == KIN_SIGMA_POWER) {
+            Lane<double> EV = W.EVcell(g);
+            for (int i = 0; i < nS; ++i) EV[i] = F0[i];  // first direction: f(y0)
+            PowerState P;
+            power_begin<R>(nS, Y, EV, X, P);
+            for (;;) {
+                feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, X, FX);
+                nfe++;
+                if (power_post(nS, Y, F0, EV, X, FX, P)) break;
+            }
+            sigma = 1.2 * P.sig;
+        } else if (METHOD == KIN_RKC && ok) {
             for (int k = 0; k < nS; ++k) {  // Gershgorin columns
                 const double eps = Tab<R>::sqrt_u * fmax(fabs(Y[k]), I.atol);
                 X[k] = Y[k] + eps;
@@ -301,6 +376,8 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
             }
             for (int i = 0; i < nS; ++i) sigma = fmax(sigma, RS[i]);
             nfe += nS;
+        }
+        if (METHOD == KIN_RKC && ok) {
             if (!isfinite(sigma)) {
                 st = KIN_CELL_NONFINITE;
             } else {
@@ -341,6 +418,7 @@ __device__ __forceinline__ int cost_bucket(const Launch& L, int64_t g)
 enum Phase : int {
     PH_F0 = 0,   // RKCK: f at the current accepted state -> F0
     PH_SIG,      // RKC: f at Y + eps_k e_k (Gershgorin column k) -> FX
+    PH_POW,      // RKC: f at Y + v (power-method product) -> FX
     PH_STAGE,    // RKC: f(w_{j-1}) -> FX, then w_j
     PH_FINAL,    // RKC: f(w_s) -> FX, error estimate and control
     PH_K,        // RKCK: f at a stage point -> F[st]
@@ -374,8 +452,9 @@ struct LaneState {
     int since_sigma;
     bool last, last_rejected, have_prev, sigma_here;
     int iw1, iw2;  // RKC: slots of w_{j-1}, w_{j-2}
-    double t, dt, h, hh, hprev, cprev, sigma, eps, rtol, atol, Ctot, invCtot;
+    double t, dt, h, hh, hprev, cprev, sigma, eps, rtol, atol, Ctot, invCtot, invN;
     int in_v, out_v;  // vectors read and written by the next f evaluation
+    PowerState P;     // RKC power-method sigma in progress
 };
 
 template <int METHOD, typename R, int STG>
@@ -424,9 +503,15 @@ struct Integrator {
                 Y[k] = I.Y[(int64_t)k * I.ldY + S.cell];
                 F0[k] = F0c[k];
             }
+            if (METHOD == KIN_RKC && L.sigma_method == KIN_SIGMA_POWER) {
+                // the pre-pass estimate's direction warm-starts the next one
+                Lane<double> EV = V(V_RS), EVc = W.EVcell(g);
+                for (int k = 0; k < M.nS; ++k) EV[k] = EVc[k];
+            }
             S.dt = I.dt;
             S.rtol = I.rtol;
             S.atol = I.atol;
+            S.invN = 1.0 / M.nS;
             S.t = 0.0;
             S.h = L.cell_h[g];
             S.sigma = L.cell_sig[g];
@@ -463,9 +548,17 @@ struct Integrator {
         finish_stats(S, code);
     }
 
-    // Start a Gershgorin estimate at Y: X = Y + eps_0 e_0, RS = 0.
+    // Start a spectral-radius estimate at Y: power method (X = Y + v) or
+    // Gershgorin (X = Y + eps_0 e_0, RS = 0).
     __device__ void sigma_begin(LaneState& S)
     {
+        if (L.sigma_method == KIN_SIGMA_POWER) {
+            power_begin<R>(M.nS, V(V_Y), V(V_RS), V(V_X), S.P);
+            S.phase = PH_POW;
+            S.in_v = V_X;
+            S.out_v = V_FX;
+            return;
+        }
         Lane<double> Y = V(V_Y), X = V(V_X), RS = V(V_RS);
         for (int i = 0; i < M.nS; ++i) {
             X[i] = Y[i];
@@ -572,6 +665,15 @@ struct Integrator {
             if (!isfinite(S.sigma)) return KIN_CELL_NONFINITE;
             return rkc_begin_step(S);
         }
+        if (S.phase == PH_POW) {
+            if (!power_post(M.nS, V(V_Y), V(V_F0), V(V_RS), V(V_X), V(V_FX), S.P)) return -1;
+            S.sigma = 1.2 * S.P.sig;
+            S.nsig++;
+            S.since_sigma = 0;
+            S.sigma_here = true;
+            if (!isfinite(S.sigma)) return KIN_CELL_NONFINITE;
+            return rkc_begin_step(S);
+        }
         // PH_FINAL: error estimate (Section 2.3) and step control
         Lane<double> Y = V(V_Y), F0 = V(V_F0), WS = V(S.iw1), FX = V(V_FX);
         double acc = 0.0;
@@ -582,17 +684,17 @@ struct Integrator {
             const double r = d / sc;
             acc += r * r;
         }
-        const double err = sqrt(acc / M.nS);
+        const double err = sqrt(acc * S.invN);
         S.attempts++;
         if (err <= 1.0) {
             S.nacc++;
             // err^(1/3) once; err^(2/3) = (err^(1/3))^2; the previous step's
-            // err^(1/3) is kept for the predictive factor.
+            // err^(1/3) is kept for the predictive factor (one division).
             const double c3 = cbrt(err);
             double fac;
             if (err == 0.0) fac = 10.0;
             else if (S.have_prev && !S.last_rejected && S.cprev > 0.0)
-                fac = 0.8 * (hh / S.hprev) * S.cprev / (c3 * c3);
+                fac = 0.8 * hh * S.cprev / (S.hprev * c3 * c3);
             else fac = 0.8 / c3;
             fac = fmin(10.0, fmax(0.1, fac));
             for (int i = 0; i < M.nS; ++i) {

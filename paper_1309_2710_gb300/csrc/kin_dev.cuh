@@ -63,7 +63,7 @@ constexpr int NVEC = 8;
 
 struct Launch {
     MechDev M;
-    int method, precision, max_steps, n_inst;
+    int method, precision, max_steps, n_inst, sigma_method;
     int64_t nslots;                 // lanes of the persistent grid
     int64_t total;                  // cells over all instances
     unsigned long long* queue;      // next position in `order`
@@ -75,6 +75,7 @@ struct Launch {
     // per cell (global cell index g over all instances)
     void* cell_k;                   // k_j [nR][total], then k0/kinf [nFO][total], rate type
     double* cell_f0;                // f(y0) [nS][total]
+    double* cell_ev;                // power-method direction [nS][total] (power sigma only)
     double* cell_sig;               // RKC spectral radius at y0 [total]
     double* cell_h;                 // first trial step [total]
     int32_t* cell_nfe;              // f evaluations spent before the main kernel [total]
@@ -86,9 +87,10 @@ struct Launch {
 
 // Workspace layout for `cells` cells and `nslots` lanes.
 struct WsLayout {
-    int64_t header, vec, lane_r, cell_k, f0, sig, h, nfe, st, order, total;
+    int64_t header, vec, lane_r, cell_k, f0, ev, sig, h, nfe, st, order, total;
 };
-WsLayout ws_layout(const MechDev& M, int precision, int64_t nslots, int64_t cells);
+WsLayout ws_layout(const MechDev& M, int precision, int sigma_method, int64_t nslots,
+                   int64_t cells);
 
 // Host-side helpers implemented in kernels.cu.
 cudaError_t launch_integrate(Launch& L, int staging, int occupancy, int blocks, int threads,

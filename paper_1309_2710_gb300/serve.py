@@ -68,6 +68,7 @@ class Group:
     method: int
     precision: int
     blocks_per_sm: int = 0
+    sigma: int = kin.SIGMA_GERSHGORIN
 
 
 @dataclass
@@ -121,7 +122,8 @@ class Server:
     def _launch(self, gname: str, slot: _Slot, batch: List[Request], now: float):
         g = self.groups[gname]
         cells = sum(r.cells for r in batch)
-        need = g.mech.workspace_bytes(g.method, g.precision, cells, 0, g.blocks_per_sm)
+        need = g.mech.workspace_bytes(g.method, g.precision, cells, 0, g.blocks_per_sm,
+                                      sigma=g.sigma)
         if slot.workspace is None or slot.workspace.numel() < need:
             slot.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
         with torch.cuda.stream(slot.stream):
@@ -134,7 +136,7 @@ class Server:
                 parts.append(kin.Cells(Td, pd, Yd, r.dt, r.rtol, r.atol, sd))
                 r.t_launch = now
             kin.integrate_batch(g.mech, parts, g.method, g.precision, workspace=slot.workspace,
-                                stream=slot.stream, blocks_per_sm=g.blocks_per_sm)
+                                stream=slot.stream, blocks_per_sm=g.blocks_per_sm, sigma=g.sigma)
             for r in batch:
                 r.Y_out.copy_(r._dev[2], non_blocking=True)
                 r.status.copy_(r._dev[3], non_blocking=True)
@@ -214,11 +216,11 @@ def one_launch_per_request(groups: Dict[str, Group], requests: List[Request], de
             _h2d(Td, r.T)
             _h2d(pd, r.p)
             _h2d(Yd, r.Y)
-            need = g.mech.workspace_bytes(g.method, g.precision, n)
+            need = g.mech.workspace_bytes(g.method, g.precision, n, sigma=g.sigma)
             if r.group not in ws or ws[r.group].numel() < need:
                 ws[r.group] = torch.empty(need, dtype=torch.uint8, device=device)
             kin.integrate(g.mech, Td, pd, Yd, r.dt, r.rtol, r.atol, g.method, g.precision,
-                          status=sd, workspace=ws[r.group], stream=stream)
+                          status=sd, workspace=ws[r.group], stream=stream, sigma=g.sigma)
             r.Y_out = torch.empty((nS, n), dtype=torch.float64, pin_memory=True)
             r.status = torch.empty(n, dtype=torch.uint8, pin_memory=True)
             r.Y_out.copy_(Yd, non_blocking=True)
@@ -276,7 +278,8 @@ def default_groups(blocks_per_sm: int = 2):
     for name in ("h2co_13sp_rkc", "ch4_53sp_rkc_mixed"):
         w = synth.WORKLOADS[name]
         m = synth.workload_mechanism(name)
-        groups[name] = Group(kin.Mechanism(m), w["method"], w["precision"], blocks_per_sm)
+        groups[name] = Group(kin.Mechanism(m), w["method"], w["precision"], blocks_per_sm,
+                             w["sigma"])
         pools[name] = StatePool(name, m, 65536 + 1024)
     return groups, pools
 

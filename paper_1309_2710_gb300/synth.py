@@ -298,23 +298,27 @@ def make_states(mech: Mechanism, cells: int, T_range=(1000.0, 1500.0),
 # ---------------------------------------------------------------------------
 RKCK, RKC = 0, 1
 FP64, MIXED = 0, 1
+GERSHGORIN, POWER = 0, 1  # RKC spectral-radius estimator
 
 WORKLOADS = {
     "h2_9sp_rkck": dict(idx=1, n_species=9, n_reactions=38, elements=("H", "O", "N"),
                         tb=0.0, fo=0.0, cells=4096, T=(1000.0, 1500.0), p=(1.0, 1.0),
-                        dt=1e-7, rtol=1e-6, atol=1e-10, method=RKCK, precision=FP64),
+                        dt=1e-7, rtol=1e-6, atol=1e-10, method=RKCK, precision=FP64,
+                        sigma=GERSHGORIN),
     "h2co_13sp_rkc": dict(idx=2, n_species=13, n_reactions=54, elements=("H", "O", "C", "N"),
                           tb=0.10, fo=0.0, cells=262144, T=(900.0, 2000.0), p=(1.0, 1.0),
-                          dt=1e-6, rtol=1e-6, atol=1e-10, method=RKC, precision=FP64),
+                          dt=1e-6, rtol=1e-6, atol=1e-10, method=RKC, precision=FP64,
+                          sigma=GERSHGORIN),
     "ch4_53sp_rkc_mixed": dict(idx=3, n_species=53, n_reactions=634,
                                elements=("H", "O", "C", "N"), tb=0.08, fo=0.04,
                                cells=131072, T=(800.0, 2200.0), p=(1.0, 20.0),
-                               dt=1e-6, rtol=1e-6, atol=1e-10, method=RKC, precision=MIXED),
+                               dt=1e-6, rtol=1e-6, atol=1e-10, method=RKC, precision=MIXED,
+                               sigma=POWER),
     "c2h4_111sp_rkc_batched": dict(idx=4, n_species=111, n_reactions=1566,
                                    elements=("H", "O", "C", "N"), tb=0.08, fo=0.04,
                                    cells=None, T=None, T_bimodal=((700.0, 900.0), (1800.0, 2400.0)),
                                    p=(1.0, 1.0), dt=(1e-6, 1e-5), rtol=1e-6, atol=1e-10,
-                                   method=RKC, precision=FP64, instances=16,
+                                   method=RKC, precision=FP64, sigma=POWER, instances=16,
                                    inst_cells=(512, 65536)),
 }
 

@@ -327,3 +327,47 @@ def test_launch_shapes_are_bitwise_identical(method, name):
             ref = Yd
         else:
             assert torch.equal(Yd, ref), shape
+
+
+# ------------------------------------------------- power-method sigma ---
+def run_gpu_sig(km, T, p, Y, dt, rtol, atol, precision, sigma, max_steps=20000):
+    cells = T.shape[0]
+    Yd = dev(Y)
+    st = torch.full((cells,), 255, dtype=torch.uint8, device=DEV)
+    sta = torch.zeros((cells, 4), dtype=torch.int32, device=DEV)
+    kin.integrate(km, dev(T), dev(p), Yd, dt, rtol, atol, kin.RKC, precision, status=st, stats=sta,
+                  max_steps=max_steps, sigma=sigma)
+    torch.cuda.synchronize()
+    return Yd.cpu().numpy(), st.cpu().numpy(), sta.cpu().numpy()
+
+
+@pytest.mark.parametrize("name,cells", [("h2co_13sp_rkc", 4133), ("ch4_53sp_rkc_mixed", 300),
+                                        ("c2h4_111sp_rkc_batched", 64)])
+def test_rkc_power_sigma_fp64(name, cells):
+    """RKC with the power-method spectral radius (the paper's estimator):
+    FP64 GPU path against the oracle's power-method variant."""
+    w = synth.WORKLOADS[name]
+    m, km, om = mech(name)
+    dt = w["dt"] if not isinstance(w["dt"], tuple) else w["dt"][1]
+    T, p, Y = synth.workload_states(name, m, cells=cells, seed_offset=21)
+    Yg, stg, stag = run_gpu_sig(km, T, p, Y, dt, w["rtol"], w["atol"], kin.FP64, kin.SIGMA_POWER)
+    Yo, sto, stao, _ = oracle.integrate(om, T, p, Y, dt, w["rtol"], w["atol"], oracle.RKC_POWER)
+    # power-iteration stopping tests can flip on rounding like the other
+    # decisions; allow a few percent of trace-divergent cells at 10 rtol
+    s = compare(Yg, Yo, stg, sto, stag, stao, w["atol"], w["rtol"], max_div_frac=0.05)
+    print("rkc power", name, s, "mean nfe gpu %.1f oracle %.1f" % (stag[:, 0].mean(), stao[:, 0].mean()))
+
+
+def test_rkc_power_sigma_mixed():
+    name = "ch4_53sp_rkc_mixed"
+    w = synth.WORKLOADS[name]
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m, cells=1024, seed_offset=22)
+    Yg, stg, stag = run_gpu_sig(km, T, p, Y, w["dt"], w["rtol"], w["atol"], kin.MIXED, kin.SIGMA_POWER)
+    idx = np.arange(0, 1024, 8)
+    Yo, sto, stao, _ = oracle.integrate(om, T[idx], p[idx], Y[:, idx], w["dt"], w["rtol"], w["atol"],
+                                        oracle.RKC_POWER)
+    assert (stg[idx] == sto).all()
+    e = tol_rel_err(Yg[:, idx], Yo, w["atol"], w["rtol"])
+    print("mixed power: max %.3e" % e.max())
+    assert e.max() <= 1e-5

@@ -50,6 +50,13 @@ MUTANTS = [
      [pins.test_gershgorin_on_linear_chain]),
     ("initial step factor", "0.1 * h0 / sqrt(e0)", "0.2 * h0 / sqrt(e0)",
      [pins.test_rkc_controller_trace_on_linear_decay]),
+    ("power margin dropped", "    return 1.2 * sig;\n}", "    return 1.0 * sig;\n}",
+     [pins.test_power_method_on_linear_chain]),
+    ("power residual sign", "fz[i] -= f0[i];", "fz[i] += f0[i];",
+     [pins.test_power_method_on_linear_chain, pins.test_power_method_diagonal_jacobian_exact]),
+    ("power direction not renormalised", "for (i = 0; i < n; i++) v[i] = fz[i] * (dyn / wnorm);",
+     "for (i = 0; i < n; i++) v[i] = fz[i];",
+     [pins.test_power_method_on_linear_chain]),
 ]
 
 

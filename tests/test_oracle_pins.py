@@ -550,3 +550,62 @@ def test_status_codes():
     Y2[3, 1] = np.nan
     Yn, st, _, _ = oracle.integrate(om, T, p, Y2, 1e-6, 1e-6, 1e-10, oracle.RKCK)
     assert st[0] == 0 and st[1] == 3
+
+
+# ------------------------------------------------------- power method ---
+def test_power_method_on_linear_chain():
+    """On A_0 -> A_1 -> ... (eigenvalues -k_i, 0) the nonlinear power method
+    converges to |lambda_max| = max k_i; the estimate carries a 1.2 margin."""
+    ks = [3e8, 1e9, 2.5e8, 7e9, 1e3]
+    om = oracle.Mech(mechs.chain(ks))
+    y = np.array([0.3, 0.2, 0.1, 0.25, 0.1, 0.05])
+    sig, v, it = oracle.sigma_power(om, 1500.0, 101325.0, y)
+    assert sig / 1.2 == pytest.approx(max(ks), rel=0.01, abs=0)
+    assert 2 <= it <= 20
+    # the direction is the dominant eigenvector: J v ~ -k_max v on species 3, 4
+    u = v / np.linalg.norm(v)
+    assert abs(u[3]) > 0.6 and abs(u[4]) > 0.6
+
+
+def test_power_method_below_gershgorin_and_warm_start():
+    """|lambda| <= Gershgorin bound: sigma/1.2 never exceeds it (up to the FD
+    error); a warm start from the last direction needs at most as many
+    products as the cold start from f(y)."""
+    name = "ch4_53sp_rkc_mixed"
+    m = synth.workload_mechanism(name)
+    om = oracle.Mech(m)
+    T, p, Y = synth.workload_states(name, m, cells=6)
+    for c in range(6):
+        g = oracle.sigma(om, T[c], p[c], Y[:, c], 1e-10)
+        s1, v, it1 = oracle.sigma_power(om, T[c], p[c], Y[:, c])
+        assert s1 / 1.2 <= g * (1 + 1e-6)
+        s2, _, it2 = oracle.sigma_power(om, T[c], p[c], Y[:, c], v0=v)
+        assert it2 <= it1
+        assert s2 == pytest.approx(s1, rel=0.03, abs=0)
+
+
+def test_power_method_diagonal_jacobian_exact():
+    """Two independent decays A -> B (k1) and C -> D (k2): the Jacobian's
+    eigenvalues are -k1, -k2, 0, 0; the power method finds max(k1, k2)."""
+    W = 20.0
+    m = mechs.mech([W] * 4, [dict(reac=[0], prod=[1], A=5e7), dict(reac=[2], prod=[3], A=2e6)])
+    om = oracle.Mech(m)
+    sig, _, it = oracle.sigma_power(om, 1000.0, 1e5, np.array([0.4, 0.1, 0.3, 0.2]))
+    assert sig / 1.2 == pytest.approx(5e7, rel=0.01, abs=0)
+
+
+@pytest.mark.parametrize("name", ["h2co_13sp_rkc", "ch4_53sp_rkc_mixed"])
+def test_power_method_integration_accuracy(name):
+    """RKC with the power-method spectral radius: conservation and agreement
+    with the Gershgorin variant within the tolerance scale; fewer f evals."""
+    m = synth.workload_mechanism(name)
+    om = oracle.Mech(m)
+    w = synth.WORKLOADS[name]
+    T, p, Y = synth.workload_states(name, m, cells=8)
+    Yg, sg, stg, _ = oracle.integrate(om, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKC)
+    Yp, sp, stp, _ = oracle.integrate(om, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKC_POWER)
+    assert (sp == 0).all()
+    np.testing.assert_allclose(Yp.sum(0), 1.0, atol=1e-13)
+    scale = np.maximum(np.abs(Yg), w["atol"] / w["rtol"])
+    assert (np.abs(Yp - Yg) / scale).max() < 10 * w["rtol"]
+    assert stp[:, 0].sum() < stg[:, 0].sum()

@@ -21,7 +21,7 @@ def setup():
     for name in ("h2co_13sp_rkc", "ch4_53sp_rkc_mixed"):
         w = synth.WORKLOADS[name]
         m = synth.workload_mechanism(name)
-        groups[name] = serve.Group(kin.Mechanism(m), w["method"], w["precision"], 2)
+        groups[name] = serve.Group(kin.Mechanism(m), w["method"], w["precision"], 2, w["sigma"])
         pools[name] = serve.StatePool(name, m, 8192, seed_offset=900)
     return groups, pools
 
@@ -47,7 +47,7 @@ def _alone(groups, r):
     Yd = r.Y.to(d).contiguous()
     st = torch.empty(r.cells, dtype=torch.uint8, device=d)
     kin.integrate(g.mech, r.T.to(d), r.p.to(d), Yd, r.dt, r.rtol, r.atol, g.method, g.precision,
-                  status=st)
+                  status=st, sigma=g.sigma)
     torch.cuda.synchronize()
     return Yd.cpu(), st.cpu()
 
