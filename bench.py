@@ -40,8 +40,11 @@ L2_FLUSH_BYTES = 256 << 20
 # 2 FP64 lanes per SM per clock x 152 SMs x 2070 MHz = 629.3 G lane-ops/s
 # (1258.6 GFLOP/s counting an FMA as 2 flops). Every FP64 add, multiply,
 # divide or FMA occupies one lane-op of that pipe, so the roofline is stated
-# in FP64 operations; the flop-based fraction is reported beside it.
+# in operations. The FP32 pipe (128 lanes per SM per clock, 40.3 T lane-ops/s)
+# runs the mixed path's rate arithmetic concurrently; the pipe with the
+# larger operations / peak binds.
 FP64_LANES_PER_SM = 2
+FP32_LANES_PER_SM = 128
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
@@ -51,32 +54,15 @@ TRAFFIC = {}
 
 
 def kernel_hash() -> str:
-    p = os.path.join(ROOT, "paper_1309_2710_gb300", "csrc", "kernels.cu")
-    return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+    d = os.path.join(ROOT, "paper_1309_2710_gb300", "csrc")
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:12]
 
 
 # ------------------------------------------------------ algorithmic work ---
-def feval_flops(m) -> int:
-    """FP64 operations of one evaluation of f (an add, multiply or divide is
-    one flop; a fused multiply-add two), counted from the mechanism tables."""
-    nS = m.n_species
-    f = 3 * nS + 1  # Y/W, sum, rho, C
-    for j in range(m.n_reactions):
-        f += int(np.count_nonzero(m.reac[j] >= 0))  # k * prod C
-        if m.rtype[j] == synth.THIRD_BODY:
-            f += 2 * nS + 1
-        elif m.rtype[j] == synth.FALLOFF:
-            f += 2 * nS + 4
-    # stoichiometric sum: one add per net nonzero (a coefficient of 2 adds a multiply)
-    for i in range(nS):
-        for j in range(m.n_reactions):
-            nu = int(np.sum(m.prod[j] == i)) - int(np.sum(m.reac[j] == i))
-            if nu:
-                f += 1 if abs(nu) == 1 else 2
-    f += 2 * nS + 1  # dY/dt = W omega / rho
-    return f
-
-
 def feval_ops(m) -> int:
     """FP64 operations of one evaluation of f in its minimal fused form
     (an FMA, add, multiply or divide is one operation)."""
@@ -96,39 +82,48 @@ def feval_ops(m) -> int:
     return o
 
 
-def algorithmic_ops(m, method, stats) -> float:
-    """Algorithmic FP64 operations of one call from the per-cell counts."""
+def algorithmic_work(m, method, precision, sigma, stats):
+    """Algorithmic operations of one call, from the per-cell counts (f
+    evaluations, accepted and rejected steps, spectral-radius estimates), as
+    (FP64 lane-ops, FP32 lane-ops, exact). An FMA, add, multiply or divide is
+    one operation; conversions are not counted.
+
+    f costs feval_ops(m). In the mixed path its rate arithmetic is FP32 and
+    only the final scaling dY/dt = W omega / rho (2 nS + 1) is FP64, while
+    every spectral-radius evaluation is FP64, including the re-evaluation of
+    f(y) that each estimate starts from. RKC vector work (FP64): per attempt
+    w_1 and the error estimate and norm (8 nS), per further stage the
+    recursion (5 nS); Gershgorin: 3 nS per column; power method: 4 nS per
+    product; initial step 6 nS. The Gershgorin count is exact. The power
+    method's number of products per estimate is not recorded, so it is bounded
+    from the side that keeps the count a lower bound: 20 products in FP64
+    (fewer stages), 2 in mixed precision (fewer FP64 evaluations)."""
     nS = m.n_species
+    fo = feval_ops(m)
+    mixed = precision == synth.MIXED
+    f64 = 2 * nS + 1 if mixed else fo  # FP64 part of one rate-type f evaluation
+    f32 = fo - f64
     nfe = stats[:, 0].astype(np.float64)
     att = (stats[:, 1] + stats[:, 2]).astype(np.float64)
     nsig = stats[:, 3].astype(np.float64)
-    total = nfe.sum() * feval_ops(m)
-    if method == synth.RKC:
-        stages = nfe - 2 - nsig * nS
-        # w_j: 5 nS per stage after the first; per attempt w_1 (nS) and the
-        # error estimate and norm (7 nS)
-        total += ((stages - att) * 5 * nS + att * 8 * nS).sum()
-        total += (nsig * 3 * nS * nS).sum() + 6 * nS * len(nfe)  # sigma, initial step
+    if method != synth.RKC:
+        return float((nfe * f64 + att * 38 * nS).sum()), float((nfe * f32).sum()), True
+    base = 1 if mixed else 0
+    if sigma == synth.GERSHGORIN:
+        sig_evals = nsig * (nS + base)
+        sig_vec = nsig * 3 * nS * nS
+        exact = True
     else:
-        total += (att * 38 * nS).sum()  # stage points (20 nS), y5, error, tolerance
-    return float(total)
-
-
-def algorithmic_flops(m, method, stats) -> float:
-    """Algorithmic FP64 flops of one call, from per-cell counts
-    (f evaluations, accepted, rejected, spectral-radius estimates)."""
-    nS = m.n_species
-    nfe = stats[:, 0].astype(np.float64)
-    att = (stats[:, 1] + stats[:, 2]).astype(np.float64)
-    nsig = stats[:, 3].astype(np.float64)
-    total = nfe.sum() * feval_flops(m)
-    if method == synth.RKC:
-        stages = nfe - 2 - nsig * nS  # sum of s over attempts
-        total += ((stages - att) * 9 * nS + att * 12 * nS).sum()  # w_1, w_j, error + norm
-        total += (nsig * (3 * nS * nS + 3 * nS)).sum() + 14 * nS * len(nfe)  # sigma, initial step
-    else:
-        total += (att * 66 * nS).sum()  # stage points, y5, error, tolerance
-    return float(total)
+        per = 2 if mixed else 20
+        sig_evals = np.minimum(nsig * (per + base), np.maximum(nfe - 2 - att, 0))
+        sig_vec = (sig_evals - nsig * base) * 4 * nS
+        exact = False
+    rate_evals = nfe - sig_evals            # f(y0), the initial-step probe, the stages
+    stages = rate_evals - 2
+    vec = (stages - att) * 5 * nS + att * 8 * nS + sig_vec + 6 * nS
+    ops64 = (rate_evals * f64 + sig_evals * fo + vec).sum()
+    ops32 = (rate_evals * f32).sum()
+    return float(ops64), float(ops32), exact
 
 
 # ------------------------------------------------------------- clocks ---
@@ -306,10 +301,12 @@ def run_kin(args):
     Yd = torch.empty_like(Y0d)
     st = torch.zeros(cells, dtype=torch.uint8, device=dev)
     sta = torch.zeros((cells, 4), dtype=torch.int32, device=dev)
-    shape = dict(block_threads=0, blocks_per_sm=0, staging=kin.STAGE_GLOBAL, occupancy=kin.OCC_DEFAULT)
+    shape = dict(block_threads=0, blocks_per_sm=0, staging=kin.STAGE_GLOBAL, occupancy=kin.OCC_DEFAULT,
+                 layout=kin.LAYOUT_AUTO)
     if args.shape:
-        bt, bps, stg, occ = (int(x) for x in args.shape.split(","))
-        shape = dict(block_threads=bt, blocks_per_sm=bps, staging=stg, occupancy=occ)
+        v = [int(x) for x in args.shape.split(",")]
+        shape = dict(zip(("block_threads", "blocks_per_sm", "staging", "occupancy", "layout"), v))
+        shape.setdefault("layout", kin.LAYOUT_AUTO)
     elif not args.no_tune:
         # launch shape from the autotuner (cached per GPU, mechanism shape and
         # cell count), timed on this workload outside the timed region
@@ -318,7 +315,7 @@ def run_kin(args):
                              sigma=sigma)
         shape = {k: best[k] for k in shape}
     ws = km.workspace(method, prec, cells, shape["block_threads"], shape["blocks_per_sm"], dev,
-                      shape["staging"], shape["occupancy"], sigma)
+                      shape["staging"], shape["occupancy"], sigma, shape["layout"])
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -360,12 +357,15 @@ def run_kin(args):
 
     stats = sta.cpu().numpy()
     status = st.cpu().numpy()
-    flops = algorithmic_flops(m, method, stats)
-    ops = algorithmic_ops(m, method, stats)
+    ops64, ops32, exact = algorithmic_work(m, method, prec, sigma, stats)
     kavg = sum(kern_ms) / len(kern_ms)
-    achieved = ops / (kavg * 1e-3) / 1e9
-    peak = FP64_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
-    flop_rate = flops / (kavg * 1e-3) / 1e9
+    peak64 = FP64_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
+    peak32 = FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
+    # the two pipes run concurrently: the binding one sets the time bound
+    t64, t32 = ops64 / peak64, ops32 / peak32
+    bind64 = t64 >= t32
+    achieved = (ops64 if bind64 else ops32) / (kavg * 1e-3) / 1e9
+    peak = peak64 if bind64 else peak32
     tr = TRAFFIC.get(kernel_hash())
 
     # end to end: host (pinned) buffers through the public API, copies timed
@@ -414,14 +414,18 @@ def run_kin(args):
             "data": "synthetic (seeded generator standing in for the paper's mechanisms and states)",
             "config": dict(workload_config(name, cells, sigma), launch_shape=shape),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "G FP64 lane-ops/s", "frac": achieved / peak, "traffic": tr,
-                         "kernel": "kin_integrate launch (init_kernel + sort + integrate_kernel)",
-                         "peak_basis": "derived: 2 FP64 lanes/SM/clk x 152 SMs x 2070 MHz",
-                         "kernel_ms": kavg, "ops_per_launch": ops, "flops_per_launch": flops,
-                         "gflops": flop_rate, "flop_frac": flop_rate / (2 * peak)},
+                         "unit": "G %s lane-ops/s" % ("FP64" if bind64 else "FP32"),
+                         "frac": achieved / peak, "traffic": tr,
+                         "kernel": "kin_integrate launch (init + sort + integrate kernels, %s layout)"
+                                   % layout_name(km, method, shape),
+                         "peak_basis": "derived: %d %s lanes/SM/clk x 152 SMs x 2070 MHz"
+                                       % ((FP64_LANES_PER_SM, "FP64") if bind64 else (FP32_LANES_PER_SM, "FP32")),
+                         "kernel_ms": kavg, "fp64_ops_per_launch": ops64,
+                         "fp32_ops_per_launch": ops32, "ops_count": "exact" if exact else "lower bound",
+                         "fp64_frac": t64 / (kavg * 1e-3 * 1e9), "fp32_frac": t32 / (kavg * 1e-3 * 1e9)},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * (5 if method == synth.RKC else 2),
             "clocks": clk.summary(),
             "cell_status": np.bincount(status, minlength=4).tolist(),
             "mean_f_evals_per_cell": float(stats[:, 0].mean()),
@@ -508,6 +512,15 @@ def run_batched(args):
     return 0
 
 
+def layout_name(km, method, shape):
+    from paper_1309_2710_gb300 import kin
+    lay = shape.get("layout", kin.LAYOUT_AUTO)
+    if lay == kin.LAYOUT_AUTO:
+        lay = (kin.LAYOUT_WARP if method == kin.RKC and km.n_reactions > kin.WARP_MIN_REACTIONS
+               else kin.LAYOUT_LANE)
+    return "warp-per-cell" if lay == kin.LAYOUT_WARP else "lane-per-cell"
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -521,8 +534,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shape")
-    ap.add_argument("--shape", default="", help="block_threads,blocks_per_sm,staging,occupancy "
-                                                "(skips the autotuner)")
+    ap.add_argument("--shape", default="", help="block_threads,blocks_per_sm,staging,occupancy"
+                                                "[,layout] (skips the autotuner)")
     ap.add_argument("--mode", choices=["headline", "batched"], default="headline")
     ap.add_argument("--sigma", choices=["default", "gershgorin", "power"], default="default",
                     help="RKC spectral-radius estimator (default: the workload's)")

@@ -69,6 +69,19 @@ extern "C" {
 #define KIN_OCC_DEFAULT 0
 #define KIN_OCC_HIGH 1
 
+/* work decomposition across the GPU's lanes */
+#define KIN_LAYOUT_AUTO 0 /* library choice: KIN_LAYOUT_WARP for RKC when n_reactions >
+                             KIN_WARP_MIN_REACTIONS, else KIN_LAYOUT_LANE */
+#define KIN_LAYOUT_LANE 1 /* one lane integrates one cell (the paper's thread-per-ODE
+                             design, Section 3): per-cell arrays in the workspace or in
+                             shared memory (kin_opts.staging) */
+#define KIN_LAYOUT_WARP 2 /* one warp integrates one cell: its 32 lanes share the
+                             reactions and species of f; the cell's concentrations and
+                             rates of progress live in shared memory. RKC only
+                             (KIN_EUNSUPPORTED for RKCK). staging and occupancy are
+                             ignored; block_threads may be up to 256 */
+#define KIN_WARP_MIN_REACTIONS 256
+
 /* per-cell status */
 #define KIN_CELL_OK 0
 #define KIN_CELL_MAXSTEPS 1  /* attempted-step limit reached */
@@ -112,7 +125,8 @@ typedef struct {
     int32_t method;        /* KIN_RKCK or KIN_RKC */
     int32_t precision;     /* KIN_FP64 or KIN_MIXED */
     int32_t max_steps;     /* attempted steps per cell; <= 0 means 100000 */
-    int32_t block_threads; /* threads per block, multiple of 32; 0 = library choice */
+    int32_t block_threads; /* threads per block, multiple of 32, <= 128 (<= 256 with
+                              KIN_LAYOUT_WARP); 0 = library choice (128) */
     int32_t blocks_per_sm; /* persistent blocks per SM; 0 = as many as fit (<= 512 threads per
                               SM, 768 with KIN_OCC_HIGH) */
     int32_t staging;       /* KIN_STAGE_*: where f's per-lane arrays live. Shared staging
@@ -125,6 +139,10 @@ typedef struct {
                               finite-difference Jacobian, n_species f evaluations) or
                               KIN_SIGMA_POWER (nonlinear power method with warm start, the
                               paper's choice, end of Section 2.3); ignored for RKCK */
+    int32_t layout;        /* KIN_LAYOUT_*: one lane or one warp per cell. Both give the
+                              same method, decisions and statistics up to the rounding
+                              order of sums (results agree within the integration
+                              tolerance, not bit for bit) */
     void *stream;          /* cudaStream_t */
 } kin_opts;
 
@@ -235,7 +253,8 @@ int kin_integrate_noalloc(const kin_mech *m, int64_t cells, const double *T, con
  * (E:spec-rate), (E:rxn-rate), (E:rxn-const)) in the given precision
  * (KIN_FP64 or KIN_MIXED), enqueued on `stream`. T, p, Y, dYdt and workspace
  * are device pointers; dYdt has the layout of Y. The workspace rule is that of
- * kin_integrate with method KIN_RKC, the same precision and `cells` cells. Errors:
+ * kin_integrate with method KIN_RKC, the same precision, layout
+ * KIN_LAYOUT_LANE, default launch shape and `cells` cells. Errors:
  * KIN_EINVAL, KIN_ENOMEM, KIN_ECUDA. */
 int kin_rates(const kin_mech *m, int64_t cells, const double *T, const double *p,
               const double *Y, int64_t ldY, double *dYdt, int32_t precision, void *stream,

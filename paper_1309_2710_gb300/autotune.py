@@ -5,6 +5,8 @@ of the caller's cells over the candidate shapes:
   block_threads  32 .. 128 lanes per block (one cell per lane),
   blocks_per_sm  persistent blocks per SM (only shapes that fit),
   staging        per-lane rate scratch in the workspace or in shared memory,
+  layout         one lane or one warp per cell (RKC; the warp layout has only
+                 block_threads and blocks_per_sm to choose),
 and keeps the fastest. Results are cached per GPU and mechanism shape in a
 JSON file next to the built library.
 """
@@ -28,15 +30,36 @@ def _key(mech: kin.Mechanism, method: int, precision: int, desc) -> str:
     return "%s|%d|%d|%d|%d|%d" % (dev, mech.n_species, mech.n_reactions, n_m, method, precision)
 
 
-def candidates(full: bool = False):
-    """Launch shapes to try; `full` adds more block sizes and lane counts."""
+def lane_candidates(full: bool = False):
     for occupancy in (kin.OCC_DEFAULT, kin.OCC_HIGH):
         for staging in (kin.STAGE_GLOBAL, kin.STAGE_SHARED, kin.STAGE_SHARED_ALL):
             for threads in ((128, 64, 32) if full else (128, 32)):
                 for lanes in ((256, 384, 512, 640, 768) if full else (384, 512, 768)):
                     bps = lanes // threads
                     yield dict(block_threads=threads, blocks_per_sm=bps, staging=staging,
-                               occupancy=occupancy)
+                               occupancy=occupancy, layout=kin.LAYOUT_LANE)
+
+
+def warp_candidates(full: bool = False):
+    for threads in ((64, 128, 256) if full else (128, 256)):
+        for warps in ((8, 12, 16, 24, 32) if full else (8, 16, 24)):
+            bps = warps * 32 // threads
+            if bps >= 1:
+                yield dict(block_threads=threads, blocks_per_sm=bps, staging=kin.STAGE_GLOBAL,
+                           occupancy=kin.OCC_DEFAULT, layout=kin.LAYOUT_WARP)
+
+
+def candidates(full: bool = False, method: int = kin.RKC, n_reactions: int = 0):
+    """Launch shapes to try; `full` adds more block sizes and lane counts.
+    Mechanisms above the warp-layout threshold try warp shapes only (one lane
+    per cell is an order of magnitude slower there); smaller RKC mechanisms
+    try both layouts."""
+    if method == kin.RKC and n_reactions > kin.WARP_MIN_REACTIONS:
+        yield from warp_candidates(full)
+        return
+    yield from lane_candidates(full)
+    if method == kin.RKC:
+        yield from warp_candidates(False)
 
 
 def time_config(mech, T, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2,
@@ -46,7 +69,7 @@ def time_config(mech, T, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2,
     cells = int(T.numel())
     try:
         ws = mech.workspace(method, precision, cells, cfg["block_threads"], cfg["blocks_per_sm"],
-                            T.device, cfg["staging"], cfg["occupancy"], sigma)
+                            T.device, cfg["staging"], cfg["occupancy"], sigma, cfg["layout"])
     except kin.KinError:
         return None
     Y = torch.empty_like(Y0)
@@ -74,7 +97,7 @@ def tune(mech: kin.Mechanism, desc, T, p, Y, dt, rtol, atol, method, precision,
     """Best launch shape for this mechanism on the current GPU, timed on the
     given (device) cells: pass the cells of a representative call, since the
     persistent grid's tail depends on the cell count."""
-    key = _key(mech, method, precision, desc) + "|%d|%d" % (int(T.numel()), sigma)
+    key = _key(mech, method, precision, desc) + "|%d|%d|v2" % (int(T.numel()), sigma)
     cache = {}
     if use_cache and os.path.exists(CACHE):
         with open(CACHE) as f:
@@ -82,7 +105,7 @@ def tune(mech: kin.Mechanism, desc, T, p, Y, dt, rtol, atol, method, precision,
         if key in cache:
             return cache[key]
     results = []
-    for cfg in candidates(full):
+    for cfg in candidates(full, method, mech.n_reactions):
         ms = time_config(mech, T, p, Y, dt, rtol, atol, method, precision, cfg, reps, sigma)
         if verbose:
             print("autotune", cfg, ms)

@@ -53,7 +53,14 @@ bool is_device_ptr(const void* p)
 struct Grid {
     int threads, blocks;  // persistent grid
     int64_t nslots;
+    int layout;           // KIN_LAYOUT_LANE or KIN_LAYOUT_WARP (resolved)
 };
+
+int resolve_layout(const kin_mech* m, const kin_opts* o)
+{
+    if (o->layout != KIN_LAYOUT_AUTO) return o->layout;
+    return (o->method == KIN_RKC && m->nR > KIN_WARP_MIN_REACTIONS) ? KIN_LAYOUT_WARP : KIN_LAYOUT_LANE;
+}
 
 int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
 {
@@ -64,34 +71,46 @@ int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
     int nsm = 0;
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    int maxsm = 0;
+    e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    const int layout = resolve_layout(m, o);
     int threads = o->block_threads > 0 ? o->block_threads : 128;
-    if (threads % 32 != 0 || threads > 128) return fail(KIN_EINVAL, "block_threads must be a multiple of 32 and <= 128");
-    const int stg = o->staging;
-    if (stg > 0) {
-        int maxsm = 0;
-        e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-        if (smem_bytes(m->dev, o->precision, threads, stg) > (size_t)maxsm)
+    int occ = 0, cap = 0;
+    if (layout == KIN_LAYOUT_WARP) {
+        if (o->method != KIN_RKC) return fail(KIN_EUNSUPPORTED, "the warp-per-cell layout implements RKC only");
+        if (threads % 32 != 0 || threads > 256) return fail(KIN_EINVAL, "block_threads must be a multiple of 32 and <= 256");
+        const size_t sm = warp_smem(m->dev, o->precision, threads);
+        if (sm > (size_t)maxsm)
+            return fail(KIN_EUNSUPPORTED, "warp layout needs %zu bytes of shared memory per block (max %d)", sm, maxsm);
+        e = o->precision == KIN_MIXED ? occ_warp_f32(m->dev, threads, &occ) : occ_warp_f64(m->dev, threads, &occ);
+        cap = occ;  // as many as fit
+    } else {
+        if (threads % 32 != 0 || threads > 128) return fail(KIN_EINVAL, "block_threads must be a multiple of 32 and <= 128");
+        const int stg = o->staging;
+        if (stg > 0 && smem_bytes(m->dev, o->precision, threads, stg) > (size_t)maxsm)
             return fail(KIN_EUNSUPPORTED, "shared-memory staging needs %zu bytes per block (max %d)",
                         smem_bytes(m->dev, o->precision, threads, stg), maxsm);
+        e = integrate_occupancy(m->dev, o->method, o->precision, stg, o->occupancy, threads, &occ);
+        cap = (o->occupancy ? 768 : 512) / threads;
     }
-    int occ = 0;
-    e = integrate_occupancy(m->dev, o->method, o->precision, stg, o->occupancy, threads, &occ);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (occ < 1) return fail(KIN_EUNSUPPORTED, "kernel does not fit on an SM with these options");
     int bps = o->blocks_per_sm;
-    if (bps <= 0) bps = std::max(1, std::min(occ, (o->occupancy ? 768 : 512) / threads));
+    if (bps <= 0) bps = std::max(1, std::min(occ, cap));
     if (bps > occ) return fail(KIN_EINVAL, "blocks_per_sm %d exceeds the %d blocks that fit per SM", bps, occ);
     g->threads = threads;
     g->blocks = nsm * bps;
     g->nslots = (int64_t)g->blocks * threads;
+    g->layout = layout;
     return KIN_OK;
 }
 
-int64_t ws_bytes(const kin_mech* m, const kin_opts* o, int64_t nslots, int64_t cells)
+// Workspace bytes; the warp layout keeps no per-lane arrays.
+int64_t ws_bytes(const kin_mech* m, const kin_opts* o, const Grid& g, int64_t cells)
 {
     const int sig = o->method == KIN_RKC ? o->sigma : KIN_SIGMA_GERSHGORIN;
-    return ws_layout(m->dev, o->precision, sig, nslots, cells).total;
+    return ws_layout(m->dev, o->precision, sig, g.layout == KIN_LAYOUT_WARP ? 0 : g.nslots, cells).total;
 }
 
 int check_opts(const kin_opts* o)
@@ -107,6 +126,8 @@ int check_opts(const kin_opts* o)
         return fail(KIN_EINVAL, "unknown occupancy %d", o->occupancy);
     if (o->sigma != KIN_SIGMA_GERSHGORIN && o->sigma != KIN_SIGMA_POWER)
         return fail(KIN_EINVAL, "unknown sigma estimator %d", o->sigma);
+    if (o->layout != KIN_LAYOUT_AUTO && o->layout != KIN_LAYOUT_LANE && o->layout != KIN_LAYOUT_WARP)
+        return fail(KIN_EINVAL, "unknown layout %d", o->layout);
     return KIN_OK;
 }
 
@@ -218,6 +239,33 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     const size_t oLA = put(d->lnA, 8 * nR), oB = put(d->beta, 8 * nR), oE = put(EaR.data(), 8 * nR);
     const size_t oLA0 = put(lnA0.data(), 8 * nR), oB0 = put(beta0.data(), 8 * nR), oE0 = put(Ea0R.data(), 8 * nR);
     const size_t oRx = put(rxn.data(), sizeof(Rxn) * nR);
+    // warp layout: reactions permuted plain, third-body, falloff (each in
+    // reaction order, so falloff ordinals keep their order); efficiency rows
+    // transposed to [species][non-plain reaction in permutation order]
+    std::vector<int> perm, pos(nR);
+    for (int t = KIN_RXN_PLAIN; t <= KIN_RXN_FALLOFF; ++t)
+        for (int j = 0; j < nR; ++j)
+            if (rxn[j].type == t) perm.push_back(j);
+    std::vector<Rxn> rxnp(nR);
+    const int nPlain = nR - nM;
+    for (int q = 0; q < nR; ++q) {
+        pos[perm[q]] = q;
+        rxnp[q] = rxn[perm[q]];
+        rxnp[q].row = rxnp[q].type != KIN_RXN_PLAIN ? q - nPlain : -1;
+    }
+    std::vector<int> crxp(nnz);
+    for (int e2 = 0; e2 < nnz; ++e2) crxp[e2] = pos[crx[e2]];
+    std::vector<double> effT((size_t)nM * nS);
+    std::vector<float> effT32((size_t)nM * nS);
+    for (int q = nPlain; q < nR; ++q)
+        for (int k = 0; k < nS; ++k) {
+            const double a = d->eff[(size_t)rxn[perm[q]].row * nS + k];
+            effT[(size_t)k * nM + (q - nPlain)] = a;
+            effT32[(size_t)k * nM + (q - nPlain)] = (float)a;
+        }
+    const size_t oPerm = put(perm.data(), 4 * nR), oRxp = put(rxnp.data(), sizeof(Rxn) * nR);
+    const size_t oCrxp = put(crxp.data(), 4 * nnz);
+    const size_t oEffT = put(effT.data(), 8 * effT.size()), oEffT32 = put(effT32.data(), 4 * effT32.size());
     const size_t oPtr = put(ptr.data(), 4 * (nS + 1)), oCrx = put(crx.data(), 4 * nnz);
     const size_t oNu = put(cnu.data(), 8 * nnz), oNu32 = put(nu32.data(), 4 * nnz);
     const size_t oEff = put(d->eff, 8 * (size_t)nM * nS), oEff32 = put(eff32.data(), 4 * (size_t)nM * nS);
@@ -240,6 +288,11 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     M.lnA = (const double*)(b + oLA); M.beta = (const double*)(b + oB); M.EaR = (const double*)(b + oE);
     M.lnA0 = (const double*)(b + oLA0); M.beta0 = (const double*)(b + oB0); M.Ea0R = (const double*)(b + oE0);
     M.rxn = (const Rxn*)(b + oRx);
+    M.rxn_perm = (const int*)(b + oPerm);
+    M.rxnp = (const Rxn*)(b + oRxp);
+    M.csrp_rxn = (const int*)(b + oCrxp);
+    M.effT = (const double*)(b + oEffT);
+    M.effT32 = (const float*)(b + oEffT32);
     M.csr_ptr = (const int*)(b + oPtr); M.csr_rxn = (const int*)(b + oCrx);
     M.csr_nu = (const double*)(b + oNu); M.csr_nu32 = (const float*)(b + oNu32);
     M.eff = (const double*)(b + oEff); M.eff32 = (const float*)(b + oEff32);
@@ -271,7 +324,7 @@ int64_t kin_workspace_bytes(const kin_mech* m, const kin_opts* o, int64_t cells)
     Grid g;
     rc = grid_for(m, o, &g);
     if (rc) return rc;
-    return ws_bytes(m, o, g.nslots, cells);
+    return ws_bytes(m, o, g, cells);
 }
 
 int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, const kin_opts* o,
@@ -312,14 +365,15 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     Grid g;
     rc = grid_for(m, o, &g);
     if (rc) return rc;
-    const int64_t need = ws_bytes(m, o, g.nslots, total);
+    const int64_t need = ws_bytes(m, o, g, total);
     if (!ws) return fail(KIN_EINVAL, "workspace is NULL");
     if (((uintptr_t)ws) % 256) return fail(KIN_EINVAL, "workspace must be 256-byte aligned");
     if (ws_size < need) return fail(KIN_ENOMEM, "workspace has %lld bytes, needs %lld", (long long)ws_size, (long long)need);
     if (!is_device_ptr(ws)) return fail(KIN_EINVAL, "workspace must be device memory");
-    // never more lanes than cells
+    // never more lanes (warps in the warp layout) than cells
     int blocks = g.blocks;
-    const int64_t want = (total + g.threads - 1) / g.threads;
+    const int per_block = g.layout == KIN_LAYOUT_WARP ? g.threads / 32 : g.threads;
+    const int64_t want = (total + per_block - 1) / per_block;
     if (want < blocks) blocks = (int)want;
     const int64_t nslots = (int64_t)blocks * g.threads;
     P.M = m->dev;
@@ -331,13 +385,14 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     P.total = total;
     char* base = (char*)ws;
     const int sig = o->method == KIN_RKC ? o->sigma : KIN_SIGMA_GERSHGORIN;
-    const WsLayout w = ws_layout(m->dev, o->precision, sig, nslots, total);
+    const WsLayout w = ws_layout(m->dev, o->precision, sig, g.layout == KIN_LAYOUT_WARP ? 0 : nslots, total);
     P.sigma_method = sig;
     P.cell_ev = sig == KIN_SIGMA_POWER ? (double*)(base + w.ev) : nullptr;
     P.queue = (unsigned long long*)(base + w.header);
     P.hist = (unsigned*)(base + w.header + 256);
     P.vec = (double*)(base + w.vec);
     P.lane_r = base + w.lane_r;
+    P.lane_sig = (double*)(base + w.lane_sig);
     P.cell_k = base + w.cell_k;
     P.cell_f0 = (double*)(base + w.f0);
     P.cell_sig = (double*)(base + w.sig);
@@ -349,7 +404,11 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     cudaStream_t st = (cudaStream_t)o->stream;
     cudaError_t e = cudaMemsetAsync(base + w.header, 0, 512, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    e = launch_integrate(P, o->staging, o->occupancy, blocks, g.threads, st);
+    if (g.layout == KIN_LAYOUT_WARP)
+        e = o->precision == KIN_MIXED ? launch_warp_f32(P, blocks, g.threads, st)
+                                      : launch_warp_f64(P, blocks, g.threads, st);
+    else
+        e = launch_integrate(P, o->staging, o->occupancy, blocks, g.threads, st);
     if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
     return KIN_OK;
 }
@@ -422,11 +481,11 @@ int kin_rates(const kin_mech* m, int64_t cells, const double* T, const double* p
     if (ldY > INT32_MAX) return fail(KIN_EINVAL, "ldY >= 2^31");
     if (!is_device_ptr(T) || !is_device_ptr(p) || !is_device_ptr(Y) || !is_device_ptr(dYdt))
         return fail(KIN_EINVAL, "T, p, Y and dYdt must be device memory");
-    kin_opts o{KIN_RKC, precision, 0, 0, 0, KIN_STAGE_GLOBAL, KIN_OCC_DEFAULT, 0, stream};
+    kin_opts o{KIN_RKC, precision, 0, 0, 0, KIN_STAGE_GLOBAL, KIN_OCC_DEFAULT, 0, KIN_LAYOUT_LANE, stream};
     Grid g;
     int rc = grid_for(m, &o, &g);
     if (rc) return rc;
-    const int64_t need = ws_bytes(m, &o, g.nslots, cells);
+    const int64_t need = ws_bytes(m, &o, g, cells);
     if (!ws || ((uintptr_t)ws) % 256) return fail(KIN_EINVAL, "workspace must be non-NULL and 256-byte aligned");
     if (ws_size < need) return fail(KIN_ENOMEM, "workspace has %lld bytes, needs %lld", (long long)ws_size, (long long)need);
     if (!is_device_ptr(ws)) return fail(KIN_EINVAL, "workspace must be device memory");

@@ -121,6 +121,7 @@ WsLayout ws_layout(const MechDev& M, int precision, int sigma_method, int64_t ns
     w.header = off;  off += 4096;
     w.vec = off;     off += al256((int64_t)NVEC * M.nS * 8 * nslots);
     w.lane_r = off;  off += al256((int64_t)(M.nS + 2 * M.nR + M.nFO) * rb * nslots);
+    w.lane_sig = off; off += precision == KIN_MIXED ? al256((int64_t)(M.nS + M.nR) * 8 * nslots) : 0;
     w.cell_k = off;  off += al256((int64_t)(M.nR + M.nFO) * rb * cells);
     w.f0 = off;      off += al256((int64_t)M.nS * 8 * cells);
     w.ev = off;      off += sigma_method == KIN_SIGMA_POWER ? al256((int64_t)M.nS * 8 * cells) : 0;

@@ -93,9 +93,12 @@ __device__ void rate_constants(const MechDev& M, double T, Lane<R> K, Lane<R> KR
 }
 
 // f(x) -> out (Eqs. (E:mass), (E:spec-rate), (E:rxn-rate)). Ctot = p/(R T) in
-// mol/cm^3, invCtot its inverse. C and OM are lane scratch (nS and nR).
-template <typename R>
-__device__ void feval(const MechDev& M, double Ctot, double invCtot, Lane<R> K, Lane<R> KR,
+// mol/cm^3, invCtot its inverse. C and OM are lane scratch (nS and nR). R is
+// the arithmetic type; the rate constants K, KR are stored in KT (float
+// constants promoted to double when the mixed-precision path evaluates f in
+// FP64 for its spectral-radius estimate).
+template <typename R, typename KT>
+__device__ void feval(const MechDev& M, double Ctot, double invCtot, Lane<KT> K, Lane<KT> KR,
                       Lane<R> C, Lane<R> OM, Lane<double> x, Lane<double> out)
 {
     const int nS = M.nS, nR = M.nR;
@@ -125,7 +128,7 @@ __device__ void feval(const MechDev& M, double Ctot, double invCtot, Lane<R> K, 
     const R* __restrict__ eff = Tab<R>::eff(M);
     for (int j = 0; j < nR; ++j) {
         const Rxn r = M.rxn[j];
-        R q = K[j];
+        R q = (R)K[j];
         if (r.r0 >= 0) q *= C[r.r0];
         if (r.r1 >= 0) q *= C[r.r1];
         if (r.type != KIN_RXN_PLAIN) {
@@ -141,7 +144,7 @@ __device__ void feval(const MechDev& M, double Ctot, double invCtot, Lane<R> K, 
             if (r.type == KIN_RXN_THIRD_BODY) {
                 q *= Mc;
             } else {
-                const R Pr = KR[r.fo] * Mc;
+                const R Pr = (R)KR[r.fo] * Mc;
                 q *= Pr / (R(1) + Pr);
             }
         }
@@ -203,6 +206,7 @@ struct Views {
     const MechDev& M;
     int64_t slot;
     Lane<R> C, OM, Kl, KRl;
+    Lane<double> C64, OM64;  // mixed precision: FP64 scratch of the spectral-radius f
     double* vbase;
     __device__ Views(const Launch& l, int64_t sl) : L(l), M(l.M), slot(sl)
     {
@@ -225,6 +229,8 @@ struct Views {
             KRl = Lane<R>{rb + (int64_t)(M.nS + 2 * M.nR) * ns, (int32_t)ns};
         }
         vbase = L.vec + sl;
+        C64 = Lane<double>{L.lane_sig + sl, (int32_t)ns};
+        OM64 = Lane<double>{L.lane_sig + (int64_t)M.nS * ns + sl, (int32_t)ns};
     }
     __device__ __forceinline__ Lane<double> V(int v) const
     {
@@ -268,13 +274,18 @@ __device__ __forceinline__ double rms(int n, double rtol, double atol, Lane<doub
 // (f(y0) at the first estimate, all ones if that is zero); stop when two
 // successive ||w||/dyn agree to 1 % or after 20 products; sigma = 1.2 x the
 // last value (the iteration approaches |lambda_max| from below).
+// Spectral-radius estimates evaluate f in FP64 in both precisions (u = 2^-52):
+// with FP32 rate arithmetic the rounding noise of f(y + v) - f(y) can exceed
+// the difference itself, and the iteration would neither converge nor agree
+// with the FP64 estimate.
+constexpr double SIG_SQRT_U = 1.4901161193847656e-08;  // sqrt(2^-52)
 struct PowerState {
     int k;
     double prev, dyn, sig;
 };
 
-template <typename R>
-__device__ void power_begin(int nS, Lane<double> Y, Lane<double> EV, Lane<double> X, PowerState& P)
+__device__ __forceinline__ void power_begin(int nS, Lane<double> Y, Lane<double> EV, Lane<double> X,
+                                            PowerState& P)
 {
     double yn = 0.0, vn = 0.0;
     for (int i = 0; i < nS; ++i) {
@@ -282,7 +293,7 @@ __device__ void power_begin(int nS, Lane<double> Y, Lane<double> EV, Lane<double
         vn += EV[i] * EV[i];
     }
     yn = sqrt(yn);
-    P.dyn = yn > 0.0 ? Tab<R>::sqrt_u * yn : Tab<R>::sqrt_u;
+    P.dyn = yn > 0.0 ? SIG_SQRT_U * yn : SIG_SQRT_U;
     vn = sqrt(vn);
     if (!(vn > 0.0) || !isfinite(vn)) {
         for (int i = 0; i < nS; ++i) EV[i] = 1.0;
@@ -298,8 +309,9 @@ __device__ void power_begin(int nS, Lane<double> Y, Lane<double> EV, Lane<double
     P.sig = 0.0;
 }
 
-// FX holds f(Y + EV). Updates EV; returns true when the estimate is final
-// (then sigma = 1.2 P.sig); otherwise X is set to the next point Y + EV.
+// FX holds f(Y + EV), F0 = f(Y) (both FP64). Updates EV; returns true when
+// the estimate is final (then sigma = 1.2 P.sig); otherwise X is set to the
+// next point Y + EV.
 __device__ __forceinline__ bool power_post(int nS, Lane<double> Y, Lane<double> F0, Lane<double> EV,
                            Lane<double> X, Lane<double> FX, PowerState& P)
 {
@@ -321,10 +333,23 @@ __device__ __forceinline__ bool power_post(int nS, Lane<double> Y, Lane<double> 
     return false;
 }
 
+// f in FP64 for a spectral-radius estimate: the lane's rate scratch in the
+// FP64 path, the separate FP64 scratch in the mixed-precision path (whose
+// rate constants are the same FP32 values, promoted).
+template <typename R, int STG>
+__device__ __forceinline__ void feval_sig(const Views<R, STG>& W, double Ctot, double invCtot,
+                                          Lane<R> K, Lane<R> KR, Lane<double> x, Lane<double> out)
+{
+    if constexpr (sizeof(R) == 4)
+        feval<double>(W.M, Ctot, invCtot, K, KR, W.C64, W.OM64, x, out);
+    else
+        feval<double>(W.M, Ctot, invCtot, K, KR, W.C, W.OM, x, out);
+}
+
 // ------------------------------------------------------------- pre-pass --
 // For every cell g (grid-stride, uniform across lanes): rate constants, f(y0),
-// and for RKC the Gershgorin bound on the FD Jacobian (Section 2.3) and the
-// initial step h1 = 0.1 h0 / ||Delta_0||^(1/2), h0 = 1/sigma.
+// and for RKC the spectral radius (Section 2.3) and the initial step
+// h1 = 0.1 h0 / ||Delta_0||^(1/2), h0 = 1/sigma.
 template <int METHOD, typename R, int STG>
 __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launch L)
 {
@@ -354,24 +379,32 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
         uint8_t st = ok ? 0 : KIN_CELL_NONFINITE;
         double sigma = 0.0, h = I.dt;
         int nfe = 1;
+        // base point of the FP64 spectral-radius differences: f(y0) itself in
+        // FP64, its FP64 re-evaluation in the mixed-precision path
+        Lane<double> B = F0;
+        if (METHOD == KIN_RKC && ok && sizeof(R) == 4) {
+            B = W.V(V_B);
+            feval_sig(W, Ctot, invCtot, K, KR, Y, B);
+            nfe++;
+        }
         if (METHOD == KIN_RKC && ok && L.sigma_method == KIN_SIGMA_POWER) {
             Lane<double> EV = W.EVcell(g);
-            for (int i = 0; i < nS; ++i) EV[i] = F0[i];  // first direction: f(y0)
+            for (int i = 0; i < nS; ++i) EV[i] = B[i];  // first direction: f(y0)
             PowerState P;
-            power_begin<R>(nS, Y, EV, X, P);
+            power_begin(nS, Y, EV, X, P);
             for (;;) {
-                feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, X, FX);
+                feval_sig(W, Ctot, invCtot, K, KR, X, FX);
                 nfe++;
-                if (power_post(nS, Y, F0, EV, X, FX, P)) break;
+                if (power_post(nS, Y, B, EV, X, FX, P)) break;
             }
             sigma = 1.2 * P.sig;
         } else if (METHOD == KIN_RKC && ok) {
             for (int k = 0; k < nS; ++k) {  // Gershgorin columns
-                const double eps = Tab<R>::sqrt_u * fmax(fabs(Y[k]), I.atol);
+                const double eps = SIG_SQRT_U * fmax(fabs(Y[k]), I.atol);
                 X[k] = Y[k] + eps;
-                feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, X, FX);
+                feval_sig(W, Ctot, invCtot, K, KR, X, FX);
                 const double ie = 1.0 / eps;
-                for (int i = 0; i < nS; ++i) RS[i] += fabs((FX[i] - F0[i]) * ie);
+                for (int i = 0; i < nS; ++i) RS[i] += fabs((FX[i] - B[i]) * ie);
                 X[k] = Y[k];
             }
             for (int i = 0; i < nS; ++i) sigma = fmax(sigma, RS[i]);
@@ -417,6 +450,7 @@ __device__ __forceinline__ int cost_bucket(const Launch& L, int64_t g)
 // ------------------------------------------------------------ integrator --
 enum Phase : int {
     PH_F0 = 0,   // RKCK: f at the current accepted state -> F0
+    PH_SIGBASE,  // RKC, mixed precision: FP64 f(Y) -> V_B, the base of the sigma differences
     PH_SIG,      // RKC: f at Y + eps_k e_k (Gershgorin column k) -> FX
     PH_POW,      // RKC: f at Y + v (power-method product) -> FX
     PH_STAGE,    // RKC: f(w_{j-1}) -> FX, then w_j
@@ -548,12 +582,28 @@ struct Integrator {
         finish_stats(S, code);
     }
 
-    // Start a spectral-radius estimate at Y: power method (X = Y + v) or
-    // Gershgorin (X = Y + eps_0 e_0, RS = 0).
+    // Slot holding f(Y) in FP64 during a spectral-radius estimate.
+    static constexpr int V_BASE = sizeof(R) == 4 ? V_B : V_F0;
+
+    // Start a spectral-radius estimate at Y; the mixed-precision path first
+    // re-evaluates f(Y) in FP64 (V_B is free: the stage vectors are formed
+    // after the estimate).
     __device__ void sigma_begin(LaneState& S)
     {
+        if (sizeof(R) == 4) {
+            S.phase = PH_SIGBASE;
+            S.in_v = V_Y;
+            S.out_v = V_B;
+            return;
+        }
+        sigma_start(S);
+    }
+
+    // Power method (X = Y + v) or Gershgorin (X = Y + eps_0 e_0, RS = 0).
+    __device__ void sigma_start(LaneState& S)
+    {
         if (L.sigma_method == KIN_SIGMA_POWER) {
-            power_begin<R>(M.nS, V(V_Y), V(V_RS), V(V_X), S.P);
+            power_begin(M.nS, V(V_Y), V(V_RS), V(V_X), S.P);
             S.phase = PH_POW;
             S.in_v = V_X;
             S.out_v = V_FX;
@@ -565,7 +615,7 @@ struct Integrator {
             RS[i] = 0.0;
         }
         S.col = 0;
-        S.eps = Tab<R>::sqrt_u * fmax(fabs(Y[0]), S.atol);
+        S.eps = SIG_SQRT_U * fmax(fabs(Y[0]), S.atol);
         X[0] = Y[0] + S.eps;
         S.phase = PH_SIG;
         S.in_v = V_X;
@@ -575,12 +625,12 @@ struct Integrator {
     // Post-processing of one Gershgorin column. Returns true when sigma is done.
     __device__ bool sigma_column(LaneState& S)
     {
-        Lane<double> Y = V(V_Y), X = V(V_X), RS = V(V_RS), FX = V(V_FX), F0 = V(V_F0);
+        Lane<double> Y = V(V_Y), X = V(V_X), RS = V(V_RS), FX = V(V_FX), F0 = V(V_BASE);
         const double ie = 1.0 / S.eps;
         for (int i = 0; i < M.nS; ++i) RS[i] += fabs((FX[i] - F0[i]) * ie);
         X[S.col] = Y[S.col];
         if (++S.col < M.nS) {
-            S.eps = Tab<R>::sqrt_u * fmax(fabs(Y[S.col]), S.atol);
+            S.eps = SIG_SQRT_U * fmax(fabs(Y[S.col]), S.atol);
             X[S.col] = Y[S.col] + S.eps;
             return false;
         }
@@ -660,13 +710,17 @@ struct Integrator {
             else S.j++;
             return -1;
         }
+        if (S.phase == PH_SIGBASE) {
+            sigma_start(S);
+            return -1;
+        }
         if (S.phase == PH_SIG) {
             if (!sigma_column(S)) return -1;
             if (!isfinite(S.sigma)) return KIN_CELL_NONFINITE;
             return rkc_begin_step(S);
         }
         if (S.phase == PH_POW) {
-            if (!power_post(M.nS, V(V_Y), V(V_F0), V(V_RS), V(V_X), V(V_FX), S.P)) return -1;
+            if (!power_post(M.nS, V(V_Y), V(V_BASE), V(V_RS), V(V_X), V(V_FX), S.P)) return -1;
             S.sigma = 1.2 * S.P.sig;
             S.nsig++;
             S.since_sigma = 0;
@@ -817,7 +871,10 @@ struct Integrator {
         LaneState S;
         if (!load_next(S)) return;
         for (;;) {
-            feval<R>(M, S.Ctot, S.invCtot, K, KR, W.C, W.OM, V(S.in_v), V(S.out_v));
+            if (sizeof(R) == 4 && METHOD == KIN_RKC && S.phase >= PH_SIGBASE && S.phase <= PH_POW)
+                feval<double>(M, S.Ctot, S.invCtot, K, KR, W.C64, W.OM64, V(S.in_v), V(S.out_v));
+            else
+                feval<R>(M, S.Ctot, S.invCtot, K, KR, W.C, W.OM, V(S.in_v), V(S.out_v));
             S.nfe++;
             const int code = METHOD == KIN_RKC ? rkc_post(S) : rkck_post(S);
             if (code >= 0) {

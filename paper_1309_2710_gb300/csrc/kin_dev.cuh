@@ -38,6 +38,12 @@ struct MechDev {
     const double* beta0;   // [nR]
     const double* Ea0R;    // [nR]
     const Rxn* rxn;        // [nR]
+    // warp-per-cell layout: reactions in the order plain, third-body, falloff
+    const int* rxn_perm;   // [nR] reaction at each permutation position
+    const Rxn* rxnp;       // [nR] descriptors in permutation order; .row indexes effT's columns
+    const int* csrp_rxn;   // [nnz] permutation position of each CSR entry's reaction
+    const double* effT;    // [nS][nM] efficiencies, column = non-plain reaction in permutation order
+    const float* effT32;   // [nS][nM]
     const int* csr_ptr;    // [nS + 1] species -> entries
     const int* csr_rxn;    // [nnz] reaction of each entry (ascending per species)
     const double* csr_nu;  // [nnz] net coefficient nu'' - nu' of the species
@@ -72,6 +78,8 @@ struct Launch {
     double* vec;                    // [NVEC * nS][nslots]
     void* lane_r;                   // C [nS], Omega [nR], k [nR], k0/kinf [nFO] of the rate
                                     // type: [nS + 2 nR + nFO][nslots]
+    double* lane_sig;               // mixed precision: FP64 C [nS], Omega [nR] for the
+                                    // spectral-radius evaluations of f: [nS + nR][nslots]
     // per cell (global cell index g over all instances)
     void* cell_k;                   // k_j [nR][total], then k0/kinf [nFO][total], rate type
     double* cell_f0;                // f(y0) [nS][total]
@@ -87,7 +95,7 @@ struct Launch {
 
 // Workspace layout for `cells` cells and `nslots` lanes.
 struct WsLayout {
-    int64_t header, vec, lane_r, cell_k, f0, ev, sig, h, nfe, st, order, total;
+    int64_t header, vec, lane_r, lane_sig, cell_k, f0, ev, sig, h, nfe, st, order, total;
 };
 WsLayout ws_layout(const MechDev& M, int precision, int sigma_method, int64_t nslots,
                    int64_t cells);
@@ -110,6 +118,12 @@ cudaError_t occ_rkc_f32(int stg, int occ, int threads, size_t sm, int* bps);
 cudaError_t occ_rkck_f64(int stg, int occ, int threads, size_t sm, int* bps);
 cudaError_t occ_rkck_f32(int stg, int occ, int threads, size_t sm, int* bps);
 cudaError_t launch_sort(Launch& L, cudaStream_t st);
+// Warp-per-cell RKC (inst_warp_*.cu): one warp integrates one cell.
+cudaError_t launch_warp_f64(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_warp_f32(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t occ_warp_f64(const MechDev& M, int threads, int* bps);
+cudaError_t occ_warp_f32(const MechDev& M, int threads, int* bps);
+size_t warp_smem(const MechDev& M, int precision, int threads);
 
 // Record `code` and a printf-style message as the calling thread's last
 // error (kin_last_error); returns `code`.

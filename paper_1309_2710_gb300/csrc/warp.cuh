@@ -1,0 +1,596 @@
+// warp.cuh -- warp-per-cell RKC for large mechanisms (templates; instantiated
+// in inst_warp_*.cu).
+//
+// With one lane per cell, every lane keeps its own concentrations, rates of
+// progress and rate constants: ~(2 n_R + n_S) words per cell, which for
+// hundreds of reactions spills out of L1/L2 and turns every f evaluation into
+// a stream from HBM. Here one warp integrates one cell:
+//  * the 32 lanes split the reactions (rates of progress, rounds of 32) and
+//    the species (state vectors in registers: species l + 32 r in slot r of
+//    lane l; stoichiometric gather over the species-major CSR);
+//  * the cell's concentrations and rates of progress live in shared memory
+//    (n_S + n_R words per warp); its rate constants, computed once per call
+//    since T is fixed, live in the workspace cell-major and are read
+//    coalesced (the working set of the resident cells stays in L2);
+//  * reactions are visited in a fixed permutation (plain, then third-body,
+//    then falloff) so that a round of 32 lanes mixes the dense efficiency dot
+//    products with plain reactions at most once; the efficiency rows are
+//    stored transposed ([species][row]) so that the lanes of a round read
+//    consecutive words;
+//  * all lanes follow the same cell, so the method's control flow is uniform
+//    and is written as straight-line code; reductions (mixture sum, error
+//    norms, spectral-radius bounds) are butterfly shuffles, which leave every
+//    lane with the same bits.
+// The method, its decisions and the statistics are those of the lane-per-cell
+// kernel (Section 2.3 and the readings listed with it).
+#pragma once
+#include "kernels.cuh"
+
+namespace kin {
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename R>
+struct TabW;
+template <>
+struct TabW<double> {
+    __device__ static const double* effT(const MechDev& M) { return M.effT; }
+};
+template <>
+struct TabW<float> {
+    __device__ static const float* effT(const MechDev& M) { return M.effT32; }
+};
+
+// Shared words per warp: C [nS] and Omega [nR], padded to 4, sized for FP64
+// (the mixed-precision path evaluates f in FP32 for its RK stages and in FP64
+// for its spectral-radius estimates, over the same words).
+__host__ __device__ __forceinline__ int warp_smem_elems(const MechDev& M)
+{
+    return (M.nS + M.nR + 3) & ~3;
+}
+
+// f for the warp's cell (Eqs. (E:mass), (E:spec-rate), (E:rxn-rate)) in
+// arithmetic type R. Kc are the cell's rate constants (stored as KT) in
+// reaction-permutation order followed by k0/kinf per falloff ordinal (written
+// earlier in the same pre-pass kernel, so not read through the read-only
+// cache); C and OM are the warp's shared arrays.
+template <typename R, typename KT, int NR>
+__device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C, R* OM,
+                                           double Ctot, double invCtot, const double (&x)[NR],
+                                           double (&out)[NR], int lane)
+{
+    const int nS = M.nS, nR = M.nR, nM = M.nM;
+    const R* __restrict__ invW = Tab<R>::invW(M);
+    R s = R(0);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int i = lane + 32 * r;
+        if (i < nS) {
+            const R m = (R)x[r] * invW[i];
+            C[i] = m;
+            s += m;
+        }
+    }
+    s = warp_sum(s);
+    const R rho = (R)Ctot * (R(1) / s);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int i = lane + 32 * r;
+        if (i < nS) C[i] = C[i] * rho;
+    }
+    __syncwarp();
+    const R* __restrict__ effT = TabW<R>::effT(M);
+    for (int q = lane; q < nR; q += 32) {
+        const Rxn rx = M.rxnp[q];
+        R v = (R)Kc[q];
+        if (rx.r0 >= 0) v *= C[rx.r0];
+        if (rx.r1 >= 0) v *= C[rx.r1];
+        if (rx.type != KIN_RXN_PLAIN) {
+            const R* a = effT + rx.row;
+            R m0 = R(0), m1 = R(0);
+            int k = 0;
+            for (; k + 1 < nS; k += 2) {
+                m0 += a[(int64_t)k * nM] * C[k];
+                m1 += a[(int64_t)(k + 1) * nM] * C[k + 1];
+            }
+            if (k < nS) m0 += a[(int64_t)k * nM] * C[k];
+            const R Mc = m0 + m1;
+            if (rx.type == KIN_RXN_THIRD_BODY) {
+                v *= Mc;
+            } else {
+                const R Pr = (R)Kc[nR + rx.fo] * Mc;
+                v *= Pr / (R(1) + Pr);
+            }
+        }
+        OM[q] = v;
+    }
+    __syncwarp();
+    const R* __restrict__ nu = Tab<R>::nu(M);
+    const double invrho = (double)s * invCtot;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int i = lane + 32 * r;
+        double o = 0.0;
+        if (i < nS) {
+            R w0 = R(0), w1 = R(0);
+            const int e1 = M.csr_ptr[i + 1];
+            int e = M.csr_ptr[i];
+            for (; e + 1 < e1; e += 2) {
+                w0 += nu[e] * OM[M.csrp_rxn[e]];
+                w1 += nu[e + 1] * OM[M.csrp_rxn[e + 1]];
+            }
+            if (e < e1) w0 += nu[e] * OM[M.csrp_rxn[e]];
+            o = (double)(w0 + w1) * (M.W[i] * invrho);
+        }
+        out[r] = o;
+    }
+    __syncwarp();  // C and OM are rewritten by the next evaluation
+}
+
+// Element r of a register vector for a warp-uniform r.
+template <int NR>
+__device__ __forceinline__ double reg_get(const double (&v)[NR], int r)
+{
+    double o = v[0];
+#pragma unroll
+    for (int q = 1; q < NR; ++q)
+        if (r == q) o = v[q];
+    return o;
+}
+
+template <typename R, int NR>
+struct WarpRKC {
+    const Launch& L;
+    const MechDev& M;
+    R* C;
+    R* OM;
+    double* C64;   // the same shared words as C and OM, for the FP64 evaluations
+    double* OM64;
+    const R* Kc;
+    int lane;
+    double Ctot, invCtot, atol, rtol;
+    int nfe, nsig;
+    double y[NR], f0[NR], w1[NR], w2[NR], fx[NR], x[NR], ev[NR];
+
+    __device__ explicit WarpRKC(const Launch& l) : L(l), M(l.M), Kc(nullptr), lane(threadIdx.x & 31)
+    {
+        C64 = reinterpret_cast<double*>(kin_smem) + (size_t)(threadIdx.x >> 5) * warp_smem_elems(M);
+        OM64 = C64 + M.nS;
+        C = reinterpret_cast<R*>(C64);
+        OM = C + M.nS;
+    }
+
+    __device__ __forceinline__ bool valid(int r) const { return lane + 32 * r < M.nS; }
+
+    __device__ __forceinline__ void f(const double (&in)[NR], double (&o)[NR])
+    {
+        warp_feval<R, R, NR>(M, Kc, C, OM, Ctot, invCtot, in, o, lane);
+        nfe++;
+    }
+
+    // f in FP64 for the spectral-radius estimates (FP32 rounding noise in
+    // f(y + v) - f(y) would swamp the difference; see SIG_SQRT_U).
+    __device__ __forceinline__ void fs(const double (&in)[NR], double (&o)[NR])
+    {
+        if constexpr (sizeof(R) == 4)
+            warp_feval<double, R, NR>(M, Kc, C64, OM64, Ctot, invCtot, in, o, lane);
+        else
+            warp_feval<double, double, NR>(M, Kc, C, OM, Ctot, invCtot, in, o, lane);
+        nfe++;
+    }
+
+    // Weighted RMS norm, Eq. (E:rmsE), of d with T_i = atol + rtol max(|a_i|, |b_i|).
+    __device__ double rms(const double (&d)[NR], const double (&a)[NR], const double (&b)[NR]) const
+    {
+        double acc = 0.0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (valid(r)) {
+                const double sc = atol + rtol * fmax(fabs(a[r]), fabs(b[r]));
+                const double q = d[r] / sc;
+                acc += q * q;
+            }
+        return sqrt(warp_sum(acc) / M.nS);
+    }
+
+    // Gershgorin bound on the finite-difference Jacobian at y (base = f(y) in FP64).
+    __device__ double gershgorin(const double (&base)[NR])
+    {
+        double rs[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) rs[r] = 0.0;
+        for (int k = 0; k < M.nS; ++k) {
+            const int kr = k >> 5, kl = k & 31;
+            const double yk = __shfl_sync(0xffffffffu, reg_get(y, kr), kl);
+            const double eps = SIG_SQRT_U * fmax(fabs(yk), atol);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) x[r] = (r == kr && lane == kl) ? yk + eps : y[r];
+            fs(x, fx);
+            const double ie = 1.0 / eps;
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                if (valid(r)) rs[r] += fabs((fx[r] - base[r]) * ie);
+        }
+        double m = 0.0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) m = fmax(m, rs[r]);
+        return warp_max(m);
+    }
+
+    // Nonlinear power method warm-started from ev (see power_begin/power_post).
+    __device__ double power(const double (&base)[NR])
+    {
+        double yn = 0.0, vn = 0.0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            yn += y[r] * y[r];
+            vn += ev[r] * ev[r];
+        }
+        yn = sqrt(warp_sum(yn));
+        vn = sqrt(warp_sum(vn));
+        const double dyn = yn > 0.0 ? SIG_SQRT_U * yn : SIG_SQRT_U;
+        if (!(vn > 0.0) || !isfinite(vn)) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) ev[r] = valid(r) ? 1.0 : 0.0;
+            vn = sqrt((double)M.nS);
+        }
+        const double sc0 = dyn / vn;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) ev[r] = ev[r] * sc0;
+        double sig = 0.0, prev = 0.0;
+        for (int k = 1; k <= 20; ++k) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) x[r] = y[r] + ev[r];
+            fs(x, fx);
+            double wn = 0.0;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                fx[r] = fx[r] - base[r];
+                wn += fx[r] * fx[r];
+            }
+            wn = sqrt(warp_sum(wn));
+            sig = wn / dyn;
+            if (!(wn > 0.0) || !isfinite(wn)) break;
+            const double sc = dyn / wn;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) ev[r] = fx[r] * sc;
+            if (k >= 2 && fabs(sig - prev) <= 0.01 * sig) break;
+            prev = sig;
+        }
+        return 1.2 * sig;
+    }
+
+    // Spectral radius at y. The mixed-precision path first re-evaluates f(y)
+    // in FP64 into w2 (free between steps). `first` starts the power method
+    // from f(y).
+    __device__ double sigma(bool first)
+    {
+        if constexpr (sizeof(R) == 4) {
+            fs(y, w2);
+            if (first)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) ev[r] = w2[r];
+            return L.sigma_method == KIN_SIGMA_POWER ? power(w2) : gershgorin(w2);
+        } else {
+            if (first)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) ev[r] = f0[r];
+            return L.sigma_method == KIN_SIGMA_POWER ? power(f0) : gershgorin(f0);
+        }
+    }
+
+    __device__ __forceinline__ const double* coef(int s, int j) const
+    {
+        return M.rkc + ((int64_t)s * RKC_TAB_S + j) * RKC_TAB_W;
+    }
+
+    // RKC integration over [0, dt] from the pre-pass state (y, f0, ev and the
+    // given sigma and first trial step h). Returns the cell status.
+    __device__ int run(double dt, double sig, double h, int& nacc, int& nrej)
+    {
+        double t = 0.0, hprev = 0.0, cprev = 0.0;
+        int attempts = 0, since = 0;
+        bool sigma_here = true, last_rej = false, have_prev = false;
+        const double invN = 1.0 / M.nS;
+        for (;;) {
+            if (attempts >= L.max_steps) return KIN_CELL_MAXSTEPS;
+            if (since >= 25 || (last_rej && !sigma_here)) {
+                sig = sigma(false);
+                nsig++;
+                since = 0;
+                sigma_here = true;
+                if (!isfinite(sig)) return KIN_CELL_NONFINITE;
+            }
+            double hh = h;
+            bool last = false;
+            if (hh >= dt - t) {
+                hh = dt - t;
+                last = true;
+            }
+            const double sr = floor(1.0 + sqrt(1.0 + 1.54 * hh * sig));
+            int s;
+            if (sr < 2.0) {
+                s = 2;
+            } else if (sr > (double)SMAX) {
+                s = SMAX;
+                hh = ((SMAX - 1.0) * (SMAX - 1.0) - 1.0) / (1.54 * sig);
+                last = false;
+            } else {
+                s = (int)sr;
+            }
+            // w_0 = y, w_1 = y + mu~_1 h f_0, then the three-term recursion
+            const double m1 = coef(s, 1)[2] * hh;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                w2[r] = y[r];
+                w1[r] = y[r] + m1 * f0[r];
+            }
+            for (int j = 2; j <= s; ++j) {
+                f(w1, fx);
+                const double* c = coef(s, j);
+                const double mu = c[0], nu = c[1], mt = c[2] * hh, gt = c[3] * hh, c0 = c[4];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const double wn = c0 * y[r] + mu * w1[r] + nu * w2[r] + mt * fx[r] + gt * f0[r];
+                    w2[r] = w1[r];
+                    w1[r] = wn;
+                }
+            }
+            f(w1, fx);  // f(w_s)
+            attempts++;
+            double acc = 0.0;
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                if (valid(r)) {
+                    const double d = 0.8 * (y[r] - w1[r]) + 0.4 * hh * (f0[r] + fx[r]);
+                    const double sc = atol + rtol * fmax(fabs(y[r]), fabs(w1[r]));
+                    const double q = d / sc;
+                    acc += q * q;
+                }
+            const double err = sqrt(warp_sum(acc) * invN);
+            if (err <= 1.0) {
+                nacc++;
+                const double c3 = cbrt(err);
+                double fac;
+                if (err == 0.0) fac = 10.0;
+                else if (have_prev && !last_rej && cprev > 0.0)
+                    fac = 0.8 * hh * cprev / (hprev * c3 * c3);
+                else fac = 0.8 / c3;
+                fac = fmin(10.0, fmax(0.1, fac));
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    y[r] = w1[r];
+                    f0[r] = fx[r];
+                }
+                if (last) return KIN_CELL_OK;
+                t += hh;
+                have_prev = true;
+                hprev = hh;
+                cprev = c3;
+                last_rej = false;
+                sigma_here = false;
+                since++;
+                h = fac * hh;
+            } else {
+                nrej++;
+                double fac = isfinite(err) ? 0.8 / cbrt(err) : 0.1;
+                if (fac < 0.1) fac = 0.1;
+                last_rej = true;
+                h = fac * hh;
+                if (h < 1e-20 * dt) return KIN_CELL_HMIN;
+            }
+        }
+    }
+};
+
+template <int NR>
+struct WarpBounds {
+    static constexpr int min_blocks = NR <= 2 ? 3 : 2;  // 85 or 128 registers at 256 threads
+};
+
+// Pre-pass, one warp per cell (grid-stride over cells): the cell's rate
+// constants (stored cell-major for the main kernel), f(y0), sigma and the
+// initial step h1 (Section 2.3).
+template <typename R, int NR>
+__global__ void __launch_bounds__(256, WarpBounds<NR>::min_blocks) warp_init_kernel(const __grid_constant__ Launch L)
+{
+    WarpRKC<R, NR> W(L);
+    const MechDev& M = L.M;
+    const int lane = W.lane, nK = M.nR + M.nFO, nS = M.nS;
+    const int64_t nwarps = L.nslots >> 5;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < L.total; g += nwarps) {
+        const int ii = find_inst(L, g);
+        const InstDev& I = L.inst[ii];
+        const int64_t c = g - L.start[ii];
+        const double T = I.T[c], p = I.p[c];
+        W.Ctot = p * 1e-6 / (R_GAS * T);
+        W.invCtot = 1.0 / W.Ctot;
+        W.atol = I.atol;
+        W.rtol = I.rtol;
+        W.nfe = 0;
+        // rate constants (Eq. (E:rxn-const)) in permutation order
+        R* kc = reinterpret_cast<R*>(L.cell_k) + g * nK;
+        const double lnT = log(T), invT = 1.0 / T;
+        for (int q = lane; q < M.nR; q += 32) {
+            const int j = M.rxn_perm[q];
+            const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
+            kc[q] = Tab<R>::ex(a);
+            const int fo = M.rxnp[q].fo;
+            if (fo >= 0) {
+                const double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
+                kc[M.nR + fo] = Tab<R>::ex(a0 - a);
+            }
+        }
+        __syncwarp();
+        W.Kc = kc;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) W.y[r] = W.valid(r) ? I.Y[(int64_t)(lane + 32 * r) * I.ldY + c] : 0.0;
+        W.f(W.y, W.f0);
+        bool fin = true;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) fin &= isfinite(W.f0[r]);
+        fin = __all_sync(0xffffffffu, fin);
+        uint8_t st = fin ? 0 : KIN_CELL_NONFINITE;
+        double sig = 0.0, h = I.dt;
+        if (fin) {
+            sig = W.sigma(true);
+            if (!isfinite(sig)) {
+                st = KIN_CELL_NONFINITE;
+            } else {
+                double h0 = sig > 0.0 ? 1.0 / sig : I.dt;
+                if (h0 > I.dt) h0 = I.dt;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) W.x[r] = W.y[r] + h0 * W.f0[r];
+                W.f(W.x, W.fx);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) W.x[r] = h0 * (W.fx[r] - W.f0[r]);  // Delta_0
+                const double e0 = W.rms(W.x, W.y, W.y);
+                if (!isfinite(e0)) h = 0.1 * h0;
+                else h = e0 > 0.0 ? 0.1 * h0 / sqrt(e0) : I.dt;
+                if (h > I.dt) h = I.dt;
+                if (h < 1e-20 * I.dt) st = KIN_CELL_HMIN;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (W.valid(r)) {
+                L.cell_f0[g * nS + lane + 32 * r] = W.f0[r];
+                if (L.cell_ev) L.cell_ev[g * nS + lane + 32 * r] = W.ev[r];
+            }
+        if (lane == 0) {
+            L.cell_sig[g] = sig;
+            L.cell_h[g] = h;
+            L.cell_nfe[g] = W.nfe;
+            L.cell_st[g] = st;
+        }
+    }
+}
+
+// Persistent main kernel: each warp takes cells from the queue in the
+// longest-first order and integrates them one after another.
+template <typename R, int NR>
+__global__ void __launch_bounds__(256, WarpBounds<NR>::min_blocks) warp_integrate_kernel(const __grid_constant__ Launch L)
+{
+    WarpRKC<R, NR> W(L);
+    const MechDev& M = L.M;
+    const int lane = W.lane, nK = M.nR + M.nFO, nS = M.nS;
+    for (;;) {
+        unsigned long long q = 0;
+        if (lane == 0) q = atomicAdd(L.queue, 1ull);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= (unsigned long long)L.total) return;
+        const int64_t g = L.order[q];
+        const int ii = find_inst(L, g);
+        const InstDev& I = L.inst[ii];
+        const int64_t c = g - L.start[ii];
+        int nacc = 0, nrej = 0, code;
+        W.nfe = L.cell_nfe[g];
+        W.nsig = 1;
+        const uint8_t pre = L.cell_st[g];
+        if (pre != 0) {
+            code = pre;  // decided by the pre-pass; Y stays as given
+        } else {
+            const double T = I.T[c], p = I.p[c];
+            W.Ctot = p * 1e-6 / (R_GAS * T);
+            W.invCtot = 1.0 / W.Ctot;
+            W.atol = I.atol;
+            W.rtol = I.rtol;
+            W.Kc = reinterpret_cast<const R*>(L.cell_k) + g * nK;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int i = lane + 32 * r;
+                const bool v = i < nS;
+                W.y[r] = v ? I.Y[(int64_t)i * I.ldY + c] : 0.0;
+                W.f0[r] = v ? L.cell_f0[g * nS + i] : 0.0;
+                W.ev[r] = (v && L.cell_ev) ? L.cell_ev[g * nS + i] : 0.0;
+            }
+            code = W.run(I.dt, L.cell_sig[g], L.cell_h[g], nacc, nrej);
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                if (W.valid(r)) I.Y[(int64_t)(lane + 32 * r) * I.ldY + c] = W.y[r];
+        }
+        if (lane == 0) {
+            if (I.status) I.status[c] = (uint8_t)code;
+            if (I.stats) {
+                int32_t* st = I.stats + 4 * c;
+                st[0] = W.nfe;
+                st[1] = nacc;
+                st[2] = nrej;
+                st[3] = W.nsig;
+            }
+        }
+    }
+}
+
+inline size_t warp_smem_bytes(const MechDev& M, int precision, int threads)
+{
+    (void)precision;  // FP64-sized in both precisions
+    return (size_t)warp_smem_elems(M) * (threads / 32) * 8;
+}
+
+template <typename R, int NR>
+inline cudaError_t warp_launch_nr(Launch& L, int blocks, int threads, cudaStream_t st)
+{
+    const size_t sm = warp_smem_bytes(L.M, L.precision, threads);
+    cudaError_t e = cudaFuncSetAttribute(warp_init_kernel<R, NR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(warp_integrate_kernel<R, NR>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    warp_init_kernel<R, NR><<<blocks, threads, sm, st>>>(L);
+    e = launch_sort(L, st);
+    if (e != cudaSuccess) return e;
+    warp_integrate_kernel<R, NR><<<blocks, threads, sm, st>>>(L);
+    return cudaGetLastError();
+}
+
+template <typename R, int NR>
+inline cudaError_t warp_occ_nr(const MechDev& M, int precision, int threads, int* bps)
+{
+    const size_t sm = warp_smem_bytes(M, precision, threads);
+    cudaError_t e = cudaFuncSetAttribute(warp_integrate_kernel<R, NR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, warp_integrate_kernel<R, NR>, threads, sm);
+}
+
+// Register-vector width for n species (species l + 32 r, r < NR).
+__host__ __device__ inline int warp_nr(int nS) { return nS <= 32 ? 1 : nS <= 64 ? 2 : nS <= 128 ? 4 : 8; }
+
+template <typename R>
+inline cudaError_t warp_launch(Launch& L, int blocks, int threads, cudaStream_t st)
+{
+    switch (warp_nr(L.M.nS)) {
+    case 1: return warp_launch_nr<R, 1>(L, blocks, threads, st);
+    case 2: return warp_launch_nr<R, 2>(L, blocks, threads, st);
+    case 4: return warp_launch_nr<R, 4>(L, blocks, threads, st);
+    default: return warp_launch_nr<R, 8>(L, blocks, threads, st);
+    }
+}
+
+template <typename R>
+inline cudaError_t warp_occ(const MechDev& M, int precision, int threads, int* bps)
+{
+    switch (warp_nr(M.nS)) {
+    case 1: return warp_occ_nr<R, 1>(M, precision, threads, bps);
+    case 2: return warp_occ_nr<R, 2>(M, precision, threads, bps);
+    case 4: return warp_occ_nr<R, 4>(M, precision, threads, bps);
+    default: return warp_occ_nr<R, 8>(M, precision, threads, bps);
+    }
+}
+
+}  // namespace kin

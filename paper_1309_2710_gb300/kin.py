@@ -23,6 +23,8 @@ CELL_OK, CELL_MAXSTEPS, CELL_HMIN, CELL_NONFINITE = 0, 1, 2, 3
 STAGE_GLOBAL, STAGE_SHARED, STAGE_SHARED_ALL = 0, 1, 2
 OCC_DEFAULT, OCC_HIGH = 0, 1
 SIGMA_GERSHGORIN, SIGMA_POWER = 0, 1
+LAYOUT_AUTO, LAYOUT_LANE, LAYOUT_WARP = 0, 1, 2
+WARP_MIN_REACTIONS = 256
 MAX_INSTANCES = 128
 
 
@@ -45,7 +47,7 @@ class Opts(ctypes.Structure):
                 ("max_steps", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("staging", ctypes.c_int32),
                 ("occupancy", ctypes.c_int32), ("sigma", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("layout", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class Instance(ctypes.Structure):
@@ -161,8 +163,8 @@ class Mechanism:
 
     def workspace_bytes(self, method=RKC, precision=FP64, cells=0, block_threads=0,
                         blocks_per_sm=0, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT,
-                        sigma=SIGMA_GERSHGORIN) -> int:
-        o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, sigma, None)
+                        sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO) -> int:
+        o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, sigma, layout, None)
         n = lib().kin_workspace_bytes(self.handle, ctypes.byref(o), int(cells))
         if n < 0:
             _check(int(n))
@@ -170,9 +172,9 @@ class Mechanism:
 
     def workspace(self, method=RKC, precision=FP64, cells=0, block_threads=0, blocks_per_sm=0,
                   device=None, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT,
-                  sigma=SIGMA_GERSHGORIN) -> torch.Tensor:
+                  sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO) -> torch.Tensor:
         n = self.workspace_bytes(method, precision, cells, block_threads, blocks_per_sm, staging,
-                                 occupancy, sigma)
+                                 occupancy, sigma, layout)
         return torch.empty(n, dtype=torch.uint8, device=device or torch.device("cuda"))
 
 
@@ -204,14 +206,14 @@ class Cells:
 def integrate(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP64,
               status=None, stats=None, workspace=None, stream=None, max_steps=0,
               block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT,
-              sigma=SIGMA_GERSHGORIN):
+              sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO):
     """Integrate every cell over dt in place (kin_integrate)."""
     cells, ld = _check_state(mech, T, p, Y)
     if workspace is None:
         workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm, Y.device,
-                                   staging, occupancy, sigma)
+                                   staging, occupancy, sigma, layout)
     o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging, occupancy, sigma,
-             _stream_handle(stream))
+             layout, _stream_handle(stream))
     _check(lib().kin_integrate(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), ld, float(dt),
                                float(rtol), float(atol), ctypes.byref(o), _ptr(status),
                                _ptr(stats), _ptr(workspace), workspace.numel()))
@@ -230,7 +232,7 @@ def make_instances(mech: Mechanism, parts: Sequence[Cells]):
 
 def integrate_batch(mech: Mechanism, parts: Sequence[Cells], method=RKC, precision=FP64,
                     workspace=None, stream=None, max_steps=0, block_threads=0, blocks_per_sm=0,
-                    staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT, sigma=SIGMA_GERSHGORIN):
+                    staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT, sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO):
     """Integrate several instances in one persistent launch (kin_integrate_batch)."""
     if not 1 <= len(parts) <= MAX_INSTANCES:
         raise ValueError("1..%d instances per launch" % MAX_INSTANCES)
@@ -238,9 +240,9 @@ def integrate_batch(mech: Mechanism, parts: Sequence[Cells], method=RKC, precisi
     if workspace is None:
         cells = sum(int(c.T.numel()) for c in parts)
         workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm,
-                                   parts[0].Y.device, staging, occupancy, sigma)
+                                   parts[0].Y.device, staging, occupancy, sigma, layout)
     o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging, occupancy, sigma,
-             _stream_handle(stream))
+             layout, _stream_handle(stream))
     _check(lib().kin_integrate_batch(mech.handle, len(parts), arr, ctypes.byref(o),
                                      _ptr(workspace), workspace.numel()))
 
@@ -251,7 +253,7 @@ def rates(mech: Mechanism, T, p, Y, precision=FP64, out=None, workspace=None, st
     if out is None:
         out = torch.empty_strided(Y.shape, Y.stride(), dtype=Y.dtype, device=Y.device)
     if workspace is None:
-        workspace = mech.workspace(RKC, precision, cells, device=Y.device)
+        workspace = mech.workspace(RKC, precision, cells, device=Y.device, layout=LAYOUT_LANE)
     _check(lib().kin_rates(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), ld, _ptr(out),
                            precision, _stream_handle(stream), _ptr(workspace), workspace.numel()))
     return out
@@ -263,9 +265,9 @@ def version() -> str:
 
 def host_buffer(mech: Mechanism, cells: int, method=RKC, precision=FP64, device=None,
                 block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL,
-                occupancy=OCC_DEFAULT, sigma=SIGMA_GERSHGORIN) -> torch.Tensor:
+                occupancy=OCC_DEFAULT, sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO) -> torch.Tensor:
     """Device buffer for integrate_host (kin_host_buffer_bytes)."""
-    o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, sigma, None)
+    o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, sigma, layout, None)
     n = lib().kin_host_buffer_bytes(mech.handle, ctypes.byref(o), int(cells))
     if n < 0:
         _check(int(n))
@@ -275,7 +277,7 @@ def host_buffer(mech: Mechanism, cells: int, method=RKC, precision=FP64, device=
 def integrate_host(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP64,
                    status=None, stats=None, buffer=None, stream=None, max_steps=0,
                    block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT,
-                   sigma=SIGMA_GERSHGORIN):
+                   sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO):
     """kin_integrate_host: T, p, Y (in place), status, stats are CPU tensors
     (pin them for asynchronous copies). Returns after enqueueing; synchronise
     the stream before reading the results."""
@@ -287,9 +289,9 @@ def integrate_host(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precisi
         raise ValueError("Y must be [n_species, >= cells] with unit column stride")
     if buffer is None:
         buffer = host_buffer(mech, cells, method, precision, None, block_threads, blocks_per_sm,
-                             staging, occupancy, sigma)
+                             staging, occupancy, sigma, layout)
     o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging, occupancy, sigma,
-             _stream_handle(stream))
+             layout, _stream_handle(stream))
     _check(lib().kin_integrate_host(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), int(Y.stride(0)),
                                     float(dt), float(rtol), float(atol), ctypes.byref(o),
                                     _ptr(status), _ptr(stats), _ptr(buffer), buffer.numel()))
