@@ -48,9 +48,16 @@ FP32_LANES_PER_SM = 128
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
-# DRAM bytes per launch of the integrate kernel from an ncu capture (see
-# profiles/), valid for the kernel source whose hash is recorded with it.
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture (profiles/), valid only for the kernel sources whose hash is the
+# key: workload -> (bytes, cells in the captured launch). A capture on fewer
+# cells than the benchmarked workload is scaled by the cell count.
+TRAFFIC = {
+    "2b7b28e9ce63": {
+        "h2co_13sp_rkc": (111.619817e9 + 92.057219e9, 262144),
+        "ch4_53sp_rkc_mixed": (270.663680e6 + 24.430848e6, 65536),
+    },
+}
 
 
 def kernel_hash() -> str:
@@ -255,7 +262,7 @@ def run_reference(args):
     return 0
 
 
-def workload_config(name, cells, sigma=None):
+def workload_config(name, cells, sigma=None, order="random"):
     w = synth.WORKLOADS[name]
     sigma = w["sigma"] if sigma is None else sigma
     rkc = "RKC (%s sigma)" % ("power-method" if sigma == synth.POWER else "Gershgorin FD")
@@ -266,7 +273,8 @@ def workload_config(name, cells, sigma=None):
                            cells, w["dt"], w["rtol"], w["atol"]),
             "cells": cells, "method": "RKC" if w["method"] == synth.RKC else "RKCK",
             "precision": "fp64" if w["precision"] == synth.FP64 else "mixed",
-            "l2": "flushed between steps (256 MiB write)", "cell_order": "random (as drawn)"}
+            "l2": "flushed between steps (256 MiB write)", "cell_order": "random (as drawn)" if order == "random" else
+            "similar (sorted by temperature, the paper's 'similar' initial conditions)"}
 
 
 # ------------------------------------------------------------ GPU arm ---
@@ -290,7 +298,8 @@ def run_kin(args):
     m = synth.workload_mechanism(name)
     cells = args.cells or w["cells"]
     # weak scaling: every rank integrates its own full-size problem (own seeds)
-    T, p, Y0 = synth.workload_states(name, m, cells=cells, seed_offset=1000 * rank)
+    T, p, Y0 = synth.workload_states(name, m, cells=cells, seed_offset=1000 * rank,
+                                     sort_by_T=args.order == "sorted")
     km = kin.Mechanism(m)
     method, prec = w["method"], w["precision"]
     sigma = w["sigma"] if args.sigma == "default" else (synth.POWER if args.sigma == "power"
@@ -366,7 +375,9 @@ def run_kin(args):
     bind64 = t64 >= t32
     achieved = (ops64 if bind64 else ops32) / (kavg * 1e-3) / 1e9
     peak = peak64 if bind64 else peak32
-    tr = TRAFFIC.get(kernel_hash())
+    tr = TRAFFIC.get(kernel_hash(), {}).get(name)
+    if tr is not None:
+        tr = tr[0] * cells / tr[1]
 
     # end to end: host (pinned) buffers through the public API, copies timed
     e2e = None
@@ -412,7 +423,7 @@ def run_kin(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32+f64",
             "data": "synthetic (seeded generator standing in for the paper's mechanisms and states)",
-            "config": dict(workload_config(name, cells, sigma), launch_shape=shape),
+            "config": dict(workload_config(name, cells, sigma, args.order), launch_shape=shape),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "G %s lane-ops/s" % ("FP64" if bind64 else "FP32"),
                          "frac": achieved / peak, "traffic": tr,
@@ -463,8 +474,25 @@ def run_batched(args):
     total = sum(n for n, _ in inst)
     sigma = w["sigma"] if args.sigma == "default" else (synth.POWER if args.sigma == "power"
                                                          else synth.GERSHGORIN)
-    ws = km.workspace(kin.RKC, prec, total, device=dev, sigma=sigma)
-    ws1 = km.workspace(kin.RKC, prec, max(n for n, _ in inst), device=dev, sigma=sigma)
+    shape = dict(block_threads=0, blocks_per_sm=0, staging=kin.STAGE_GLOBAL, occupancy=kin.OCC_DEFAULT,
+                 layout=kin.LAYOUT_AUTO)
+    if args.shape:
+        v = [int(x) for x in args.shape.split(",")]
+        shape.update(zip(("block_threads", "blocks_per_sm", "staging", "occupancy", "layout"), v))
+    elif not args.no_tune:
+        # block shape from the autotuner, timed on a 16384-cell sample of the
+        # mechanism's states (outside the timed region)
+        from paper_1309_2710_gb300 import autotune
+        Ts, ps, Ys = synth.workload_states(name, m, cells=16384, seed_offset=99)
+        best = autotune.tune(km, m, torch.as_tensor(Ts, device=dev), torch.as_tensor(ps, device=dev),
+                             torch.as_tensor(Ys, device=dev).contiguous(), inst[0][1], w["rtol"],
+                             w["atol"], kin.RKC, prec, sigma=sigma)
+        shape = {k: best[k] for k in shape}
+    ws = km.workspace(kin.RKC, prec, total, shape["block_threads"], shape["blocks_per_sm"], dev,
+                      shape["staging"], shape["occupancy"], sigma, shape["layout"])
+    ws1 = km.workspace(kin.RKC, prec, max(n for n, _ in inst), shape["block_threads"],
+                       shape["blocks_per_sm"], dev, shape["staging"], shape["occupancy"], sigma,
+                       shape["layout"])
     stream = torch.cuda.Stream()
 
     def reset():
@@ -474,15 +502,15 @@ def run_batched(args):
     def separate():
         for c in parts:
             kin.integrate(km, c.T, c.p, c.Y, c.dt, c.rtol, c.atol, kin.RKC, prec, status=c.status,
-                          stats=c.stats, workspace=ws1, stream=stream, sigma=sigma)
+                          stats=c.stats, workspace=ws1, stream=stream, sigma=sigma, **shape)
 
     with torch.cuda.stream(stream):
         reset()
-        kin.integrate_batch(km, parts, kin.RKC, prec, workspace=ws, stream=stream, sigma=sigma)
+        kin.integrate_batch(km, parts, kin.RKC, prec, workspace=ws, stream=stream, sigma=sigma, **shape)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
-        kin.integrate_batch(km, parts, kin.RKC, prec, workspace=ws, sigma=sigma)
+        kin.integrate_batch(km, parts, kin.RKC, prec, workspace=ws, sigma=sigma, **shape)
     out = {}
     for label, fn in (("persistent_graph", g.replay), ("separate_launches", separate)):
         for _ in range(args.warmup):
@@ -507,7 +535,7 @@ def run_batched(args):
     print(json.dumps({"mode": "batched", "workload": name, "instances": len(inst), "cells": total,
                       "scale": args.scale, "precision": args.precision, "mean_f_evals": nfe,
                       "sigma": "power" if sigma == synth.POWER else "gershgorin",
-                      "sizes": [n for n, _ in inst], **out,
+                      "sizes": [n for n, _ in inst], "launch_shape": shape, **out,
                       "speedup": out["separate_launches"]["ms"] / out["persistent_graph"]["ms"]}))
     return 0
 
@@ -537,6 +565,8 @@ def main():
     ap.add_argument("--shape", default="", help="block_threads,blocks_per_sm,staging,occupancy"
                                                 "[,layout] (skips the autotuner)")
     ap.add_argument("--mode", choices=["headline", "batched"], default="headline")
+    ap.add_argument("--order", choices=["random", "sorted"], default="random",
+                    help="cell order: as drawn, or sorted by temperature ('similar')")
     ap.add_argument("--sigma", choices=["default", "gershgorin", "power"], default="default",
                     help="RKC spectral-radius estimator (default: the workload's)")
     ap.add_argument("--scale", type=float, default=1.0, help="batched mode: instance size scale")

@@ -78,8 +78,10 @@ extern "C" {
 #define KIN_LAYOUT_WARP 2 /* one warp integrates one cell: its 32 lanes share the
                              reactions and species of f; the cell's concentrations and
                              rates of progress live in shared memory. RKC only
-                             (KIN_EUNSUPPORTED for RKCK). staging and occupancy are
-                             ignored; block_threads may be up to 256 */
+                             (KIN_EUNSUPPORTED for RKCK). staging is ignored;
+                             occupancy selects the register budget (KIN_OCC_HIGH: 80
+                             registers for up to 64 species, 24 warps per SM);
+                             block_threads may be up to 256 */
 #define KIN_WARP_MIN_REACTIONS 256
 
 /* per-cell status */

@@ -5,8 +5,8 @@ of the caller's cells over the candidate shapes:
   block_threads  32 .. 128 lanes per block (one cell per lane),
   blocks_per_sm  persistent blocks per SM (only shapes that fit),
   staging        per-lane rate scratch in the workspace or in shared memory,
-  layout         one lane or one warp per cell (RKC; the warp layout has only
-                 block_threads and blocks_per_sm to choose),
+  layout         one lane or one warp per cell (RKC; the warp layout chooses
+                 block_threads, blocks_per_sm and the register budget),
 and keeps the fastest. Results are cached per GPU and mechanism shape in a
 JSON file next to the built library.
 """
@@ -41,12 +41,13 @@ def lane_candidates(full: bool = False):
 
 
 def warp_candidates(full: bool = False):
-    for threads in ((64, 128, 256) if full else (128, 256)):
-        for warps in ((8, 12, 16, 24, 32) if full else (8, 16, 24)):
-            bps = warps * 32 // threads
-            if bps >= 1:
-                yield dict(block_threads=threads, blocks_per_sm=bps, staging=kin.STAGE_GLOBAL,
-                           occupancy=kin.OCC_DEFAULT, layout=kin.LAYOUT_WARP)
+    for occupancy in (kin.OCC_DEFAULT, kin.OCC_HIGH):
+        for threads in ((64, 128, 256) if full else (128, 256)):
+            for warps in ((8, 12, 16, 24, 32) if full else (8, 16, 24)):
+                bps = warps * 32 // threads
+                if bps >= 1:
+                    yield dict(block_threads=threads, blocks_per_sm=bps, staging=kin.STAGE_GLOBAL,
+                               occupancy=occupancy, layout=kin.LAYOUT_WARP)
 
 
 def candidates(full: bool = False, method: int = kin.RKC, n_reactions: int = 0):

@@ -83,7 +83,10 @@ int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
         const size_t sm = warp_smem(m->dev, o->precision, threads);
         if (sm > (size_t)maxsm)
             return fail(KIN_EUNSUPPORTED, "warp layout needs %zu bytes of shared memory per block (max %d)", sm, maxsm);
-        e = o->precision == KIN_MIXED ? occ_warp_f32(m->dev, threads, &occ) : occ_warp_f64(m->dev, threads, &occ);
+        if (o->precision == KIN_MIXED)
+            e = o->occupancy ? occ_warp_f32_o1(m->dev, threads, &occ) : occ_warp_f32_o0(m->dev, threads, &occ);
+        else
+            e = o->occupancy ? occ_warp_f64_o1(m->dev, threads, &occ) : occ_warp_f64_o0(m->dev, threads, &occ);
         cap = occ;  // as many as fit
     } else {
         if (threads % 32 != 0 || threads > 128) return fail(KIN_EINVAL, "block_threads must be a multiple of 32 and <= 128");
@@ -404,9 +407,12 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     cudaStream_t st = (cudaStream_t)o->stream;
     cudaError_t e = cudaMemsetAsync(base + w.header, 0, 512, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    if (g.layout == KIN_LAYOUT_WARP)
-        e = o->precision == KIN_MIXED ? launch_warp_f32(P, blocks, g.threads, st)
-                                      : launch_warp_f64(P, blocks, g.threads, st);
+    if (g.layout == KIN_LAYOUT_WARP && o->precision == KIN_MIXED)
+        e = o->occupancy ? launch_warp_f32_o1(P, blocks, g.threads, st)
+                         : launch_warp_f32_o0(P, blocks, g.threads, st);
+    else if (g.layout == KIN_LAYOUT_WARP)
+        e = o->occupancy ? launch_warp_f64_o1(P, blocks, g.threads, st)
+                         : launch_warp_f64_o0(P, blocks, g.threads, st);
     else
         e = launch_integrate(P, o->staging, o->occupancy, blocks, g.threads, st);
     if (e != cudaSuccess) return cuda_fail(e, "integrate launch");

@@ -1,0 +1,18 @@
+// inst_warp_f32_hi.cu -- the warp-per-cell RKC kernels with float rate arithmetic and
+// the high-occupancy register budget (own translation unit so the build runs in
+// parallel).
+#include "warp.cuh"
+
+namespace kin {
+
+cudaError_t launch_warp_f32_o1(Launch& L, int blocks, int threads, cudaStream_t st)
+{
+    return warp_launch<float, 1>(L, blocks, threads, st);
+}
+
+cudaError_t occ_warp_f32_o1(const MechDev& M, int threads, int* bps)
+{
+    return warp_occ<float, 1>(M, KIN_MIXED, threads, bps);
+}
+
+}  // namespace kin

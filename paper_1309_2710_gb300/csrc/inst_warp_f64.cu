@@ -1,22 +1,18 @@
-// inst_warp_f64.cu -- instantiation of the warp-per-cell RKC kernels with double
-// rate arithmetic (own translation unit so the build runs in parallel).
+// inst_warp_f64.cu -- the warp-per-cell RKC kernels with double rate arithmetic and the
+// default register budget (own translation unit so the build runs in parallel).
 #include "warp.cuh"
 
 namespace kin {
 
-cudaError_t launch_warp_f64(Launch& L, int blocks, int threads, cudaStream_t st)
+cudaError_t launch_warp_f64_o0(Launch& L, int blocks, int threads, cudaStream_t st)
 {
-    return warp_launch<double>(L, blocks, threads, st);
+    return warp_launch<double, 0>(L, blocks, threads, st);
 }
 
-cudaError_t occ_warp_f64(const MechDev& M, int threads, int* bps)
+cudaError_t occ_warp_f64_o0(const MechDev& M, int threads, int* bps)
 {
-    return warp_occ<double>(M, KIN_FP64, threads, bps);
+    return warp_occ<double, 0>(M, KIN_FP64, threads, bps);
 }
-
-}  // namespace kin
-
-namespace kin {
 
 size_t warp_smem(const MechDev& M, int precision, int threads)
 {

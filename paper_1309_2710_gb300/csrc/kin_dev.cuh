@@ -118,11 +118,16 @@ cudaError_t occ_rkc_f32(int stg, int occ, int threads, size_t sm, int* bps);
 cudaError_t occ_rkck_f64(int stg, int occ, int threads, size_t sm, int* bps);
 cudaError_t occ_rkck_f32(int stg, int occ, int threads, size_t sm, int* bps);
 cudaError_t launch_sort(Launch& L, cudaStream_t st);
-// Warp-per-cell RKC (inst_warp_*.cu): one warp integrates one cell.
-cudaError_t launch_warp_f64(Launch& L, int blocks, int threads, cudaStream_t st);
-cudaError_t launch_warp_f32(Launch& L, int blocks, int threads, cudaStream_t st);
-cudaError_t occ_warp_f64(const MechDev& M, int threads, int* bps);
-cudaError_t occ_warp_f32(const MechDev& M, int threads, int* bps);
+// Warp-per-cell RKC (inst_warp_*.cu): one warp integrates one cell; one
+// translation unit per rate precision and register budget (occupancy).
+cudaError_t launch_warp_f64_o0(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_warp_f64_o1(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_warp_f32_o0(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_warp_f32_o1(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t occ_warp_f64_o0(const MechDev& M, int threads, int* bps);
+cudaError_t occ_warp_f64_o1(const MechDev& M, int threads, int* bps);
+cudaError_t occ_warp_f32_o0(const MechDev& M, int threads, int* bps);
+cudaError_t occ_warp_f32_o1(const MechDev& M, int threads, int* bps);
 size_t warp_smem(const MechDev& M, int precision, int threads);
 
 // Record `code` and a printf-style message as the calling thread's last

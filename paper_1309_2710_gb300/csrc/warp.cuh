@@ -396,16 +396,20 @@ struct WarpRKC {
     }
 };
 
-template <int NR>
+// Register budget at 256 threads per block. OCC 0: 128 registers (no spills
+// for up to 4 vector slots; 16 resident warps per SM); OCC 1: 80 registers
+// for 2 or fewer slots (24 warps per SM; a few values spill to local memory),
+// 128 for 4 and 8 slots.
+template <int NR, int OCC>
 struct WarpBounds {
-    static constexpr int min_blocks = NR <= 2 ? 3 : 2;  // 85 or 128 registers at 256 threads
+    static constexpr int min_blocks = NR == 8 ? (OCC ? 2 : 1) : (OCC && NR <= 2 ? 3 : 2);
 };
 
 // Pre-pass, one warp per cell (grid-stride over cells): the cell's rate
 // constants (stored cell-major for the main kernel), f(y0), sigma and the
 // initial step h1 (Section 2.3).
-template <typename R, int NR>
-__global__ void __launch_bounds__(256, WarpBounds<NR>::min_blocks) warp_init_kernel(const __grid_constant__ Launch L)
+template <typename R, int NR, int OCC>
+__global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_init_kernel(const __grid_constant__ Launch L)
 {
     WarpRKC<R, NR> W(L);
     const MechDev& M = L.M;
@@ -481,8 +485,8 @@ __global__ void __launch_bounds__(256, WarpBounds<NR>::min_blocks) warp_init_ker
 
 // Persistent main kernel: each warp takes cells from the queue in the
 // longest-first order and integrates them one after another.
-template <typename R, int NR>
-__global__ void __launch_bounds__(256, WarpBounds<NR>::min_blocks) warp_integrate_kernel(const __grid_constant__ Launch L)
+template <typename R, int NR, int OCC>
+__global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_integrate_kernel(const __grid_constant__ Launch L)
 {
     WarpRKC<R, NR> W(L);
     const MechDev& M = L.M;
@@ -541,55 +545,56 @@ inline size_t warp_smem_bytes(const MechDev& M, int precision, int threads)
     return (size_t)warp_smem_elems(M) * (threads / 32) * 8;
 }
 
-template <typename R, int NR>
+template <typename R, int NR, int OCC>
 inline cudaError_t warp_launch_nr(Launch& L, int blocks, int threads, cudaStream_t st)
 {
     const size_t sm = warp_smem_bytes(L.M, L.precision, threads);
-    cudaError_t e = cudaFuncSetAttribute(warp_init_kernel<R, NR>,
+    cudaError_t e = cudaFuncSetAttribute(warp_init_kernel<R, NR, OCC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(warp_integrate_kernel<R, NR>,
+        e = cudaFuncSetAttribute(warp_integrate_kernel<R, NR, OCC>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    warp_init_kernel<R, NR><<<blocks, threads, sm, st>>>(L);
+    warp_init_kernel<R, NR, OCC><<<blocks, threads, sm, st>>>(L);
     e = launch_sort(L, st);
     if (e != cudaSuccess) return e;
-    warp_integrate_kernel<R, NR><<<blocks, threads, sm, st>>>(L);
+    warp_integrate_kernel<R, NR, OCC><<<blocks, threads, sm, st>>>(L);
     return cudaGetLastError();
 }
 
-template <typename R, int NR>
+template <typename R, int NR, int OCC>
 inline cudaError_t warp_occ_nr(const MechDev& M, int precision, int threads, int* bps)
 {
     const size_t sm = warp_smem_bytes(M, precision, threads);
-    cudaError_t e = cudaFuncSetAttribute(warp_integrate_kernel<R, NR>,
+    cudaError_t e = cudaFuncSetAttribute(warp_integrate_kernel<R, NR, OCC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, warp_integrate_kernel<R, NR>, threads, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, warp_integrate_kernel<R, NR, OCC>, threads,
+                                                         sm);
 }
 
 // Register-vector width for n species (species l + 32 r, r < NR).
 __host__ __device__ inline int warp_nr(int nS) { return nS <= 32 ? 1 : nS <= 64 ? 2 : nS <= 128 ? 4 : 8; }
 
-template <typename R>
+template <typename R, int OCC>
 inline cudaError_t warp_launch(Launch& L, int blocks, int threads, cudaStream_t st)
 {
     switch (warp_nr(L.M.nS)) {
-    case 1: return warp_launch_nr<R, 1>(L, blocks, threads, st);
-    case 2: return warp_launch_nr<R, 2>(L, blocks, threads, st);
-    case 4: return warp_launch_nr<R, 4>(L, blocks, threads, st);
-    default: return warp_launch_nr<R, 8>(L, blocks, threads, st);
+    case 1: return warp_launch_nr<R, 1, OCC>(L, blocks, threads, st);
+    case 2: return warp_launch_nr<R, 2, OCC>(L, blocks, threads, st);
+    case 4: return warp_launch_nr<R, 4, OCC>(L, blocks, threads, st);
+    default: return warp_launch_nr<R, 8, OCC>(L, blocks, threads, st);
     }
 }
 
-template <typename R>
+template <typename R, int OCC>
 inline cudaError_t warp_occ(const MechDev& M, int precision, int threads, int* bps)
 {
     switch (warp_nr(M.nS)) {
-    case 1: return warp_occ_nr<R, 1>(M, precision, threads, bps);
-    case 2: return warp_occ_nr<R, 2>(M, precision, threads, bps);
-    case 4: return warp_occ_nr<R, 4>(M, precision, threads, bps);
-    default: return warp_occ_nr<R, 8>(M, precision, threads, bps);
+    case 1: return warp_occ_nr<R, 1, OCC>(M, precision, threads, bps);
+    case 2: return warp_occ_nr<R, 2, OCC>(M, precision, threads, bps);
+    case 4: return warp_occ_nr<R, 4, OCC>(M, precision, threads, bps);
+    default: return warp_occ_nr<R, 8, OCC>(M, precision, threads, bps);
     }
 }
 

@@ -64,10 +64,14 @@ class Request:
 
 @dataclass
 class Group:
+    """One mechanism/method/precision served together. `shape` is the launch
+    shape of one slot's persistent launch (kin_opts fields block_threads,
+    blocks_per_sm, staging, occupancy, layout): a slot that leaves SM
+    resources free lets the other slots' launches run beside it."""
     mech: kin.Mechanism
     method: int
     precision: int
-    blocks_per_sm: int = 0
+    shape: Dict[str, int] = field(default_factory=dict)
     sigma: int = kin.SIGMA_GERSHGORIN
 
 
@@ -122,8 +126,10 @@ class Server:
     def _launch(self, gname: str, slot: _Slot, batch: List[Request], now: float):
         g = self.groups[gname]
         cells = sum(r.cells for r in batch)
-        need = g.mech.workspace_bytes(g.method, g.precision, cells, 0, g.blocks_per_sm,
-                                      sigma=g.sigma)
+        sh = g.shape
+        need = g.mech.workspace_bytes(g.method, g.precision, cells, sh.get("block_threads", 0),
+                                      sh.get("blocks_per_sm", 0), sh.get("staging", 0),
+                                      sh.get("occupancy", 0), g.sigma, sh.get("layout", 0))
         if slot.workspace is None or slot.workspace.numel() < need:
             slot.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
         with torch.cuda.stream(slot.stream):
@@ -136,7 +142,7 @@ class Server:
                 parts.append(kin.Cells(Td, pd, Yd, r.dt, r.rtol, r.atol, sd))
                 r.t_launch = now
             kin.integrate_batch(g.mech, parts, g.method, g.precision, workspace=slot.workspace,
-                                stream=slot.stream, blocks_per_sm=g.blocks_per_sm, sigma=g.sigma)
+                                stream=slot.stream, sigma=g.sigma, **g.shape)
             for r in batch:
                 r.Y_out.copy_(r._dev[2], non_blocking=True)
                 r.status.copy_(r._dev[3], non_blocking=True)
@@ -273,12 +279,21 @@ def percentiles(reqs: List[Request]):
             "throughput_cells_per_s": cells / span, "requests": len(reqs), "cells": int(cells)}
 
 
-def default_groups(blocks_per_sm: int = 2):
+# Per-slot launch shapes of the serving groups: about a third of an SM's
+# registers each, so that launches of the other slots and group fit beside.
+SERVE_SHAPES = {
+    "h2co_13sp_rkc": dict(block_threads=128, blocks_per_sm=2, occupancy=kin.OCC_HIGH,
+                          layout=kin.LAYOUT_LANE),
+    "ch4_53sp_rkc_mixed": dict(block_threads=256, blocks_per_sm=1, layout=kin.LAYOUT_WARP),
+}
+
+
+def default_groups():
     groups, pools = {}, {}
     for name in ("h2co_13sp_rkc", "ch4_53sp_rkc_mixed"):
         w = synth.WORKLOADS[name]
         m = synth.workload_mechanism(name)
-        groups[name] = Group(kin.Mechanism(m), w["method"], w["precision"], blocks_per_sm,
+        groups[name] = Group(kin.Mechanism(m), w["method"], w["precision"], dict(SERVE_SHAPES[name]),
                              w["sigma"])
         pools[name] = StatePool(name, m, 65536 + 1024)
     return groups, pools
@@ -290,11 +305,10 @@ def main():
     ap.add_argument("--loads", default="0.5,0.8,0.95")
     ap.add_argument("--budget-gb", type=float, default=16.0)
     ap.add_argument("--slots", type=int, default=2)
-    ap.add_argument("--blocks-per-sm", type=int, default=2)
     args = ap.parse_args()
     from . import build as _b
     _b.build()
-    groups, pools = default_groups(args.blocks_per_sm)
+    groups, pools = default_groups()
     budget = int(args.budget_gb * (1 << 30))
     # warm up both paths (module loads, workspaces, pinned pools)
     warm = make_requests(8, pools, seed=7)

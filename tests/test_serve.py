@@ -21,7 +21,8 @@ def setup():
     for name in ("h2co_13sp_rkc", "ch4_53sp_rkc_mixed"):
         w = synth.WORKLOADS[name]
         m = synth.workload_mechanism(name)
-        groups[name] = serve.Group(kin.Mechanism(m), w["method"], w["precision"], 2, w["sigma"])
+        groups[name] = serve.Group(kin.Mechanism(m), w["method"], w["precision"],
+                                   dict(serve.SERVE_SHAPES[name]), w["sigma"])
         pools[name] = serve.StatePool(name, m, 8192, seed_offset=900)
     return groups, pools
 
