@@ -692,16 +692,44 @@ struct Integrator {
 
     __device__ int rkc_post(LaneState& S)
     {
-        if (S.phase == PH_STAGE) {
-            // FX = f(w_{j-1}); w_j = (1-mu-nu) y + mu w_{j-1} + nu w_{j-2}
-            //                       + mu~ h f_{j-1} + gamma~ h f_0
-            const double* c = coef(S.s, S.j);
-            const double mu = c[0], nu = c[1], mt = c[2] * S.hh, gt = c[3] * S.hh, c0 = c[4];
+        if (S.phase == PH_STAGE || S.phase == PH_FINAL) {
+            // One pass serves both phases, so that lanes of a warp in either
+            // share it instead of running two loops in turn. FX = f(w_{j-1}):
+            //   stage j: w_j = (1-mu-nu) y + mu w_{j-1} + nu w_{j-2}
+            //                  + mu~ h f_{j-1} + gamma~ h f_0;
+            //   final:   Delta = 0.8 (y - w_s) + 0.4 h (f_0 + f_s), the same
+            //            five-term form (nu = 0), and its weighted RMS norm.
+            const bool fin = S.phase == PH_FINAL;
+            double c0, mu, nu, mt, gt;
+            if (fin) {
+                c0 = 0.8;
+                mu = -0.8;
+                nu = 0.0;
+                mt = gt = 0.4 * S.hh;
+            } else {
+                const double* c = coef(S.s, S.j);
+                mu = c[0];
+                nu = c[1];
+                mt = c[2] * S.hh;
+                gt = c[3] * S.hh;
+                c0 = c[4];
+            }
             const int nw = (S.iw1 == V_A) ? V_B : (S.iw1 == V_B ? V_C : V_A);
-            Lane<double> Y = V(V_Y), F0 = V(V_F0), W1 = V(S.iw1), W2 = V(S.iw2), FJ = V(V_FX),
-                         WN = V(nw);
-            for (int i = 0; i < M.nS; ++i)
-                WN[i] = c0 * Y[i] + mu * W1[i] + nu * W2[i] + mt * FJ[i] + gt * F0[i];
+            Lane<double> Y = V(V_Y), F0 = V(V_F0), W1 = V(S.iw1), W2 = V(fin ? S.iw1 : S.iw2),
+                         FJ = V(V_FX), WN = V(nw);
+            double acc = 0.0;
+            for (int i = 0; i < M.nS; ++i) {
+                const double y = Y[i], w1 = W1[i];
+                const double v = c0 * y + mu * w1 + nu * W2[i] + mt * FJ[i] + gt * F0[i];
+                if (fin) {
+                    const double sc = S.atol + S.rtol * fmax(fabs(y), fabs(w1));
+                    const double r = v / sc;
+                    acc += r * r;
+                } else {
+                    WN[i] = v;
+                }
+            }
+            if (fin) return rkc_final(S, acc);
             S.iw2 = S.iw1;
             S.iw1 = nw;
             S.in_v = nw;
@@ -728,16 +756,15 @@ struct Integrator {
             if (!isfinite(S.sigma)) return KIN_CELL_NONFINITE;
             return rkc_begin_step(S);
         }
-        // PH_FINAL: error estimate (Section 2.3) and step control
+        return -1;  // not reached: every RKC phase is handled above
+    }
+
+    // Step control after the final evaluation (Section 2.3): acc is the sum
+    // of the squared weighted error components.
+    __device__ int rkc_final(LaneState& S, double acc)
+    {
         Lane<double> Y = V(V_Y), F0 = V(V_F0), WS = V(S.iw1), FX = V(V_FX);
-        double acc = 0.0;
         const double hh = S.hh;
-        for (int i = 0; i < M.nS; ++i) {
-            const double d = 0.8 * (Y[i] - WS[i]) + 0.4 * hh * (F0[i] + FX[i]);
-            const double sc = S.atol + S.rtol * fmax(fabs(Y[i]), fabs(WS[i]));
-            const double r = d / sc;
-            acc += r * r;
-        }
         const double err = sqrt(acc * S.invN);
         S.attempts++;
         if (err <= 1.0) {

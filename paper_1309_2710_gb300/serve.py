@@ -73,6 +73,7 @@ class Group:
     precision: int
     shape: Dict[str, int] = field(default_factory=dict)
     sigma: int = kin.SIGMA_GERSHGORIN
+    max_batch_cells: Optional[int] = None  # cap on one launch's cells (None: the server's)
 
 
 @dataclass
@@ -189,8 +190,9 @@ class Server:
                     if slot.event is None and ready[gname]:
                         batch, cells = [], 0
                         q = ready[gname]
+                        cap = self.groups[gname].max_batch_cells or self.max_batch_cells
                         while q and len(batch) < self.max_instances and (
-                                not batch or cells + q[0].cells <= self.max_batch_cells):
+                                not batch or cells + q[0].cells <= cap):
                             r = q.pop(0)
                             batch.append(r)
                             cells += r.cells
@@ -281,6 +283,11 @@ def percentiles(reqs: List[Request]):
 
 # Per-slot launch shapes of the serving groups: about a third of an SM's
 # registers each, so that launches of the other slots and group fit beside.
+# Each launch is capped (about 75 ms of work at the 13-species and 190 ms at
+# the 53-species throughput), so a request that arrives behind a large batch
+# waits for a short launch rather than a long one.
+SERVE_BATCH_CELLS = {"h2co_13sp_rkc": 131072, "ch4_53sp_rkc_mixed": 32768}
+SERVE_SLOTS = 4
 SERVE_SHAPES = {
     "h2co_13sp_rkc": dict(block_threads=128, blocks_per_sm=2, occupancy=kin.OCC_HIGH,
                           layout=kin.LAYOUT_LANE),
@@ -294,7 +301,7 @@ def default_groups():
         w = synth.WORKLOADS[name]
         m = synth.workload_mechanism(name)
         groups[name] = Group(kin.Mechanism(m), w["method"], w["precision"], dict(SERVE_SHAPES[name]),
-                             w["sigma"])
+                             w["sigma"], SERVE_BATCH_CELLS[name])
         pools[name] = StatePool(name, m, 65536 + 1024)
     return groups, pools
 
@@ -304,7 +311,7 @@ def main():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--loads", default="0.5,0.8,0.95")
     ap.add_argument("--budget-gb", type=float, default=16.0)
-    ap.add_argument("--slots", type=int, default=2)
+    ap.add_argument("--slots", type=int, default=SERVE_SLOTS)
     args = ap.parse_args()
     from . import build as _b
     _b.build()
