@@ -531,11 +531,23 @@ def run_batched(args):
         st = torch.cat([c.status for c in parts]).cpu().numpy()
         out[label] = {"ms": float(np.median(ms)), "cells_per_s": total / (np.median(ms) * 1e-3),
                       "status": np.bincount(st, minlength=4).tolist()}
-    nfe = torch.cat([c.stats[:, 0] for c in parts]).double().mean().item()
+    stats = torch.cat([c.stats for c in parts]).cpu().numpy()
+    nfe = float(stats[:, 0].mean())
+    ops64, ops32, exact = algorithmic_work(m, synth.RKC, prec, sigma, stats)
+    peak64 = FP64_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
+    peak32 = FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
+    kms = out["persistent_graph"]["ms"]
+    bind64 = ops64 / peak64 >= ops32 / peak32
+    ach = (ops64 if bind64 else ops32) / (kms * 1e-3) / 1e9
+    pk = peak64 if bind64 else peak32
+    roof = {"bound": "alu", "achieved": ach, "peak": pk, "frac": ach / pk,
+            "unit": "G %s lane-ops/s" % ("FP64" if bind64 else "FP32"),
+            "ops_count": "exact" if exact else "lower bound", "kernel_ms": kms,
+            "fp64_ops": ops64, "fp32_ops": ops32}
     print(json.dumps({"mode": "batched", "workload": name, "instances": len(inst), "cells": total,
                       "scale": args.scale, "precision": args.precision, "mean_f_evals": nfe,
                       "sigma": "power" if sigma == synth.POWER else "gershgorin",
-                      "sizes": [n for n, _ in inst], "launch_shape": shape, **out,
+                      "sizes": [n for n, _ in inst], "launch_shape": shape, **out, "roofline": roof,
                       "speedup": out["separate_launches"]["ms"] / out["persistent_graph"]["ms"]}))
     return 0
 

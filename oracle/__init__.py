@@ -72,17 +72,20 @@ def bind(path: str) -> ctypes.CDLL:
     L.orc_rkc_single.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
                                  ctypes.c_void_p]
+    L.orc_mech_set_thermo.argtypes = [ctypes.c_void_p] * 3
+    L.orc_rates_energy.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                   ctypes.c_void_p]
     L.orc_integrate.restype = ctypes.c_int
     L.orc_integrate.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                 ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
-                                ctypes.c_void_p, ctypes.c_int]
+                                ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
     L.orc_trace_cell.restype = ctypes.c_int
     L.orc_trace_cell.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                 ctypes.c_int] + [ctypes.c_void_p] * 5
+                                 ctypes.c_int] + [ctypes.c_void_p] * 5 + [ctypes.c_int]
     L.orc_sigma_power.restype = ctypes.c_double
     L.orc_sigma_power.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -100,7 +103,9 @@ def _f64(a):
 
 class Mech:
     """Oracle copy of a mechanism given as plain arrays (attributes W, lnA,
-    beta, Ea, reac, prod, rtype, eff, lnA0, beta0, Ea0)."""
+    beta, Ea, reac, prod, rtype, eff, lnA0, beta0, Ea0, and optionally the
+    thermochemistry cp [J/(mol K)] and Hf [J/mol] used by the energy
+    equation)."""
 
     def __init__(self, m):
         self.n_species = int(len(m.W))
@@ -114,6 +119,10 @@ class Mech:
         self._keep = keep
         self.ptr = lib().orc_mech_new(self.n_species, self.n_reactions,
                                       *[_ptr(a) for a in keep])
+        self.has_thermo = getattr(m, "cp", None) is not None
+        if self.has_thermo:
+            cp, Hf = _f64(m.cp), _f64(m.Hf)
+            lib().orc_mech_set_thermo(self.ptr, _ptr(cp), _ptr(Hf))
 
     def __del__(self):
         try:
@@ -129,6 +138,15 @@ def rates(om: Mech, T: float, p: float, Y) -> np.ndarray:
     y = _f64(Y)
     out = np.empty(om.n_species)
     lib().orc_rates(om.ptr, float(T), float(p), _ptr(y), _ptr(out))
+    return out
+
+
+def rates_energy(om: Mech, p: float, y) -> np.ndarray:
+    """f with the energy equation: y = (Y_1..Y_nS, T) -> dy/dt for one cell."""
+    y = _f64(y)
+    assert y.shape == (om.n_species + 1,) and om.has_thermo
+    out = np.empty_like(y)
+    lib().orc_rates_energy(om.ptr, float(p), _ptr(y), _ptr(out))
     return out
 
 
@@ -183,11 +201,15 @@ def rkc_single(om: Mech, T, p, y, h, s):
     return out
 
 
-def integrate(om: Mech, T, p, Y, dt, rtol, atol, method, max_steps=0, nthreads=0):
+def integrate(om: Mech, T, p, Y, dt, rtol, atol, method, max_steps=0, nthreads=0,
+              energy=False):
     """Integrate every cell over dt. Y is [n_species, cells] (species-major).
     Returns (Y_new, status[cells] uint8, stats[cells, 4] int32 = nfe, accepted,
-    rejected, sigma estimates, threads used)."""
-    T = _f64(T); p = _f64(p)
+    rejected, sigma estimates, threads used), and T_new with `energy` (T is
+    then integrated with the energy equation)."""
+    T = np.array(T, dtype=np.float64, copy=True); p = _f64(p)
+    if energy and not om.has_thermo:
+        raise ValueError("the energy equation needs the mechanism's thermochemistry")
     Yn = np.array(Y, dtype=np.float64, order="C", copy=True)
     cells = int(T.shape[0])
     assert Yn.shape == (om.n_species, cells)
@@ -195,19 +217,22 @@ def integrate(om: Mech, T, p, Y, dt, rtol, atol, method, max_steps=0, nthreads=0
     stats = np.zeros((cells, 4), dtype=np.int32)
     nt = lib().orc_integrate(om.ptr, cells, _ptr(T), _ptr(p), _ptr(Yn), cells, float(dt),
                              float(rtol), float(atol), int(method), int(max_steps),
-                             _ptr(status), _ptr(stats), int(nthreads))
+                             _ptr(status), _ptr(stats), int(nthreads), int(bool(energy)))
+    if energy:
+        return Yn, status, stats, nt, T
     return Yn, status, stats, nt
 
 
-def trace_cell(om: Mech, T, p, y, dt, rtol, atol, method, max_steps=0, cap=100000):
+def trace_cell(om: Mech, T, p, y, dt, rtol, atol, method, max_steps=0, cap=100000,
+               energy=False):
     """Integrate one cell recording every attempt. Returns (y_new, status,
-    dict(h, err, s, accepted) arrays)."""
+    dict(h, err, s, accepted) arrays). With `energy`, y = (Y_1..Y_nS, T)."""
     y = np.array(y, dtype=np.float64, copy=True)
     h = np.zeros(cap); e = np.zeros(cap)
     s = np.zeros(cap, dtype=np.int32); a = np.zeros(cap, dtype=np.int32)
     n = ctypes.c_int32(0)
     st = lib().orc_trace_cell(om.ptr, float(T), float(p), _ptr(y), float(dt), float(rtol),
                               float(atol), int(method), int(max_steps), int(cap), _ptr(h),
-                              _ptr(e), _ptr(s), _ptr(a), ctypes.byref(n))
+                              _ptr(e), _ptr(s), _ptr(a), ctypes.byref(n), int(bool(energy)))
     k = min(n.value, cap)
     return y, st, dict(h=h[:k], err=e[:k], s=s[:k], accepted=a[:k].astype(bool))

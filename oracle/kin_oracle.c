@@ -49,6 +49,18 @@
  *     with the largest decrease (0.1); a non-finite initial-step estimate
  *     gives h = 0.1 h0.
  *
+ * Energy equation (Eq. (E:energy)), used when a call asks for it and the
+ * mechanism has thermochemistry (orc_mech_set_thermo):
+ *   - the state is y = {Y_1..Y_nS, T} (the paper lists T first; the order of
+ *     the components changes neither the RMS norm, nor the Gershgorin bound,
+ *     nor the power method), N = nS + 1;
+ *   - dT/dt = -(1 / (rho cp)) sum_i h_i omega_i W_i, with the mass-averaged
+ *     cp = sum_i Y_i cp_i / W_i and the specific enthalpy h_i = H_i / W_i;
+ *   - the thermochemistry of the synthetic mechanisms is one constant molar
+ *     heat capacity cp_i [J/(mol K)] and formation enthalpy Hf_i [J/mol] at
+ *     298.15 K per species: H_i(T) = Hf_i + cp_i (T - 298.15);
+ *   - k_j, rho and the concentrations follow T at every evaluation of f.
+ *
  * Per-cell status codes: 0 ok, 1 step limit reached, 2 step size below hmin,
  * 3 non-finite f at an accepted state (or at the initial state), or a
  * non-finite spectral-radius bound. On 1-3 the cell keeps its last accepted
@@ -73,7 +85,10 @@ typedef struct {
     int *type;                 /* [nR] 0 plain, 1 third body, 2 falloff */
     int *row;                  /* [nR] efficiency row or -1 */
     double *eff;               /* [n_rows][nS] */
+    double *cp, *Hf;           /* [nS] J/(mol K), J/mol at ORC_TREF; NULL without thermo */
 } orc_mech;
+
+#define ORC_TREF 298.15 /* K */
 
 static void *xmalloc(size_t n) { void *p = malloc(n ? n : 1); return p; }
 
@@ -122,7 +137,22 @@ void *orc_mech_new(int nS, int nR, const double *W, const double *lnA,
     }
     m->eff = (double *)xmalloc(sizeof(double) * (size_t)rows * nS);
     if (rows) memcpy(m->eff, eff, sizeof(double) * (size_t)rows * nS);
+    m->cp = NULL;
+    m->Hf = NULL;
     return m;
+}
+
+/* Species thermochemistry for the energy equation: constant molar heat
+ * capacities cp [J/(mol K)] and formation enthalpies Hf [J/mol] at 298.15 K. */
+void orc_mech_set_thermo(void *mp, const double *cp, const double *Hf)
+{
+    orc_mech *m = (orc_mech *)mp;
+    free(m->cp);
+    free(m->Hf);
+    m->cp = (double *)xmalloc(sizeof(double) * m->nS);
+    m->Hf = (double *)xmalloc(sizeof(double) * m->nS);
+    memcpy(m->cp, cp, sizeof(double) * m->nS);
+    memcpy(m->Hf, Hf, sizeof(double) * m->nS);
 }
 
 void orc_mech_free(void *p)
@@ -132,6 +162,7 @@ void orc_mech_free(void *p)
     free(m->W); free(m->lnA); free(m->beta); free(m->Ea);
     free(m->lnA0); free(m->beta0); free(m->Ea0);
     free(m->reac); free(m->prod); free(m->type); free(m->row); free(m->eff);
+    free(m->cp); free(m->Hf);
     free(m);
 }
 
@@ -150,16 +181,14 @@ void orc_rate_constants(const void *mp, double T, double *k, double *k0)
     }
 }
 
-/* f: dY/dt at fixed T and p, Eqs. (E:mass), (E:spec-rate), (E:rxn-rate).
- * k, k0 from orc_rate_constants at the same T. work: nS + nR doubles. */
-static void rates(const orc_mech *m, double T, double p, const double *k,
-                  const double *k0, const double *Y, double *dYdt, double *work)
+/* Molar production rates omega [mol/(cm^3 s)] (Eqs. (E:spec-rate),
+ * (E:rxn-rate)) and the density rho [g/cm^3] at T, p, Y; k, k0 from
+ * orc_rate_constants at the same T. C: nS doubles of scratch. */
+static double production(const orc_mech *m, double T, double p, const double *k,
+                         const double *k0, const double *Y, double *omega, double *C)
 {
-    int nS = m->nS, nR = m->nR, i, j, s;
-    double *C = work;          /* [nS] mol/cm^3 */
-    double *omega = work + nS; /* [nS] mol/(cm^3 s) */
+    int nS = m->nS, i, j, s;
     double sum = 0.0, Wbar, rho;
-    (void)nR;
     for (i = 0; i < nS; i++) sum += Y[i] / m->W[i];
     Wbar = 1.0 / sum;
     rho = p * Wbar / (ORC_R * T) * 1e-6;
@@ -186,7 +215,46 @@ static void rates(const orc_mech *m, double T, double p, const double *k,
             if (m->reac[2 * j + s] >= 0) omega[m->reac[2 * j + s]] -= q;
         }
     }
-    for (i = 0; i < nS; i++) dYdt[i] = m->W[i] * omega[i] / rho;
+    return rho;
+}
+
+/* f: dY/dt at fixed T and p, Eq. (E:mass). k, k0 from orc_rate_constants at
+ * the same T. work: 2 nS doubles. */
+static void rates(const orc_mech *m, double T, double p, const double *k,
+                  const double *k0, const double *Y, double *dYdt, double *work)
+{
+    int i;
+    double *C = work, *omega = work + m->nS;
+    double rho = production(m, T, p, k, k0, Y, omega, C);
+    for (i = 0; i < m->nS; i++) dYdt[i] = m->W[i] * omega[i] / rho;
+}
+
+/* f with the energy equation: y = {Y_1..Y_nS, T} -> dy/dt, Eqs. (E:mass) and
+ * (E:energy). The rate constants, density and concentrations are those of the
+ * state's own T. work: 2 nS + 2 nR doubles. */
+static void rates_energy(const orc_mech *m, double p, const double *y, double *dydt,
+                         double *work)
+{
+    int i, nS = m->nS;
+    double *C = work, *omega = work + nS, *k = work + 2 * nS, *k0 = k + m->nR;
+    double T = y[nS], rho, cpm = 0.0, hw = 0.0;
+    orc_rate_constants(m, T, k, k0);
+    rho = production(m, T, p, k, k0, y, omega, C);
+    for (i = 0; i < nS; i++) {
+        dydt[i] = m->W[i] * omega[i] / rho;
+        cpm += y[i] * m->cp[i] / m->W[i];                     /* J/(g K) */
+        hw += (m->Hf[i] + m->cp[i] * (T - ORC_TREF)) * omega[i]; /* h_i W_i omega_i, J/(cm^3 s) */
+    }
+    dydt[nS] = -hw / (rho * cpm);
+}
+
+/* Public f with the energy equation for tests: y = {Y, T} -> dy/dt. */
+void orc_rates_energy(const void *mp, double p, const double *y, double *dydt)
+{
+    const orc_mech *m = (const orc_mech *)mp;
+    double *work = (double *)xmalloc(sizeof(double) * (2 * m->nS + 2 * m->nR));
+    rates_energy(m, p, y, dydt, work);
+    free(work);
 }
 
 /* Public f for tests: computes k at T, then dY/dt. */
@@ -194,7 +262,7 @@ void orc_rates(const void *mp, double T, double p, const double *Y, double *dYdt
 {
     const orc_mech *m = (const orc_mech *)mp;
     double *k = (double *)xmalloc(sizeof(double) * 2 * m->nR);
-    double *work = (double *)xmalloc(sizeof(double) * (2 * m->nS + m->nR));
+    double *work = (double *)xmalloc(sizeof(double) * 2 * m->nS);
     orc_rate_constants(m, T, k, k + m->nR);
     rates(m, T, p, k, k + m->nR, Y, dYdt, work);
     free(k);
@@ -226,17 +294,23 @@ void orc_rkck_table(double *a, double *b, double *c, double *cs)
     }
 }
 
+/* The right-hand side of one cell: isothermal (T fixed, k precomputed) or,
+ * with `energy`, the coupled species and energy equations. */
 typedef struct {
     const orc_mech *m;
     double T, p;
     const double *k, *k0;
-    double *work;
+    double *work;              /* 2 nS + 2 nR doubles */
+    int energy;
     long nfe;
 } orc_f;
 
 static void feval(orc_f *F, const double *y, double *out)
 {
-    rates(F->m, F->T, F->p, F->k, F->k0, y, out, F->work);
+    if (F->energy)
+        rates_energy(F->m, F->p, y, out, F->work);
+    else
+        rates(F->m, F->T, F->p, F->k, F->k0, y, out, F->work);
     F->nfe++;
 }
 
@@ -490,12 +564,12 @@ double orc_sigma_power(const void *mp, double T, double p, const double *y, doub
     const orc_mech *m = (const orc_mech *)mp;
     int n = m->nS, it = 0;
     double *k = (double *)xmalloc(sizeof(double) * 2 * m->nR);
-    double *work = (double *)xmalloc(sizeof(double) * (2 * n + m->nR));
+    double *work = (double *)xmalloc(sizeof(double) * (2 * m->nS + 2 * m->nR));
     double *w = (double *)xmalloc(sizeof(double) * 3 * n);
     orc_f F;
     double sigma;
     orc_rate_constants(m, T, k, k + m->nR);
-    F.m = m; F.T = T; F.p = p; F.k = k; F.k0 = k + m->nR; F.work = work; F.nfe = 0;
+    F.m = m; F.T = T; F.p = p; F.k = k; F.k0 = k + m->nR; F.work = work; F.energy = 0; F.nfe = 0;
     feval(&F, y, w);
     sigma = power_sigma(&F, n, y, w, v, w + n, w + 2 * n, &it);
     *iters = it;
@@ -508,12 +582,12 @@ double orc_sigma(const void *mp, double T, double p, const double *y, double ato
     const orc_mech *m = (const orc_mech *)mp;
     int n = m->nS;
     double *k = (double *)xmalloc(sizeof(double) * 2 * m->nR);
-    double *work = (double *)xmalloc(sizeof(double) * (2 * n + m->nR));
+    double *work = (double *)xmalloc(sizeof(double) * (2 * m->nS + 2 * m->nR));
     double *v = (double *)xmalloc(sizeof(double) * 4 * n);
     orc_f F;
     double sigma;
     orc_rate_constants(m, T, k, k + m->nR);
-    F.m = m; F.T = T; F.p = p; F.k = k; F.k0 = k + m->nR; F.work = work; F.nfe = 0;
+    F.m = m; F.T = T; F.p = p; F.k = k; F.k0 = k + m->nR; F.work = work; F.energy = 0; F.nfe = 0;
     feval(&F, y, v);
     sigma = gershgorin(&F, n, y, v, atol, v + n, v + 2 * n, v + 3 * n);
     free(k); free(work); free(v);
@@ -637,11 +711,11 @@ void orc_rkck_single(const void *mp, double T, double p, const double *y, double
     const orc_mech *m = (const orc_mech *)mp;
     int n = m->nS;
     double *k = (double *)xmalloc(sizeof(double) * 2 * m->nR);
-    double *work = (double *)xmalloc(sizeof(double) * (2 * n + m->nR));
+    double *work = (double *)xmalloc(sizeof(double) * (2 * m->nS + 2 * m->nR));
     double *v = (double *)xmalloc(sizeof(double) * 8 * n);
     orc_f F;
     orc_rate_constants(m, T, k, k + m->nR);
-    F.m = m; F.T = T; F.p = p; F.k = k; F.k0 = k + m->nR; F.work = work; F.nfe = 0;
+    F.m = m; F.T = T; F.p = p; F.k = k; F.k0 = k + m->nR; F.work = work; F.energy = 0; F.nfe = 0;
     feval(&F, y, v);
     rkck_step(&F, n, y, v, h, y5, err, v + 2 * n, v + n);
     free(k); free(work); free(v);
@@ -653,11 +727,11 @@ void orc_rkc_single(const void *mp, double T, double p, const double *y, double 
     const orc_mech *m = (const orc_mech *)mp;
     int n = m->nS;
     double *k = (double *)xmalloc(sizeof(double) * 2 * m->nR);
-    double *work = (double *)xmalloc(sizeof(double) * (2 * n + m->nR));
+    double *work = (double *)xmalloc(sizeof(double) * (2 * m->nS + 2 * m->nR));
     double *v = (double *)xmalloc(sizeof(double) * 4 * n);
     orc_f F;
     orc_rate_constants(m, T, k, k + m->nR);
-    F.m = m; F.T = T; F.p = p; F.k = k; F.k0 = k + m->nR; F.work = work; F.nfe = 0;
+    F.m = m; F.T = T; F.p = p; F.k = k; F.k0 = k + m->nR; F.work = work; F.energy = 0; F.nfe = 0;
     feval(&F, y, v);
     rkc_step(&F, n, y, v, h, s, ys, v + n);
     free(k); free(work); free(v);
@@ -666,38 +740,45 @@ void orc_rkc_single(const void *mp, double T, double p, const double *y, double 
 /* Integrate `cells` independent cells over dt. Y is species-major,
  * Y[i * ldY + cell]; it is updated in place. method 0 = RKCK, 1 = RKC with
  * the Gershgorin spectral radius, 2 = RKC with the power-method one.
+ * energy != 0 integrates T with the energy equation as the (nS+1)-th
+ * component and writes it back to Tc (the mechanism needs thermochemistry;
+ * without it nothing is done and -1 is returned).
  * Per-cell outputs (any may be NULL): status, and stats[cell] =
  * {f evaluations, accepted steps, rejected steps, sigma estimates}.
  * Returns the number of threads used.
  * nthreads > 0 sets the OpenMP thread count when built with OpenMP
  * (<= 0: all available threads). */
-int orc_integrate(const void *mp, int64_t cells, const double *Tc, const double *pc,
+int orc_integrate(const void *mp, int64_t cells, double *Tc, const double *pc,
                   double *Y, int64_t ldY, double dt, double rtol, double atol, int method,
-                  int max_steps, uint8_t *status, int32_t *stats, int nthreads)
+                  int max_steps, uint8_t *status, int32_t *stats, int nthreads, int energy)
 {
     const orc_mech *m = (const orc_mech *)mp;
     int64_t c;
     int nt = 1;
+    if (energy && !m->cp) return -1;
     if (max_steps <= 0) max_steps = 100000;
 #ifdef _OPENMP
     nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
 #endif
     for (c = 0; c < cells; c++) {
-        int n = m->nS, i, st;
+        int n = m->nS + (energy ? 1 : 0), i, st;
         double *y = (double *)xmalloc(sizeof(double) * n);
         double *k = (double *)xmalloc(sizeof(double) * 2 * m->nR);
-        double *work = (double *)xmalloc(sizeof(double) * (2 * n + m->nR));
+        double *work = (double *)xmalloc(sizeof(double) * (2 * m->nS + 2 * m->nR));
         orc_stats S = {0, 0, 0, 0, 0, 0, NULL, NULL, NULL, NULL};
         orc_f F;
-        for (i = 0; i < n; i++) y[i] = Y[(int64_t)i * ldY + c];
+        for (i = 0; i < m->nS; i++) y[i] = Y[(int64_t)i * ldY + c];
+        if (energy) y[m->nS] = Tc[c];
         orc_rate_constants(m, Tc[c], k, k + m->nR);
-        F.m = m; F.T = Tc[c]; F.p = pc[c]; F.k = k; F.k0 = k + m->nR; F.work = work; F.nfe = 0;
+        F.m = m; F.T = Tc[c]; F.p = pc[c]; F.k = k; F.k0 = k + m->nR; F.work = work;
+        F.energy = energy; F.nfe = 0;
         if (method == 0)
             st = rkck_cell(&F, n, y, dt, rtol, atol, max_steps, &S);
         else
             st = rkc_cell(&F, n, y, dt, rtol, atol, max_steps, &S, method);
-        for (i = 0; i < n; i++) Y[(int64_t)i * ldY + c] = y[i];
+        for (i = 0; i < m->nS; i++) Y[(int64_t)i * ldY + c] = y[i];
+        if (energy) Tc[c] = y[m->nS];
         if (status) status[c] = (uint8_t)st;
         if (stats) {
             stats[4 * c + 0] = (int32_t)F.nfe;
@@ -711,20 +792,24 @@ int orc_integrate(const void *mp, int64_t cells, const double *Tc, const double 
 }
 
 /* One cell with a per-attempt trace of at most cap entries. Returns the cell
- * status; *len receives the number of attempts (may exceed cap). */
+ * status; *len receives the number of attempts (may exceed cap). With
+ * energy != 0, y holds nS + 1 components, T last (T is ignored). */
 int orc_trace_cell(const void *mp, double T, double p, double *y, double dt, double rtol,
                    double atol, int method, int max_steps, int cap, double *tr_h,
-                   double *tr_err, int32_t *tr_s, int32_t *tr_acc, int32_t *len)
+                   double *tr_err, int32_t *tr_s, int32_t *tr_acc, int32_t *len, int energy)
 {
     const orc_mech *m = (const orc_mech *)mp;
-    int n = m->nS, st;
+    int n = m->nS + (energy ? 1 : 0), st;
     double *k = (double *)xmalloc(sizeof(double) * 2 * m->nR);
-    double *work = (double *)xmalloc(sizeof(double) * (2 * n + m->nR));
+    double *work = (double *)xmalloc(sizeof(double) * (2 * m->nS + 2 * m->nR));
     orc_stats S = {0, 0, 0, 0, cap, 0, tr_h, tr_err, (int *)tr_s, (int *)tr_acc};
     orc_f F;
+    if (energy && !m->cp) { free(k); free(work); return -1; }
     if (max_steps <= 0) max_steps = 100000;
+    if (energy) T = y[m->nS];
     orc_rate_constants(m, T, k, k + m->nR);
-    F.m = m; F.T = T; F.p = p; F.k = k; F.k0 = k + m->nR; F.work = work; F.nfe = 0;
+    F.m = m; F.T = T; F.p = p; F.k = k; F.k0 = k + m->nR; F.work = work;
+    F.energy = energy; F.nfe = 0;
     st = method == 0 ? rkck_cell(&F, n, y, dt, rtol, atol, max_steps, &S)
                      : rkc_cell(&F, n, y, dt, rtol, atol, max_steps, &S, method);
     *len = S.len;

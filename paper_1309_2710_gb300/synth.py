@@ -70,6 +70,8 @@ class Mechanism:
     oxidiser: int
     diluent: int  # -1 when the element set has no N
     seed: int
+    cp: Optional[np.ndarray] = None  # [n_species] J/(mol K), for the energy equation
+    Hf: Optional[np.ndarray] = None  # [n_species] J/mol at 298.15 K
 
     @property
     def n_species(self) -> int:
@@ -241,6 +243,38 @@ def make_mechanism(n_species: int, n_reactions: int, elements: Sequence[str],
                      rtype=rtype, eff=eff, lnA0=lnA0, beta0=beta0, Ea0=Ea0,
                      fuel=1, oxidiser=0,
                      diluent=len(species) - 1 if has_n else -1, seed=seed)
+
+
+R_GAS = 8.314462618  # J/(mol K)
+
+
+def make_thermo(mech: Mechanism, seed: int):
+    """Synthetic species thermochemistry for the energy equation: one constant
+    molar heat capacity and one formation enthalpy at 298.15 K per species
+    (the species enthalpy is then H_i(T) = Hf_i + cp_i (T - 298.15)).
+
+    cp_i = R (2.5 + (atoms_i - 1)) (1 + 0.1 U(-1, 1)): 2.5 R for an atom,
+    3.5 R for a diatomic, one R more per further atom. Hf_i = 150 kJ/mol
+    U(-1, 1) minus 120 kJ/mol per O atom that can bind to H or C (so products
+    rich in O-H and O-C bonds release heat, as in combustion); O2, N2 and H2
+    are reference states with Hf = 0."""
+    rng = np.random.default_rng(seed)
+    comp = np.asarray(mech.comp)
+    nS = comp.shape[0]
+    atoms = comp.sum(axis=1)
+    cp = R_GAS * (2.5 + (atoms - 1.0)) * (1.0 + 0.1 * rng.uniform(-1.0, 1.0, nS))
+    col = {e: i for i, e in enumerate(mech.elements)}
+    nO = comp[:, col["O"]] if "O" in col else np.zeros(nS)
+    nH = comp[:, col["H"]] if "H" in col else np.zeros(nS)
+    nC = comp[:, col["C"]] if "C" in col else np.zeros(nS)
+    bound_O = np.minimum(nO, nH // 2 + 2 * nC)
+    Hf = 1e3 * (150.0 * rng.uniform(-1.0, 1.0, nS) - 120.0 * bound_O)
+    for i in range(nS):
+        v = {e: int(comp[i, col[e]]) for e in mech.elements}
+        if sum(v.values()) == 2 and max(v.values()) == 2 and (v.get("O") == 2 or v.get("N") == 2
+                                                            or v.get("H") == 2):
+            Hf[i] = 0.0  # O2, N2, H2
+    return cp, Hf
 
 
 def make_states(mech: Mechanism, cells: int, T_range=(1000.0, 1500.0),

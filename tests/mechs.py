@@ -4,9 +4,11 @@ import types
 import numpy as np
 
 
-def mech(W, reactions, eff_rows=None):
+def mech(W, reactions, eff_rows=None, cp=None, Hf=None):
     """reactions: list of dicts with reac, prod (species index lists of length
-    <= 2), A, beta, Ea, type (0/1/2), and for falloff A0, beta0, Ea0."""
+    <= 2), A, beta, Ea, type (0/1/2), and for falloff A0, beta0, Ea0. cp, Hf:
+    optional species thermochemistry (J/(mol K), J/mol) for the energy
+    equation."""
     nR = len(reactions)
     reac = np.full((nR, 2), -1, np.int32)
     prod = np.full((nR, 2), -1, np.int32)
@@ -24,7 +26,9 @@ def mech(W, reactions, eff_rows=None):
     eff = np.zeros((nM, len(W))) if eff_rows is None else np.asarray(eff_rows, float)
     return types.SimpleNamespace(W=np.asarray(W, float), lnA=lnA, beta=beta, Ea=Ea,
                                  reac=reac, prod=prod, rtype=rtype, eff=eff,
-                                 lnA0=lnA0, beta0=beta0, Ea0=Ea0)
+                                 lnA0=lnA0, beta0=beta0, Ea0=Ea0,
+                                 cp=None if cp is None else np.asarray(cp, float),
+                                 Hf=None if Hf is None else np.asarray(Hf, float))
 
 
 def a_to_b(k, W=28.0):

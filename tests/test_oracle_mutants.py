@@ -57,6 +57,19 @@ MUTANTS = [
     ("power direction not renormalised", "for (i = 0; i < n; i++) v[i] = fz[i] * (dyn / wnorm);",
      "for (i = 0; i < n; i++) v[i] = fz[i];",
      [pins.test_power_method_on_linear_chain]),
+    ("energy sign", "dydt[nS] = -hw / (rho * cpm);", "dydt[nS] = hw / (rho * cpm);",
+     [pins.test_energy_f_conserves_mixture_enthalpy,
+      lambda: pins.test_energy_adiabatic_temperature_rise_closed_form(oracle.RKCK)]),
+    ("molar instead of mass heat capacity", "cpm += y[i] * m->cp[i] / m->W[i];",
+     "cpm += y[i] * m->cp[i];",
+     [pins.test_energy_f_conserves_mixture_enthalpy,
+      lambda: pins.test_energy_adiabatic_temperature_rise_closed_form(oracle.RKCK)]),
+    ("sensible enthalpy dropped", "hw += (m->Hf[i] + m->cp[i] * (T - ORC_TREF)) * omega[i];",
+     "hw += m->Hf[i] * omega[i];",
+     [pins.test_energy_f_conserves_mixture_enthalpy]),
+    ("rates at a fixed temperature", "rho = production(m, T, p, k, k0, y, omega, C);",
+     "rho = production(m, 1000.0, p, k, k0, y, omega, C);",
+     [pins.test_energy_species_part_is_the_isothermal_f_at_the_state_temperature]),
 ]
 
 

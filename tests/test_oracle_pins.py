@@ -609,3 +609,104 @@ def test_power_method_integration_accuracy(name):
     scale = np.maximum(np.abs(Yg), w["atol"] / w["rtol"])
     assert (np.abs(Yp - Yg) / scale).max() < 10 * w["rtol"]
     assert stp[:, 0].sum() < stg[:, 0].sum()
+
+
+# ----------------------------------------------------- energy equation ---
+def _thermo_mech(name, seed=4000):
+    import dataclasses
+    m = synth.workload_mechanism(name)
+    cp, Hf = synth.make_thermo(m, seed)
+    return dataclasses.replace(m, cp=cp, Hf=Hf)
+
+
+def test_energy_f_conserves_mixture_enthalpy():
+    """Adiabatic, constant pressure, closed: the mixture enthalpy
+    h = sum_i Y_i H_i(T) / W_i is constant, so along f
+    sum_i (dY_i/dt) H_i / W_i + cp (dT/dt) = 0 with cp = sum_i Y_i cp_i / W_i,
+    H_i(T) = Hf_i + cp_i (T - 298.15) (the species model of the synthetic
+    thermochemistry). Holds to rounding at random states."""
+    m = _thermo_mech("h2co_13sp_rkc")
+    om = oracle.Mech(m)
+    T, p, Y = synth.workload_states("h2co_13sp_rkc", m, cells=16, seed_offset=77)
+    for c in range(16):
+        y = np.append(Y[:, c], T[c])
+        f = oracle.rates_energy(om, p[c], y)
+        H = m.Hf + m.cp * (T[c] - 298.15)
+        terms = f[:-1] * H / m.W
+        cpm = np.sum(Y[:, c] * m.cp / m.W)
+        balance = terms.sum() + cpm * f[-1]
+        assert abs(balance) <= 1e-11 * (np.abs(terms).sum() + abs(cpm * f[-1]))
+        assert f[-1] != 0.0
+
+
+def test_energy_species_part_is_the_isothermal_f_at_the_state_temperature():
+    """The species rows of the coupled f are Eq. (E:mass) with k_j, rho and
+    C_k at the state's own temperature (not the cell's initial one)."""
+    m = _thermo_mech("ch4_53sp_rkc_mixed")
+    om = oracle.Mech(m)
+    T, p, Y = synth.workload_states("ch4_53sp_rkc_mixed", m, cells=6, seed_offset=78)
+    for c in range(6):
+        for Ts in (T[c], T[c] + 137.0):
+            f = oracle.rates_energy(om, p[c], np.append(Y[:, c], Ts))
+            np.testing.assert_array_equal(f[:-1], oracle.rates(om, Ts, p[c], Y[:, c]))
+
+
+def _a_to_b_thermo(k, dH, cp=30.0, W=28.0):
+    """A -> B with T-independent k (beta = 0, E = 0), equal W and cp, and an
+    inert third species; B lies dH below A."""
+    return mechs.mech([W, W, W], [dict(reac=[0], prod=[1], A=k)],
+                      cp=[cp, cp, cp], Hf=[0.0, -dH, 0.0])
+
+
+@pytest.mark.parametrize("method", [oracle.RKCK, oracle.RKC, oracle.RKC_POWER])
+def test_energy_adiabatic_temperature_rise_closed_form(method):
+    """With equal W and cp, enthalpy conservation gives
+    T(t) = T0 + dH (Y_A0 - Y_A(t)) / cp and Y_A(t) = Y_A0 exp(-k t): the
+    integrated temperature follows the released heat."""
+    k, dH, cp = 1e6, 1e5, 30.0
+    om = oracle.Mech(_a_to_b_thermo(k, dH, cp))
+    T0, dt = 1000.0, 1e-6
+    Y = np.array([[0.1], [0.0], [0.9]])
+    Yn, st, sta, _, Tn = oracle.integrate(om, np.array([T0]), np.array([101325.0]), Y, dt,
+                                          1e-10, 1e-14, method, energy=True)
+    assert st[0] == 0
+    ya = 0.1 * math.exp(-k * dt)
+    assert Yn[0, 0] == pytest.approx(ya, rel=1e-7, abs=0)
+    rise = dH * (0.1 - ya) / cp  # about 211 K
+    assert Tn[0] - T0 == pytest.approx(rise, rel=1e-7, abs=0)
+
+
+def test_energy_integration_against_tight_scipy_reference():
+    """Thermal feedback on: RKC with the power-method sigma on the coupled
+    (nS + 1)-vector against scipy's DOP853 on the oracle's own f."""
+    from scipy.integrate import solve_ivp
+    m = _thermo_mech("h2co_13sp_rkc")
+    om = oracle.Mech(m)
+    T, p, Y = synth.workload_states("h2co_13sp_rkc", m, cells=3, seed_offset=79)
+    Yn, st, sta, _, Tn = oracle.integrate(om, T, p, Y, 1e-6, 1e-9, 1e-13, oracle.RKC_POWER,
+                                          energy=True)
+    assert (st == 0).all()
+    for c in range(3):
+        y0 = np.append(Y[:, c], T[c])
+        ref = solve_ivp(lambda t, y: oracle.rates_energy(om, p[c], y), (0.0, 1e-6), y0,
+                        method="DOP853", rtol=1e-12, atol=1e-16).y[:, -1]
+        assert abs(Tn[c] - ref[-1]) <= 1e-6 * ref[-1]
+        assert abs(Tn[c] - T[c]) > 1e-3  # the temperature moved
+        np.testing.assert_allclose(Yn[:, c], ref[:-1], rtol=1e-5, atol=1e-12)
+
+
+def test_energy_conserves_enthalpy_and_mass_over_a_flow_step():
+    """Integrated over the flow step: sum Y = 1 and the mixture enthalpy stay
+    at their initial values to the integration tolerance."""
+    m = _thermo_mech("h2co_13sp_rkc")
+    om = oracle.Mech(m)
+    T, p, Y = synth.workload_states("h2co_13sp_rkc", m, cells=8, seed_offset=80)
+    Yn, st, sta, _, Tn = oracle.integrate(om, T, p, Y, 1e-6, 1e-8, 1e-14, oracle.RKC_POWER,
+                                          energy=True)
+
+    def h(Y, T):
+        return np.sum(Y * (m.Hf[:, None] + m.cp[:, None] * (T[None, :] - 298.15)) / m.W[:, None], axis=0)
+
+    cpm = np.sum(Y * m.cp[:, None] / m.W[:, None], axis=0)
+    assert np.abs(Yn.sum(0) - 1).max() < 1e-12
+    assert np.all(np.abs(h(Yn, Tn) - h(Y, T)) < 1e-6 * cpm * T)
