@@ -89,7 +89,17 @@ def feval_ops(m) -> int:
     return o
 
 
-def algorithmic_work(m, method, precision, sigma, stats):
+def feval_ops_energy(m) -> int:
+    """feval_ops plus the work the energy equation adds to one evaluation: the
+    rate constants from T (2 per reaction for the exponent, one exp; falloff
+    reactions a second exponent and exp), log T and the reciprocals (3), the
+    enthalpy sum and mixture heat capacity (3 per species) and dT/dt (3). An
+    exp or log counts as one operation, so this is a lower bound."""
+    n_fo = int(np.count_nonzero(m.rtype == synth.FALLOFF))
+    return feval_ops(m) + 3 * m.n_reactions + 3 * n_fo + 3 + 3 * m.n_species + 3
+
+
+def algorithmic_work(m, method, precision, sigma, stats, energy=False):
     """Algorithmic operations of one call, from the per-cell counts (f
     evaluations, accepted and rejected steps, spectral-radius estimates), as
     (FP64 lane-ops, FP32 lane-ops, exact). An FMA, add, multiply or divide is
@@ -105,10 +115,13 @@ def algorithmic_work(m, method, precision, sigma, stats):
     method's number of products per estimate is not recorded, so it is bounded
     from the side that keeps the count a lower bound: 20 products in FP64
     (fewer stages), 2 in mixed precision (fewer FP64 evaluations)."""
-    nS = m.n_species
-    fo = feval_ops(m)
+    nS = m.n_species + (1 if energy else 0)  # state length
+    fo = feval_ops_energy(m) if energy else feval_ops(m)
     mixed = precision == synth.MIXED
-    f64 = 2 * nS + 1 if mixed else fo  # FP64 part of one rate-type f evaluation
+    # FP64 part of one rate-type f evaluation: in the mixed path the final
+    # scaling (and with the energy equation the exponents and the enthalpy
+    # sums) stay FP64
+    f64 = (2 * nS + 1 + (fo - feval_ops(m) if energy else 0)) if mixed else fo
     f32 = fo - f64
     nfe = stats[:, 0].astype(np.float64)
     att = (stats[:, 1] + stats[:, 2]).astype(np.float64)
@@ -211,12 +224,14 @@ def oracle_rate(name, cells_target_s=10.0, max_cells=None, seed_offset=0):
     probe = min(2048, total)
     t0 = time.perf_counter()
     meth = oracle_method(w)
-    _, _, _, nt = oracle.integrate(om, T[:probe], p[:probe], Y[:, :probe], w["dt"], w["rtol"],
-                                   w["atol"], meth)
+    en = bool(w.get("energy"))
+    nt = oracle.integrate(om, T[:probe], p[:probe], Y[:, :probe], w["dt"], w["rtol"],
+                          w["atol"], meth, energy=en)[3]
     per_cell = (time.perf_counter() - t0) / probe
     n = int(min(total if max_cells is None else max_cells, max(probe, cells_target_s / per_cell)))
     t0 = time.perf_counter()
-    _, st, _, nt = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], meth)
+    nt = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], meth,
+                          energy=en)[3]
     el = time.perf_counter() - t0
     return n / el, nt, "first %d of the %d cells of %s (same seeds), %.1f s wall" % (n, total, name, el)
 
@@ -235,17 +250,20 @@ def run_reference(args):
     probe = 1024
     t0 = time.perf_counter()
     meth = oracle_method(w)
-    oracle.integrate(om, T[:probe], p[:probe], Y[:, :probe], w["dt"], w["rtol"], w["atol"], meth)
+    en = bool(w.get("energy"))
+    oracle.integrate(om, T[:probe], p[:probe], Y[:, :probe], w["dt"], w["rtol"], w["atol"], meth,
+                     energy=en)
     per_cell = (time.perf_counter() - t0) / probe
     budget = 120.0 / max(1, args.steps + args.warmup)
     n = int(min(w["cells"], max(probe, budget / per_cell)))
     for _ in range(args.warmup):
-        oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], meth)
+        oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], meth, energy=en)
     times = []
     nt = 1
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        _, _, _, nt = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], meth)
+        nt = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], meth,
+                              energy=en)[3]
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = n * len(times) / tot
@@ -266,11 +284,13 @@ def workload_config(name, cells, sigma=None, order="random"):
     w = synth.WORKLOADS[name]
     sigma = w["sigma"] if sigma is None else sigma
     rkc = "RKC (%s sigma)" % ("power-method" if sigma == synth.POWER else "Gershgorin FD")
-    return {"workload": "%s: %d species / %d reactions, %s %s, %d cells, dt %g s, rtol %g, atol %g"
+    return {"workload": "%s: %d species / %d reactions, %s %s%s, %d cells, dt %g s, rtol %g, atol %g"
                         % (name, w["n_species"], w["n_reactions"],
                            rkc if w["method"] == synth.RKC else "RKCK",
                            "FP64" if w["precision"] == synth.FP64 else "mixed FP32/FP64",
+                           ", constant-pressure energy equation" if w.get("energy") else "",
                            cells, w["dt"], w["rtol"], w["atol"]),
+            "energy_equation": bool(w.get("energy")),
             "cells": cells, "method": "RKC" if w["method"] == synth.RKC else "RKCK",
             "precision": "fp64" if w["precision"] == synth.FP64 else "mixed",
             "l2": "flushed between steps (256 MiB write)", "cell_order": "random (as drawn)" if order == "random" else
@@ -304,7 +324,9 @@ def run_kin(args):
     method, prec = w["method"], w["precision"]
     sigma = w["sigma"] if args.sigma == "default" else (synth.POWER if args.sigma == "power"
                                                          else synth.GERSHGORIN)
-    Td = torch.as_tensor(T, device=dev)
+    energy = int(bool(w.get("energy")))
+    T0d = torch.as_tensor(T, device=dev)
+    Td = T0d.clone()  # integrated (and reset every step) with the energy equation
     pd = torch.as_tensor(p, device=dev)
     Y0d = torch.as_tensor(Y0, device=dev).contiguous()
     Yd = torch.empty_like(Y0d)
@@ -320,21 +342,24 @@ def run_kin(args):
         # launch shape from the autotuner (cached per GPU, mechanism shape and
         # cell count), timed on this workload outside the timed region
         from paper_1309_2710_gb300 import autotune
-        best = autotune.tune(km, m, Td, pd, Y0d, w["dt"], w["rtol"], w["atol"], method, prec,
-                             sigma=sigma)
+        best = autotune.tune(km, m, T0d, pd, Y0d, w["dt"], w["rtol"], w["atol"], method, prec,
+                             sigma=sigma, energy=energy)
         shape = {k: best[k] for k in shape}
     ws = km.workspace(method, prec, cells, shape["block_threads"], shape["blocks_per_sm"], dev,
-                      shape["staging"], shape["occupancy"], sigma, shape["layout"])
+                      shape["staging"], shape["occupancy"], sigma, shape["layout"], energy)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
         flush.zero_()
         Yd.copy_(Y0d)
+        if energy:
+            Td.copy_(T0d)
         if ev:
             ev[0].record(stream)
         kin.integrate(km, Td, pd, Yd, w["dt"], w["rtol"], w["atol"], method, prec,
-                      status=st, stats=sta, workspace=ws, stream=stream, sigma=sigma, **shape)
+                      status=st, stats=sta, workspace=ws, stream=stream, sigma=sigma,
+                      energy=energy, **shape)
         if ev:
             ev[1].record(stream)
 
@@ -366,7 +391,7 @@ def run_kin(args):
 
     stats = sta.cpu().numpy()
     status = st.cpu().numpy()
-    ops64, ops32, exact = algorithmic_work(m, method, prec, sigma, stats)
+    ops64, ops32, exact = algorithmic_work(m, method, prec, sigma, stats, energy)
     kavg = sum(kern_ms) / len(kern_ms)
     peak64 = FP64_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
     peak32 = FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
@@ -382,18 +407,23 @@ def run_kin(args):
     # end to end: host (pinned) buffers through the public API, copies timed
     e2e = None
     if not args.no_e2e:
-        Th = torch.as_tensor(T).pin_memory()
+        T0h = torch.as_tensor(T)
+        Th = T0h.clone().pin_memory()
         ph = torch.as_tensor(p).pin_memory()
         Y0h = torch.as_tensor(Y0).contiguous()
         Yh = torch.empty_like(Y0h).pin_memory()
         sth = torch.empty(cells, dtype=torch.uint8).pin_memory()
-        hbuf = kin.host_buffer(km, cells, method, prec, device=dev, sigma=sigma, **shape)
+        hbuf = kin.host_buffer(km, cells, method, prec, device=dev, sigma=sigma, energy=energy,
+                               **shape)
 
         def e2e_step():
             # the flow solver hands over its state in host memory every step
             Yh.copy_(Y0h)
+            if energy:
+                Th.copy_(T0h)
             kin.integrate_host(km, Th, ph, Yh, w["dt"], w["rtol"], w["atol"], method, prec,
-                               status=sth, buffer=hbuf, stream=stream, sigma=sigma, **shape)
+                               status=sth, buffer=hbuf, stream=stream, sigma=sigma,
+                               energy=energy, **shape)
             stream.synchronize()
 
         e2e_step()
@@ -409,7 +439,7 @@ def run_kin(args):
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e = {"value": world * cells * ne / float(te.item()), "unit": UNIT,
                "h2d_bytes_per_step": int(Th.numel() * 8 + ph.numel() * 8 + Yh.numel() * 8),
-               "d2h_bytes_per_step": int(Yh.numel() * 8 + sth.numel()),
+               "d2h_bytes_per_step": int(Yh.numel() * 8 + sth.numel() + (Th.numel() * 8 if energy else 0)),
                "api": "kin_integrate_host (pinned host buffers)"}
 
     cpu = None

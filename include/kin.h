@@ -12,8 +12,11 @@
  *             nonlinear power method (kin_opts.sigma).
  * f is the species source term of Section 2.1, Eqs. (E:mass), (E:spec-rate),
  * (E:rxn-rate) and (E:rxn-const), with third-body and Lindemann falloff
- * reactions. Temperature and pressure are held fixed over the flow step
- * (no energy equation), so N = n_species.
+ * reactions. By default temperature and pressure are held fixed over the flow
+ * step, so N = n_species. With kin_opts.energy the constant-pressure energy
+ * equation of Section 2.1, Eq. (E:energy), is integrated too (N = n_species +
+ * 1): T changes and is written back, and k_j, density and concentrations follow
+ * it at every evaluation of f.
  *
  * Conventions for every entry point:
  *  - Device pointers are CUDA device memory of the current device; host
@@ -115,6 +118,11 @@ typedef struct {
     const double *lnA0;  /* [n_reactions] low-pressure limit of falloff reactions */
     const double *beta0; /* (read only where type == KIN_RXN_FALLOFF; the three */
     const double *Ea0;   /*  may be NULL when there is none) */
+    const double *cp;    /* [n_species] molar heat capacity at constant pressure,
+                            J/(mol K), > 0; and */
+    const double *Hf;    /* [n_species] formation enthalpy at 298.15 K, J/mol: the
+                            species enthalpy is H_i(T) = Hf_i + cp_i (T - 298.15).
+                            Both NULL when the energy equation is not needed */
 } kin_mech_desc;
 
 #define KIN_MAX_SPECIES 256
@@ -145,6 +153,12 @@ typedef struct {
                               same method, decisions and statistics up to the rounding
                               order of sums (results agree within the integration
                               tolerance, not bit for bit) */
+    int32_t energy;        /* 0: T fixed over the flow step. 1: integrate the energy
+                              equation, Eq. (E:energy): dT/dt = -(1/(rho cp)) sum_i
+                              h_i omega_i W_i with cp = sum_i Y_i cp_i / W_i; T is part
+                              of the state (error norm, spectral radius) and is
+                              written back to T. Needs the mechanism's cp and Hf
+                              (else KIN_EUNSUPPORTED) */
     void *stream;          /* cudaStream_t */
 } kin_opts;
 
@@ -152,7 +166,7 @@ typedef struct {
  * are device pointers with the layouts described above. */
 typedef struct {
     int64_t cells;     /* >= 0 */
-    const double *T;   /* [cells] */
+    double *T;         /* [cells]; updated in place with opts->energy, else read only */
     const double *p;   /* [cells] */
     double *Y;         /* [n_species][ldY], updated in place */
     int64_t ldY;       /* >= cells */
@@ -192,7 +206,7 @@ int64_t kin_workspace_bytes(const kin_mech *m, const kin_opts *opts, int64_t cel
  * kin_workspace_bytes(m, opts, cells) bytes, 256-byte aligned; it must not be
  * used by another call that may run concurrently. Errors: KIN_EINVAL, KIN_ENOMEM
  * (workspace too small), KIN_EUNSUPPORTED, KIN_ECUDA. */
-int kin_integrate(const kin_mech *m, int64_t cells, const double *T, const double *p,
+int kin_integrate(const kin_mech *m, int64_t cells, double *T, const double *p,
                   double *Y, int64_t ldY, double dt, double rtol, double atol,
                   const kin_opts *opts, uint8_t *status, int32_t *stats,
                   void *workspace, int64_t workspace_bytes);
@@ -216,10 +230,10 @@ int64_t kin_host_buffer_bytes(const kin_mech *m, const kin_opts *opts, int64_t c
  * layouts above (status and stats may be NULL). On opts->stream the call
  * copies T, p and Y into `device_buffer` (device memory of at least
  * kin_host_buffer_bytes bytes, 256-byte aligned), integrates there, and copies
- * Y, status and stats back. Page-locked host memory makes every copy
+ * Y (and T with opts->energy), status and stats back. Page-locked host memory makes every copy
  * asynchronous; with pageable memory the copies may block. Host results are
  * valid after the stream is synchronised. Errors as kin_integrate. */
-int kin_integrate_host(const kin_mech *m, int64_t cells, const double *T, const double *p,
+int kin_integrate_host(const kin_mech *m, int64_t cells, double *T, const double *p,
                        double *Y, int64_t ldY, double dt, double rtol, double atol,
                        const kin_opts *opts, uint8_t *status, int32_t *stats,
                        void *device_buffer, int64_t device_bytes);
@@ -247,7 +261,7 @@ int kin_integrate_host(const kin_mech *m, int64_t cells, const double *T, const 
  *    with KIN_ENOMEM and launches nothing. Fewer persistent blocks per SM
  *    than requested are used when that makes the call fit.
  * The paper has no counterpart of this entry point. */
-int kin_integrate_noalloc(const kin_mech *m, int64_t cells, const double *T, const double *p,
+int kin_integrate_noalloc(const kin_mech *m, int64_t cells, double *T, const double *p,
                           double *Y, int64_t ldY, double dt, double rtol, double atol,
                           const kin_opts *opts, uint8_t *status, int32_t *stats);
 

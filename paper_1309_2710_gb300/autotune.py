@@ -63,25 +63,27 @@ def candidates(full: bool = False, method: int = kin.RKC, n_reactions: int = 0):
         yield from warp_candidates(False)
 
 
-def time_config(mech, T, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2,
-                sigma=kin.SIGMA_GERSHGORIN) -> Optional[float]:
+def time_config(mech, T0, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2,
+                sigma=kin.SIGMA_GERSHGORIN, energy=0) -> Optional[float]:
     """Mean kernel milliseconds of kin_integrate with `cfg`, or None if the
     shape is not supported."""
-    cells = int(T.numel())
+    cells = int(T0.numel())
     try:
         ws = mech.workspace(method, precision, cells, cfg["block_threads"], cfg["blocks_per_sm"],
-                            T.device, cfg["staging"], cfg["occupancy"], sigma, cfg["layout"])
+                            T0.device, cfg["staging"], cfg["occupancy"], sigma, cfg["layout"], energy)
     except kin.KinError:
         return None
     Y = torch.empty_like(Y0)
+    T = torch.empty_like(T0)  # the energy equation writes T back
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     best = None
     for r in range(reps + 1):
         Y.copy_(Y0)
+        T.copy_(T0)
         ev[0].record()
         try:
             kin.integrate(mech, T, p, Y, dt, rtol, atol, method, precision, workspace=ws,
-                          sigma=sigma, **cfg)
+                          sigma=sigma, energy=energy, **cfg)
         except kin.KinError:
             return None
         ev[1].record()
@@ -94,11 +96,11 @@ def time_config(mech, T, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2,
 
 def tune(mech: kin.Mechanism, desc, T, p, Y, dt, rtol, atol, method, precision,
          use_cache: bool = True, verbose: bool = False, full: bool = False, reps: int = 1,
-         sigma: int = kin.SIGMA_GERSHGORIN) -> Dict:
+         sigma: int = kin.SIGMA_GERSHGORIN, energy: int = 0) -> Dict:
     """Best launch shape for this mechanism on the current GPU, timed on the
     given (device) cells: pass the cells of a representative call, since the
     persistent grid's tail depends on the cell count."""
-    key = _key(mech, method, precision, desc) + "|%d|%d|v2" % (int(T.numel()), sigma)
+    key = _key(mech, method, precision, desc) + "|%d|%d|%d|v2" % (int(T.numel()), sigma, energy)
     cache = {}
     if use_cache and os.path.exists(CACHE):
         with open(CACHE) as f:
@@ -107,7 +109,7 @@ def tune(mech: kin.Mechanism, desc, T, p, Y, dt, rtol, atol, method, precision,
             return cache[key]
     results = []
     for cfg in candidates(full, method, mech.n_reactions):
-        ms = time_config(mech, T, p, Y, dt, rtol, atol, method, precision, cfg, reps, sigma)
+        ms = time_config(mech, T, p, Y, dt, rtol, atol, method, precision, cfg, reps, sigma, energy)
         if verbose:
             print("autotune", cfg, ms)
         if ms is not None:

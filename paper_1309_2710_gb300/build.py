@@ -12,7 +12,9 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkin.so")
 SOURCES = ["kernels.cu", "abi.cu", "no_alloc.cu", "inst_rkc_f64.cu", "inst_rkc_f32.cu",
            "inst_rkck_f64.cu", "inst_rkck_f32.cu", "inst_warp_f64.cu", "inst_warp_f32.cu",
-           "inst_warp_f64_hi.cu", "inst_warp_f32_hi.cu"]
+           "inst_warp_f64_hi.cu", "inst_warp_f32_hi.cu", "inst_energy_f64.cu", "inst_energy_f32.cu",
+           "inst_warp_energy_f64.cu", "inst_warp_energy_f32.cu", "inst_warp_energy_f64_hi.cu",
+           "inst_warp_energy_f32_hi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

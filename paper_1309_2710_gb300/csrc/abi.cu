@@ -19,6 +19,7 @@ struct kin_mech {
     void* buf;
     int device;
     int nS, nR, nM;
+    bool thermo;  // cp and Hf given (energy equation available)
 };
 
 namespace {
@@ -74,6 +75,8 @@ int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
     int maxsm = 0;
     e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    if (o->energy && !m->thermo)
+        return fail(KIN_EUNSUPPORTED, "the energy equation needs the mechanism's cp and Hf");
     const int layout = resolve_layout(m, o);
     int threads = o->block_threads > 0 ? o->block_threads : 128;
     int occ = 0, cap = 0;
@@ -83,18 +86,22 @@ int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
         const size_t sm = warp_smem(m->dev, o->precision, threads);
         if (sm > (size_t)maxsm)
             return fail(KIN_EUNSUPPORTED, "warp layout needs %zu bytes of shared memory per block (max %d)", sm, maxsm);
-        if (o->precision == KIN_MIXED)
-            e = o->occupancy ? occ_warp_f32_o1(m->dev, threads, &occ) : occ_warp_f32_o0(m->dev, threads, &occ);
-        else
-            e = o->occupancy ? occ_warp_f64_o1(m->dev, threads, &occ) : occ_warp_f64_o0(m->dev, threads, &occ);
+        const int nV = m->nS + o->energy;
+        using OccFn = cudaError_t (*)(const MechDev&, int, int, int*);
+        // [energy][precision][occupancy]
+        static const OccFn fns[2][2][2] = {
+            {{occ_warp_f64_o0, occ_warp_f64_o1}, {occ_warp_f32_o0, occ_warp_f32_o1}},
+            {{occ_warp_f64_en_o0, occ_warp_f64_en_o1}, {occ_warp_f32_en_o0, occ_warp_f32_en_o1}}};
+        e = fns[o->energy][o->precision == KIN_MIXED][o->occupancy ? 1 : 0](m->dev, nV, threads, &occ);
         cap = occ;  // as many as fit
     } else {
         if (threads % 32 != 0 || threads > 128) return fail(KIN_EINVAL, "block_threads must be a multiple of 32 and <= 128");
-        const int stg = o->staging;
+        const int stg = o->energy ? KIN_STAGE_GLOBAL : o->staging;  // energy: nothing to stage
         if (stg > 0 && smem_bytes(m->dev, o->precision, threads, stg) > (size_t)maxsm)
             return fail(KIN_EUNSUPPORTED, "shared-memory staging needs %zu bytes per block (max %d)",
                         smem_bytes(m->dev, o->precision, threads, stg), maxsm);
-        e = integrate_occupancy(m->dev, o->method, o->precision, stg, o->occupancy, threads, &occ);
+        e = integrate_occupancy(m->dev, o->method, o->precision, stg, o->occupancy, o->energy, threads,
+                                &occ);
         cap = (o->occupancy ? 768 : 512) / threads;
     }
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -113,7 +120,8 @@ int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
 int64_t ws_bytes(const kin_mech* m, const kin_opts* o, const Grid& g, int64_t cells)
 {
     const int sig = o->method == KIN_RKC ? o->sigma : KIN_SIGMA_GERSHGORIN;
-    return ws_layout(m->dev, o->precision, sig, g.layout == KIN_LAYOUT_WARP ? 0 : g.nslots, cells).total;
+    return ws_layout(m->dev, o->precision, sig, o->energy, g.layout == KIN_LAYOUT_WARP ? 0 : g.nslots,
+                     cells).total;
 }
 
 int check_opts(const kin_opts* o)
@@ -131,6 +139,7 @@ int check_opts(const kin_opts* o)
         return fail(KIN_EINVAL, "unknown sigma estimator %d", o->sigma);
     if (o->layout != KIN_LAYOUT_AUTO && o->layout != KIN_LAYOUT_LANE && o->layout != KIN_LAYOUT_WARP)
         return fail(KIN_EINVAL, "unknown layout %d", o->layout);
+    if (o->energy != 0 && o->energy != 1) return fail(KIN_EINVAL, "energy must be 0 or 1");
     return KIN_OK;
 }
 
@@ -272,6 +281,17 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     const size_t oPtr = put(ptr.data(), 4 * (nS + 1)), oCrx = put(crx.data(), 4 * nnz);
     const size_t oNu = put(cnu.data(), 8 * nnz), oNu32 = put(nu32.data(), 4 * nnz);
     const size_t oEff = put(d->eff, 8 * (size_t)nM * nS), oEff32 = put(eff32.data(), 4 * (size_t)nM * nS);
+    // thermochemistry for the energy equation: cp, cp/W, Hf
+    const bool thermo = d->cp && d->Hf;
+    if ((d->cp != nullptr) != (d->Hf != nullptr)) return fail(KIN_EINVAL, "give both cp and Hf, or neither");
+    std::vector<double> cpW(thermo ? nS : 0);
+    for (int i = 0; thermo && i < nS; ++i) {
+        if (!finite_pos(d->cp[i])) return fail(KIN_EINVAL, "cp[%d] must be finite and > 0", i);
+        if (!std::isfinite(d->Hf[i])) return fail(KIN_EINVAL, "Hf[%d] must be finite", i);
+        cpW[i] = d->cp[i] / d->W[i];
+    }
+    const size_t oCp = thermo ? put(d->cp, 8 * nS) : 0, oCpW = thermo ? put(cpW.data(), 8 * nS) : 0;
+    const size_t oHf = thermo ? put(d->Hf, 8 * nS) : 0;
     const size_t oTab = put(nullptr, 0);
     const size_t tabBytes = sizeof(double) * RKC_TAB_S * RKC_TAB_S * RKC_TAB_W;
     host.resize(oTab + tabBytes, 0);
@@ -300,7 +320,11 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     M.csr_nu = (const double*)(b + oNu); M.csr_nu32 = (const float*)(b + oNu32);
     M.eff = (const double*)(b + oEff); M.eff32 = (const float*)(b + oEff32);
     M.rkc = (const double*)(b + oTab);
+    M.cp = thermo ? (const double*)(b + oCp) : nullptr;
+    M.cpW = thermo ? (const double*)(b + oCpW) : nullptr;
+    M.Hf = thermo ? (const double*)(b + oHf) : nullptr;
     m->nS = nS; m->nR = nR; m->nM = nM;
+    m->thermo = thermo;
     e = launch_rkc_table((double*)(b + oTab), 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { cudaFree(m->buf); delete m; return cuda_fail(e, "RKC table"); }
@@ -388,7 +412,10 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     P.total = total;
     char* base = (char*)ws;
     const int sig = o->method == KIN_RKC ? o->sigma : KIN_SIGMA_GERSHGORIN;
-    const WsLayout w = ws_layout(m->dev, o->precision, sig, g.layout == KIN_LAYOUT_WARP ? 0 : nslots, total);
+    const WsLayout w = ws_layout(m->dev, o->precision, sig, o->energy,
+                                 g.layout == KIN_LAYOUT_WARP ? 0 : nslots, total);
+    P.energy = o->energy;
+    P.nV = m->nS + o->energy;
     P.sigma_method = sig;
     P.cell_ev = sig == KIN_SIGMA_POWER ? (double*)(base + w.ev) : nullptr;
     P.queue = (unsigned long long*)(base + w.header);
@@ -407,19 +434,22 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     cudaStream_t st = (cudaStream_t)o->stream;
     cudaError_t e = cudaMemsetAsync(base + w.header, 0, 512, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    if (g.layout == KIN_LAYOUT_WARP && o->precision == KIN_MIXED)
-        e = o->occupancy ? launch_warp_f32_o1(P, blocks, g.threads, st)
-                         : launch_warp_f32_o0(P, blocks, g.threads, st);
-    else if (g.layout == KIN_LAYOUT_WARP)
-        e = o->occupancy ? launch_warp_f64_o1(P, blocks, g.threads, st)
-                         : launch_warp_f64_o0(P, blocks, g.threads, st);
+    if (g.layout == KIN_LAYOUT_WARP) {
+        using LaunchFn = cudaError_t (*)(Launch&, int, int, cudaStream_t);
+        // [energy][precision][occupancy]
+        static const LaunchFn fns[2][2][2] = {
+            {{launch_warp_f64_o0, launch_warp_f64_o1}, {launch_warp_f32_o0, launch_warp_f32_o1}},
+            {{launch_warp_f64_en_o0, launch_warp_f64_en_o1}, {launch_warp_f32_en_o0, launch_warp_f32_en_o1}}};
+        e = fns[o->energy][o->precision == KIN_MIXED][o->occupancy ? 1 : 0](P, blocks, g.threads, st);
+    }
     else
-        e = launch_integrate(P, o->staging, o->occupancy, blocks, g.threads, st);
+        e = launch_integrate(P, o->energy ? KIN_STAGE_GLOBAL : o->staging, o->occupancy, blocks,
+                             g.threads, st);
     if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
     return KIN_OK;
 }
 
-int kin_integrate(const kin_mech* m, int64_t cells, const double* T, const double* p, double* Y,
+int kin_integrate(const kin_mech* m, int64_t cells, double* T, const double* p, double* Y,
                   int64_t ldY, double dt, double rtol, double atol, const kin_opts* o,
                   uint8_t* status, int32_t* stats, void* ws, int64_t ws_size)
 {
@@ -438,7 +468,7 @@ int64_t kin_host_buffer_bytes(const kin_mech* m, const kin_opts* o, int64_t cell
     return al256(ws) + 2 * al256(8 * cells) + al256(8 * cells * m->nS) + al256(cells) + al256(16 * cells);
 }
 
-int kin_integrate_host(const kin_mech* m, int64_t cells, const double* T, const double* p, double* Y,
+int kin_integrate_host(const kin_mech* m, int64_t cells, double* T, const double* p, double* Y,
                        int64_t ldY, double dt, double rtol, double atol, const kin_opts* o,
                        uint8_t* status, int32_t* stats, void* buf, int64_t bytes)
 {
@@ -468,6 +498,7 @@ int kin_integrate_host(const kin_mech* m, int64_t cells, const double* T, const 
     int rc = kin_integrate(m, cells, Td, pd, Yd, cells, dt, rtol, atol, o, sd, stats ? xd : nullptr, buf, ws);
     if (rc) return rc;
     e = cudaMemcpy2DAsync(Y, 8 * ldY, Yd, 8 * cells, 8 * cells, m->nS, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && o->energy) e = cudaMemcpyAsync(T, Td, 8 * cells, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, sd, cells, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && stats) e = cudaMemcpyAsync(stats, xd, 16 * cells, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
@@ -487,7 +518,7 @@ int kin_rates(const kin_mech* m, int64_t cells, const double* T, const double* p
     if (ldY > INT32_MAX) return fail(KIN_EINVAL, "ldY >= 2^31");
     if (!is_device_ptr(T) || !is_device_ptr(p) || !is_device_ptr(Y) || !is_device_ptr(dYdt))
         return fail(KIN_EINVAL, "T, p, Y and dYdt must be device memory");
-    kin_opts o{KIN_RKC, precision, 0, 0, 0, KIN_STAGE_GLOBAL, KIN_OCC_DEFAULT, 0, KIN_LAYOUT_LANE, stream};
+    kin_opts o{KIN_RKC, precision, 0, 0, 0, KIN_STAGE_GLOBAL, KIN_OCC_DEFAULT, 0, KIN_LAYOUT_LANE, 0, stream};
     Grid g;
     int rc = grid_for(m, &o, &g);
     if (rc) return rc;

@@ -1,0 +1,18 @@
+// inst_warp_energy_f32_hi.cu -- the warp-per-cell RKC kernels with the
+// energy equation (Eq. (E:energy)), float rate arithmetic and the high-occupancy
+// register budget (own translation unit so the build runs in parallel).
+#include "warp.cuh"
+
+namespace kin {
+
+cudaError_t launch_warp_f32_en_o1(Launch& L, int blocks, int threads, cudaStream_t st)
+{
+    return warp_launch<float, 1, true>(L, blocks, threads, st);
+}
+
+cudaError_t occ_warp_f32_en_o1(const MechDev& M, int nV, int threads, int* bps)
+{
+    return warp_occ<float, 1, true>(M, nV, KIN_MIXED, threads, bps);
+}
+
+}  // namespace kin

@@ -7,12 +7,12 @@ namespace kin {
 
 cudaError_t launch_warp_f32_o1(Launch& L, int blocks, int threads, cudaStream_t st)
 {
-    return warp_launch<float, 1>(L, blocks, threads, st);
+    return warp_launch<float, 1, false>(L, blocks, threads, st);
 }
 
-cudaError_t occ_warp_f32_o1(const MechDev& M, int threads, int* bps)
+cudaError_t occ_warp_f32_o1(const MechDev& M, int nV, int threads, int* bps)
 {
-    return warp_occ<float, 1>(M, KIN_MIXED, threads, bps);
+    return warp_occ<float, 1, false>(M, nV, KIN_MIXED, threads, bps);
 }
 
 }  // namespace kin

@@ -6,12 +6,12 @@ namespace kin {
 
 cudaError_t launch_warp_f64_o0(Launch& L, int blocks, int threads, cudaStream_t st)
 {
-    return warp_launch<double, 0>(L, blocks, threads, st);
+    return warp_launch<double, 0, false>(L, blocks, threads, st);
 }
 
-cudaError_t occ_warp_f64_o0(const MechDev& M, int threads, int* bps)
+cudaError_t occ_warp_f64_o0(const MechDev& M, int nV, int threads, int* bps)
 {
-    return warp_occ<double, 0>(M, KIN_FP64, threads, bps);
+    return warp_occ<double, 0, false>(M, nV, KIN_FP64, threads, bps);
 }
 
 size_t warp_smem(const MechDev& M, int precision, int threads)

@@ -7,12 +7,12 @@ namespace kin {
 
 cudaError_t launch_warp_f64_o1(Launch& L, int blocks, int threads, cudaStream_t st)
 {
-    return warp_launch<double, 1>(L, blocks, threads, st);
+    return warp_launch<double, 1, false>(L, blocks, threads, st);
 }
 
-cudaError_t occ_warp_f64_o1(const MechDev& M, int threads, int* bps)
+cudaError_t occ_warp_f64_o1(const MechDev& M, int nV, int threads, int* bps)
 {
-    return warp_occ<double, 1>(M, KIN_FP64, threads, bps);
+    return warp_occ<double, 1, false>(M, nV, KIN_FP64, threads, bps);
 }
 
 }  // namespace kin

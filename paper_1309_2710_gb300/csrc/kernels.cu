@@ -112,19 +112,21 @@ __global__ void rkc_table_kernel(double* tab)
 // -------------------------------------------------------- host launchers --
 static int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
 
-WsLayout ws_layout(const MechDev& M, int precision, int sigma_method, int64_t nslots,
+WsLayout ws_layout(const MechDev& M, int precision, int sigma_method, int energy, int64_t nslots,
                    int64_t cells)
 {
     const int64_t rb = precision == KIN_MIXED ? 4 : 8;
+    const int64_t nV = M.nS + (energy ? 1 : 0);
     WsLayout w;
     int64_t off = 0;
     w.header = off;  off += 4096;
-    w.vec = off;     off += al256((int64_t)NVEC * M.nS * 8 * nslots);
+    w.vec = off;     off += al256((int64_t)NVEC * nV * 8 * nslots);
     w.lane_r = off;  off += al256((int64_t)(M.nS + 2 * M.nR + M.nFO) * rb * nslots);
     w.lane_sig = off; off += precision == KIN_MIXED ? al256((int64_t)(M.nS + M.nR) * 8 * nslots) : 0;
-    w.cell_k = off;  off += al256((int64_t)(M.nR + M.nFO) * rb * cells);
-    w.f0 = off;      off += al256((int64_t)M.nS * 8 * cells);
-    w.ev = off;      off += sigma_method == KIN_SIGMA_POWER ? al256((int64_t)M.nS * 8 * cells) : 0;
+    // rate constants per cell, unless they follow T (energy equation)
+    w.cell_k = off;  off += energy ? 0 : al256((int64_t)(M.nR + M.nFO) * rb * cells);
+    w.f0 = off;      off += al256(nV * 8 * cells);
+    w.ev = off;      off += sigma_method == KIN_SIGMA_POWER ? al256(nV * 8 * cells) : 0;
     w.sig = off;     off += al256(8 * cells);
     w.h = off;       off += al256(8 * cells);
     w.nfe = off;     off += al256(4 * cells);
@@ -142,6 +144,13 @@ size_t smem_bytes(const MechDev& M, int precision, int threads, int stg)
 
 cudaError_t launch_integrate(Launch& L, int stg, int occ, int blocks, int threads, cudaStream_t st)
 {
+    if (L.energy) {
+        if (L.method == KIN_RKCK)
+            return L.precision == KIN_MIXED ? launch_rkck_f32_en(L, occ, blocks, threads, st)
+                                            : launch_rkck_f64_en(L, occ, blocks, threads, st);
+        return L.precision == KIN_MIXED ? launch_rkc_f32_en(L, occ, blocks, threads, st)
+                                        : launch_rkc_f64_en(L, occ, blocks, threads, st);
+    }
     if (L.method == KIN_RKCK)
         return L.precision == KIN_MIXED ? launch_rkck_f32(L, stg, occ, blocks, threads, st)
                                         : launch_rkck_f64(L, stg, occ, blocks, threads, st);
@@ -150,8 +159,15 @@ cudaError_t launch_integrate(Launch& L, int stg, int occ, int blocks, int thread
 }
 
 cudaError_t integrate_occupancy(const MechDev& M, int method, int precision, int stg, int occ,
-                                int threads, int* bps)
+                                int energy, int threads, int* bps)
 {
+    if (energy) {
+        if (method == KIN_RKCK)
+            return precision == KIN_MIXED ? occ_rkck_f32_en(occ, threads, 0, bps)
+                                          : occ_rkck_f64_en(occ, threads, 0, bps);
+        return precision == KIN_MIXED ? occ_rkc_f32_en(occ, threads, 0, bps)
+                                      : occ_rkc_f64_en(occ, threads, 0, bps);
+    }
     const size_t sm = smem_bytes(M, precision, threads, stg);
     if (method == KIN_RKCK)
         return precision == KIN_MIXED ? occ_rkck_f32(stg, occ, threads, sm, bps)
@@ -174,7 +190,7 @@ cudaError_t launch_rates(const MechDev& M, int64_t cells, const double* T, const
                          const double* Y, int64_t ldY, double* dYdt, int precision, void* ws,
                          int64_t nslots, int blocks, int threads, cudaStream_t st)
 {
-    const WsLayout w = ws_layout(M, precision, KIN_SIGMA_GERSHGORIN, nslots, cells);
+    const WsLayout w = ws_layout(M, precision, KIN_SIGMA_GERSHGORIN, 0, nslots, cells);
     char* b = (char*)ws;
     if (precision == KIN_MIXED)
         rates_kernel<float><<<blocks, threads, 0, st>>>(M, cells, T, p, Y, ldY, dYdt, b + w.lane_r,

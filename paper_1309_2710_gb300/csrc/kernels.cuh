@@ -166,6 +166,86 @@ __device__ void feval(const MechDev& M, double Ctot, double invCtot, Lane<KT> K,
     }
 }
 
+// f with the energy equation (Eqs. (E:mass), (E:energy)): x = {Y_1..Y_nS, T}.
+// The rate constants (Eq. (E:rxn-const)), the density and the concentrations
+// follow the state's own T at every evaluation; the enthalpy sum
+// sum_i H_i(T) omega_i and the mixture heat capacity cp = sum_i Y_i cp_i/W_i
+// are FP64. dT/dt = -(sum_i H_i omega_i) / (rho cp), H_i = Hf_i + cp_i (T - T_REF).
+template <typename R>
+__device__ void feval_energy(const MechDev& M, double p, Lane<R> C, Lane<R> OM, Lane<double> x,
+                             Lane<double> out)
+{
+    const int nS = M.nS, nR = M.nR;
+    const double T = x[nS];
+    const double lnT = log(T), invT = 1.0 / T;
+    const double Ctot = p * 1e-6 * invT * (1.0 / R_GAS), invCtot = 1.0 / Ctot;
+    const R* __restrict__ invW = Tab<R>::invW(M);
+    R S0 = R(0), S1 = R(0);
+    int i = 0;
+    for (; i + 1 < nS; i += 2) {
+        const R m0 = (R)x[i] * invW[i];
+        const R m1 = (R)x[i + 1] * invW[i + 1];
+        C[i] = m0;
+        C[i + 1] = m1;
+        S0 += m0;
+        S1 += m1;
+    }
+    if (i < nS) {
+        const R m0 = (R)x[i] * invW[i];
+        C[i] = m0;
+        S0 += m0;
+    }
+    const R S = S0 + S1;
+    const R rho = (R)Ctot * (R(1) / S);
+    for (int k = 0; k < nS; ++k) C[k] = C[k] * rho;
+    const R* __restrict__ eff = Tab<R>::eff(M);
+    for (int j = 0; j < nR; ++j) {
+        const Rxn r = M.rxn[j];
+        const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
+        R q = Tab<R>::ex(a);
+        if (r.r0 >= 0) q *= C[r.r0];
+        if (r.r1 >= 0) q *= C[r.r1];
+        if (r.type != KIN_RXN_PLAIN) {
+            const R* a_ = eff + (int64_t)r.row * nS;
+            R M0 = R(0), M1 = R(0);
+            int k = 0;
+            for (; k + 1 < nS; k += 2) {
+                M0 += a_[k] * C[k];
+                M1 += a_[k + 1] * C[k + 1];
+            }
+            if (k < nS) M0 += a_[k] * C[k];
+            const R Mc = M0 + M1;
+            if (r.type == KIN_RXN_THIRD_BODY) {
+                q *= Mc;
+            } else {
+                const double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
+                const R Pr = Tab<R>::ex(a0 - a) * Mc;
+                q *= Pr / (R(1) + Pr);
+            }
+        }
+        OM[j] = q;
+    }
+    const R* __restrict__ nu = Tab<R>::nu(M);
+    const double invrho = (double)S * invCtot;
+    const double dT = T - T_REF;
+    double hw = 0.0, cpm = 0.0;
+    for (int sp = 0; sp < nS; ++sp) {
+        R w0 = R(0), w1 = R(0);
+        const int e1 = M.csr_ptr[sp + 1];
+        int e = M.csr_ptr[sp];
+        for (; e + 1 < e1; e += 2) {
+            w0 += nu[e] * OM[M.csr_rxn[e]];
+            w1 += nu[e + 1] * OM[M.csr_rxn[e + 1]];
+        }
+        if (e < e1) w0 += nu[e] * OM[M.csr_rxn[e]];
+        const double om = (double)(w0 + w1);
+        out[sp] = om * (M.W[sp] * invrho);
+        hw += (M.Hf[sp] + M.cp[sp] * dT) * om;
+        cpm += x[sp] * M.cpW[sp];
+    }
+    out[nS] = -hw * invrho / cpm;
+}
+
 __device__ __forceinline__ int find_inst(const Launch& L, long long g)
 {
     int lo = 0, hi = L.n_inst - 1;
@@ -234,7 +314,7 @@ struct Views {
     }
     __device__ __forceinline__ Lane<double> V(int v) const
     {
-        return Lane<double>{vbase + (int64_t)v * M.nS * L.nslots, (int32_t)L.nslots};
+        return Lane<double>{vbase + (int64_t)v * L.nV * L.nslots, (int32_t)L.nslots};
     }
     __device__ __forceinline__ Lane<R> K(int64_t g) const
     {
@@ -350,14 +430,14 @@ __device__ __forceinline__ void feval_sig(const Views<R, STG>& W, double Ctot, d
 // For every cell g (grid-stride, uniform across lanes): rate constants, f(y0),
 // and for RKC the spectral radius (Section 2.3) and the initial step
 // h1 = 0.1 h0 / ||Delta_0||^(1/2), h0 = 1/sigma.
-template <int METHOD, typename R, int STG>
+template <int METHOD, typename R, int STG, bool EN>
 __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launch L)
 {
     const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= L.nslots) return;
     Views<R, STG> W(L, slot);
     const MechDev& M = L.M;
-    const int nS = M.nS;
+    const int nS = M.nS, n = L.nV;
     for (int64_t g = slot; g < L.total; g += L.nslots) {
         const int ii = find_inst(L, g);
         const InstDev& I = L.inst[ii];
@@ -365,17 +445,30 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
         const double T = I.T[c], p = I.p[c];
         const double Ctot = p * 1e-6 / (R_GAS * T), invCtot = 1.0 / Ctot;
         Lane<R> K = W.K(g), KR = W.KR(g);
-        rate_constants<R>(M, T, K, KR);
+        if constexpr (!EN) rate_constants<R>(M, T, K, KR);
+        // f in the rate type, and f in FP64 for the spectral radius
+        auto frate = [&](Lane<double> x, Lane<double> o) {
+            if constexpr (EN) feval_energy<R>(M, p, W.C, W.OM, x, o);
+            else feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, x, o);
+        };
+        auto fsig = [&](Lane<double> x, Lane<double> o) {
+            if constexpr (EN) {
+                if constexpr (sizeof(R) == 4) feval_energy<double>(M, p, W.C64, W.OM64, x, o);
+                else feval_energy<double>(M, p, W.C, W.OM, x, o);
+            } else {
+                feval_sig(W, Ctot, invCtot, K, KR, x, o);
+            }
+        };
         Lane<double> Y = W.V(V_Y), F0 = W.F0cell(g), X = W.V(V_X), FX = W.V(V_FX), RS = W.V(V_RS);
         bool ok = true;
-        for (int i = 0; i < nS; ++i) {
-            const double y = I.Y[(int64_t)i * I.ldY + c];
+        for (int i = 0; i < n; ++i) {
+            const double y = i < nS ? I.Y[(int64_t)i * I.ldY + c] : T;
             Y[i] = y;
             X[i] = y;
             RS[i] = 0.0;
         }
-        feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, Y, F0);
-        for (int i = 0; i < nS; ++i) ok &= isfinite(F0[i]);
+        frate(Y, F0);
+        for (int i = 0; i < n; ++i) ok &= isfinite(F0[i]);
         uint8_t st = ok ? 0 : KIN_CELL_NONFINITE;
         double sigma = 0.0, h = I.dt;
         int nfe = 1;
@@ -384,31 +477,31 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
         Lane<double> B = F0;
         if (METHOD == KIN_RKC && ok && sizeof(R) == 4) {
             B = W.V(V_B);
-            feval_sig(W, Ctot, invCtot, K, KR, Y, B);
+            fsig(Y, B);
             nfe++;
         }
         if (METHOD == KIN_RKC && ok && L.sigma_method == KIN_SIGMA_POWER) {
             Lane<double> EV = W.EVcell(g);
-            for (int i = 0; i < nS; ++i) EV[i] = B[i];  // first direction: f(y0)
+            for (int i = 0; i < n; ++i) EV[i] = B[i];  // first direction: f(y0)
             PowerState P;
-            power_begin(nS, Y, EV, X, P);
+            power_begin(n, Y, EV, X, P);
             for (;;) {
-                feval_sig(W, Ctot, invCtot, K, KR, X, FX);
+                fsig(X, FX);
                 nfe++;
-                if (power_post(nS, Y, B, EV, X, FX, P)) break;
+                if (power_post(n, Y, B, EV, X, FX, P)) break;
             }
             sigma = 1.2 * P.sig;
         } else if (METHOD == KIN_RKC && ok) {
-            for (int k = 0; k < nS; ++k) {  // Gershgorin columns
+            for (int k = 0; k < n; ++k) {  // Gershgorin columns
                 const double eps = SIG_SQRT_U * fmax(fabs(Y[k]), I.atol);
                 X[k] = Y[k] + eps;
-                feval_sig(W, Ctot, invCtot, K, KR, X, FX);
+                fsig(X, FX);
                 const double ie = 1.0 / eps;
-                for (int i = 0; i < nS; ++i) RS[i] += fabs((FX[i] - B[i]) * ie);
+                for (int i = 0; i < n; ++i) RS[i] += fabs((FX[i] - B[i]) * ie);
                 X[k] = Y[k];
             }
-            for (int i = 0; i < nS; ++i) sigma = fmax(sigma, RS[i]);
-            nfe += nS;
+            for (int i = 0; i < n; ++i) sigma = fmax(sigma, RS[i]);
+            nfe += n;
         }
         if (METHOD == KIN_RKC && ok) {
             if (!isfinite(sigma)) {
@@ -416,11 +509,11 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
             } else {
                 double h0 = sigma > 0.0 ? 1.0 / sigma : I.dt;
                 if (h0 > I.dt) h0 = I.dt;
-                for (int i = 0; i < nS; ++i) X[i] = Y[i] + h0 * F0[i];
-                feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, X, FX);
+                for (int i = 0; i < n; ++i) X[i] = Y[i] + h0 * F0[i];
+                frate(X, FX);
                 nfe++;
-                for (int i = 0; i < nS; ++i) X[i] = h0 * (FX[i] - F0[i]);  // Delta_0
-                const double e0 = rms(nS, I.rtol, I.atol, X, Y, Y);
+                for (int i = 0; i < n; ++i) X[i] = h0 * (FX[i] - F0[i]);  // Delta_0
+                const double e0 = rms(n, I.rtol, I.atol, X, Y, Y);
                 if (!isfinite(e0)) h = 0.1 * h0;
                 else h = e0 > 0.0 ? 0.1 * h0 / sqrt(e0) : I.dt;
                 if (h > I.dt) h = I.dt;
@@ -486,12 +579,12 @@ struct LaneState {
     int since_sigma;
     bool last, last_rejected, have_prev, sigma_here;
     int iw1, iw2;  // RKC: slots of w_{j-1}, w_{j-2}
-    double t, dt, h, hh, hprev, cprev, sigma, eps, rtol, atol, Ctot, invCtot, invN;
+    double t, dt, h, hh, hprev, cprev, sigma, eps, rtol, atol, Ctot, invCtot, invN, p;
     int in_v, out_v;  // vectors read and written by the next f evaluation
     PowerState P;     // RKC power-method sigma in progress
 };
 
-template <int METHOD, typename R, int STG>
+template <int METHOD, typename R, int STG, bool EN>
 struct Integrator {
     Views<R, STG> W;
     const Launch& L;
@@ -524,28 +617,32 @@ struct Integrator {
                 continue;
             }
             const double T = I.T[S.cell], p = I.p[S.cell];
+            S.p = p;
             S.Ctot = p * 1e-6 / (R_GAS * T);
             S.invCtot = 1.0 / S.Ctot;
-            // the cell's rate constants into the lane's (coalesced or shared) copy
-            K = W.Kl;
-            KR = W.KRl;
-            const Lane<R> Kc = W.K(g), KRc = W.KR(g);
-            for (int j = 0; j < M.nR; ++j) K[j] = Kc[j];
-            for (int j = 0; j < M.nFO; ++j) KR[j] = KRc[j];
+            if constexpr (!EN) {
+                // the cell's rate constants into the lane's (coalesced or shared) copy
+                K = W.Kl;
+                KR = W.KRl;
+                const Lane<R> Kc = W.K(g), KRc = W.KR(g);
+                for (int j = 0; j < M.nR; ++j) K[j] = Kc[j];
+                for (int j = 0; j < M.nFO; ++j) KR[j] = KRc[j];
+            }
+            const int n = L.nV;
             Lane<double> Y = V(V_Y), F0 = V(V_F0), F0c = W.F0cell(g);
-            for (int k = 0; k < M.nS; ++k) {
-                Y[k] = I.Y[(int64_t)k * I.ldY + S.cell];
+            for (int k = 0; k < n; ++k) {
+                Y[k] = k < M.nS ? I.Y[(int64_t)k * I.ldY + S.cell] : T;
                 F0[k] = F0c[k];
             }
             if (METHOD == KIN_RKC && L.sigma_method == KIN_SIGMA_POWER) {
                 // the pre-pass estimate's direction warm-starts the next one
                 Lane<double> EV = V(V_RS), EVc = W.EVcell(g);
-                for (int k = 0; k < M.nS; ++k) EV[k] = EVc[k];
+                for (int k = 0; k < n; ++k) EV[k] = EVc[k];
             }
             S.dt = I.dt;
             S.rtol = I.rtol;
             S.atol = I.atol;
-            S.invN = 1.0 / M.nS;
+            S.invN = 1.0 / n;
             S.t = 0.0;
             S.h = L.cell_h[g];
             S.sigma = L.cell_sig[g];
@@ -579,6 +676,7 @@ struct Integrator {
         const InstDev& I = L.inst[S.inst];
         Lane<double> Y = V(V_Y);
         for (int k = 0; k < M.nS; ++k) I.Y[(int64_t)k * I.ldY + S.cell] = Y[k];
+        if constexpr (EN) I.T[S.cell] = Y[M.nS];
         finish_stats(S, code);
     }
 
@@ -603,14 +701,14 @@ struct Integrator {
     __device__ void sigma_start(LaneState& S)
     {
         if (L.sigma_method == KIN_SIGMA_POWER) {
-            power_begin(M.nS, V(V_Y), V(V_RS), V(V_X), S.P);
+            power_begin(L.nV, V(V_Y), V(V_RS), V(V_X), S.P);
             S.phase = PH_POW;
             S.in_v = V_X;
             S.out_v = V_FX;
             return;
         }
         Lane<double> Y = V(V_Y), X = V(V_X), RS = V(V_RS);
-        for (int i = 0; i < M.nS; ++i) {
+        for (int i = 0; i < L.nV; ++i) {
             X[i] = Y[i];
             RS[i] = 0.0;
         }
@@ -627,15 +725,15 @@ struct Integrator {
     {
         Lane<double> Y = V(V_Y), X = V(V_X), RS = V(V_RS), FX = V(V_FX), F0 = V(V_BASE);
         const double ie = 1.0 / S.eps;
-        for (int i = 0; i < M.nS; ++i) RS[i] += fabs((FX[i] - F0[i]) * ie);
+        for (int i = 0; i < L.nV; ++i) RS[i] += fabs((FX[i] - F0[i]) * ie);
         X[S.col] = Y[S.col];
-        if (++S.col < M.nS) {
+        if (++S.col < L.nV) {
             S.eps = SIG_SQRT_U * fmax(fabs(Y[S.col]), S.atol);
             X[S.col] = Y[S.col] + S.eps;
             return false;
         }
         double sg = 0.0;
-        for (int i = 0; i < M.nS; ++i) sg = fmax(sg, RS[i]);
+        for (int i = 0; i < L.nV; ++i) sg = fmax(sg, RS[i]);
         S.sigma = sg;
         S.nsig++;
         S.since_sigma = 0;
@@ -680,7 +778,7 @@ struct Integrator {
         // w_1 = y + mu~_1 h f_0 into slot A; w_0 = y stays in V_Y
         const double m1 = coef(s, 1)[2] * hh;
         Lane<double> Y = V(V_Y), F0 = V(V_F0), A = V(V_A);
-        for (int i = 0; i < M.nS; ++i) A[i] = Y[i] + m1 * F0[i];
+        for (int i = 0; i < L.nV; ++i) A[i] = Y[i] + m1 * F0[i];
         S.iw1 = V_A;
         S.iw2 = V_Y;
         S.j = 2;
@@ -718,7 +816,7 @@ struct Integrator {
             Lane<double> Y = V(V_Y), F0 = V(V_F0), W1 = V(S.iw1), W2 = V(fin ? S.iw1 : S.iw2),
                          FJ = V(V_FX), WN = V(nw);
             double acc = 0.0;
-            for (int i = 0; i < M.nS; ++i) {
+            for (int i = 0; i < L.nV; ++i) {
                 const double y = Y[i], w1 = W1[i];
                 const double v = c0 * y + mu * w1 + nu * W2[i] + mt * FJ[i] + gt * F0[i];
                 if (fin) {
@@ -748,7 +846,7 @@ struct Integrator {
             return rkc_begin_step(S);
         }
         if (S.phase == PH_POW) {
-            if (!power_post(M.nS, V(V_Y), V(V_BASE), V(V_RS), V(V_X), V(V_FX), S.P)) return -1;
+            if (!power_post(L.nV, V(V_Y), V(V_BASE), V(V_RS), V(V_X), V(V_FX), S.P)) return -1;
             S.sigma = 1.2 * S.P.sig;
             S.nsig++;
             S.since_sigma = 0;
@@ -778,7 +876,7 @@ struct Integrator {
                 fac = 0.8 * hh * S.cprev / (S.hprev * c3 * c3);
             else fac = 0.8 / c3;
             fac = fmin(10.0, fmax(0.1, fac));
-            for (int i = 0; i < M.nS; ++i) {
+            for (int i = 0; i < L.nV; ++i) {
                 Y[i] = WS[i];
                 F0[i] = FX[i];
             }
@@ -810,7 +908,7 @@ struct Integrator {
     __device__ void rkck_stage_point(LaneState& S, int st)
     {
         Lane<double> Y = V(V_Y), X = V(V_X);
-        for (int i = 0; i < M.nS; ++i) {
+        for (int i = 0; i < L.nV; ++i) {
             double acc = 0.0;
             for (int l = 0; l < st; ++l) acc += CK_B[st][l] * V(ck_slot(l))[i];
             X[i] = Y[i] + S.hh * acc;
@@ -849,7 +947,7 @@ struct Integrator {
         Lane<double> Y = V(V_Y), F0 = V(V_F0), X = V(V_X);
         const double hh = S.hh;
         double errmax = 0.0;
-        for (int i = 0; i < M.nS; ++i) {
+        for (int i = 0; i < L.nV; ++i) {
             double s5 = 0.0, e = 0.0;
             for (int l = 0; l < 6; ++l) {
                 const double f = V(ck_slot(l))[i];
@@ -864,7 +962,7 @@ struct Integrator {
         S.attempts++;
         if (errmax <= 1.0) {
             S.nacc++;
-            for (int i = 0; i < M.nS; ++i) Y[i] = X[i];
+            for (int i = 0; i < L.nV; ++i) Y[i] = X[i];
             if (S.last) {
                 S.t = S.dt;
                 return KIN_CELL_OK;
@@ -888,7 +986,7 @@ struct Integrator {
     {
         Lane<double> a = V(v);
         bool ok = true;
-        for (int i = 0; i < M.nS; ++i) ok &= isfinite(a[i]);
+        for (int i = 0; i < L.nV; ++i) ok &= isfinite(a[i]);
         return ok;
     }
 
@@ -898,10 +996,19 @@ struct Integrator {
         LaneState S;
         if (!load_next(S)) return;
         for (;;) {
-            if (sizeof(R) == 4 && METHOD == KIN_RKC && S.phase >= PH_SIGBASE && S.phase <= PH_POW)
+            const bool sig = METHOD == KIN_RKC && S.phase >= PH_SIGBASE && S.phase <= PH_POW;
+            if constexpr (EN) {
+                if (!sig)
+                    feval_energy<R>(M, S.p, W.C, W.OM, V(S.in_v), V(S.out_v));
+                else if constexpr (sizeof(R) == 4)
+                    feval_energy<double>(M, S.p, W.C64, W.OM64, V(S.in_v), V(S.out_v));
+                else
+                    feval_energy<double>(M, S.p, W.C, W.OM, V(S.in_v), V(S.out_v));
+            } else if (sizeof(R) == 4 && sig) {
                 feval<double>(M, S.Ctot, S.invCtot, K, KR, W.C64, W.OM64, V(S.in_v), V(S.out_v));
-            else
+            } else {
                 feval<R>(M, S.Ctot, S.invCtot, K, KR, W.C, W.OM, V(S.in_v), V(S.out_v));
+            }
             S.nfe++;
             const int code = METHOD == KIN_RKC ? rkc_post(S) : rkck_post(S);
             if (code >= 0) {
@@ -915,43 +1022,43 @@ struct Integrator {
 // OCC selects the register budget: 0 = at most 128 registers (16 resident
 // warps per SM), 1 = at most 85 (24 resident warps per SM; the rarely used
 // state spills to L1-backed local memory).
-template <int METHOD, typename R, int STG, int OCC>
+template <int METHOD, typename R, int STG, int OCC, bool EN>
 __global__ void __launch_bounds__(128, OCC ? 6 : 4) integrate_kernel(const __grid_constant__ Launch L)
 {
     const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= L.nslots) return;
-    Integrator<METHOD, R, STG> I(L, slot);
+    Integrator<METHOD, R, STG, EN> I(L, slot);
     I.run();
 }
 
 // ------------------------------------------------------- launch templates --
-template <int METHOD, typename R, int STG, int OCC>
+template <int METHOD, typename R, int STG, int OCC, bool EN>
 inline cudaError_t launch_all(Launch& L, int blocks, int threads, cudaStream_t st)
 {
     const size_t sm = smem_bytes(L.M, L.precision, threads, STG);
     if (STG > 0) {
-        cudaError_t e = cudaFuncSetAttribute(init_kernel<METHOD, R, STG>,
+        cudaError_t e = cudaFuncSetAttribute(init_kernel<METHOD, R, STG, EN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(integrate_kernel<METHOD, R, STG, OCC>,
+            e = cudaFuncSetAttribute(integrate_kernel<METHOD, R, STG, OCC, EN>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    init_kernel<METHOD, R, STG><<<blocks, threads, sm, st>>>(L);
+    init_kernel<METHOD, R, STG, EN><<<blocks, threads, sm, st>>>(L);
     if (METHOD == KIN_RKC) {
         const cudaError_t e = launch_sort(L, st);
         if (e != cudaSuccess) return e;
     }
-    integrate_kernel<METHOD, R, STG, OCC><<<blocks, threads, sm, st>>>(L);
+    integrate_kernel<METHOD, R, STG, OCC, EN><<<blocks, threads, sm, st>>>(L);
     return cudaGetLastError();
 }
 
 template <int METHOD, typename R, int OCC>
 inline cudaError_t launch_staged(Launch& L, int stg, int blocks, int threads, cudaStream_t st)
 {
-    if (stg == 2) return launch_all<METHOD, R, 2, OCC>(L, blocks, threads, st);
-    if (stg == 1) return launch_all<METHOD, R, 1, OCC>(L, blocks, threads, st);
-    return launch_all<METHOD, R, 0, OCC>(L, blocks, threads, st);
+    if (stg == 2) return launch_all<METHOD, R, 2, OCC, false>(L, blocks, threads, st);
+    if (stg == 1) return launch_all<METHOD, R, 1, OCC, false>(L, blocks, threads, st);
+    return launch_all<METHOD, R, 0, OCC, false>(L, blocks, threads, st);
 }
 
 template <int METHOD, typename R>
@@ -961,15 +1068,15 @@ inline cudaError_t launch_occ(Launch& L, int stg, int occ, int blocks, int threa
                : launch_staged<METHOD, R, 0>(L, stg, blocks, threads, st);
 }
 
-template <int METHOD, typename R, int STG, int OCC>
+template <int METHOD, typename R, int STG, int OCC, bool EN = false>
 inline cudaError_t occ_one(int threads, size_t sm, int* bps)
 {
     if (STG > 0) {
-        cudaError_t e = cudaFuncSetAttribute(integrate_kernel<METHOD, R, STG, OCC>,
+        cudaError_t e = cudaFuncSetAttribute(integrate_kernel<METHOD, R, STG, OCC, EN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, integrate_kernel<METHOD, R, STG, OCC>,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, integrate_kernel<METHOD, R, STG, OCC, EN>,
                                                          threads, sm);
 }
 
@@ -986,6 +1093,22 @@ inline cudaError_t occ_sel(int stg, int occ, int threads, size_t sm, int* bps)
 {
     return occ ? occ_staged<METHOD, R, 1>(stg, threads, sm, bps)
                : occ_staged<METHOD, R, 0>(stg, threads, sm, bps);
+}
+
+// The energy-equation variants (staging level 0: their rate constants are
+// formed inside f, so there is no per-lane copy to stage).
+template <int METHOD, typename R>
+inline cudaError_t launch_energy(Launch& L, int occ, int blocks, int threads, cudaStream_t st)
+{
+    return occ ? launch_all<METHOD, R, 0, 1, true>(L, blocks, threads, st)
+               : launch_all<METHOD, R, 0, 0, true>(L, blocks, threads, st);
+}
+
+template <int METHOD, typename R>
+inline cudaError_t occ_energy(int occ, int threads, size_t sm, int* bps)
+{
+    return occ ? occ_one<METHOD, R, 0, 1, true>(threads, sm, bps)
+               : occ_one<METHOD, R, 0, 0, true>(threads, sm, bps);
 }
 
 }  // namespace kin

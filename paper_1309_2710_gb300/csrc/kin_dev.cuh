@@ -12,6 +12,7 @@
 namespace kin {
 
 constexpr double R_GAS = 8.314462618;  // J/(mol K)
+constexpr double T_REF = 298.15;        // K, reference of the formation enthalpies
 constexpr int SMAX = KIN_MAX_STAGES;
 constexpr int RKC_TAB_S = SMAX + 1;    // rows s = 0..250 (2..250 used)
 constexpr int RKC_TAB_W = 5;           // mu, nu, mu~, gamma~, 1 - mu - nu
@@ -51,11 +52,15 @@ struct MechDev {
     const double* eff;     // [nM][nS]
     const float* eff32;    // [nM][nS]
     const double* rkc;     // [RKC_TAB_S][RKC_TAB_S][RKC_TAB_W]
+    // energy equation (null without thermochemistry)
+    const double* cp;      // [nS] J/(mol K)
+    const double* cpW;     // [nS] cp_i / W_i, J/(g K)
+    const double* Hf;      // [nS] J/mol at T_REF
 };
 
 // One instance of a batched launch (device pointers).
 struct InstDev {
-    const double* T;
+    double* T;  // written back with the energy equation
     const double* p;
     double* Y;
     int64_t ldY;
@@ -70,20 +75,22 @@ constexpr int NVEC = 8;
 struct Launch {
     MechDev M;
     int method, precision, max_steps, n_inst, sigma_method;
+    int energy;  // 1: T is state component nS (Eq. (E:energy))
+    int nV;      // state length: nS + energy
     int64_t nslots;                 // lanes of the persistent grid
     int64_t total;                  // cells over all instances
     unsigned long long* queue;      // next position in `order`
     unsigned* hist;                 // [NBUCKET] counts, then cursors
     // per lane
-    double* vec;                    // [NVEC * nS][nslots]
+    double* vec;                    // [NVEC * nV][nslots]
     void* lane_r;                   // C [nS], Omega [nR], k [nR], k0/kinf [nFO] of the rate
                                     // type: [nS + 2 nR + nFO][nslots]
     double* lane_sig;               // mixed precision: FP64 C [nS], Omega [nR] for the
                                     // spectral-radius evaluations of f: [nS + nR][nslots]
     // per cell (global cell index g over all instances)
     void* cell_k;                   // k_j [nR][total], then k0/kinf [nFO][total], rate type
-    double* cell_f0;                // f(y0) [nS][total]
-    double* cell_ev;                // power-method direction [nS][total] (power sigma only)
+    double* cell_f0;                // f(y0) [nV][total]
+    double* cell_ev;                // power-method direction [nV][total] (power sigma only)
     double* cell_sig;               // RKC spectral radius at y0 [total]
     double* cell_h;                 // first trial step [total]
     int32_t* cell_nfe;              // f evaluations spent before the main kernel [total]
@@ -97,7 +104,7 @@ struct Launch {
 struct WsLayout {
     int64_t header, vec, lane_r, lane_sig, cell_k, f0, ev, sig, h, nfe, st, order, total;
 };
-WsLayout ws_layout(const MechDev& M, int precision, int sigma_method, int64_t nslots,
+WsLayout ws_layout(const MechDev& M, int precision, int sigma_method, int energy, int64_t nslots,
                    int64_t cells);
 
 // Host-side helpers implemented in kernels.cu.
@@ -118,22 +125,39 @@ cudaError_t occ_rkc_f32(int stg, int occ, int threads, size_t sm, int* bps);
 cudaError_t occ_rkck_f64(int stg, int occ, int threads, size_t sm, int* bps);
 cudaError_t occ_rkck_f32(int stg, int occ, int threads, size_t sm, int* bps);
 cudaError_t launch_sort(Launch& L, cudaStream_t st);
+// Energy-equation variants of the lane kernels (inst_energy_*.cu, staging 0).
+cudaError_t launch_rkc_f64_en(Launch& L, int occ, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_rkc_f32_en(Launch& L, int occ, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_rkck_f64_en(Launch& L, int occ, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_rkck_f32_en(Launch& L, int occ, int blocks, int threads, cudaStream_t st);
+cudaError_t occ_rkc_f64_en(int occ, int threads, size_t sm, int* bps);
+cudaError_t occ_rkc_f32_en(int occ, int threads, size_t sm, int* bps);
+cudaError_t occ_rkck_f64_en(int occ, int threads, size_t sm, int* bps);
+cudaError_t occ_rkck_f32_en(int occ, int threads, size_t sm, int* bps);
 // Warp-per-cell RKC (inst_warp_*.cu): one warp integrates one cell; one
 // translation unit per rate precision and register budget (occupancy).
 cudaError_t launch_warp_f64_o0(Launch& L, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_warp_f64_o1(Launch& L, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_warp_f32_o0(Launch& L, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_warp_f32_o1(Launch& L, int blocks, int threads, cudaStream_t st);
-cudaError_t occ_warp_f64_o0(const MechDev& M, int threads, int* bps);
-cudaError_t occ_warp_f64_o1(const MechDev& M, int threads, int* bps);
-cudaError_t occ_warp_f32_o0(const MechDev& M, int threads, int* bps);
-cudaError_t occ_warp_f32_o1(const MechDev& M, int threads, int* bps);
+cudaError_t occ_warp_f64_o0(const MechDev& M, int nV, int threads, int* bps);
+cudaError_t occ_warp_f64_o1(const MechDev& M, int nV, int threads, int* bps);
+cudaError_t occ_warp_f32_o0(const MechDev& M, int nV, int threads, int* bps);
+cudaError_t occ_warp_f32_o1(const MechDev& M, int nV, int threads, int* bps);
+cudaError_t launch_warp_f64_en_o0(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_warp_f64_en_o1(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_warp_f32_en_o0(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_warp_f32_en_o1(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t occ_warp_f64_en_o0(const MechDev& M, int nV, int threads, int* bps);
+cudaError_t occ_warp_f64_en_o1(const MechDev& M, int nV, int threads, int* bps);
+cudaError_t occ_warp_f32_en_o0(const MechDev& M, int nV, int threads, int* bps);
+cudaError_t occ_warp_f32_en_o1(const MechDev& M, int nV, int threads, int* bps);
 size_t warp_smem(const MechDev& M, int precision, int threads);
 
 // Record `code` and a printf-style message as the calling thread's last
 // error (kin_last_error); returns `code`.
 int set_last_error(int code, const char* fmt, ...);
 cudaError_t integrate_occupancy(const MechDev& M, int method, int precision, int staging,
-                                int occupancy, int threads, int* blocks_per_sm);
+                                int occupancy, int energy, int threads, int* blocks_per_sm);
 
 }  // namespace kin

@@ -48,7 +48,7 @@ cudaError_t scratch_address(void** out)
 
 }  // namespace
 
-extern "C" int kin_integrate_noalloc(const kin_mech* m, int64_t cells, const double* T,
+extern "C" int kin_integrate_noalloc(const kin_mech* m, int64_t cells, double* T,
                                      const double* p, double* Y, int64_t ldY, double dt,
                                      double rtol, double atol, const kin_opts* opts,
                                      uint8_t* status, int32_t* stats)

@@ -142,6 +142,103 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
 
 // Element r of a register vector for a warp-uniform r.
 template <int NR>
+__device__ __forceinline__ double reg_get(const double (&v)[NR], int r);
+
+// f with the energy equation (Eqs. (E:mass), (E:energy)) for the warp's cell:
+// state component nS is T (lane nS % 32, slot nS / 32). Each lane computes the
+// rate constants of its reactions from T (they follow T at every
+// evaluation); the enthalpy sum and the mixture heat capacity are FP64 warp
+// sums, and dT/dt lands in T's slot.
+template <typename R, int NR>
+__device__ __forceinline__ void warp_feval_energy(const MechDev& M, double p, R* C, R* OM,
+                                                  const double (&x)[NR], double (&out)[NR], int lane)
+{
+    const int nS = M.nS, nR = M.nR, nM = M.nM;
+    const double T = __shfl_sync(0xffffffffu, reg_get(x, nS >> 5), nS & 31);
+    const double lnT = log(T), invT = 1.0 / T;
+    const double Ctot = p * 1e-6 * invT * (1.0 / R_GAS), invCtot = 1.0 / Ctot;
+    const R* __restrict__ invW = Tab<R>::invW(M);
+    R s = R(0);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int i = lane + 32 * r;
+        if (i < nS) {
+            const R m = (R)x[r] * invW[i];
+            C[i] = m;
+            s += m;
+        }
+    }
+    s = warp_sum(s);
+    const R rho = (R)Ctot * (R(1) / s);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int i = lane + 32 * r;
+        if (i < nS) C[i] = C[i] * rho;
+    }
+    __syncwarp();
+    const R* __restrict__ effT = TabW<R>::effT(M);
+    for (int q = lane; q < nR; q += 32) {
+        const Rxn rx = M.rxnp[q];
+        const int j = M.rxn_perm[q];
+        const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
+        R v = Tab<R>::ex(a);
+        if (rx.r0 >= 0) v *= C[rx.r0];
+        if (rx.r1 >= 0) v *= C[rx.r1];
+        if (rx.type != KIN_RXN_PLAIN) {
+            const R* ea = effT + rx.row;
+            R m0 = R(0), m1 = R(0);
+            int k = 0;
+            for (; k + 1 < nS; k += 2) {
+                m0 += ea[(int64_t)k * nM] * C[k];
+                m1 += ea[(int64_t)(k + 1) * nM] * C[k + 1];
+            }
+            if (k < nS) m0 += ea[(int64_t)k * nM] * C[k];
+            const R Mc = m0 + m1;
+            if (rx.type == KIN_RXN_THIRD_BODY) {
+                v *= Mc;
+            } else {
+                const double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
+                const R Pr = Tab<R>::ex(a0 - a) * Mc;
+                v *= Pr / (R(1) + Pr);
+            }
+        }
+        OM[q] = v;
+    }
+    __syncwarp();
+    const R* __restrict__ nu = Tab<R>::nu(M);
+    const double invrho = (double)s * invCtot, dT = T - T_REF;
+    double hw = 0.0, cpm = 0.0;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int i = lane + 32 * r;
+        double o = 0.0;
+        if (i < nS) {
+            R w0 = R(0), w1 = R(0);
+            const int e1 = M.csr_ptr[i + 1];
+            int e = M.csr_ptr[i];
+            for (; e + 1 < e1; e += 2) {
+                w0 += nu[e] * OM[M.csrp_rxn[e]];
+                w1 += nu[e + 1] * OM[M.csrp_rxn[e + 1]];
+            }
+            if (e < e1) w0 += nu[e] * OM[M.csrp_rxn[e]];
+            const double om = (double)(w0 + w1);
+            o = om * (M.W[i] * invrho);
+            hw += (M.Hf[i] + M.cp[i] * dT) * om;
+            cpm += x[r] * M.cpW[i];
+        }
+        out[r] = o;
+    }
+    hw = warp_sum(hw);
+    cpm = warp_sum(cpm);
+    const double dTdt = -hw * invrho / cpm;
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+        if (lane + 32 * r == nS) out[r] = dTdt;
+    __syncwarp();  // C and OM are rewritten by the next evaluation
+}
+
+// Element r of a register vector for a warp-uniform r.
+template <int NR>
 __device__ __forceinline__ double reg_get(const double (&v)[NR], int r)
 {
     double o = v[0];
@@ -151,7 +248,7 @@ __device__ __forceinline__ double reg_get(const double (&v)[NR], int r)
     return o;
 }
 
-template <typename R, int NR>
+template <typename R, int NR, bool EN>
 struct WarpRKC {
     const Launch& L;
     const MechDev& M;
@@ -160,12 +257,12 @@ struct WarpRKC {
     double* C64;   // the same shared words as C and OM, for the FP64 evaluations
     double* OM64;
     const R* Kc;
-    int lane;
-    double Ctot, invCtot, atol, rtol;
+    int lane, nV;  // nV: state length, nS + 1 with the energy equation
+    double Ctot, invCtot, atol, rtol, p;
     int nfe, nsig;
     double y[NR], f0[NR], w1[NR], w2[NR], fx[NR], x[NR], ev[NR];
 
-    __device__ explicit WarpRKC(const Launch& l) : L(l), M(l.M), Kc(nullptr), lane(threadIdx.x & 31)
+    __device__ explicit WarpRKC(const Launch& l) : L(l), M(l.M), Kc(nullptr), lane(threadIdx.x & 31), nV(l.nV)
     {
         C64 = reinterpret_cast<double*>(kin_smem) + (size_t)(threadIdx.x >> 5) * warp_smem_elems(M);
         OM64 = C64 + M.nS;
@@ -173,11 +270,12 @@ struct WarpRKC {
         OM = C + M.nS;
     }
 
-    __device__ __forceinline__ bool valid(int r) const { return lane + 32 * r < M.nS; }
+    __device__ __forceinline__ bool valid(int r) const { return lane + 32 * r < nV; }
 
     __device__ __forceinline__ void f(const double (&in)[NR], double (&o)[NR])
     {
-        warp_feval<R, R, NR>(M, Kc, C, OM, Ctot, invCtot, in, o, lane);
+        if constexpr (EN) warp_feval_energy<R, NR>(M, p, C, OM, in, o, lane);
+        else warp_feval<R, R, NR>(M, Kc, C, OM, Ctot, invCtot, in, o, lane);
         nfe++;
     }
 
@@ -185,7 +283,9 @@ struct WarpRKC {
     // f(y + v) - f(y) would swamp the difference; see SIG_SQRT_U).
     __device__ __forceinline__ void fs(const double (&in)[NR], double (&o)[NR])
     {
-        if constexpr (sizeof(R) == 4)
+        if constexpr (EN)
+            warp_feval_energy<double, NR>(M, p, C64, OM64, in, o, lane);
+        else if constexpr (sizeof(R) == 4)
             warp_feval<double, R, NR>(M, Kc, C64, OM64, Ctot, invCtot, in, o, lane);
         else
             warp_feval<double, double, NR>(M, Kc, C, OM, Ctot, invCtot, in, o, lane);
@@ -203,7 +303,7 @@ struct WarpRKC {
                 const double q = d[r] / sc;
                 acc += q * q;
             }
-        return sqrt(warp_sum(acc) / M.nS);
+        return sqrt(warp_sum(acc) / nV);
     }
 
     // Gershgorin bound on the finite-difference Jacobian at y (base = f(y) in FP64).
@@ -212,7 +312,7 @@ struct WarpRKC {
         double rs[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) rs[r] = 0.0;
-        for (int k = 0; k < M.nS; ++k) {
+        for (int k = 0; k < nV; ++k) {
             const int kr = k >> 5, kl = k & 31;
             const double yk = __shfl_sync(0xffffffffu, reg_get(y, kr), kl);
             const double eps = SIG_SQRT_U * fmax(fabs(yk), atol);
@@ -245,7 +345,7 @@ struct WarpRKC {
         if (!(vn > 0.0) || !isfinite(vn)) {
 #pragma unroll
             for (int r = 0; r < NR; ++r) ev[r] = valid(r) ? 1.0 : 0.0;
-            vn = sqrt((double)M.nS);
+            vn = sqrt((double)nV);
         }
         const double sc0 = dyn / vn;
 #pragma unroll
@@ -304,7 +404,7 @@ struct WarpRKC {
         double t = 0.0, hprev = 0.0, cprev = 0.0;
         int attempts = 0, since = 0;
         bool sigma_here = true, last_rej = false, have_prev = false;
-        const double invN = 1.0 / M.nS;
+        const double invN = 1.0 / nV;
         for (;;) {
             if (attempts >= L.max_steps) return KIN_CELL_MAXSTEPS;
             if (since >= 25 || (last_rej && !sigma_here)) {
@@ -408,12 +508,12 @@ struct WarpBounds {
 // Pre-pass, one warp per cell (grid-stride over cells): the cell's rate
 // constants (stored cell-major for the main kernel), f(y0), sigma and the
 // initial step h1 (Section 2.3).
-template <typename R, int NR, int OCC>
+template <typename R, int NR, int OCC, bool EN>
 __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_init_kernel(const __grid_constant__ Launch L)
 {
-    WarpRKC<R, NR> W(L);
+    WarpRKC<R, NR, EN> W(L);
     const MechDev& M = L.M;
-    const int lane = W.lane, nK = M.nR + M.nFO, nS = M.nS;
+    const int lane = W.lane, nK = M.nR + M.nFO, nS = M.nS, nV = L.nV;
     const int64_t nwarps = L.nslots >> 5;
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < L.total; g += nwarps) {
         const int ii = find_inst(L, g);
@@ -424,24 +524,31 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_ini
         W.invCtot = 1.0 / W.Ctot;
         W.atol = I.atol;
         W.rtol = I.rtol;
+        W.p = p;
         W.nfe = 0;
-        // rate constants (Eq. (E:rxn-const)) in permutation order
-        R* kc = reinterpret_cast<R*>(L.cell_k) + g * nK;
-        const double lnT = log(T), invT = 1.0 / T;
-        for (int q = lane; q < M.nR; q += 32) {
-            const int j = M.rxn_perm[q];
-            const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
-            kc[q] = Tab<R>::ex(a);
-            const int fo = M.rxnp[q].fo;
-            if (fo >= 0) {
-                const double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
-                kc[M.nR + fo] = Tab<R>::ex(a0 - a);
+        if constexpr (!EN) {
+            // rate constants (Eq. (E:rxn-const)) in permutation order; with the
+            // energy equation they follow T and are formed inside f instead
+            R* kc = reinterpret_cast<R*>(L.cell_k) + g * nK;
+            const double lnT = log(T), invT = 1.0 / T;
+            for (int q = lane; q < M.nR; q += 32) {
+                const int j = M.rxn_perm[q];
+                const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
+                kc[q] = Tab<R>::ex(a);
+                const int fo = M.rxnp[q].fo;
+                if (fo >= 0) {
+                    const double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
+                    kc[M.nR + fo] = Tab<R>::ex(a0 - a);
+                }
             }
+            __syncwarp();
+            W.Kc = kc;
         }
-        __syncwarp();
-        W.Kc = kc;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) W.y[r] = W.valid(r) ? I.Y[(int64_t)(lane + 32 * r) * I.ldY + c] : 0.0;
+        for (int r = 0; r < NR; ++r) {
+            const int i = lane + 32 * r;
+            W.y[r] = i < nS ? I.Y[(int64_t)i * I.ldY + c] : (i == nS && EN ? T : 0.0);
+        }
         W.f(W.y, W.f0);
         bool fin = true;
 #pragma unroll
@@ -471,8 +578,8 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_ini
 #pragma unroll
         for (int r = 0; r < NR; ++r)
             if (W.valid(r)) {
-                L.cell_f0[g * nS + lane + 32 * r] = W.f0[r];
-                if (L.cell_ev) L.cell_ev[g * nS + lane + 32 * r] = W.ev[r];
+                L.cell_f0[g * nV + lane + 32 * r] = W.f0[r];
+                if (L.cell_ev) L.cell_ev[g * nV + lane + 32 * r] = W.ev[r];
             }
         if (lane == 0) {
             L.cell_sig[g] = sig;
@@ -485,12 +592,12 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_ini
 
 // Persistent main kernel: each warp takes cells from the queue in the
 // longest-first order and integrates them one after another.
-template <typename R, int NR, int OCC>
+template <typename R, int NR, int OCC, bool EN>
 __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_integrate_kernel(const __grid_constant__ Launch L)
 {
-    WarpRKC<R, NR> W(L);
+    WarpRKC<R, NR, EN> W(L);
     const MechDev& M = L.M;
-    const int lane = W.lane, nK = M.nR + M.nFO, nS = M.nS;
+    const int lane = W.lane, nK = M.nR + M.nFO, nS = M.nS, nV = L.nV;
     for (;;) {
         unsigned long long q = 0;
         if (lane == 0) q = atomicAdd(L.queue, 1ull);
@@ -512,19 +619,23 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_int
             W.invCtot = 1.0 / W.Ctot;
             W.atol = I.atol;
             W.rtol = I.rtol;
-            W.Kc = reinterpret_cast<const R*>(L.cell_k) + g * nK;
+            W.p = p;
+            W.Kc = EN ? nullptr : reinterpret_cast<const R*>(L.cell_k) + g * nK;
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 const int i = lane + 32 * r;
-                const bool v = i < nS;
-                W.y[r] = v ? I.Y[(int64_t)i * I.ldY + c] : 0.0;
-                W.f0[r] = v ? L.cell_f0[g * nS + i] : 0.0;
-                W.ev[r] = (v && L.cell_ev) ? L.cell_ev[g * nS + i] : 0.0;
+                const bool v = i < nV;
+                W.y[r] = i < nS ? I.Y[(int64_t)i * I.ldY + c] : (v ? T : 0.0);
+                W.f0[r] = v ? L.cell_f0[g * nV + i] : 0.0;
+                W.ev[r] = (v && L.cell_ev) ? L.cell_ev[g * nV + i] : 0.0;
             }
             code = W.run(I.dt, L.cell_sig[g], L.cell_h[g], nacc, nrej);
 #pragma unroll
-            for (int r = 0; r < NR; ++r)
-                if (W.valid(r)) I.Y[(int64_t)(lane + 32 * r) * I.ldY + c] = W.y[r];
+            for (int r = 0; r < NR; ++r) {
+                const int i = lane + 32 * r;
+                if (i < nS) I.Y[(int64_t)i * I.ldY + c] = W.y[r];
+                else if (i == nS && EN) I.T[c] = W.y[r];
+            }
         }
         if (lane == 0) {
             if (I.status) I.status[c] = (uint8_t)code;
@@ -545,56 +656,56 @@ inline size_t warp_smem_bytes(const MechDev& M, int precision, int threads)
     return (size_t)warp_smem_elems(M) * (threads / 32) * 8;
 }
 
-template <typename R, int NR, int OCC>
+template <typename R, int NR, int OCC, bool EN>
 inline cudaError_t warp_launch_nr(Launch& L, int blocks, int threads, cudaStream_t st)
 {
     const size_t sm = warp_smem_bytes(L.M, L.precision, threads);
-    cudaError_t e = cudaFuncSetAttribute(warp_init_kernel<R, NR, OCC>,
+    cudaError_t e = cudaFuncSetAttribute(warp_init_kernel<R, NR, OCC, EN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(warp_integrate_kernel<R, NR, OCC>,
+        e = cudaFuncSetAttribute(warp_integrate_kernel<R, NR, OCC, EN>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    warp_init_kernel<R, NR, OCC><<<blocks, threads, sm, st>>>(L);
+    warp_init_kernel<R, NR, OCC, EN><<<blocks, threads, sm, st>>>(L);
     e = launch_sort(L, st);
     if (e != cudaSuccess) return e;
-    warp_integrate_kernel<R, NR, OCC><<<blocks, threads, sm, st>>>(L);
+    warp_integrate_kernel<R, NR, OCC, EN><<<blocks, threads, sm, st>>>(L);
     return cudaGetLastError();
 }
 
-template <typename R, int NR, int OCC>
+template <typename R, int NR, int OCC, bool EN>
 inline cudaError_t warp_occ_nr(const MechDev& M, int precision, int threads, int* bps)
 {
     const size_t sm = warp_smem_bytes(M, precision, threads);
-    cudaError_t e = cudaFuncSetAttribute(warp_integrate_kernel<R, NR, OCC>,
+    cudaError_t e = cudaFuncSetAttribute(warp_integrate_kernel<R, NR, OCC, EN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, warp_integrate_kernel<R, NR, OCC>, threads,
-                                                         sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, warp_integrate_kernel<R, NR, OCC, EN>,
+                                                         threads, sm);
 }
 
-// Register-vector width for n species (species l + 32 r, r < NR).
-__host__ __device__ inline int warp_nr(int nS) { return nS <= 32 ? 1 : nS <= 64 ? 2 : nS <= 128 ? 4 : 8; }
+// Register-vector width for a state of n components (component l + 32 r, r < NR).
+__host__ __device__ inline int warp_nr(int n) { return n <= 32 ? 1 : n <= 64 ? 2 : n <= 128 ? 4 : 8; }
 
-template <typename R, int OCC>
+template <typename R, int OCC, bool EN>
 inline cudaError_t warp_launch(Launch& L, int blocks, int threads, cudaStream_t st)
 {
-    switch (warp_nr(L.M.nS)) {
-    case 1: return warp_launch_nr<R, 1, OCC>(L, blocks, threads, st);
-    case 2: return warp_launch_nr<R, 2, OCC>(L, blocks, threads, st);
-    case 4: return warp_launch_nr<R, 4, OCC>(L, blocks, threads, st);
-    default: return warp_launch_nr<R, 8, OCC>(L, blocks, threads, st);
+    switch (warp_nr(L.nV)) {
+    case 1: return warp_launch_nr<R, 1, OCC, EN>(L, blocks, threads, st);
+    case 2: return warp_launch_nr<R, 2, OCC, EN>(L, blocks, threads, st);
+    case 4: return warp_launch_nr<R, 4, OCC, EN>(L, blocks, threads, st);
+    default: return warp_launch_nr<R, 8, OCC, EN>(L, blocks, threads, st);
     }
 }
 
-template <typename R, int OCC>
-inline cudaError_t warp_occ(const MechDev& M, int precision, int threads, int* bps)
+template <typename R, int OCC, bool EN>
+inline cudaError_t warp_occ(const MechDev& M, int nV, int precision, int threads, int* bps)
 {
-    switch (warp_nr(M.nS)) {
-    case 1: return warp_occ_nr<R, 1, OCC>(M, precision, threads, bps);
-    case 2: return warp_occ_nr<R, 2, OCC>(M, precision, threads, bps);
-    case 4: return warp_occ_nr<R, 4, OCC>(M, precision, threads, bps);
-    default: return warp_occ_nr<R, 8, OCC>(M, precision, threads, bps);
+    switch (warp_nr(nV)) {
+    case 1: return warp_occ_nr<R, 1, OCC, EN>(M, precision, threads, bps);
+    case 2: return warp_occ_nr<R, 2, OCC, EN>(M, precision, threads, bps);
+    case 4: return warp_occ_nr<R, 4, OCC, EN>(M, precision, threads, bps);
+    default: return warp_occ_nr<R, 8, OCC, EN>(M, precision, threads, bps);
     }
 }
 

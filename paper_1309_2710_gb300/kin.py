@@ -39,7 +39,8 @@ class MechDesc(ctypes.Structure):
                 ("W", ctypes.c_void_p), ("lnA", ctypes.c_void_p), ("beta", ctypes.c_void_p),
                 ("Ea", ctypes.c_void_p), ("reac", ctypes.c_void_p), ("prod", ctypes.c_void_p),
                 ("type", ctypes.c_void_p), ("eff", ctypes.c_void_p), ("lnA0", ctypes.c_void_p),
-                ("beta0", ctypes.c_void_p), ("Ea0", ctypes.c_void_p)]
+                ("beta0", ctypes.c_void_p), ("Ea0", ctypes.c_void_p), ("cp", ctypes.c_void_p),
+                ("Hf", ctypes.c_void_p)]
 
 
 class Opts(ctypes.Structure):
@@ -47,7 +48,8 @@ class Opts(ctypes.Structure):
                 ("max_steps", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("staging", ctypes.c_int32),
                 ("occupancy", ctypes.c_int32), ("sigma", ctypes.c_int32),
-                ("layout", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("layout", ctypes.c_int32), ("energy", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
 
 
 class Instance(ctypes.Structure):
@@ -128,7 +130,7 @@ def _stream_handle(stream) -> ctypes.c_void_p:
 class Mechanism:
     """Device-resident mechanism tables (kin_create_mechanism). `desc` has the
     array attributes W, lnA, beta, Ea, reac, prod, rtype, eff, lnA0, beta0, Ea0
-    (e.g. a synth.Mechanism)."""
+    and optionally cp, Hf (e.g. a synth.Mechanism)."""
 
     def __init__(self, desc):
         self.n_species = int(len(desc.W))
@@ -141,11 +143,14 @@ class Mechanism:
             type=np.ascontiguousarray(desc.rtype, dtype=np.int8),
             eff=f64(np.asarray(desc.eff).reshape(-1)), lnA0=f64(desc.lnA0),
             beta0=f64(desc.beta0), Ea0=f64(desc.Ea0))
+        self.has_thermo = getattr(desc, "cp", None) is not None
+        if self.has_thermo:
+            self._arrays.update(cp=f64(desc.cp), Hf=f64(desc.Hf))
         a = self._arrays
         d = MechDesc(self.n_species, self.n_reactions,
-                     *[a[k].ctypes.data if a[k].size else None
+                     *[a[k].ctypes.data if k in a and a[k].size else None
                        for k in ("W", "lnA", "beta", "Ea", "reac", "prod", "type", "eff",
-                                 "lnA0", "beta0", "Ea0")])
+                                 "lnA0", "beta0", "Ea0", "cp", "Hf")])
         h = ctypes.c_void_p()
         _check(lib().kin_create_mechanism(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -163,8 +168,8 @@ class Mechanism:
 
     def workspace_bytes(self, method=RKC, precision=FP64, cells=0, block_threads=0,
                         blocks_per_sm=0, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT,
-                        sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO) -> int:
-        o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, sigma, layout, None)
+                        sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0) -> int:
+        o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, sigma, layout, energy, None)
         n = lib().kin_workspace_bytes(self.handle, ctypes.byref(o), int(cells))
         if n < 0:
             _check(int(n))
@@ -172,9 +177,9 @@ class Mechanism:
 
     def workspace(self, method=RKC, precision=FP64, cells=0, block_threads=0, blocks_per_sm=0,
                   device=None, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT,
-                  sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO) -> torch.Tensor:
+                  sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0) -> torch.Tensor:
         n = self.workspace_bytes(method, precision, cells, block_threads, blocks_per_sm, staging,
-                                 occupancy, sigma, layout)
+                                 occupancy, sigma, layout, energy)
         return torch.empty(n, dtype=torch.uint8, device=device or torch.device("cuda"))
 
 
@@ -206,14 +211,14 @@ class Cells:
 def integrate(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP64,
               status=None, stats=None, workspace=None, stream=None, max_steps=0,
               block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT,
-              sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO):
+              sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0):
     """Integrate every cell over dt in place (kin_integrate)."""
     cells, ld = _check_state(mech, T, p, Y)
     if workspace is None:
         workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm, Y.device,
-                                   staging, occupancy, sigma, layout)
+                                   staging, occupancy, sigma, layout, energy)
     o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging, occupancy, sigma,
-             layout, _stream_handle(stream))
+             layout, energy, _stream_handle(stream))
     _check(lib().kin_integrate(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), ld, float(dt),
                                float(rtol), float(atol), ctypes.byref(o), _ptr(status),
                                _ptr(stats), _ptr(workspace), workspace.numel()))
@@ -232,7 +237,7 @@ def make_instances(mech: Mechanism, parts: Sequence[Cells]):
 
 def integrate_batch(mech: Mechanism, parts: Sequence[Cells], method=RKC, precision=FP64,
                     workspace=None, stream=None, max_steps=0, block_threads=0, blocks_per_sm=0,
-                    staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT, sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO):
+                    staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT, sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0):
     """Integrate several instances in one persistent launch (kin_integrate_batch)."""
     if not 1 <= len(parts) <= MAX_INSTANCES:
         raise ValueError("1..%d instances per launch" % MAX_INSTANCES)
@@ -240,9 +245,9 @@ def integrate_batch(mech: Mechanism, parts: Sequence[Cells], method=RKC, precisi
     if workspace is None:
         cells = sum(int(c.T.numel()) for c in parts)
         workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm,
-                                   parts[0].Y.device, staging, occupancy, sigma, layout)
+                                   parts[0].Y.device, staging, occupancy, sigma, layout, energy)
     o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging, occupancy, sigma,
-             layout, _stream_handle(stream))
+             layout, energy, _stream_handle(stream))
     _check(lib().kin_integrate_batch(mech.handle, len(parts), arr, ctypes.byref(o),
                                      _ptr(workspace), workspace.numel()))
 
@@ -265,9 +270,9 @@ def version() -> str:
 
 def host_buffer(mech: Mechanism, cells: int, method=RKC, precision=FP64, device=None,
                 block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL,
-                occupancy=OCC_DEFAULT, sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO) -> torch.Tensor:
+                occupancy=OCC_DEFAULT, sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0) -> torch.Tensor:
     """Device buffer for integrate_host (kin_host_buffer_bytes)."""
-    o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, sigma, layout, None)
+    o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, sigma, layout, energy, None)
     n = lib().kin_host_buffer_bytes(mech.handle, ctypes.byref(o), int(cells))
     if n < 0:
         _check(int(n))
@@ -277,7 +282,7 @@ def host_buffer(mech: Mechanism, cells: int, method=RKC, precision=FP64, device=
 def integrate_host(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP64,
                    status=None, stats=None, buffer=None, stream=None, max_steps=0,
                    block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT,
-                   sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO):
+                   sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0):
     """kin_integrate_host: T, p, Y (in place), status, stats are CPU tensors
     (pin them for asynchronous copies). Returns after enqueueing; synchronise
     the stream before reading the results."""
@@ -289,9 +294,9 @@ def integrate_host(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precisi
         raise ValueError("Y must be [n_species, >= cells] with unit column stride")
     if buffer is None:
         buffer = host_buffer(mech, cells, method, precision, None, block_threads, blocks_per_sm,
-                             staging, occupancy, sigma, layout)
+                             staging, occupancy, sigma, layout, energy)
     o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging, occupancy, sigma,
-             layout, _stream_handle(stream))
+             layout, energy, _stream_handle(stream))
     _check(lib().kin_integrate_host(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), int(Y.stride(0)),
                                     float(dt), float(rtol), float(atol), ctypes.byref(o),
                                     _ptr(status), _ptr(stats), _ptr(buffer), buffer.numel()))

@@ -356,11 +356,24 @@ WORKLOADS = {
                                    inst_cells=(512, 65536)),
 }
 
+# The constant-pressure energy equation (Eq. (E:energy)) on the first three
+# workloads: same mechanisms and states, plus synthetic thermochemistry (seed
+# 4000+n). RKC uses the power-method sigma: with T in the state, Gershgorin row
+# sums add entries of different units (K per unit mass fraction and back) and
+# overestimate the spectral radius about tenfold.
+for _base, _sigma in (("h2_9sp_rkck", GERSHGORIN), ("h2co_13sp_rkc", POWER),
+                      ("ch4_53sp_rkc_mixed", POWER)):
+    WORKLOADS[_base + "_energy"] = dict(WORKLOADS[_base], sigma=_sigma, energy=True)
+
 
 def workload_mechanism(name: str) -> Mechanism:
     w = WORKLOADS[name]
-    return make_mechanism(w["n_species"], w["n_reactions"], w["elements"],
-                          w["tb"], w["fo"], seed=1000 + w["idx"])
+    m = make_mechanism(w["n_species"], w["n_reactions"], w["elements"],
+                       w["tb"], w["fo"], seed=1000 + w["idx"])
+    if w.get("energy"):
+        cp, Hf = make_thermo(m, 4000 + w["idx"])
+        m = dataclasses.replace(m, cp=cp, Hf=Hf)
+    return m
 
 
 def workload_states(name: str, mech: Mechanism, cells: Optional[int] = None,
