@@ -458,7 +458,7 @@ def run_kin(args):
                          "unit": "G %s lane-ops/s" % ("FP64" if bind64 else "FP32"),
                          "frac": achieved / peak, "traffic": tr,
                          "kernel": "kin_integrate launch (init + sort + integrate kernels, %s layout)"
-                                   % layout_name(km, method, shape),
+                                   % layout_name(km, method, shape, cells),
                          "peak_basis": "derived: %d %s lanes/SM/clk x 152 SMs x 2070 MHz"
                                        % ((FP64_LANES_PER_SM, "FP64") if bind64 else (FP32_LANES_PER_SM, "FP32")),
                          "kernel_ms": kavg, "fp64_ops_per_launch": ops64,
@@ -466,7 +466,9 @@ def run_kin(args):
                          "fp64_frac": t64 / (kavg * 1e-3 * 1e9), "fp32_frac": t32 / (kavg * 1e-3 * 1e9)},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * (5 if method == synth.RKC else 2),
+            "gpu_launches": args.steps * (5 if method == synth.RKC else
+                                          (1 if layout_name(km, method, shape, cells) == "warp-per-cell"
+                                           else 2)),
             "clocks": clk.summary(),
             "cell_status": np.bincount(status, minlength=4).tolist(),
             "mean_f_evals_per_cell": float(stats[:, 0].mean()),
@@ -582,12 +584,14 @@ def run_batched(args):
     return 0
 
 
-def layout_name(km, method, shape):
+def layout_name(km, method, shape, cells):
     from paper_1309_2710_gb300 import kin
+    import torch
     lay = shape.get("layout", kin.LAYOUT_AUTO)
     if lay == kin.LAYOUT_AUTO:
-        lay = (kin.LAYOUT_WARP if method == kin.RKC and km.n_reactions > kin.WARP_MIN_REACTIONS
-               else kin.LAYOUT_LANE)
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        small = cells < kin.WARP_MAX_CELLS_PER_SM * nsm
+        lay = kin.LAYOUT_WARP if km.n_reactions > kin.WARP_MIN_REACTIONS or small else kin.LAYOUT_LANE
     return "warp-per-cell" if lay == kin.LAYOUT_WARP else "lane-per-cell"
 
 

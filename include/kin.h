@@ -73,19 +73,22 @@ extern "C" {
 #define KIN_OCC_HIGH 1
 
 /* work decomposition across the GPU's lanes */
-#define KIN_LAYOUT_AUTO 0 /* library choice: KIN_LAYOUT_WARP for RKC when n_reactions >
-                             KIN_WARP_MIN_REACTIONS, else KIN_LAYOUT_LANE */
+#define KIN_LAYOUT_AUTO 0 /* library choice: KIN_LAYOUT_WARP when n_reactions >
+                             KIN_WARP_MIN_REACTIONS or the call has fewer than
+                             KIN_WARP_MAX_CELLS_PER_SM cells per SM of the device (too
+                             few to give every lane a cell), else KIN_LAYOUT_LANE */
 #define KIN_LAYOUT_LANE 1 /* one lane integrates one cell (the paper's thread-per-ODE
                              design, Section 3): per-cell arrays in the workspace or in
                              shared memory (kin_opts.staging) */
 #define KIN_LAYOUT_WARP 2 /* one warp integrates one cell: its 32 lanes share the
                              reactions and species of f; the cell's concentrations and
-                             rates of progress live in shared memory. RKC only
-                             (KIN_EUNSUPPORTED for RKCK). staging is ignored;
-                             occupancy selects the register budget (KIN_OCC_HIGH: 80
-                             registers for up to 64 species, 24 warps per SM);
-                             block_threads may be up to 256 */
+                             rates of progress live in shared memory. staging is
+                             ignored; for RKC, occupancy selects the register budget
+                             (KIN_OCC_HIGH: 80 registers for up to 64 state
+                             components, 24 warps per SM); block_threads may be up to
+                             256 */
 #define KIN_WARP_MIN_REACTIONS 256
+#define KIN_WARP_MAX_CELLS_PER_SM 64
 
 /* per-cell status */
 #define KIN_CELL_OK 0

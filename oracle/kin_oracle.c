@@ -381,7 +381,8 @@ static int rkck_cell(orc_f *F, int n, double *y, double dt, double rtol, double 
         for (i = 0; i < n; i++) {
             double tol = rtol * (fabs(y[i]) + fabs(hh * f0[i])) + atol;
             double r = fabs(err[i]) / tol;
-            if (!(r <= errmax)) errmax = r; /* NaN propagates into errmax */
+            if (isnan(r)) { errmax = NAN; break; } /* a blown-up component: reject */
+            if (r > errmax) errmax = r;
         }
         trace(st, hh, errmax, 0, errmax <= 1.0);
         if (errmax <= 1.0) {

@@ -40,8 +40,9 @@ def lane_candidates(full: bool = False):
                                occupancy=occupancy, layout=kin.LAYOUT_LANE)
 
 
-def warp_candidates(full: bool = False):
-    for occupancy in (kin.OCC_DEFAULT, kin.OCC_HIGH):
+def warp_candidates(full: bool = False, method: int = kin.RKC):
+    # the register budget is a choice of the RKC warp kernels only
+    for occupancy in ((kin.OCC_DEFAULT, kin.OCC_HIGH) if method == kin.RKC else (kin.OCC_DEFAULT,)):
         for threads in ((64, 128, 256) if full else (128, 256)):
             for warps in ((8, 12, 16, 24, 32) if full else (8, 16, 24)):
                 bps = warps * 32 // threads
@@ -53,14 +54,13 @@ def warp_candidates(full: bool = False):
 def candidates(full: bool = False, method: int = kin.RKC, n_reactions: int = 0):
     """Launch shapes to try; `full` adds more block sizes and lane counts.
     Mechanisms above the warp-layout threshold try warp shapes only (one lane
-    per cell is an order of magnitude slower there); smaller RKC mechanisms
-    try both layouts."""
-    if method == kin.RKC and n_reactions > kin.WARP_MIN_REACTIONS:
-        yield from warp_candidates(full)
+    per cell is an order of magnitude slower there); smaller mechanisms try
+    both layouts (one warp per cell wins on calls with few cells)."""
+    if n_reactions > kin.WARP_MIN_REACTIONS:
+        yield from warp_candidates(full, method)
         return
     yield from lane_candidates(full)
-    if method == kin.RKC:
-        yield from warp_candidates(False)
+    yield from warp_candidates(False, method)
 
 
 def time_config(mech, T0, p, Y0, dt, rtol, atol, method, precision, cfg, reps=2,

@@ -14,7 +14,7 @@ SOURCES = ["kernels.cu", "abi.cu", "no_alloc.cu", "inst_rkc_f64.cu", "inst_rkc_f
            "inst_rkck_f64.cu", "inst_rkck_f32.cu", "inst_warp_f64.cu", "inst_warp_f32.cu",
            "inst_warp_f64_hi.cu", "inst_warp_f32_hi.cu", "inst_energy_f64.cu", "inst_energy_f32.cu",
            "inst_warp_energy_f64.cu", "inst_warp_energy_f32.cu", "inst_warp_energy_f64_hi.cu",
-           "inst_warp_energy_f32_hi.cu"]
+           "inst_warp_energy_f32_hi.cu", "inst_warp_rkck_f64.cu", "inst_warp_rkck_f32.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

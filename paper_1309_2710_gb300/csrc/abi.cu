@@ -57,13 +57,17 @@ struct Grid {
     int layout;           // KIN_LAYOUT_LANE or KIN_LAYOUT_WARP (resolved)
 };
 
-int resolve_layout(const kin_mech* m, const kin_opts* o)
+// Automatic layout: one warp per cell for large mechanisms (a lane's working
+// set would stream from memory) and for calls too small to give every lane of
+// the GPU a cell; one lane per cell otherwise.
+int resolve_layout(const kin_mech* m, const kin_opts* o, int64_t cells, int nsm)
 {
     if (o->layout != KIN_LAYOUT_AUTO) return o->layout;
-    return (o->method == KIN_RKC && m->nR > KIN_WARP_MIN_REACTIONS) ? KIN_LAYOUT_WARP : KIN_LAYOUT_LANE;
+    if (m->nR > KIN_WARP_MIN_REACTIONS) return KIN_LAYOUT_WARP;
+    return cells < (int64_t)KIN_WARP_MAX_CELLS_PER_SM * nsm ? KIN_LAYOUT_WARP : KIN_LAYOUT_LANE;
 }
 
-int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
+int grid_for(const kin_mech* m, const kin_opts* o, int64_t cells, Grid* g)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -77,22 +81,26 @@ int grid_for(const kin_mech* m, const kin_opts* o, Grid* g)
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     if (o->energy && !m->thermo)
         return fail(KIN_EUNSUPPORTED, "the energy equation needs the mechanism's cp and Hf");
-    const int layout = resolve_layout(m, o);
+    const int layout = resolve_layout(m, o, cells, nsm);
     int threads = o->block_threads > 0 ? o->block_threads : 128;
     int occ = 0, cap = 0;
     if (layout == KIN_LAYOUT_WARP) {
-        if (o->method != KIN_RKC) return fail(KIN_EUNSUPPORTED, "the warp-per-cell layout implements RKC only");
         if (threads % 32 != 0 || threads > 256) return fail(KIN_EINVAL, "block_threads must be a multiple of 32 and <= 256");
         const size_t sm = warp_smem(m->dev, o->precision, threads);
         if (sm > (size_t)maxsm)
             return fail(KIN_EUNSUPPORTED, "warp layout needs %zu bytes of shared memory per block (max %d)", sm, maxsm);
         const int nV = m->nS + o->energy;
-        using OccFn = cudaError_t (*)(const MechDev&, int, int, int*);
-        // [energy][precision][occupancy]
-        static const OccFn fns[2][2][2] = {
-            {{occ_warp_f64_o0, occ_warp_f64_o1}, {occ_warp_f32_o0, occ_warp_f32_o1}},
-            {{occ_warp_f64_en_o0, occ_warp_f64_en_o1}, {occ_warp_f32_en_o0, occ_warp_f32_en_o1}}};
-        e = fns[o->energy][o->precision == KIN_MIXED][o->occupancy ? 1 : 0](m->dev, nV, threads, &occ);
+        if (o->method == KIN_RKCK) {
+            e = o->precision == KIN_MIXED ? occ_warp_rkck_f32(m->dev, nV, o->energy, threads, &occ)
+                                          : occ_warp_rkck_f64(m->dev, nV, o->energy, threads, &occ);
+        } else {
+            using OccFn = cudaError_t (*)(const MechDev&, int, int, int*);
+            // [energy][precision][occupancy]
+            static const OccFn fns[2][2][2] = {
+                {{occ_warp_f64_o0, occ_warp_f64_o1}, {occ_warp_f32_o0, occ_warp_f32_o1}},
+                {{occ_warp_f64_en_o0, occ_warp_f64_en_o1}, {occ_warp_f32_en_o0, occ_warp_f32_en_o1}}};
+            e = fns[o->energy][o->precision == KIN_MIXED][o->occupancy ? 1 : 0](m->dev, nV, threads, &occ);
+        }
         cap = occ;  // as many as fit
     } else {
         if (threads % 32 != 0 || threads > 128) return fail(KIN_EINVAL, "block_threads must be a multiple of 32 and <= 128");
@@ -349,7 +357,7 @@ int64_t kin_workspace_bytes(const kin_mech* m, const kin_opts* o, int64_t cells)
     int rc = check_opts(o);
     if (rc) return rc;
     Grid g;
-    rc = grid_for(m, o, &g);
+    rc = grid_for(m, o, cells, &g);
     if (rc) return rc;
     return ws_bytes(m, o, g, cells);
 }
@@ -390,7 +398,7 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     P.start[n] = total;
     if (total == 0) return KIN_OK;
     Grid g;
-    rc = grid_for(m, o, &g);
+    rc = grid_for(m, o, total, &g);
     if (rc) return rc;
     const int64_t need = ws_bytes(m, o, g, total);
     if (!ws) return fail(KIN_EINVAL, "workspace is NULL");
@@ -434,7 +442,10 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     cudaStream_t st = (cudaStream_t)o->stream;
     cudaError_t e = cudaMemsetAsync(base + w.header, 0, 512, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    if (g.layout == KIN_LAYOUT_WARP) {
+    if (g.layout == KIN_LAYOUT_WARP && o->method == KIN_RKCK) {
+        e = o->precision == KIN_MIXED ? launch_warp_rkck_f32(P, blocks, g.threads, st)
+                                      : launch_warp_rkck_f64(P, blocks, g.threads, st);
+    } else if (g.layout == KIN_LAYOUT_WARP) {
         using LaunchFn = cudaError_t (*)(Launch&, int, int, cudaStream_t);
         // [energy][precision][occupancy]
         static const LaunchFn fns[2][2][2] = {
@@ -520,7 +531,7 @@ int kin_rates(const kin_mech* m, int64_t cells, const double* T, const double* p
         return fail(KIN_EINVAL, "T, p, Y and dYdt must be device memory");
     kin_opts o{KIN_RKC, precision, 0, 0, 0, KIN_STAGE_GLOBAL, KIN_OCC_DEFAULT, 0, KIN_LAYOUT_LANE, 0, stream};
     Grid g;
-    int rc = grid_for(m, &o, &g);
+    int rc = grid_for(m, &o, cells, &g);
     if (rc) return rc;
     const int64_t need = ws_bytes(m, &o, g, cells);
     if (!ws || ((uintptr_t)ws) % 256) return fail(KIN_EINVAL, "workspace must be non-NULL and 256-byte aligned");

@@ -947,6 +947,7 @@ struct Integrator {
         Lane<double> Y = V(V_Y), F0 = V(V_F0), X = V(V_X);
         const double hh = S.hh;
         double errmax = 0.0;
+        bool blown = false;  // a NaN component makes the estimate non-finite (a rejection)
         for (int i = 0; i < L.nV; ++i) {
             double s5 = 0.0, e = 0.0;
             for (int l = 0; l < 6; ++l) {
@@ -957,8 +958,10 @@ struct Integrator {
             X[i] = Y[i] + hh * s5;
             const double tol = S.rtol * (fabs(Y[i]) + fabs(hh * F0[i])) + S.atol;
             const double r = fabs(hh * e) / tol;
-            if (!(r <= errmax)) errmax = r;
+            blown |= isnan(r);
+            if (r > errmax) errmax = r;
         }
+        if (blown) errmax = __longlong_as_double(0x7ff8000000000000ll);
         S.attempts++;
         if (errmax <= 1.0) {
             S.nacc++;

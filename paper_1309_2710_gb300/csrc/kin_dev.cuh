@@ -152,6 +152,10 @@ cudaError_t occ_warp_f64_en_o0(const MechDev& M, int nV, int threads, int* bps);
 cudaError_t occ_warp_f64_en_o1(const MechDev& M, int nV, int threads, int* bps);
 cudaError_t occ_warp_f32_en_o0(const MechDev& M, int nV, int threads, int* bps);
 cudaError_t occ_warp_f32_en_o1(const MechDev& M, int nV, int threads, int* bps);
+cudaError_t launch_warp_rkck_f64(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_warp_rkck_f32(Launch& L, int blocks, int threads, cudaStream_t st);
+cudaError_t occ_warp_rkck_f64(const MechDev& M, int nV, int energy, int threads, int* bps);
+cudaError_t occ_warp_rkck_f32(const MechDev& M, int nV, int energy, int threads, int* bps);
 size_t warp_smem(const MechDev& M, int precision, int threads);
 
 // Record `code` and a printf-style message as the calling thread's last

@@ -656,6 +656,209 @@ inline size_t warp_smem_bytes(const MechDev& M, int precision, int threads)
     return (size_t)warp_smem_elems(M) * (threads / 32) * 8;
 }
 
+// ---------------------------------------------------- RKCK, warp per cell --
+// Cash-Karp 5(4) with the step rule of Section 2.2 (Table 1, Eq. (E:hnew)),
+// one warp per cell, in one persistent kernel: RKCK needs no spectral radius
+// or initial-step estimate, so there is no pre-pass and no cost ordering. A
+// warp takes the next cell, forms its rate constants (cell-major in the
+// workspace, unless they follow T with the energy equation) and integrates
+// it with straight-line control flow; the decisions are those of the
+// lane-per-cell kernel.
+template <typename R, int NR, bool EN>
+struct WarpRKCK {
+    const Launch& L;
+    const MechDev& M;
+    R* C;
+    R* OM;
+    const R* Kc;
+    int lane, nV;
+    double Ctot, invCtot, atol, rtol, p;
+    int nfe;
+    double y[NR], x[NR], kx[NR], k[6][NR];
+
+    __device__ explicit WarpRKCK(const Launch& l) : L(l), M(l.M), Kc(nullptr), lane(threadIdx.x & 31), nV(l.nV)
+    {
+        C = reinterpret_cast<R*>(reinterpret_cast<double*>(kin_smem) +
+                                 (size_t)(threadIdx.x >> 5) * warp_smem_elems(M));
+        OM = C + M.nS;
+    }
+
+    __device__ __forceinline__ bool valid(int r) const { return lane + 32 * r < nV; }
+
+    __device__ __forceinline__ void f(const double (&in)[NR], double (&o)[NR])
+    {
+        if constexpr (EN) warp_feval_energy<R, NR>(M, p, C, OM, in, o, lane);
+        else warp_feval<R, R, NR>(M, Kc, C, OM, Ctot, invCtot, in, o, lane);
+        nfe++;
+    }
+
+    // Integrate over [0, dt] from y with k[0] = f(y); returns the cell status.
+    __device__ int run(double dt, int& nacc, int& nrej)
+    {
+        double t = 0.0, h = dt;  // first trial step: the whole flow step
+        int attempts = 0;
+        for (;;) {
+            if (attempts >= L.max_steps) return KIN_CELL_MAXSTEPS;
+            double hh = h;
+            bool last = false;
+            if (hh >= dt - t) {
+                hh = dt - t;
+                last = true;
+            }
+            for (int st = 1; st < 6; ++st) {  // stage points y + hh sum_l b_{st,l} k_l
+                // (stage indices are resolved with unrolled selects, so k stays
+                // in registers)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int l = 0; l < 5; ++l)
+                        if (l < st) acc += CK_B[st][l] * k[l][r];
+                    x[r] = y[r] + hh * acc;
+                }
+                f(x, kx);
+#pragma unroll
+                for (int l = 1; l < 6; ++l)
+                    if (l == st)
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) k[l][r] = kx[r];
+            }
+            double errmax = 0.0;
+            bool blown = false;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                double s5 = 0.0, e = 0.0;
+#pragma unroll
+                for (int l = 0; l < 6; ++l) {
+                    s5 += CK_C[l] * k[l][r];
+                    e += CK_E[l] * k[l][r];
+                }
+                x[r] = y[r] + hh * s5;
+                if (valid(r)) {
+                    const double tol = rtol * (fabs(y[r]) + fabs(hh * k[0][r])) + atol;
+                    const double q = fabs(hh * e) / tol;
+                    blown |= isnan(q);
+                    if (q > errmax) errmax = q;
+                }
+            }
+            // warp maximum; a NaN component makes the estimate non-finite
+            errmax = warp_max(errmax);
+            if (__any_sync(0xffffffffu, blown)) errmax = __longlong_as_double(0x7ff8000000000000ll);
+            attempts++;
+            if (errmax <= 1.0) {
+                nacc++;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) y[r] = x[r];
+                if (last) return KIN_CELL_OK;
+                t += hh;
+                const double hn = errmax == 0.0 ? 5.0 * hh : 0.9 * hh * pow(errmax, -0.2);
+                h = fmin(hn, 5.0 * hh);
+                f(y, k[0]);
+                bool fin = true;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) fin &= isfinite(k[0][r]);
+                if (!__all_sync(0xffffffffu, fin)) return KIN_CELL_NONFINITE;
+            } else {
+                nrej++;
+                const double hn = isfinite(errmax) ? 0.9 * hh * pow(errmax, -0.25) : 0.1 * hh;
+                h = fmax(hn, 0.1 * hh);
+                if (h < 1e-20 * dt) return KIN_CELL_HMIN;
+            }
+        }
+    }
+};
+
+template <typename R, int NR, bool EN>
+__global__ void __launch_bounds__(256, NR == 8 ? 1 : 2) warp_rkck_kernel(const __grid_constant__ Launch L)
+{
+    WarpRKCK<R, NR, EN> W(L);
+    const MechDev& M = L.M;
+    const int lane = W.lane, nK = M.nR + M.nFO, nS = M.nS;
+    for (;;) {
+        unsigned long long q = 0;
+        if (lane == 0) q = atomicAdd(L.queue, 1ull);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= (unsigned long long)L.total) return;
+        const int64_t g = (int64_t)q;
+        const int ii = find_inst(L, g);
+        const InstDev& I = L.inst[ii];
+        const int64_t c = g - L.start[ii];
+        const double T = I.T[c], p = I.p[c];
+        W.Ctot = p * 1e-6 / (R_GAS * T);
+        W.invCtot = 1.0 / W.Ctot;
+        W.atol = I.atol;
+        W.rtol = I.rtol;
+        W.p = p;
+        W.nfe = 0;
+        if constexpr (!EN) {
+            R* kc = reinterpret_cast<R*>(L.cell_k) + g * nK;
+            const double lnT = log(T), invT = 1.0 / T;
+            for (int qq = lane; qq < M.nR; qq += 32) {
+                const int j = M.rxn_perm[qq];
+                const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
+                kc[qq] = Tab<R>::ex(a);
+                const int fo = M.rxnp[qq].fo;
+                if (fo >= 0) {
+                    const double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
+                    kc[M.nR + fo] = Tab<R>::ex(a0 - a);
+                }
+            }
+            __syncwarp();
+            W.Kc = kc;
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int i = lane + 32 * r;
+            W.y[r] = i < nS ? I.Y[(int64_t)i * I.ldY + c] : (i == nS && EN ? T : 0.0);
+        }
+        W.f(W.y, W.k[0]);
+        bool fin = true;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) fin &= isfinite(W.k[0][r]);
+        int nacc = 0, nrej = 0, code = KIN_CELL_NONFINITE;
+        if (__all_sync(0xffffffffu, fin)) {
+            code = W.run(I.dt, nacc, nrej);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int i = lane + 32 * r;
+                if (i < nS) I.Y[(int64_t)i * I.ldY + c] = W.y[r];
+                else if (i == nS && EN) I.T[c] = W.y[r];
+            }
+        }
+        if (lane == 0) {
+            if (I.status) I.status[c] = (uint8_t)code;
+            if (I.stats) {
+                int32_t* st = I.stats + 4 * c;
+                st[0] = W.nfe;
+                st[1] = nacc;
+                st[2] = nrej;
+                st[3] = 0;
+            }
+        }
+    }
+}
+
+template <typename R, int NR, bool EN>
+inline cudaError_t warp_rkck_launch_nr(Launch& L, int blocks, int threads, cudaStream_t st)
+{
+    const size_t sm = warp_smem_bytes(L.M, L.precision, threads);
+    cudaError_t e = cudaFuncSetAttribute(warp_rkck_kernel<R, NR, EN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    warp_rkck_kernel<R, NR, EN><<<blocks, threads, sm, st>>>(L);
+    return cudaGetLastError();
+}
+
+template <typename R, int NR, bool EN>
+inline cudaError_t warp_rkck_occ_nr(const MechDev& M, int precision, int threads, int* bps)
+{
+    const size_t sm = warp_smem_bytes(M, precision, threads);
+    cudaError_t e = cudaFuncSetAttribute(warp_rkck_kernel<R, NR, EN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, warp_rkck_kernel<R, NR, EN>, threads, sm);
+}
+
 template <typename R, int NR, int OCC, bool EN>
 inline cudaError_t warp_launch_nr(Launch& L, int blocks, int threads, cudaStream_t st)
 {
@@ -706,6 +909,28 @@ inline cudaError_t warp_occ(const MechDev& M, int nV, int precision, int threads
     case 2: return warp_occ_nr<R, 2, OCC, EN>(M, precision, threads, bps);
     case 4: return warp_occ_nr<R, 4, OCC, EN>(M, precision, threads, bps);
     default: return warp_occ_nr<R, 8, OCC, EN>(M, precision, threads, bps);
+    }
+}
+
+template <typename R, bool EN>
+inline cudaError_t warp_rkck_launch(Launch& L, int blocks, int threads, cudaStream_t st)
+{
+    switch (warp_nr(L.nV)) {
+    case 1: return warp_rkck_launch_nr<R, 1, EN>(L, blocks, threads, st);
+    case 2: return warp_rkck_launch_nr<R, 2, EN>(L, blocks, threads, st);
+    case 4: return warp_rkck_launch_nr<R, 4, EN>(L, blocks, threads, st);
+    default: return warp_rkck_launch_nr<R, 8, EN>(L, blocks, threads, st);
+    }
+}
+
+template <typename R, bool EN>
+inline cudaError_t warp_rkck_occ(const MechDev& M, int nV, int precision, int threads, int* bps)
+{
+    switch (warp_nr(nV)) {
+    case 1: return warp_rkck_occ_nr<R, 1, EN>(M, precision, threads, bps);
+    case 2: return warp_rkck_occ_nr<R, 2, EN>(M, precision, threads, bps);
+    case 4: return warp_rkck_occ_nr<R, 4, EN>(M, precision, threads, bps);
+    default: return warp_rkck_occ_nr<R, 8, EN>(M, precision, threads, bps);
     }
 }
 

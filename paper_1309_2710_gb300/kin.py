@@ -25,6 +25,7 @@ OCC_DEFAULT, OCC_HIGH = 0, 1
 SIGMA_GERSHGORIN, SIGMA_POWER = 0, 1
 LAYOUT_AUTO, LAYOUT_LANE, LAYOUT_WARP = 0, 1, 2
 WARP_MIN_REACTIONS = 256
+WARP_MAX_CELLS_PER_SM = 64
 MAX_INSTANCES = 128
 
 

@@ -13,7 +13,8 @@ the tolerances, for one of the registered mechanisms. The server
   completion times (latency = completion - arrival).
 
 `one_launch_per_request` is the plain alternative: one kin_integrate per
-request, in arrival order, on one stream.
+request, in arrival order, on one stream, with the same kernels and launch
+shape as the server's slots.
 
 Every cell is integrated independently by the same per-lane arithmetic, so a
 request's result does not depend on what it is batched with (the tests check
@@ -224,11 +225,14 @@ def one_launch_per_request(groups: Dict[str, Group], requests: List[Request], de
             _h2d(Td, r.T)
             _h2d(pd, r.p)
             _h2d(Yd, r.Y)
-            need = g.mech.workspace_bytes(g.method, g.precision, n, sigma=g.sigma)
+            sh = g.shape
+            need = g.mech.workspace_bytes(g.method, g.precision, n, sh.get("block_threads", 0),
+                                          sh.get("blocks_per_sm", 0), sh.get("staging", 0),
+                                          sh.get("occupancy", 0), g.sigma, sh.get("layout", 0))
             if r.group not in ws or ws[r.group].numel() < need:
                 ws[r.group] = torch.empty(need, dtype=torch.uint8, device=device)
             kin.integrate(g.mech, Td, pd, Yd, r.dt, r.rtol, r.atol, g.method, g.precision,
-                          status=sd, workspace=ws[r.group], stream=stream, sigma=g.sigma)
+                          status=sd, workspace=ws[r.group], stream=stream, sigma=g.sigma, **sh)
             r.Y_out = torch.empty((nS, n), dtype=torch.float64, pin_memory=True)
             r.status = torch.empty(n, dtype=torch.uint8, pin_memory=True)
             r.Y_out.copy_(Yd, non_blocking=True)

@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
 same seeded inputs. Sizes span several blocks with ragged tails; the full-size
 13-species workload is checked on sampled cells in the benchmark's launch
-configuration."""
+configuration. These tests pin the lane-per-cell layout (LANE); the warp
+layout has its own file."""
 import numpy as np
 import pytest
 
@@ -23,6 +24,7 @@ from paper_1309_2710_gb300 import kin  # noqa: E402
 
 DEV = torch.device("cuda:0")
 MECHS = {}
+LANE = kin.LAYOUT_LANE
 
 
 def mech(name):
@@ -44,7 +46,7 @@ def run_gpu(km, T, p, Y, dt, rtol, atol, method, precision=kin.FP64, max_steps=2
     st = torch.full((cells,), 255, dtype=torch.uint8, device=DEV)
     sta = torch.zeros((cells, 4), dtype=torch.int32, device=DEV)
     kin.integrate(km, dev(T), dev(p), Yd, dt, rtol, atol, method, precision, status=st, stats=sta,
-                  max_steps=max_steps)
+                  max_steps=max_steps, layout=LANE)
     torch.cuda.synchronize()
     return Yd.cpu().numpy(), st.cpu().numpy(), sta.cpu().numpy()
 
@@ -170,7 +172,7 @@ def test_batched_c2h4_reduced():
     """16 uneven instances of the 111-species mechanism (sizes scaled by
     1/128) in one launch; every instance's sampled cells against the oracle."""
     m, km, om, parts, host = _c4_parts(1 / 128)
-    kin.integrate_batch(km, parts, kin.RKC)
+    kin.integrate_batch(km, parts, kin.RKC, layout=LANE)
     torch.cuda.synchronize()
     tot = 0
     for (T, p, Y, dt), c in zip(host, parts):
@@ -193,9 +195,9 @@ def test_batch_equals_separate_calls():
         dt = [1e-6, 3e-7, 1e-6, 2e-6][i]
         parts.append(kin.Cells(dev(T), dev(p), dev(Y), dt))
         Ys = dev(Y)
-        kin.integrate(km, dev(T), dev(p), Ys, dt, 1e-6, 1e-10, kin.RKC)
+        kin.integrate(km, dev(T), dev(p), Ys, dt, 1e-6, 1e-10, kin.RKC, layout=LANE)
         singles.append(Ys)
-    kin.integrate_batch(km, parts, kin.RKC)
+    kin.integrate_batch(km, parts, kin.RKC, layout=LANE)
     torch.cuda.synchronize()
     for c, Ys in zip(parts, singles):
         assert torch.equal(c.Y, Ys)
@@ -206,7 +208,7 @@ def test_zero_cells_is_a_noop():
     m, km, om = mech("h2co_13sp_rkc")
     Y = torch.ones((m.n_species, 4), dtype=torch.float64, device=DEV)
     e = torch.empty(0, dtype=torch.float64, device=DEV)
-    kin.integrate(km, e, e, Y, 1e-6, 1e-6, 1e-10, kin.RKC)
+    kin.integrate(km, e, e, Y, 1e-6, 1e-6, 1e-10, kin.RKC, layout=LANE)
     torch.cuda.synchronize()
     assert torch.all(Y == 1)
 
@@ -279,11 +281,11 @@ def test_batch_in_cuda_graph():
     parts = [kin.Cells(dev(T), dev(p), dev(Y), 1e-6, 1e-6, 1e-10,
                        torch.zeros(len(T), dtype=torch.uint8, device=DEV)) for T, p, Y in host]
     Y0 = [c.Y.clone() for c in parts]
-    ws = km.workspace(kin.RKC, kin.FP64, sum(sizes))
+    ws = km.workspace(kin.RKC, kin.FP64, sum(sizes), layout=LANE)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
-        kin.integrate_batch(km, parts, kin.RKC, workspace=ws)
+        kin.integrate_batch(km, parts, kin.RKC, workspace=ws, layout=LANE)
     torch.cuda.current_stream().wait_stream(s)
     torch.cuda.synchronize()
     eager = [c.Y.clone() for c in parts]
@@ -292,7 +294,7 @@ def test_batch_in_cuda_graph():
         c.Y.copy_(y0)
     torch.cuda.synchronize()
     with torch.cuda.graph(g):
-        kin.integrate_batch(km, parts, kin.RKC, workspace=ws)
+        kin.integrate_batch(km, parts, kin.RKC, workspace=ws, layout=LANE)
     for rep in range(2):
         for c, y0 in zip(parts, Y0):
             c.Y.copy_(y0)
@@ -318,7 +320,8 @@ def test_launch_shapes_are_bitwise_identical(method, name):
                   dict(block_threads=64, blocks_per_sm=1, staging=kin.STAGE_SHARED_ALL)]:
         Yd = dev(Y)
         try:
-            kin.integrate(km, dev(T), dev(p), Yd, w["dt"], w["rtol"], w["atol"], method, prec, **shape)
+            kin.integrate(km, dev(T), dev(p), Yd, w["dt"], w["rtol"], w["atol"], method, prec,
+                          layout=LANE, **shape)
         except kin.KinError as e:
             assert e.code == kin.KIN_EUNSUPPORTED  # staging that does not fit in shared memory
             continue
@@ -336,7 +339,7 @@ def run_gpu_sig(km, T, p, Y, dt, rtol, atol, precision, sigma, max_steps=20000):
     st = torch.full((cells,), 255, dtype=torch.uint8, device=DEV)
     sta = torch.zeros((cells, 4), dtype=torch.int32, device=DEV)
     kin.integrate(km, dev(T), dev(p), Yd, dt, rtol, atol, kin.RKC, precision, status=st, stats=sta,
-                  max_steps=max_steps, sigma=sigma)
+                  max_steps=max_steps, sigma=sigma, layout=LANE)
     torch.cuda.synchronize()
     return Yd.cpu().numpy(), st.cpu().numpy(), sta.cpu().numpy()
 

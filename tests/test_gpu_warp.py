@@ -229,18 +229,16 @@ def test_warp_step_limit_and_nonfinite_cell():
             tol=1e-5)
 
 
-def test_warp_zero_cells_and_rkck_refused():
+def test_warp_zero_cells_and_bad_block_size():
     name = "ch4_53sp_rkc_mixed"
     m, km, om = mech(name)
     Y = torch.ones((m.n_species, 4), dtype=torch.float64, device=DEV)
     e = torch.empty(0, dtype=torch.float64, device=DEV)
     kin.integrate(km, e, e, Y, 1e-6, 1e-6, 1e-10, kin.RKC, layout=WARP)
+    kin.integrate(km, e, e, Y, 1e-6, 1e-6, 1e-10, kin.RKCK, layout=WARP)
     torch.cuda.synchronize()
     assert torch.all(Y == 1)
     T, p, Yh = states(name, m, 4, 38)
-    with pytest.raises(kin.KinError) as ex:
-        kin.integrate(km, dev(T), dev(p), dev(Yh), 1e-6, 1e-6, 1e-10, kin.RKCK, layout=WARP)
-    assert ex.value.code == kin.KIN_EUNSUPPORTED
     with pytest.raises(kin.KinError) as ex:
         kin.integrate(km, dev(T), dev(p), dev(Yh), 1e-6, 1e-6, 1e-10, kin.RKC, layout=WARP,
                       block_threads=512)
@@ -267,3 +265,61 @@ def test_warp_full_size_ch4_sampled():
     assert e.max() <= 1e-5
     print("mass drift %.2e" % np.abs(Yg.sum(0) - 1).max())
     assert np.abs(Yg.sum(0) - 1).max() < 1e-7
+
+
+# ------------------------------------------------------------------- RKCK ---
+@pytest.mark.parametrize("name,cells,precision", [
+    ("h2_9sp_rkck", 4096, kin.FP64),       # the full 9-species workload, 1 slot
+    ("ch4_53sp_rkc_mixed", 77, kin.FP64),  # 2 slots
+    ("wide_140sp", 19, kin.FP64),          # 8 slots
+])
+def test_warp_rkck_against_oracle(name, cells, precision):
+    """Cash-Karp with one warp per cell (one persistent kernel, no pre-pass)."""
+    m, km, om = mech(name)
+    T, p, Y = states(name, m, cells, 71)
+    dt = 1e-7
+    Yd = dev(Y)
+    st = torch.full((cells,), 255, dtype=torch.uint8, device=DEV)
+    sta = torch.zeros((cells, 4), dtype=torch.int32, device=DEV)
+    kin.integrate(km, dev(T), dev(p), Yd, dt, 1e-6, 1e-10, kin.RKCK, precision, status=st,
+                  stats=sta, layout=WARP)
+    torch.cuda.synchronize()
+    Yo, sto, stao, _ = oracle.integrate(om, T, p, Y, dt, 1e-6, 1e-10, oracle.RKCK)
+    s = compare(Yd.cpu().numpy(), Yo, st.cpu().numpy(), sto, sta.cpu().numpy(), stao, 1e-10, 1e-6)
+    print("warp rkck", name, cells, s)
+
+
+def test_small_calls_choose_the_warp_layout():
+    """Fewer cells than KIN_WARP_MAX_CELLS_PER_SM per SM: the automatic layout is
+    one warp per cell (bit-identical to asking for it)."""
+    name = "h2_9sp_rkck"
+    m, km, om = mech(name)
+    T, p, Y = states(name, m, 4096, 72)
+    assert 4096 < kin.WARP_MAX_CELLS_PER_SM * torch.cuda.get_device_properties(0).multi_processor_count
+    out = []
+    for layout in (kin.LAYOUT_AUTO, WARP):
+        Yd = dev(Y)
+        kin.integrate(km, dev(T), dev(p), Yd, 1e-7, 1e-6, 1e-10, kin.RKCK, layout=layout)
+        out.append(Yd.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_warp_rkck_batch_equals_separate_and_nonfinite():
+    name = "h2_9sp_rkck"
+    m, km, om = mech(name)
+    parts, singles = [], []
+    for i, n in enumerate([50, 3, 400]):
+        T, p, Y = states(name, m, n, 80 + i)
+        if i == 2:
+            Y[3, 7] = np.nan
+        st = torch.zeros(n, dtype=torch.uint8, device=DEV)
+        parts.append(kin.Cells(dev(T), dev(p), dev(Y), 1e-7, 1e-6, 1e-10, st))
+        Ys = dev(Y)
+        kin.integrate(km, dev(T), dev(p), Ys, 1e-7, 1e-6, 1e-10, kin.RKCK, layout=WARP)
+        singles.append(Ys)
+    kin.integrate_batch(km, parts, kin.RKCK, layout=WARP)
+    torch.cuda.synchronize()
+    for c, Ys in zip(parts, singles):
+        assert torch.equal(torch.nan_to_num(c.Y), torch.nan_to_num(Ys))
+    s2 = parts[2].status.cpu().numpy()
+    assert s2[7] == kin.CELL_NONFINITE and (np.delete(s2, 7) == 0).all()
