@@ -72,6 +72,8 @@ class Mechanism:
     seed: int
     cp: Optional[np.ndarray] = None  # [n_species] J/(mol K), for the energy equation
     Hf: Optional[np.ndarray] = None  # [n_species] J/mol at 298.15 K
+    S0: Optional[np.ndarray] = None  # [n_species] J/(mol K) at 298.15 K and 1 atm (equilibrium
+    #                                  constants of reversible reactions)
 
     @property
     def n_species(self) -> int:
@@ -275,6 +277,35 @@ def make_thermo(mech: Mechanism, seed: int):
                                                             or v.get("H") == 2):
             Hf[i] = 0.0  # O2, N2, H2
     return cp, Hf
+
+
+def make_entropy(mech: Mechanism, seed: int):
+    """Synthetic standard molar entropies at 298.15 K and 1 atm [J/(mol K)],
+    for the equilibrium constants of reversible reactions: 110 + 35 (atoms - 1)
+    J/(mol K) (more atoms, more degrees of freedom; H ~ 115, O2 ~ 205, H2O
+    ~ 190 in real tables) times 1 + 0.1 U(-1, 1). Drawn from its own seed so
+    that the heat capacities and enthalpies of make_thermo do not change."""
+    rng = np.random.default_rng(seed)
+    atoms = np.asarray(mech.comp).sum(axis=1)
+    return (110.0 + 35.0 * (atoms - 1.0)) * (1.0 + 0.1 * rng.uniform(-1.0, 1.0, len(atoms)))
+
+
+def make_reversible_mechanism(n_species: int, n_reactions: int, elements: Sequence[str],
+                              tb_frac: float = 0.0, fo_frac: float = 0.0, seed: int = 0) -> Mechanism:
+    """A synthetic mechanism of reversible reactions with its thermochemistry
+    (cp, Hf, S0; seeds seed+3000 and seed+4000), each reaction written in its
+    exothermic direction (reaction enthalpy at 298.15 K <= 0), as mechanisms
+    usually list them: the fitted reverse rate is then the slow, endothermic
+    one. Convert with irrev.to_irreversible before integrating."""
+    m = make_mechanism(n_species, n_reactions, elements, tb_frac, fo_frac, seed)
+    cp, Hf = make_thermo(m, seed + 3000)
+    m = dataclasses.replace(m, cp=cp, Hf=Hf, S0=make_entropy(m, seed + 4000))
+    reac, prod = m.reac.copy(), m.prod.copy()
+    for j in range(n_reactions):
+        dH = sum(Hf[s] for s in m.prod[j] if s >= 0) - sum(Hf[s] for s in m.reac[j] if s >= 0)
+        if dH > 0:
+            reac[j], prod[j] = m.prod[j], m.reac[j]
+    return dataclasses.replace(m, reac=reac, prod=prod)
 
 
 def make_states(mech: Mechanism, cells: int, T_range=(1000.0, 1500.0),

@@ -4,7 +4,7 @@ import types
 import numpy as np
 
 
-def mech(W, reactions, eff_rows=None, cp=None, Hf=None):
+def mech(W, reactions, eff_rows=None, cp=None, Hf=None, S0=None):
     """reactions: list of dicts with reac, prod (species index lists of length
     <= 2), A, beta, Ea, type (0/1/2), and for falloff A0, beta0, Ea0. cp, Hf:
     optional species thermochemistry (J/(mol K), J/mol) for the energy
@@ -28,7 +28,8 @@ def mech(W, reactions, eff_rows=None, cp=None, Hf=None):
                                  reac=reac, prod=prod, rtype=rtype, eff=eff,
                                  lnA0=lnA0, beta0=beta0, Ea0=Ea0,
                                  cp=None if cp is None else np.asarray(cp, float),
-                                 Hf=None if Hf is None else np.asarray(Hf, float))
+                                 Hf=None if Hf is None else np.asarray(Hf, float),
+                                 S0=None if S0 is None else np.asarray(S0, float))
 
 
 def a_to_b(k, W=28.0):
