@@ -359,6 +359,36 @@ __device__ __forceinline__ double rms(int n, double rtol, double atol, Lane<doub
 // the difference itself, and the iteration would neither converge nor agree
 // with the FP64 estimate.
 constexpr double SIG_SQRT_U = 1.4901161193847656e-08;  // sqrt(2^-52)
+
+// ------------------------------------------ Newton-refined FP64 helpers ---
+// The per-lane step control runs on the FP64 pipe while the other lanes of
+// the warp wait, so its FP64 instruction count matters. These two helpers
+// take a single-precision seed (the SFU reciprocal, the FP32 cube root) and
+// refine it with one Newton-Raphson step in FP64, which squares the seed's
+// relative error (<= 2^-21 -> ~2^-42, about 2e-13): enough for an error norm
+// and a step-size factor, which only need to reproduce the FP64 decisions.
+// Outside the FP32 normal range the plain FP64 operation is used.
+__device__ __forceinline__ bool f32_normal(double x)
+{
+    const int e = (__double2hiint(x) >> 20) & 0x7ff;  // biased exponent (sign ignored)
+    return e > 1023 - 120 && e < 1023 + 120;
+}
+
+// 1/x: Newton r1 = r0 + r0 (1 - x r0).
+__device__ __forceinline__ double rcp_newton(double x)
+{
+    if (!f32_normal(x)) return 1.0 / x;
+    const double r0 = (double)__frcp_rn((float)x);
+    return fma(r0, fma(-x, r0, 1.0), r0);
+}
+
+// a^(1/3) for a > 0: Newton c1 = c0 - (c0^3 - a) / (3 c0^2) = c0 + (a / c0^2 - c0) / 3.
+__device__ __forceinline__ double cbrt_newton(double a)
+{
+    if (!f32_normal(a)) return cbrt(a);
+    const double c0 = (double)cbrtf((float)a);
+    return c0 + (a * rcp_newton(c0 * c0) - c0) * (1.0 / 3.0);
+}
 struct PowerState {
     int k;
     double prev, dyn, sig;
@@ -821,7 +851,7 @@ struct Integrator {
                 const double v = c0 * y + mu * w1 + nu * W2[i] + mt * FJ[i] + gt * F0[i];
                 if (fin) {
                     const double sc = S.atol + S.rtol * fmax(fabs(y), fabs(w1));
-                    const double r = v / sc;
+                    const double r = v * rcp_newton(sc);
                     acc += r * r;
                 } else {
                     WN[i] = v;
@@ -869,7 +899,7 @@ struct Integrator {
             S.nacc++;
             // err^(1/3) once; err^(2/3) = (err^(1/3))^2; the previous step's
             // err^(1/3) is kept for the predictive factor (one division).
-            const double c3 = cbrt(err);
+            const double c3 = err > 0.0 ? cbrt_newton(err) : 0.0;
             double fac;
             if (err == 0.0) fac = 10.0;
             else if (S.have_prev && !S.last_rejected && S.cprev > 0.0)
