@@ -86,7 +86,8 @@ int grid_for(const kin_mech* m, const kin_opts* o, int64_t cells, Grid* g)
     int occ = 0, cap = 0;
     if (layout == KIN_LAYOUT_WARP) {
         if (threads % 32 != 0 || threads > 256) return fail(KIN_EINVAL, "block_threads must be a multiple of 32 and <= 256");
-        const size_t sm = warp_smem(m->dev, o->precision, threads);
+        const int cell_lanes = warp_cell_lanes(o->method, m->nS + o->energy);
+        const size_t sm = warp_smem(m->dev, o->precision, threads) * (32 / cell_lanes);
         if (sm > (size_t)maxsm)
             return fail(KIN_EUNSUPPORTED, "warp layout needs %zu bytes of shared memory per block (max %d)", sm, maxsm);
         const int nV = m->nS + o->energy;
@@ -407,7 +408,9 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     if (!is_device_ptr(ws)) return fail(KIN_EINVAL, "workspace must be device memory");
     // never more lanes (warps in the warp layout) than cells
     int blocks = g.blocks;
-    const int per_block = g.layout == KIN_LAYOUT_WARP ? g.threads / 32 : g.threads;
+    const int per_block = g.layout == KIN_LAYOUT_WARP
+                              ? g.threads / warp_cell_lanes(o->method, m->nS + o->energy)
+                              : g.threads;
     const int64_t want = (total + per_block - 1) / per_block;
     if (want < blocks) blocks = (int)want;
     const int64_t nslots = (int64_t)blocks * g.threads;

@@ -158,6 +158,11 @@ cudaError_t occ_warp_rkck_f64(const MechDev& M, int nV, int energy, int threads,
 cudaError_t occ_warp_rkck_f32(const MechDev& M, int nV, int energy, int threads, int* bps);
 size_t warp_smem(const MechDev& M, int precision, int threads);
 
+// Lanes that integrate one cell in the warp-per-cell layout: a whole warp,
+// or half of one (two cells per warp) for RKCK on states of at most 16
+// components.
+inline int warp_cell_lanes(int method, int nV) { return method == KIN_RKCK && nV <= 16 ? 16 : 32; }
+
 // Record `code` and a printf-style message as the calling thread's last
 // error (kin_last_error); returns `code`.
 int set_last_error(int code, const char* fmt, ...);

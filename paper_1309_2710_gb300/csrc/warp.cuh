@@ -36,6 +36,24 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+// Butterfly sum over a group of G lanes (a whole warp, or a 16-lane half
+// that owns one cell); mask names the group's lanes.
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v, unsigned mask)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ double group_max(double v, unsigned mask)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, o));
+    return v;
+}
+
 __device__ __forceinline__ double warp_max(double v)
 {
 #pragma unroll
@@ -67,33 +85,33 @@ __host__ __device__ __forceinline__ int warp_smem_elems(const MechDev& M)
 // reaction-permutation order followed by k0/kinf per falloff ordinal (written
 // earlier in the same pre-pass kernel, so not read through the read-only
 // cache); C and OM are the warp's shared arrays.
-template <typename R, typename KT, int NR>
+template <typename R, typename KT, int NR, int G = 32>
 __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C, R* OM,
                                            double Ctot, double invCtot, const double (&x)[NR],
-                                           double (&out)[NR], int lane)
+                                           double (&out)[NR], int lane, unsigned mask = 0xffffffffu)
 {
     const int nS = M.nS, nR = M.nR, nM = M.nM;
     const R* __restrict__ invW = Tab<R>::invW(M);
     R s = R(0);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const int i = lane + 32 * r;
+        const int i = lane + G * r;
         if (i < nS) {
             const R m = (R)x[r] * invW[i];
             C[i] = m;
             s += m;
         }
     }
-    s = warp_sum(s);
+    s = group_sum<G>(s, mask);
     const R rho = (R)Ctot * (R(1) / s);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const int i = lane + 32 * r;
+        const int i = lane + G * r;
         if (i < nS) C[i] = C[i] * rho;
     }
-    __syncwarp();
+    __syncwarp(mask);
     const R* __restrict__ effT = TabW<R>::effT(M);
-    for (int q = lane; q < nR; q += 32) {
+    for (int q = lane; q < nR; q += G) {
         const Rxn rx = M.rxnp[q];
         R v = (R)Kc[q];
         if (rx.r0 >= 0) v *= C[rx.r0];
@@ -117,12 +135,12 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
         }
         OM[q] = v;
     }
-    __syncwarp();
+    __syncwarp(mask);
     const R* __restrict__ nu = Tab<R>::nu(M);
     const double invrho = (double)s * invCtot;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const int i = lane + 32 * r;
+        const int i = lane + G * r;
         double o = 0.0;
         if (i < nS) {
             R w0 = R(0), w1 = R(0);
@@ -137,7 +155,7 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
         }
         out[r] = o;
     }
-    __syncwarp();  // C and OM are rewritten by the next evaluation
+    __syncwarp(mask);  // C and OM are rewritten by the next evaluation
 }
 
 // Element r of a register vector for a warp-uniform r.
@@ -149,35 +167,36 @@ __device__ __forceinline__ double reg_get(const double (&v)[NR], int r);
 // rate constants of its reactions from T (they follow T at every
 // evaluation); the enthalpy sum and the mixture heat capacity are FP64 warp
 // sums, and dT/dt lands in T's slot.
-template <typename R, int NR>
+template <typename R, int NR, int G = 32>
 __device__ __forceinline__ void warp_feval_energy(const MechDev& M, double p, R* C, R* OM,
-                                                  const double (&x)[NR], double (&out)[NR], int lane)
+                                                  const double (&x)[NR], double (&out)[NR], int lane,
+                                                  unsigned mask = 0xffffffffu)
 {
     const int nS = M.nS, nR = M.nR, nM = M.nM;
-    const double T = __shfl_sync(0xffffffffu, reg_get(x, nS >> 5), nS & 31);
+    const double T = __shfl_sync(mask, reg_get(x, nS / G), nS % G, G);
     const double lnT = log(T), invT = 1.0 / T;
     const double Ctot = p * 1e-6 * invT * (1.0 / R_GAS), invCtot = 1.0 / Ctot;
     const R* __restrict__ invW = Tab<R>::invW(M);
     R s = R(0);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const int i = lane + 32 * r;
+        const int i = lane + G * r;
         if (i < nS) {
             const R m = (R)x[r] * invW[i];
             C[i] = m;
             s += m;
         }
     }
-    s = warp_sum(s);
+    s = group_sum<G>(s, mask);
     const R rho = (R)Ctot * (R(1) / s);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const int i = lane + 32 * r;
+        const int i = lane + G * r;
         if (i < nS) C[i] = C[i] * rho;
     }
-    __syncwarp();
+    __syncwarp(mask);
     const R* __restrict__ effT = TabW<R>::effT(M);
-    for (int q = lane; q < nR; q += 32) {
+    for (int q = lane; q < nR; q += G) {
         const Rxn rx = M.rxnp[q];
         const int j = M.rxn_perm[q];
         const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
@@ -204,13 +223,13 @@ __device__ __forceinline__ void warp_feval_energy(const MechDev& M, double p, R*
         }
         OM[q] = v;
     }
-    __syncwarp();
+    __syncwarp(mask);
     const R* __restrict__ nu = Tab<R>::nu(M);
     const double invrho = (double)s * invCtot, dT = T - T_REF;
     double hw = 0.0, cpm = 0.0;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const int i = lane + 32 * r;
+        const int i = lane + G * r;
         double o = 0.0;
         if (i < nS) {
             R w0 = R(0), w1 = R(0);
@@ -228,13 +247,13 @@ __device__ __forceinline__ void warp_feval_energy(const MechDev& M, double p, R*
         }
         out[r] = o;
     }
-    hw = warp_sum(hw);
-    cpm = warp_sum(cpm);
+    hw = group_sum<G>(hw, mask);
+    cpm = group_sum<G>(cpm, mask);
     const double dTdt = -hw * invrho / cpm;
 #pragma unroll
     for (int r = 0; r < NR; ++r)
-        if (lane + 32 * r == nS) out[r] = dTdt;
-    __syncwarp();  // C and OM are rewritten by the next evaluation
+        if (lane + G * r == nS) out[r] = dTdt;
+    __syncwarp(mask);  // C and OM are rewritten by the next evaluation
 }
 
 // Element r of a register vector for a warp-uniform r.
@@ -658,13 +677,16 @@ inline size_t warp_smem_bytes(const MechDev& M, int precision, int threads)
 
 // ---------------------------------------------------- RKCK, warp per cell --
 // Cash-Karp 5(4) with the step rule of Section 2.2 (Table 1, Eq. (E:hnew)),
-// one warp per cell, in one persistent kernel: RKCK needs no spectral radius
-// or initial-step estimate, so there is no pre-pass and no cost ordering. A
-// warp takes the next cell, forms its rate constants (cell-major in the
-// workspace, unless they follow T with the energy equation) and integrates
-// it with straight-line control flow; the decisions are those of the
-// lane-per-cell kernel.
-template <typename R, int NR, bool EN>
+// one group of G lanes per cell (G = 32, a warp; or G = 16, two cells per
+// warp, for states of at most 16 components, where a whole warp would leave
+// most of its FP64 lanes idle), in one persistent kernel: RKCK needs no
+// spectral radius or initial-step estimate, so there is no pre-pass and no
+// cost ordering. A group takes the next cell, forms its rate constants
+// (cell-major in the workspace, unless they follow T with the energy
+// equation) and integrates it with straight-line control flow; the decisions
+// are those of the lane-per-cell kernel. Every collective of a group names
+// only the group's lanes, so the two halves of a warp may diverge.
+template <typename R, int NR, bool EN, int G>
 struct WarpRKCK {
     const Launch& L;
     const MechDev& M;
@@ -672,23 +694,26 @@ struct WarpRKCK {
     R* OM;
     const R* Kc;
     int lane, nV;
+    unsigned mask;  // the group's lanes
     double Ctot, invCtot, atol, rtol, p;
     int nfe;
     double y[NR], x[NR], kx[NR], k[6][NR];
 
-    __device__ explicit WarpRKCK(const Launch& l) : L(l), M(l.M), Kc(nullptr), lane(threadIdx.x & 31), nV(l.nV)
+    __device__ explicit WarpRKCK(const Launch& l)
+        : L(l), M(l.M), Kc(nullptr), lane(threadIdx.x & (G - 1)), nV(l.nV),
+          mask(G == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16)))
     {
         C = reinterpret_cast<R*>(reinterpret_cast<double*>(kin_smem) +
-                                 (size_t)(threadIdx.x >> 5) * warp_smem_elems(M));
+                                 (size_t)(threadIdx.x / G) * warp_smem_elems(M));
         OM = C + M.nS;
     }
 
-    __device__ __forceinline__ bool valid(int r) const { return lane + 32 * r < nV; }
+    __device__ __forceinline__ bool valid(int r) const { return lane + G * r < nV; }
 
     __device__ __forceinline__ void f(const double (&in)[NR], double (&o)[NR])
     {
-        if constexpr (EN) warp_feval_energy<R, NR>(M, p, C, OM, in, o, lane);
-        else warp_feval<R, R, NR>(M, Kc, C, OM, Ctot, invCtot, in, o, lane);
+        if constexpr (EN) warp_feval_energy<R, NR, G>(M, p, C, OM, in, o, lane, mask);
+        else warp_feval<R, R, NR, G>(M, Kc, C, OM, Ctot, invCtot, in, o, lane, mask);
         nfe++;
     }
 
@@ -741,9 +766,9 @@ struct WarpRKCK {
                     if (q > errmax) errmax = q;
                 }
             }
-            // warp maximum; a NaN component makes the estimate non-finite
-            errmax = warp_max(errmax);
-            if (__any_sync(0xffffffffu, blown)) errmax = __longlong_as_double(0x7ff8000000000000ll);
+            // group maximum; a NaN component makes the estimate non-finite
+            errmax = group_max<G>(errmax, mask);
+            if (__any_sync(mask, blown)) errmax = __longlong_as_double(0x7ff8000000000000ll);
             attempts++;
             if (errmax <= 1.0) {
                 nacc++;
@@ -757,7 +782,7 @@ struct WarpRKCK {
                 bool fin = true;
 #pragma unroll
                 for (int r = 0; r < NR; ++r) fin &= isfinite(k[0][r]);
-                if (!__all_sync(0xffffffffu, fin)) return KIN_CELL_NONFINITE;
+                if (!__all_sync(mask, fin)) return KIN_CELL_NONFINITE;
             } else {
                 nrej++;
                 const double hn = isfinite(errmax) ? 0.9 * hh * pow(errmax, -0.25) : 0.1 * hh;
@@ -768,16 +793,16 @@ struct WarpRKCK {
     }
 };
 
-template <typename R, int NR, bool EN>
+template <typename R, int NR, bool EN, int G>
 __global__ void __launch_bounds__(256, NR == 8 ? 1 : 2) warp_rkck_kernel(const __grid_constant__ Launch L)
 {
-    WarpRKCK<R, NR, EN> W(L);
+    WarpRKCK<R, NR, EN, G> W(L);
     const MechDev& M = L.M;
     const int lane = W.lane, nK = M.nR + M.nFO, nS = M.nS;
     for (;;) {
         unsigned long long q = 0;
         if (lane == 0) q = atomicAdd(L.queue, 1ull);
-        q = __shfl_sync(0xffffffffu, q, 0);
+        q = __shfl_sync(W.mask, q, 0, G);
         if (q >= (unsigned long long)L.total) return;
         const int64_t g = (int64_t)q;
         const int ii = find_inst(L, g);
@@ -793,7 +818,7 @@ __global__ void __launch_bounds__(256, NR == 8 ? 1 : 2) warp_rkck_kernel(const _
         if constexpr (!EN) {
             R* kc = reinterpret_cast<R*>(L.cell_k) + g * nK;
             const double lnT = log(T), invT = 1.0 / T;
-            for (int qq = lane; qq < M.nR; qq += 32) {
+            for (int qq = lane; qq < M.nR; qq += G) {
                 const int j = M.rxn_perm[qq];
                 const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
                 kc[qq] = Tab<R>::ex(a);
@@ -803,12 +828,12 @@ __global__ void __launch_bounds__(256, NR == 8 ? 1 : 2) warp_rkck_kernel(const _
                     kc[M.nR + fo] = Tab<R>::ex(a0 - a);
                 }
             }
-            __syncwarp();
+            __syncwarp(W.mask);
             W.Kc = kc;
         }
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            const int i = lane + 32 * r;
+            const int i = lane + G * r;
             W.y[r] = i < nS ? I.Y[(int64_t)i * I.ldY + c] : (i == nS && EN ? T : 0.0);
         }
         W.f(W.y, W.k[0]);
@@ -816,11 +841,11 @@ __global__ void __launch_bounds__(256, NR == 8 ? 1 : 2) warp_rkck_kernel(const _
 #pragma unroll
         for (int r = 0; r < NR; ++r) fin &= isfinite(W.k[0][r]);
         int nacc = 0, nrej = 0, code = KIN_CELL_NONFINITE;
-        if (__all_sync(0xffffffffu, fin)) {
+        if (__all_sync(W.mask, fin)) {
             code = W.run(I.dt, nacc, nrej);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                const int i = lane + 32 * r;
+                const int i = lane + G * r;
                 if (i < nS) I.Y[(int64_t)i * I.ldY + c] = W.y[r];
                 else if (i == nS && EN) I.T[c] = W.y[r];
             }
@@ -838,25 +863,32 @@ __global__ void __launch_bounds__(256, NR == 8 ? 1 : 2) warp_rkck_kernel(const _
     }
 }
 
-template <typename R, int NR, bool EN>
+inline int rkck_group(int nV) { return warp_cell_lanes(KIN_RKCK, nV); }
+
+inline size_t group_smem_bytes(const MechDev& M, int threads, int G)
+{
+    return (size_t)warp_smem_elems(M) * (threads / G) * 8;
+}
+
+template <typename R, int NR, bool EN, int G>
 inline cudaError_t warp_rkck_launch_nr(Launch& L, int blocks, int threads, cudaStream_t st)
 {
-    const size_t sm = warp_smem_bytes(L.M, L.precision, threads);
-    cudaError_t e = cudaFuncSetAttribute(warp_rkck_kernel<R, NR, EN>,
+    const size_t sm = group_smem_bytes(L.M, threads, G);
+    cudaError_t e = cudaFuncSetAttribute(warp_rkck_kernel<R, NR, EN, G>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    warp_rkck_kernel<R, NR, EN><<<blocks, threads, sm, st>>>(L);
+    warp_rkck_kernel<R, NR, EN, G><<<blocks, threads, sm, st>>>(L);
     return cudaGetLastError();
 }
 
-template <typename R, int NR, bool EN>
-inline cudaError_t warp_rkck_occ_nr(const MechDev& M, int precision, int threads, int* bps)
+template <typename R, int NR, bool EN, int G>
+inline cudaError_t warp_rkck_occ_nr(const MechDev& M, int threads, int* bps)
 {
-    const size_t sm = warp_smem_bytes(M, precision, threads);
-    cudaError_t e = cudaFuncSetAttribute(warp_rkck_kernel<R, NR, EN>,
+    const size_t sm = group_smem_bytes(M, threads, G);
+    cudaError_t e = cudaFuncSetAttribute(warp_rkck_kernel<R, NR, EN, G>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, warp_rkck_kernel<R, NR, EN>, threads, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, warp_rkck_kernel<R, NR, EN, G>, threads, sm);
 }
 
 template <typename R, int NR, int OCC, bool EN>
@@ -915,22 +947,25 @@ inline cudaError_t warp_occ(const MechDev& M, int nV, int precision, int threads
 template <typename R, bool EN>
 inline cudaError_t warp_rkck_launch(Launch& L, int blocks, int threads, cudaStream_t st)
 {
+    if (rkck_group(L.nV) == 16) return warp_rkck_launch_nr<R, 1, EN, 16>(L, blocks, threads, st);
     switch (warp_nr(L.nV)) {
-    case 1: return warp_rkck_launch_nr<R, 1, EN>(L, blocks, threads, st);
-    case 2: return warp_rkck_launch_nr<R, 2, EN>(L, blocks, threads, st);
-    case 4: return warp_rkck_launch_nr<R, 4, EN>(L, blocks, threads, st);
-    default: return warp_rkck_launch_nr<R, 8, EN>(L, blocks, threads, st);
+    case 1: return warp_rkck_launch_nr<R, 1, EN, 32>(L, blocks, threads, st);
+    case 2: return warp_rkck_launch_nr<R, 2, EN, 32>(L, blocks, threads, st);
+    case 4: return warp_rkck_launch_nr<R, 4, EN, 32>(L, blocks, threads, st);
+    default: return warp_rkck_launch_nr<R, 8, EN, 32>(L, blocks, threads, st);
     }
 }
 
 template <typename R, bool EN>
 inline cudaError_t warp_rkck_occ(const MechDev& M, int nV, int precision, int threads, int* bps)
 {
+    (void)precision;
+    if (rkck_group(nV) == 16) return warp_rkck_occ_nr<R, 1, EN, 16>(M, threads, bps);
     switch (warp_nr(nV)) {
-    case 1: return warp_rkck_occ_nr<R, 1, EN>(M, precision, threads, bps);
-    case 2: return warp_rkck_occ_nr<R, 2, EN>(M, precision, threads, bps);
-    case 4: return warp_rkck_occ_nr<R, 4, EN>(M, precision, threads, bps);
-    default: return warp_rkck_occ_nr<R, 8, EN>(M, precision, threads, bps);
+    case 1: return warp_rkck_occ_nr<R, 1, EN, 32>(M, threads, bps);
+    case 2: return warp_rkck_occ_nr<R, 2, EN, 32>(M, threads, bps);
+    case 4: return warp_rkck_occ_nr<R, 4, EN, 32>(M, threads, bps);
+    default: return warp_rkck_occ_nr<R, 8, EN, 32>(M, threads, bps);
     }
 }
 
