@@ -111,10 +111,9 @@ def algorithmic_work(m, method, precision, sigma, stats, energy=False):
     f(y) that each estimate starts from. RKC vector work (FP64): per attempt
     w_1 and the error estimate and norm (8 nS), per further stage the
     recursion (5 nS); Gershgorin: 3 nS per column; power method: 4 nS per
-    product; initial step 6 nS. The Gershgorin count is exact. The power
-    method's number of products per estimate is not recorded, so it is bounded
-    from the side that keeps the count a lower bound: 20 products in FP64
-    (fewer stages), 2 in mixed precision (fewer FP64 evaluations)."""
+    product; initial step 6 nS. The per-cell counters split the f evaluations
+    between spectral-radius estimates and rate evaluations, so the count is
+    exact (with the energy equation an exp or log counts as one operation)."""
     nS = m.n_species + (1 if energy else 0)  # state length
     fo = feval_ops_energy(m) if energy else feval_ops(m)
     mixed = precision == synth.MIXED
@@ -129,15 +128,13 @@ def algorithmic_work(m, method, precision, sigma, stats, energy=False):
     if method != synth.RKC:
         return float((nfe * f64 + att * 38 * nS).sum()), float((nfe * f32).sum()), True
     base = 1 if mixed else 0
-    if sigma == synth.GERSHGORIN:
-        sig_evals = nsig * (nS + base)
-        sig_vec = nsig * 3 * nS * nS
-        exact = True
-    else:
-        per = 2 if mixed else 20
-        sig_evals = np.minimum(nsig * (per + base), np.maximum(nfe - 2 - att, 0))
-        sig_vec = (sig_evals - nsig * base) * 4 * nS
-        exact = False
+    # the fifth statistic counts the f evaluations inside the spectral-radius
+    # estimates (Gershgorin columns or power products, plus the FP64 base
+    # evaluation of the mixed path), so the split is exact
+    sig_evals = stats[:, 4].astype(np.float64)
+    per_eval = 3 * nS if sigma == synth.GERSHGORIN else 4 * nS
+    sig_vec = (sig_evals - nsig * base) * per_eval
+    exact = not energy  # an exp or log of the energy path counts as one operation
     rate_evals = nfe - sig_evals            # f(y0), the initial-step probe, the stages
     stages = rate_evals - 2
     vec = (stages - att) * 5 * nS + att * 8 * nS + sig_vec + 6 * nS
@@ -331,7 +328,7 @@ def run_kin(args):
     Y0d = torch.as_tensor(Y0, device=dev).contiguous()
     Yd = torch.empty_like(Y0d)
     st = torch.zeros(cells, dtype=torch.uint8, device=dev)
-    sta = torch.zeros((cells, 4), dtype=torch.int32, device=dev)
+    sta = torch.zeros((cells, kin.NSTATS), dtype=torch.int32, device=dev)
     shape = dict(block_threads=0, blocks_per_sm=0, staging=kin.STAGE_GLOBAL, occupancy=kin.OCC_DEFAULT,
                  layout=kin.LAYOUT_AUTO)
     if args.shape:
@@ -502,7 +499,7 @@ def run_batched(args):
         Y0s.append(Yd.clone())
         parts.append(kin.Cells(torch.as_tensor(T, device=dev), torch.as_tensor(p, device=dev), Yd, dt,
                                w["rtol"], w["atol"], torch.zeros(n, dtype=torch.uint8, device=dev),
-                               torch.zeros((n, 4), dtype=torch.int32, device=dev)))
+                               torch.zeros((n, kin.NSTATS), dtype=torch.int32, device=dev)))
     total = sum(n for n, _ in inst)
     sigma = w["sigma"] if args.sigma == "default" else (synth.POWER if args.sigma == "power"
                                                          else synth.GERSHGORIN)

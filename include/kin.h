@@ -175,11 +175,14 @@ typedef struct {
     int64_t ldY;       /* >= cells */
     double dt, rtol, atol; /* dt > 0, rtol > 0, atol >= 0, all finite */
     uint8_t *status;   /* [cells] KIN_CELL_*, or NULL */
-    int32_t *stats;    /* [cells][4]: f evaluations, accepted steps, rejected
-                          steps, spectral-radius estimates; or NULL */
+    int32_t *stats;    /* [cells][KIN_NSTATS]: f evaluations, accepted steps,
+                          rejected steps, spectral-radius estimates, and the f
+                          evaluations spent inside those estimates (part of the
+                          first count); or NULL */
 } kin_instance;
 
 #define KIN_MAX_INSTANCES 128
+#define KIN_NSTATS 5 /* statistics per cell */
 
 /* Copy and validate a mechanism, upload its tables to the current device and
  * precompute the RKC coefficient table there (Section 2.3, s = 2..250).

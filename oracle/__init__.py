@@ -204,9 +204,9 @@ def rkc_single(om: Mech, T, p, y, h, s):
 def integrate(om: Mech, T, p, Y, dt, rtol, atol, method, max_steps=0, nthreads=0,
               energy=False):
     """Integrate every cell over dt. Y is [n_species, cells] (species-major).
-    Returns (Y_new, status[cells] uint8, stats[cells, 4] int32 = nfe, accepted,
-    rejected, sigma estimates, threads used), and T_new with `energy` (T is
-    then integrated with the energy equation)."""
+    Returns (Y_new, status[cells] uint8, stats[cells, 5] int32 = nfe, accepted,
+    rejected, sigma estimates, f evaluations inside them, threads used), and
+    T_new with `energy` (T is then integrated with the energy equation)."""
     T = np.array(T, dtype=np.float64, copy=True); p = _f64(p)
     if energy and not om.has_thermo:
         raise ValueError("the energy equation needs the mechanism's thermochemistry")
@@ -214,7 +214,7 @@ def integrate(om: Mech, T, p, Y, dt, rtol, atol, method, max_steps=0, nthreads=0
     cells = int(T.shape[0])
     assert Yn.shape == (om.n_species, cells)
     status = np.zeros(cells, dtype=np.uint8)
-    stats = np.zeros((cells, 4), dtype=np.int32)
+    stats = np.zeros((cells, 5), dtype=np.int32)
     nt = lib().orc_integrate(om.ptr, cells, _ptr(T), _ptr(p), _ptr(Yn), cells, float(dt),
                              float(rtol), float(atol), int(method), int(max_steps),
                              _ptr(status), _ptr(stats), int(nthreads), int(bool(energy)))

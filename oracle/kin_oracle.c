@@ -345,7 +345,7 @@ static void rkck_step(orc_f *F, int n, const double *y, const double *f0, double
 /* Per-cell counters, and an optional per-attempt trace (step size tried,
  * error measure, stage count or 0 for RKCK, 1 if accepted) used by tests. */
 typedef struct {
-    int nfe, nacc, nrej, nsig;
+    int nfe, nacc, nrej, nsig, nfs; /* nfs: f evaluations inside sigma estimates */
     int cap, len;
     double *tr_h, *tr_err;
     int *tr_s, *tr_acc;
@@ -622,11 +622,14 @@ static int rkc_cell(orc_f *F, int n, double *y, double dt, double rtol, double a
     double t = 0.0, hmin = 1e-20 * dt, sigma, h, h0, e0, err_prev = 0.0, h_prev = 0.0;
     int i, status = 0, attempts = 0, since_sigma = 0, sigma_here, last_rejected = 0;
     int have_prev = 0;
+    long nfe0;
 
     feval(F, y, f0);
     if (!all_finite(n, f0)) { free(v); return 3; }
     memcpy(ev, f0, sizeof(double) * n); /* first power-method direction */
+    nfe0 = F->nfe;
     sigma = estimate_sigma(F, n, est, y, f0, atol, x, fx, rowsum, ev);
+    st->nfs += (int)(F->nfe - nfe0);
     st->nsig++;
     sigma_here = 1;
     if (!isfinite(sigma)) { free(v); return 3; }
@@ -651,7 +654,9 @@ static int rkc_cell(orc_f *F, int n, double *y, double dt, double rtol, double a
         int s, last = 0;
         if (attempts >= max_steps) { status = 1; break; }
         if (since_sigma >= 25 || (last_rejected && !sigma_here)) {
+            nfe0 = F->nfe;
             sigma = estimate_sigma(F, n, est, y, f0, atol, x, fx, rowsum, ev);
+            st->nfs += (int)(F->nfe - nfe0);
             st->nsig++;
             since_sigma = 0;
             sigma_here = 1;
@@ -745,7 +750,8 @@ void orc_rkc_single(const void *mp, double T, double p, const double *y, double 
  * component and writes it back to Tc (the mechanism needs thermochemistry;
  * without it nothing is done and -1 is returned).
  * Per-cell outputs (any may be NULL): status, and stats[cell] =
- * {f evaluations, accepted steps, rejected steps, sigma estimates}.
+ * {f evaluations, accepted steps, rejected steps, sigma estimates, f
+ * evaluations inside the sigma estimates}.
  * Returns the number of threads used.
  * nthreads > 0 sets the OpenMP thread count when built with OpenMP
  * (<= 0: all available threads). */
@@ -767,7 +773,7 @@ int orc_integrate(const void *mp, int64_t cells, double *Tc, const double *pc,
         double *y = (double *)xmalloc(sizeof(double) * n);
         double *k = (double *)xmalloc(sizeof(double) * 2 * m->nR);
         double *work = (double *)xmalloc(sizeof(double) * (2 * m->nS + 2 * m->nR));
-        orc_stats S = {0, 0, 0, 0, 0, 0, NULL, NULL, NULL, NULL};
+        orc_stats S = {0, 0, 0, 0, 0, 0, 0, NULL, NULL, NULL, NULL};
         orc_f F;
         for (i = 0; i < m->nS; i++) y[i] = Y[(int64_t)i * ldY + c];
         if (energy) y[m->nS] = Tc[c];
@@ -782,10 +788,11 @@ int orc_integrate(const void *mp, int64_t cells, double *Tc, const double *pc,
         if (energy) Tc[c] = y[m->nS];
         if (status) status[c] = (uint8_t)st;
         if (stats) {
-            stats[4 * c + 0] = (int32_t)F.nfe;
-            stats[4 * c + 1] = S.nacc;
-            stats[4 * c + 2] = S.nrej;
-            stats[4 * c + 3] = S.nsig;
+            stats[5 * c + 0] = (int32_t)F.nfe;
+            stats[5 * c + 1] = S.nacc;
+            stats[5 * c + 2] = S.nrej;
+            stats[5 * c + 3] = S.nsig;
+            stats[5 * c + 4] = S.nfs;
         }
         free(y); free(k); free(work);
     }
@@ -803,7 +810,7 @@ int orc_trace_cell(const void *mp, double T, double p, double *y, double dt, dou
     int n = m->nS + (energy ? 1 : 0), st;
     double *k = (double *)xmalloc(sizeof(double) * 2 * m->nR);
     double *work = (double *)xmalloc(sizeof(double) * (2 * m->nS + 2 * m->nR));
-    orc_stats S = {0, 0, 0, 0, cap, 0, tr_h, tr_err, (int *)tr_s, (int *)tr_acc};
+    orc_stats S = {0, 0, 0, 0, 0, cap, 0, tr_h, tr_err, (int *)tr_s, (int *)tr_acc};
     orc_f F;
     if (energy && !m->cp) { free(k); free(work); return -1; }
     if (max_steps <= 0) max_steps = 100000;

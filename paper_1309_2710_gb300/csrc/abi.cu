@@ -169,7 +169,7 @@ extern "C" {
 
 const char* kin_last_error(void) { return g_err; }
 
-const char* kin_version(void) { return "kin 0.1 (sm_103a)"; }
+const char* kin_version(void) { return "kin 0.2 (sm_103a)"; }
 
 int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
 {
@@ -439,6 +439,7 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     P.cell_sig = (double*)(base + w.sig);
     P.cell_h = (double*)(base + w.h);
     P.cell_nfe = (int32_t*)(base + w.nfe);
+    P.cell_nfs = (int32_t*)(base + w.nfs);
     P.cell_st = (uint8_t*)(base + w.st);
     P.order = (int32_t*)(base + w.order);
     if (total > INT32_MAX) return fail(KIN_EINVAL, "more than 2^31-1 cells in one call");
@@ -479,7 +480,7 @@ int64_t kin_host_buffer_bytes(const kin_mech* m, const kin_opts* o, int64_t cell
     if (cells < 0) return fail(KIN_EINVAL, "cells < 0");
     int64_t ws = kin_workspace_bytes(m, o, cells);
     if (ws < 0) return ws;
-    return al256(ws) + 2 * al256(8 * cells) + al256(8 * cells * m->nS) + al256(cells) + al256(16 * cells);
+    return al256(ws) + 2 * al256(8 * cells) + al256(8 * cells * m->nS) + al256(cells) + al256(4 * KIN_NSTATS * cells);
 }
 
 int kin_integrate_host(const kin_mech* m, int64_t cells, double* T, const double* p, double* Y,
@@ -514,7 +515,7 @@ int kin_integrate_host(const kin_mech* m, int64_t cells, double* T, const double
     e = cudaMemcpy2DAsync(Y, 8 * ldY, Yd, 8 * cells, 8 * cells, m->nS, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && o->energy) e = cudaMemcpyAsync(T, Td, 8 * cells, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, sd, cells, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && stats) e = cudaMemcpyAsync(stats, xd, 16 * cells, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && stats) e = cudaMemcpyAsync(stats, xd, 4 * KIN_NSTATS * cells, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
     return KIN_OK;
 }

@@ -130,6 +130,7 @@ WsLayout ws_layout(const MechDev& M, int precision, int sigma_method, int energy
     w.sig = off;     off += al256(8 * cells);
     w.h = off;       off += al256(8 * cells);
     w.nfe = off;     off += al256(4 * cells);
+    w.nfs = off;     off += al256(4 * cells);
     w.st = off;      off += al256(cells);
     w.order = off;   off += al256(4 * cells);
     w.total = off;

@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
         for (int i = 0; i < n; ++i) ok &= isfinite(F0[i]);
         uint8_t st = ok ? 0 : KIN_CELL_NONFINITE;
         double sigma = 0.0, h = I.dt;
-        int nfe = 1;
+        int nfe = 1, nfs = 0;  // f evaluations, and those inside the sigma estimate
         // base point of the FP64 spectral-radius differences: f(y0) itself in
         // FP64, its FP64 re-evaluation in the mixed-precision path
         Lane<double> B = F0;
@@ -509,6 +509,7 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
             B = W.V(V_B);
             fsig(Y, B);
             nfe++;
+            nfs++;
         }
         if (METHOD == KIN_RKC && ok && L.sigma_method == KIN_SIGMA_POWER) {
             Lane<double> EV = W.EVcell(g);
@@ -518,6 +519,7 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
             for (;;) {
                 fsig(X, FX);
                 nfe++;
+                nfs++;
                 if (power_post(n, Y, B, EV, X, FX, P)) break;
             }
             sigma = 1.2 * P.sig;
@@ -532,6 +534,7 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
             }
             for (int i = 0; i < n; ++i) sigma = fmax(sigma, RS[i]);
             nfe += n;
+            nfs += n;
         }
         if (METHOD == KIN_RKC && ok) {
             if (!isfinite(sigma)) {
@@ -553,6 +556,7 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
         L.cell_sig[g] = sigma;
         L.cell_h[g] = h;
         L.cell_nfe[g] = nfe;
+        L.cell_nfs[g] = nfs;
         L.cell_st[g] = st;
     }
 }
@@ -605,7 +609,7 @@ struct LaneState {
     long long cell;  // index within the instance
     int inst;
     int phase, st, j, s, col;
-    int attempts, nacc, nrej, nsig, nfe;
+    int attempts, nacc, nrej, nsig, nfe, nfs;
     int since_sigma;
     bool last, last_rejected, have_prev, sigma_here;
     int iw1, iw2;  // RKC: slots of w_{j-1}, w_{j-2}
@@ -641,6 +645,7 @@ struct Integrator {
             S.attempts = S.nacc = S.nrej = 0;
             S.nsig = METHOD == KIN_RKC ? 1 : 0;
             S.nfe = L.cell_nfe[g];
+            S.nfs = L.cell_nfs[g];
             const uint8_t pre = L.cell_st[g];
             if (pre != 0) {  // Y stays as given
                 finish_stats(S, pre);
@@ -693,11 +698,12 @@ struct Integrator {
         const InstDev& I = L.inst[S.inst];
         if (I.status) I.status[S.cell] = (uint8_t)code;
         if (I.stats) {
-            int32_t* st = I.stats + 4 * S.cell;
+            int32_t* st = I.stats + KIN_NSTATS * S.cell;
             st[0] = S.nfe;
             st[1] = S.nacc;
             st[2] = S.nrej;
             st[3] = S.nsig;
+            st[4] = S.nfs;
         }
     }
 
@@ -1043,6 +1049,7 @@ struct Integrator {
                 feval<R>(M, S.Ctot, S.invCtot, K, KR, W.C, W.OM, V(S.in_v), V(S.out_v));
             }
             S.nfe++;
+            S.nfs += sig;
             const int code = METHOD == KIN_RKC ? rkc_post(S) : rkck_post(S);
             if (code >= 0) {
                 store(S, code);

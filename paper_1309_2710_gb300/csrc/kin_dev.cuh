@@ -94,6 +94,7 @@ struct Launch {
     double* cell_sig;               // RKC spectral radius at y0 [total]
     double* cell_h;                 // first trial step [total]
     int32_t* cell_nfe;              // f evaluations spent before the main kernel [total]
+    int32_t* cell_nfs;              // ... of which inside the spectral-radius estimate [total]
     uint8_t* cell_st;               // 0, or a final status decided before the main kernel
     int32_t* order;                 // processing order (longest predicted first) [total]
     int64_t start[KIN_MAX_INSTANCES + 1];  // prefix sums of instance cells
@@ -102,7 +103,7 @@ struct Launch {
 
 // Workspace layout for `cells` cells and `nslots` lanes.
 struct WsLayout {
-    int64_t header, vec, lane_r, lane_sig, cell_k, f0, ev, sig, h, nfe, st, order, total;
+    int64_t header, vec, lane_r, lane_sig, cell_k, f0, ev, sig, h, nfe, nfs, st, order, total;
 };
 WsLayout ws_layout(const MechDev& M, int precision, int sigma_method, int energy, int64_t nslots,
                    int64_t cells);

@@ -278,7 +278,7 @@ struct WarpRKC {
     const R* Kc;
     int lane, nV;  // nV: state length, nS + 1 with the energy equation
     double Ctot, invCtot, atol, rtol, p;
-    int nfe, nsig;
+    int nfe, nsig, nfs;  // f evaluations, sigma estimates, f evaluations inside them
     double y[NR], f0[NR], w1[NR], w2[NR], fx[NR], x[NR], ev[NR];
 
     __device__ explicit WarpRKC(const Launch& l) : L(l), M(l.M), Kc(nullptr), lane(threadIdx.x & 31), nV(l.nV)
@@ -309,6 +309,7 @@ struct WarpRKC {
         else
             warp_feval<double, double, NR>(M, Kc, C, OM, Ctot, invCtot, in, o, lane);
         nfe++;
+        nfs++;
     }
 
     // Weighted RMS norm, Eq. (E:rmsE), of d with T_i = atol + rtol max(|a_i|, |b_i|).
@@ -545,6 +546,7 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_ini
         W.rtol = I.rtol;
         W.p = p;
         W.nfe = 0;
+        W.nfs = 0;
         if constexpr (!EN) {
             // rate constants (Eq. (E:rxn-const)) in permutation order; with the
             // energy equation they follow T and are formed inside f instead
@@ -604,6 +606,7 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_ini
             L.cell_sig[g] = sig;
             L.cell_h[g] = h;
             L.cell_nfe[g] = W.nfe;
+            L.cell_nfs[g] = W.nfs;
             L.cell_st[g] = st;
         }
     }
@@ -628,6 +631,7 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_int
         const int64_t c = g - L.start[ii];
         int nacc = 0, nrej = 0, code;
         W.nfe = L.cell_nfe[g];
+        W.nfs = L.cell_nfs[g];
         W.nsig = 1;
         const uint8_t pre = L.cell_st[g];
         if (pre != 0) {
@@ -659,11 +663,12 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_int
         if (lane == 0) {
             if (I.status) I.status[c] = (uint8_t)code;
             if (I.stats) {
-                int32_t* st = I.stats + 4 * c;
+                int32_t* st = I.stats + KIN_NSTATS * c;
                 st[0] = W.nfe;
                 st[1] = nacc;
                 st[2] = nrej;
                 st[3] = W.nsig;
+                st[4] = W.nfs;
             }
         }
     }
@@ -853,11 +858,12 @@ __global__ void __launch_bounds__(256, NR == 8 ? 1 : 2) warp_rkck_kernel(const _
         if (lane == 0) {
             if (I.status) I.status[c] = (uint8_t)code;
             if (I.stats) {
-                int32_t* st = I.stats + 4 * c;
+                int32_t* st = I.stats + KIN_NSTATS * c;
                 st[0] = W.nfe;
                 st[1] = nacc;
                 st[2] = nrej;
                 st[3] = 0;
+                st[4] = 0;
             }
         }
     }

@@ -27,6 +27,7 @@ LAYOUT_AUTO, LAYOUT_LANE, LAYOUT_WARP = 0, 1, 2
 WARP_MIN_REACTIONS = 256
 WARP_MAX_CELLS_PER_SM = 64
 MAX_INSTANCES = 128
+NSTATS = 5  # per-cell statistics: f evals, accepted, rejected, sigma estimates, f evals in them
 
 
 class KinError(RuntimeError):
@@ -196,6 +197,18 @@ def _check_state(mech: Mechanism, T, p, Y):
     return cells, int(Y.stride(0))
 
 
+def _check_outputs(cells: int, status, stats, cuda: bool = True):
+    """The library writes `cells` status bytes and cells x NSTATS int32
+    statistics: refuse smaller or mistyped buffers before the call."""
+    if status is not None and (status.dtype != torch.uint8 or not status.is_contiguous()
+                               or status.numel() < cells or status.is_cuda != cuda):
+        raise ValueError("status must be a contiguous uint8 tensor of >= %d entries" % cells)
+    if stats is not None and (stats.dtype != torch.int32 or not stats.is_contiguous()
+                              or stats.numel() < cells * NSTATS or stats.is_cuda != cuda):
+        raise ValueError("stats must be a contiguous int32 tensor of >= %d x %d entries"
+                         % (cells, NSTATS))
+
+
 @dataclass
 class Cells:
     """One instance of a batched call: device tensors and its dt/tolerances."""
@@ -215,6 +228,7 @@ def integrate(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP
               sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0):
     """Integrate every cell over dt in place (kin_integrate)."""
     cells, ld = _check_state(mech, T, p, Y)
+    _check_outputs(cells, status, stats)
     if workspace is None:
         workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm, Y.device,
                                    staging, occupancy, sigma, layout, energy)
@@ -229,6 +243,7 @@ def make_instances(mech: Mechanism, parts: Sequence[Cells]):
     arr = (Instance * len(parts))()
     for i, c in enumerate(parts):
         cells, ld = _check_state(mech, c.T, c.p, c.Y)
+        _check_outputs(cells, c.status, c.stats)
         arr[i] = Instance(cells, c.T.data_ptr(), c.p.data_ptr(), c.Y.data_ptr(), ld,
                           float(c.dt), float(c.rtol), float(c.atol),
                           None if c.status is None else c.status.data_ptr(),
@@ -293,6 +308,7 @@ def integrate_host(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precisi
             raise ValueError("%s must be a float64 CPU tensor" % name)
     if Y.dim() != 2 or Y.shape[0] != mech.n_species or Y.stride(1) != 1 or Y.shape[1] < cells:
         raise ValueError("Y must be [n_species, >= cells] with unit column stride")
+    _check_outputs(cells, status, stats, cuda=False)
     if buffer is None:
         buffer = host_buffer(mech, cells, method, precision, None, block_threads, blocks_per_sm,
                              staging, occupancy, sigma, layout, energy)

@@ -45,7 +45,7 @@ def run(km, T, p, Y, dt, method, precision=kin.FP64, sigma=kin.SIGMA_POWER, layo
     cells = T.shape[0]
     Td, Yd = dev(T), dev(Y)
     st = torch.full((cells,), 255, dtype=torch.uint8, device=DEV)
-    sta = torch.zeros((cells, 4), dtype=torch.int32, device=DEV)
+    sta = torch.zeros((cells, kin.NSTATS), dtype=torch.int32, device=DEV)
     kin.integrate(km, Td, dev(p), Yd, dt, 1e-6, 1e-10, method, precision, status=st, stats=sta,
                   max_steps=max_steps, sigma=sigma, layout=layout, energy=1, **shape)
     torch.cuda.synchronize()

@@ -46,7 +46,7 @@ def test_converted_mechanism_against_oracle(energy, layout):
     T, p, Y = synth.make_states(mi, 300, T_range=(1800.0, 2800.0), seed=2102)
     Td, Yd = dev(T), dev(Y)
     st = torch.zeros(300, dtype=torch.uint8, device=DEV)
-    sta = torch.zeros((300, 4), dtype=torch.int32, device=DEV)
+    sta = torch.zeros((300, kin.NSTATS), dtype=torch.int32, device=DEV)
     kin.integrate(km, Td, dev(p), Yd, 1e-4, 1e-6, 1e-10, kin.RKC, status=st, stats=sta,
                   sigma=kin.SIGMA_POWER, energy=energy, layout=layout, max_steps=20000)
     torch.cuda.synchronize()

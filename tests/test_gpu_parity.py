@@ -44,7 +44,7 @@ def run_gpu(km, T, p, Y, dt, rtol, atol, method, precision=kin.FP64, max_steps=2
     Yd = torch.zeros((Y.shape[0], ld), dtype=torch.float64, device=DEV)
     Yd[:, :cells] = dev(Y)
     st = torch.full((cells,), 255, dtype=torch.uint8, device=DEV)
-    sta = torch.zeros((cells, 4), dtype=torch.int32, device=DEV)
+    sta = torch.zeros((cells, kin.NSTATS), dtype=torch.int32, device=DEV)
     kin.integrate(km, dev(T), dev(p), Yd, dt, rtol, atol, method, precision, status=st, stats=sta,
                   max_steps=max_steps, layout=LANE)
     torch.cuda.synchronize()
@@ -164,7 +164,7 @@ def _c4_parts(scale):
         host.append((T, p, Y, dt))
         parts.append(kin.Cells(dev(T), dev(p), dev(Y), dt, 1e-6, 1e-10,
                                torch.zeros(n, dtype=torch.uint8, device=DEV),
-                               torch.zeros((n, 4), dtype=torch.int32, device=DEV)))
+                               torch.zeros((n, kin.NSTATS), dtype=torch.int32, device=DEV)))
     return m, km, om, parts, host
 
 
@@ -337,7 +337,7 @@ def run_gpu_sig(km, T, p, Y, dt, rtol, atol, precision, sigma, max_steps=20000):
     cells = T.shape[0]
     Yd = dev(Y)
     st = torch.full((cells,), 255, dtype=torch.uint8, device=DEV)
-    sta = torch.zeros((cells, 4), dtype=torch.int32, device=DEV)
+    sta = torch.zeros((cells, kin.NSTATS), dtype=torch.int32, device=DEV)
     kin.integrate(km, dev(T), dev(p), Yd, dt, rtol, atol, kin.RKC, precision, status=st, stats=sta,
                   max_steps=max_steps, sigma=sigma, layout=LANE)
     torch.cuda.synchronize()

@@ -58,7 +58,7 @@ def run(km, T, p, Y, dt, precision=kin.FP64, sigma=kin.SIGMA_GERSHGORIN, layout=
     Yd = torch.zeros((Y.shape[0], ld), dtype=torch.float64, device=DEV)
     Yd[:, :cells] = dev(Y)
     st = torch.full((cells,), 255, dtype=torch.uint8, device=DEV)
-    sta = torch.zeros((cells, 4), dtype=torch.int32, device=DEV)
+    sta = torch.zeros((cells, kin.NSTATS), dtype=torch.int32, device=DEV)
     kin.integrate(km, dev(T), dev(p), Yd, dt, 1e-6, 1e-10, kin.RKC, precision, status=st,
                   stats=sta, max_steps=max_steps, sigma=sigma, layout=layout, **shape)
     torch.cuda.synchronize()
@@ -280,7 +280,7 @@ def test_warp_rkck_against_oracle(name, cells, precision):
     dt = 1e-7
     Yd = dev(Y)
     st = torch.full((cells,), 255, dtype=torch.uint8, device=DEV)
-    sta = torch.zeros((cells, 4), dtype=torch.int32, device=DEV)
+    sta = torch.zeros((cells, kin.NSTATS), dtype=torch.int32, device=DEV)
     kin.integrate(km, dev(T), dev(p), Yd, dt, 1e-6, 1e-10, kin.RKCK, precision, status=st,
                   stats=sta, layout=WARP)
     torch.cuda.synchronize()

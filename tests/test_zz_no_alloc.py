@@ -29,7 +29,7 @@ def _run(fn_name, km, T, p, Y, dt, ws=None):
     pd = torch.as_tensor(p, device=DEV)
     Yd = torch.as_tensor(np.ascontiguousarray(Y), device=DEV)
     st = torch.zeros(cells, dtype=torch.uint8, device=DEV)
-    sta = torch.zeros((cells, 4), dtype=torch.int32, device=DEV)
+    sta = torch.zeros((cells, kin.NSTATS), dtype=torch.int32, device=DEV)
     o = kin.Opts(kin.RKC, kin.FP64, 0, 0, 0, 0, 0, 0, kin.LAYOUT_AUTO, 0,
                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     args = [km.handle, cells, kin._ptr(Td), kin._ptr(pd), kin._ptr(Yd), cells, dt, 1e-6, 1e-10,
