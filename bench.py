@@ -85,7 +85,7 @@ def feval_ops(m) -> int:
         for j in range(m.n_reactions):
             if int(np.sum(m.prod[j] == i)) != int(np.sum(m.reac[j] == i)):
                 o += 1  # one fused multiply-add per net nonzero
-    o += 2 * nS + 1
+    o += nS + 1  # 1/rho, dY_i/dt = (W_i omega_i) / rho (W_i folded into the coefficients)
     return o
 
 
@@ -106,7 +106,7 @@ def algorithmic_work(m, method, precision, sigma, stats, energy=False):
     one operation; conversions are not counted.
 
     f costs feval_ops(m). In the mixed path its rate arithmetic is FP32 and
-    only the final scaling dY/dt = W omega / rho (2 nS + 1) is FP64, while
+    only the final scaling dY/dt = W omega / rho (nS + 1) is FP64, while
     every spectral-radius evaluation is FP64, including the re-evaluation of
     f(y) that each estimate starts from. RKC vector work (FP64): per attempt
     w_1 and the error estimate and norm (8 nS), per further stage the
@@ -120,7 +120,7 @@ def algorithmic_work(m, method, precision, sigma, stats, energy=False):
     # FP64 part of one rate-type f evaluation: in the mixed path the final
     # scaling (and with the energy equation the exponents and the enthalpy
     # sums) stay FP64
-    f64 = (2 * nS + 1 + (fo - feval_ops(m) if energy else 0)) if mixed else fo
+    f64 = (m.n_species + 1 + (fo - feval_ops(m) if energy else 0)) if mixed else fo
     f32 = fo - f64
     nfe = stats[:, 0].astype(np.float64)
     att = (stats[:, 1] + stats[:, 2]).astype(np.float64)
@@ -209,26 +209,27 @@ def oracle_method(w):
     return 2 if w["sigma"] == synth.POWER else 1
 
 
-def oracle_rate(name, cells_target_s=10.0, max_cells=None, seed_offset=0):
-    """Time the FP64 oracle on the host cores on a bounded sample of the
-    workload. Returns (cells/s, threads, sample description)."""
+def oracle_rate(name, cells_target_s=10.0, max_cells=None, seed_offset=0, nthreads=0):
+    """Time the FP64 oracle on the host cores (all of them, or `nthreads`) on
+    a bounded sample of the workload. Returns (cells/s, threads, sample
+    description)."""
     import oracle
     w = synth.WORKLOADS[name]
     m = synth.workload_mechanism(name)
     om = oracle.Mech(m)
     total = w["cells"]
     T, p, Y = synth.workload_states(name, m, seed_offset=seed_offset)
-    probe = min(2048, total)
+    probe = min(2048 if nthreads == 0 else 64, total)
     t0 = time.perf_counter()
     meth = oracle_method(w)
     en = bool(w.get("energy"))
     nt = oracle.integrate(om, T[:probe], p[:probe], Y[:, :probe], w["dt"], w["rtol"],
-                          w["atol"], meth, energy=en)[3]
+                          w["atol"], meth, nthreads=nthreads, energy=en)[3]
     per_cell = (time.perf_counter() - t0) / probe
     n = int(min(total if max_cells is None else max_cells, max(probe, cells_target_s / per_cell)))
     t0 = time.perf_counter()
     nt = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], meth,
-                          energy=en)[3]
+                          nthreads=nthreads, energy=en)[3]
     el = time.perf_counter() - t0
     return n / el, nt, "first %d of the %d cells of %s (same seeds), %.1f s wall" % (n, total, name, el)
 
@@ -443,6 +444,8 @@ def run_kin(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, nt, sample = oracle_rate(name, cells_target_s=args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": sample}
+        v1, _, sample1 = oracle_rate(name, cells_target_s=args.cpu_seconds / 2, nthreads=1)
+        cpu["single_core"] = {"value": v1, "unit": UNIT, "cores": 1, "sample": sample1}
 
     if rank == 0:
         line = {
@@ -581,6 +584,87 @@ def run_batched(args):
     return 0
 
 
+def run_divergence(args):
+    """The divergence study of Section 3.1: `--global-steps` consecutive calls
+    (flow steps) on the same cells, 65,536 by default as in the paper, once
+    with the cells in 'similar' order (sorted by temperature) and once as
+    drawn ('random'). Reports each order's time and the distribution of the
+    warp divergence measure D over the per-cell f evaluations summed over the
+    calls, for the paper's fixed thread-per-cell mapping and for the best
+    fixed mapping (cells sorted by count)."""
+    import torch
+    from paper_1309_2710_gb300 import build as kbuild
+    from paper_1309_2710_gb300 import divergence
+    kbuild.build()
+    from paper_1309_2710_gb300 import kin
+    name = args.workload
+    w = synth.WORKLOADS[name]
+    m = synth.workload_mechanism(name)
+    km = kin.Mechanism(m)
+    cells = args.cells or 65536
+    dev = torch.device("cuda")
+    method, prec = w["method"], w["precision"]
+    sigma = w["sigma"] if args.sigma == "default" else (synth.POWER if args.sigma == "power"
+                                                         else synth.GERSHGORIN)
+    energy = int(bool(w.get("energy")))
+    states = {o: synth.workload_states(name, m, cells=cells, sort_by_T=o == "similar")
+              for o in ("similar", "random")}
+    shape = dict(block_threads=0, blocks_per_sm=0, staging=kin.STAGE_GLOBAL, occupancy=kin.OCC_DEFAULT,
+                 layout=kin.LAYOUT_AUTO)
+    if args.shape:
+        v = [int(x) for x in args.shape.split(",")]
+        shape.update(zip(("block_threads", "blocks_per_sm", "staging", "occupancy", "layout"), v))
+    elif not args.no_tune:
+        from paper_1309_2710_gb300 import autotune
+        T, p, Y = states["random"]
+        best = autotune.tune(km, m, torch.as_tensor(T, device=dev), torch.as_tensor(p, device=dev),
+                             torch.as_tensor(Y, device=dev).contiguous(), w["dt"], w["rtol"],
+                             w["atol"], method, prec, sigma=sigma, energy=energy)
+        shape = {k: best[k] for k in shape}
+    ws = km.workspace(method, prec, cells, shape["block_threads"], shape["blocks_per_sm"], dev,
+                      shape["staging"], shape["occupancy"], sigma, shape["layout"], energy)
+    stream = torch.cuda.current_stream()
+    st = torch.zeros(cells, dtype=torch.uint8, device=dev)
+    sta = torch.zeros((cells, kin.NSTATS), dtype=torch.int32, device=dev)
+    out = {}
+    for order, (T, p, Y) in states.items():
+        T0d, pd = torch.as_tensor(T, device=dev), torch.as_tensor(p, device=dev)
+        Y0d = torch.as_tensor(Y, device=dev).contiguous()
+        Td, Yd = T0d.clone(), Y0d.clone()
+
+        def call():
+            kin.integrate(km, Td, pd, Yd, w["dt"], w["rtol"], w["atol"], method, prec, status=st,
+                          stats=sta, workspace=ws, stream=stream, sigma=sigma, energy=energy, **shape)
+
+        for _ in range(args.warmup):
+            call()
+        Td.copy_(T0d)
+        Yd.copy_(Y0d)
+        torch.cuda.synchronize()
+        d = np.zeros(cells, dtype=np.int64)
+        ms, bad = [], 0
+        for _ in range(args.global_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            d += sta[:, 0].cpu().numpy()
+            bad += int((st != 0).sum().item())
+        out[order] = {"ms_total": float(sum(ms)), "ms_per_call": [float(x) for x in ms],
+                      "cells_per_s": cells * len(ms) / (sum(ms) * 1e-3), "nonzero_status": bad,
+                      "mean_f_evals_per_call": float(d.mean() / len(ms)),
+                      "D": divergence.summary(d)}
+    print(json.dumps({"mode": "divergence", "workload": name, "cells": cells,
+                      "global_steps": args.global_steps, "launch_shape": shape,
+                      "layout": layout_name(km, method, shape, cells),
+                      "similar_over_random_time": out["similar"]["ms_total"] / out["random"]["ms_total"],
+                      **out}))
+    km.close()
+    return 0
+
+
 def layout_name(km, method, shape, cells):
     from paper_1309_2710_gb300 import kin
     import torch
@@ -607,7 +691,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="library default launch shape")
     ap.add_argument("--shape", default="", help="block_threads,blocks_per_sm,staging,occupancy"
                                                 "[,layout] (skips the autotuner)")
-    ap.add_argument("--mode", choices=["headline", "batched"], default="headline")
+    ap.add_argument("--mode", choices=["headline", "batched", "divergence"], default="headline")
+    ap.add_argument("--global-steps", type=int, default=10,
+                    help="divergence mode: consecutive calls whose f evaluations are summed")
     ap.add_argument("--order", choices=["random", "sorted"], default="random",
                     help="cell order: as drawn, or sorted by temperature ('similar')")
     ap.add_argument("--sigma", choices=["default", "gershgorin", "power"], default="default",
@@ -618,6 +704,8 @@ def main():
     args = ap.parse_args()
     if args.mode == "batched":
         return run_batched(args)
+    if args.mode == "divergence":
+        return run_divergence(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_kin(args)

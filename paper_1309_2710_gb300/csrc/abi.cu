@@ -87,7 +87,7 @@ int grid_for(const kin_mech* m, const kin_opts* o, int64_t cells, Grid* g)
     if (layout == KIN_LAYOUT_WARP) {
         if (threads % 32 != 0 || threads > 256) return fail(KIN_EINVAL, "block_threads must be a multiple of 32 and <= 256");
         const int cell_lanes = warp_cell_lanes(o->method, m->nS + o->energy);
-        const size_t sm = warp_smem(m->dev, o->precision, threads) * (32 / cell_lanes);
+        const size_t sm = warp_smem(m->dev, o->precision, o->energy, threads) * (32 / cell_lanes);
         if (sm > (size_t)maxsm)
             return fail(KIN_EUNSUPPORTED, "warp layout needs %zu bytes of shared memory per block (max %d)", sm, maxsm);
         const int nV = m->nS + o->energy;
@@ -289,6 +289,15 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     const size_t oEffT = put(effT.data(), 8 * effT.size()), oEffT32 = put(effT32.data(), 4 * effT32.size());
     const size_t oPtr = put(ptr.data(), 4 * (nS + 1)), oCrx = put(crx.data(), 4 * nnz);
     const size_t oNu = put(cnu.data(), 8 * nnz), oNu32 = put(nu32.data(), 4 * nnz);
+    // the species' molar mass folded into its row (a common factor of the row)
+    std::vector<double> cnuW(nnz);
+    std::vector<float> nuW32(nnz);
+    for (int i = 0; i < nS; ++i)
+        for (int e2 = ptr[i]; e2 < ptr[i + 1]; ++e2) {
+            cnuW[e2] = cnu[e2] * d->W[i];
+            nuW32[e2] = (float)cnuW[e2];
+        }
+    const size_t oNuW = put(cnuW.data(), 8 * nnz), oNuW32 = put(nuW32.data(), 4 * nnz);
     const size_t oEff = put(d->eff, 8 * (size_t)nM * nS), oEff32 = put(eff32.data(), 4 * (size_t)nM * nS);
     // thermochemistry for the energy equation: cp, cp/W, Hf
     const bool thermo = d->cp && d->Hf;
@@ -327,6 +336,7 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     M.effT32 = (const float*)(b + oEffT32);
     M.csr_ptr = (const int*)(b + oPtr); M.csr_rxn = (const int*)(b + oCrx);
     M.csr_nu = (const double*)(b + oNu); M.csr_nu32 = (const float*)(b + oNu32);
+    M.csr_nuW = (const double*)(b + oNuW); M.csr_nuW32 = (const float*)(b + oNuW32);
     M.eff = (const double*)(b + oEff); M.eff32 = (const float*)(b + oEff32);
     M.rkc = (const double*)(b + oTab);
     M.cp = thermo ? (const double*)(b + oCp) : nullptr;

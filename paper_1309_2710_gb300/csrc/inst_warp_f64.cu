@@ -14,9 +14,13 @@ cudaError_t occ_warp_f64_o0(const MechDev& M, int nV, int threads, int* bps)
     return warp_occ<double, 0, false>(M, nV, KIN_FP64, threads, bps);
 }
 
-size_t warp_smem(const MechDev& M, int precision, int threads)
+size_t warp_smem(const MechDev& M, int precision, int energy, int threads)
 {
-    return warp_smem_bytes(M, precision, threads);
+    if (energy)
+        return precision == KIN_MIXED ? warp_smem_bytes<float, true>(M, threads)
+                                      : warp_smem_bytes<double, true>(M, threads);
+    return precision == KIN_MIXED ? warp_smem_bytes<float, false>(M, threads)
+                                  : warp_smem_bytes<double, false>(M, threads);
 }
 
 }  // namespace kin

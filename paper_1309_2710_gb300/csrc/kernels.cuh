@@ -54,7 +54,9 @@ struct Tab<double> {
     __device__ static const double* invW(const MechDev& M) { return M.invW; }
     __device__ static const double* eff(const MechDev& M) { return M.eff; }
     __device__ static const double* nu(const MechDev& M) { return M.csr_nu; }
+    __device__ static const double* nuW(const MechDev& M) { return M.csr_nuW; }
     __device__ static double ex(double a) { return exp(a); }
+    __device__ static double inv(double a);
     static constexpr double sqrt_u = 1.4901161193847656e-08;  // sqrt(2^-52)
 };
 template <>
@@ -62,6 +64,8 @@ struct Tab<float> {
     __device__ static const float* invW(const MechDev& M) { return M.invW32; }
     __device__ static const float* eff(const MechDev& M) { return M.eff32; }
     __device__ static const float* nu(const MechDev& M) { return M.csr_nu32; }
+    __device__ static const float* nuW(const MechDev& M) { return M.csr_nuW32; }
+    __device__ static float inv(float a) { return 1.0f / a; }
     // exp in FP32 after an exact split a = n ln2 + r formed in FP64, so the
     // FP32 rounding of a large exponent (|a| ~ 40) does not cost 2e-6
     // relative accuracy: k = 2^n expf(r) with |r| <= ln2/2.
@@ -121,8 +125,7 @@ __device__ void feval(const MechDev& M, double Ctot, double invCtot, Lane<KT> K,
         S0 += m0;
     }
     const R S = S0 + S1;
-    const R invS = R(1) / S;
-    const R rho = (R)Ctot * invS;
+    const R rho = (R)Ctot * Tab<R>::inv(S);
     for (int k = 0; k < nS; ++k) C[k] = C[k] * rho;
     // rates of progress
     const R* __restrict__ eff = Tab<R>::eff(M);
@@ -150,19 +153,20 @@ __device__ void feval(const MechDev& M, double Ctot, double invCtot, Lane<KT> K,
         }
         OM[j] = q;
     }
-    // omega_i = sum_j nu_ij Omega_j (gather); dY_i/dt = W_i omega_i / rho
-    const R* __restrict__ nu = Tab<R>::nu(M);
+    // W_i omega_i = sum_j (W_i nu_ij) Omega_j (gather over the species' row,
+    // W_i folded into its coefficients); dY_i/dt = W_i omega_i / rho
+    const R* __restrict__ nuW = Tab<R>::nuW(M);
     const double invrho = (double)S * invCtot;
     for (int sp = 0; sp < nS; ++sp) {
         R w0 = R(0), w1 = R(0);
         const int e1 = M.csr_ptr[sp + 1];
         int e = M.csr_ptr[sp];
         for (; e + 1 < e1; e += 2) {
-            w0 += nu[e] * OM[M.csr_rxn[e]];
-            w1 += nu[e + 1] * OM[M.csr_rxn[e + 1]];
+            w0 += nuW[e] * OM[M.csr_rxn[e]];
+            w1 += nuW[e + 1] * OM[M.csr_rxn[e + 1]];
         }
-        if (e < e1) w0 += nu[e] * OM[M.csr_rxn[e]];
-        out[sp] = (double)(w0 + w1) * (M.W[sp] * invrho);
+        if (e < e1) w0 += nuW[e] * OM[M.csr_rxn[e]];
+        out[sp] = (double)(w0 + w1) * invrho;
     }
 }
 
@@ -196,7 +200,7 @@ __device__ void feval_energy(const MechDev& M, double p, Lane<R> C, Lane<R> OM, 
         S0 += m0;
     }
     const R S = S0 + S1;
-    const R rho = (R)Ctot * (R(1) / S);
+    const R rho = (R)Ctot * Tab<R>::inv(S);
     for (int k = 0; k < nS; ++k) C[k] = C[k] * rho;
     const R* __restrict__ eff = Tab<R>::eff(M);
     for (int j = 0; j < nR; ++j) {
@@ -362,23 +366,26 @@ constexpr double SIG_SQRT_U = 1.4901161193847656e-08;  // sqrt(2^-52)
 
 // ------------------------------------------ Newton-refined FP64 helpers ---
 // The per-lane step control runs on the FP64 pipe while the other lanes of
-// the warp wait, so its FP64 instruction count matters. These two helpers
-// take a single-precision seed (the SFU reciprocal, the FP32 cube root) and
-// refine it with one Newton-Raphson step in FP64, which squares the seed's
-// relative error (<= 2^-21 -> ~2^-42, about 2e-13): enough for an error norm
-// and a step-size factor, which only need to reproduce the FP64 decisions.
-// Outside the FP32 normal range the plain FP64 operation is used.
+// the warp wait, so its FP64 instruction count matters. These helpers take a
+// low-precision seed (the approximate FP64 reciprocal instruction, the FP32
+// cube root or power) and refine it with one Newton-Raphson step in FP64,
+// which squares the seed's relative error (reciprocal: below 2^-19.9, measured
+// over 4M log-uniform inputs on GB300 -> ~1e-12 after the step): enough for an
+// error norm and a step-size factor, which only need to reproduce the FP64
+// decisions. Outside the FP32 normal range the plain FP64 operation is used.
 __device__ __forceinline__ bool f32_normal(double x)
 {
     const int e = (__double2hiint(x) >> 20) & 0x7ff;  // biased exponent (sign ignored)
     return e > 1023 - 120 && e < 1023 + 120;
 }
 
-// 1/x: Newton r1 = r0 + r0 (1 - x r0).
+// 1/x: Newton r1 = r0 + r0 (1 - x r0) from rcp.approx.ftz.f64 (no FP32
+// round trip, so no conversions on the FP64 pipe).
 __device__ __forceinline__ double rcp_newton(double x)
 {
     if (!f32_normal(x)) return 1.0 / x;
-    const double r0 = (double)__frcp_rn((float)x);
+    double r0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(x));
     return fma(r0, fma(-x, r0, 1.0), r0);
 }
 
@@ -389,6 +396,47 @@ __device__ __forceinline__ double cbrt_newton(double a)
     const double c0 = (double)cbrtf((float)a);
     return c0 + (a * rcp_newton(c0 * c0) - c0) * (1.0 / 3.0);
 }
+
+// x^(-1/5) and x^(-1/4) for x > 0, the RKCK step-size factors: Newton on
+// y^(-p) = x, y1 = y0 + y0 (1 - x y0^p) / p, from y0 = powf(x, -1/p). A seed
+// error e becomes (p + 1)/2 e^2 (powf is within 4 ulp: below 5e-12 after the
+// step, ample for a step-size factor).
+__device__ __forceinline__ double rpow5_newton(double x)
+{
+    if (!f32_normal(x)) return pow(x, -0.2);
+    const double y0 = (double)powf((float)x, -0.2f);
+    const double y2 = y0 * y0;
+    const double u = fma(-(x * y0), y2 * y2, 1.0);
+    return fma(y0 * u, 0.2, y0);
+}
+
+// x^(-1/6) for x > 0: the RKC controller's err^(-1/3) from x = err^2.
+__device__ __forceinline__ double rpow6_newton(double x)
+{
+    if (!f32_normal(x)) return pow(x, -1.0 / 6.0);
+    const double y0 = (double)powf((float)x, -1.0f / 6.0f);
+    const double y2 = y0 * y0;
+    const double u = fma(-(x * y2), y2 * y2, 1.0);
+    return fma(y0 * u, 1.0 / 6.0, y0);
+}
+
+__device__ __forceinline__ double rpow4_newton(double x)
+{
+    if (!f32_normal(x)) return pow(x, -0.25);
+    const double y0 = (double)powf((float)x, -0.25f);
+    const double y2 = y0 * y0;
+    const double u = fma(-(x * y2), y2, 1.0);
+    return fma(y0 * u, 0.25, y0);
+}
+// 1/x in the FP64 evaluation of f (the mixture density): a second Newton
+// step on rcp_newton takes the error from ~1e-12 to rounding level, so f
+// stays an FP64-accurate function of the state.
+__device__ __forceinline__ double Tab<double>::inv(double a)
+{
+    const double r = rcp_newton(a);
+    return fma(r, fma(-a, r, 1.0), r);
+}
+
 struct PowerState {
     int k;
     double prev, dyn, sig;
@@ -760,7 +808,7 @@ struct Integrator {
     __device__ bool sigma_column(LaneState& S)
     {
         Lane<double> Y = V(V_Y), X = V(V_X), RS = V(V_RS), FX = V(V_FX), F0 = V(V_BASE);
-        const double ie = 1.0 / S.eps;
+        const double ie = rcp_newton(S.eps);
         for (int i = 0; i < L.nV; ++i) RS[i] += fabs((FX[i] - F0[i]) * ie);
         X[S.col] = Y[S.col];
         if (++S.col < L.nV) {
@@ -899,18 +947,23 @@ struct Integrator {
     {
         Lane<double> Y = V(V_Y), F0 = V(V_F0), WS = V(S.iw1), FX = V(V_FX);
         const double hh = S.hh;
-        const double err = sqrt(acc * S.invN);
+        // x = ||Delta||^2: err <= 1 iff x <= 1, and the controller's powers
+        // of err come from z = x^(-1/6) = err^(-1/3) (no square or cube root):
+        // err^(1/3) = x z^5, err^(-2/3) = z^2.
+        const double x = acc * S.invN;
         S.attempts++;
-        if (err <= 1.0) {
+        if (x <= 1.0) {
             S.nacc++;
-            // err^(1/3) once; err^(2/3) = (err^(1/3))^2; the previous step's
-            // err^(1/3) is kept for the predictive factor (one division).
-            const double c3 = err > 0.0 ? cbrt_newton(err) : 0.0;
-            double fac;
-            if (err == 0.0) fac = 10.0;
-            else if (S.have_prev && !S.last_rejected && S.cprev > 0.0)
-                fac = 0.8 * hh * S.cprev / (S.hprev * c3 * c3);
-            else fac = 0.8 / c3;
+            double fac, c3 = 0.0;
+            if (x == 0.0) {
+                fac = 10.0;
+            } else {
+                const double z = rpow6_newton(x), z2 = z * z;
+                c3 = x * (z2 * z2 * z);
+                if (S.have_prev && !S.last_rejected && S.cprev > 0.0)
+                    fac = 0.8 * hh * S.cprev * z2 * rcp_newton(S.hprev);
+                else fac = 0.8 * z;
+            }
             fac = fmin(10.0, fmax(0.1, fac));
             for (int i = 0; i < L.nV; ++i) {
                 Y[i] = WS[i];
@@ -930,7 +983,7 @@ struct Integrator {
             S.h = fac * hh;
         } else {
             S.nrej++;
-            double fac = isfinite(err) ? 0.8 / cbrt(err) : 0.1;
+            double fac = isfinite(x) ? 0.8 * rpow6_newton(x) : 0.1;
             if (fac < 0.1) fac = 0.1;
             S.last_rejected = true;
             S.h = fac * hh;
@@ -993,7 +1046,7 @@ struct Integrator {
             }
             X[i] = Y[i] + hh * s5;
             const double tol = S.rtol * (fabs(Y[i]) + fabs(hh * F0[i])) + S.atol;
-            const double r = fabs(hh * e) / tol;
+            const double r = fabs(hh * e) * rcp_newton(tol);
             blown |= isnan(r);
             if (r > errmax) errmax = r;
         }
@@ -1007,7 +1060,7 @@ struct Integrator {
                 return KIN_CELL_OK;
             }
             S.t += hh;
-            const double hn = errmax == 0.0 ? 5.0 * hh : 0.9 * hh * pow(errmax, -0.2);
+            const double hn = errmax == 0.0 ? 5.0 * hh : 0.9 * hh * rpow5_newton(errmax);
             S.h = fmin(hn, 5.0 * hh);
             S.phase = PH_F0;
             S.in_v = V_Y;
@@ -1015,7 +1068,7 @@ struct Integrator {
             return -1;
         }
         S.nrej++;
-        const double hn = isfinite(errmax) ? 0.9 * hh * pow(errmax, -0.25) : 0.1 * hh;
+        const double hn = isfinite(errmax) ? 0.9 * hh * rpow4_newton(errmax) : 0.1 * hh;
         S.h = fmax(hn, 0.1 * hh);
         if (S.h < 1e-20 * S.dt) return KIN_CELL_HMIN;
         return rkck_begin_attempt(S);

@@ -49,6 +49,8 @@ struct MechDev {
     const int* csr_rxn;    // [nnz] reaction of each entry (ascending per species)
     const double* csr_nu;  // [nnz] net coefficient nu'' - nu' of the species
     const float* csr_nu32; // [nnz]
+    const double* csr_nuW; // [nnz] nu'' - nu' times the species' W (isothermal f: dY/dt = (sum) / rho)
+    const float* csr_nuW32; // [nnz]
     const double* eff;     // [nM][nS]
     const float* eff32;    // [nM][nS]
     const double* rkc;     // [RKC_TAB_S][RKC_TAB_S][RKC_TAB_W]
@@ -157,7 +159,9 @@ cudaError_t launch_warp_rkck_f64(Launch& L, int blocks, int threads, cudaStream_
 cudaError_t launch_warp_rkck_f32(Launch& L, int blocks, int threads, cudaStream_t st);
 cudaError_t occ_warp_rkck_f64(const MechDev& M, int nV, int energy, int threads, int* bps);
 cudaError_t occ_warp_rkck_f32(const MechDev& M, int nV, int energy, int threads, int* bps);
-size_t warp_smem(const MechDev& M, int precision, int threads);
+// Dynamic shared memory of a 32-lane warp's worth of cell groups per block of
+// `threads` (RKC: one cell per warp; RKCK with 16-lane groups: multiply by 2).
+size_t warp_smem(const MechDev& M, int precision, int energy, int threads);
 
 // Lanes that integrate one cell in the warp-per-cell layout: a whole warp,
 // or half of one (two cells per warp) for RKCK on states of at most 16

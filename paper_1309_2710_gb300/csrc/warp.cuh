@@ -80,6 +80,31 @@ __host__ __device__ __forceinline__ int warp_smem_elems(const MechDev& M)
     return (M.nS + M.nR + 3) & ~3;
 }
 
+// The cell's rate constants in shared memory too: f reads every k_j once per
+// evaluation, and staged behind C and Omega that read is a shared load instead
+// of an L2 round trip on the f's critical path. Isothermal only (with the
+// energy equation k follows T inside f), and only for small mechanisms, whose
+// group words stay within WARP_K_SMEM_MAX_BYTES: shared memory comes out of
+// the same on-chip array as L1, and for 53 species / 634 reactions the larger
+// carve-out cost more in L1 misses (tables, spills) than the staged k saved
+// (163 K vs 174 K cells/s on GB300), while 9 species / 38 reactions gained.
+constexpr int WARP_K_SMEM_MAX_BYTES = 2048;
+
+template <typename R, bool EN>
+__host__ __device__ __forceinline__ int warp_k_words(const MechDev& M)
+{
+    if (EN) return 0;
+    const int kw = ((M.nR + M.nFO) * (int)sizeof(R) + 7) / 8;
+    return (warp_smem_elems(M) + kw) * 8 <= WARP_K_SMEM_MAX_BYTES ? kw : 0;
+}
+
+// Shared FP64 words per cell group: C and Omega, then the staged k (if any).
+template <typename R, bool EN>
+__host__ __device__ __forceinline__ int warp_group_words(const MechDev& M)
+{
+    return warp_smem_elems(M) + warp_k_words<R, EN>(M);
+}
+
 // f for the warp's cell (Eqs. (E:mass), (E:spec-rate), (E:rxn-rate)) in
 // arithmetic type R. Kc are the cell's rate constants (stored as KT) in
 // reaction-permutation order followed by k0/kinf per falloff ordinal (written
@@ -103,7 +128,7 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
         }
     }
     s = group_sum<G>(s, mask);
-    const R rho = (R)Ctot * (R(1) / s);
+    const R rho = (R)Ctot * Tab<R>::inv(s);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int i = lane + G * r;
@@ -136,7 +161,8 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
         OM[q] = v;
     }
     __syncwarp(mask);
-    const R* __restrict__ nu = Tab<R>::nu(M);
+    // W_i omega_i over the species' row (W_i folded into its coefficients)
+    const R* __restrict__ nuW = Tab<R>::nuW(M);
     const double invrho = (double)s * invCtot;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
@@ -147,11 +173,11 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
             const int e1 = M.csr_ptr[i + 1];
             int e = M.csr_ptr[i];
             for (; e + 1 < e1; e += 2) {
-                w0 += nu[e] * OM[M.csrp_rxn[e]];
-                w1 += nu[e + 1] * OM[M.csrp_rxn[e + 1]];
+                w0 += nuW[e] * OM[M.csrp_rxn[e]];
+                w1 += nuW[e + 1] * OM[M.csrp_rxn[e + 1]];
             }
-            if (e < e1) w0 += nu[e] * OM[M.csrp_rxn[e]];
-            o = (double)(w0 + w1) * (M.W[i] * invrho);
+            if (e < e1) w0 += nuW[e] * OM[M.csrp_rxn[e]];
+            o = (double)(w0 + w1) * invrho;
         }
         out[r] = o;
     }
@@ -188,7 +214,7 @@ __device__ __forceinline__ void warp_feval_energy(const MechDev& M, double p, R*
         }
     }
     s = group_sum<G>(s, mask);
-    const R rho = (R)Ctot * (R(1) / s);
+    const R rho = (R)Ctot * Tab<R>::inv(s);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int i = lane + G * r;
@@ -275,6 +301,7 @@ struct WarpRKC {
     R* OM;
     double* C64;   // the same shared words as C and OM, for the FP64 evaluations
     double* OM64;
+    R* Ks;         // the warp's staged rate constants, or null
     const R* Kc;
     int lane, nV;  // nV: state length, nS + 1 with the energy equation
     double Ctot, invCtot, atol, rtol, p;
@@ -283,10 +310,11 @@ struct WarpRKC {
 
     __device__ explicit WarpRKC(const Launch& l) : L(l), M(l.M), Kc(nullptr), lane(threadIdx.x & 31), nV(l.nV)
     {
-        C64 = reinterpret_cast<double*>(kin_smem) + (size_t)(threadIdx.x >> 5) * warp_smem_elems(M);
+        C64 = reinterpret_cast<double*>(kin_smem) + (size_t)(threadIdx.x >> 5) * warp_group_words<R, EN>(M);
         OM64 = C64 + M.nS;
         C = reinterpret_cast<R*>(C64);
         OM = C + M.nS;
+        Ks = warp_k_words<R, EN>(M) ? reinterpret_cast<R*>(C64 + warp_smem_elems(M)) : nullptr;
     }
 
     __device__ __forceinline__ bool valid(int r) const { return lane + 32 * r < nV; }
@@ -339,7 +367,7 @@ struct WarpRKC {
 #pragma unroll
             for (int r = 0; r < NR; ++r) x[r] = (r == kr && lane == kl) ? yk + eps : y[r];
             fs(x, fx);
-            const double ie = 1.0 / eps;
+            const double ie = rcp_newton(eps);
 #pragma unroll
             for (int r = 0; r < NR; ++r)
                 if (valid(r)) rs[r] += fabs((fx[r] - base[r]) * ie);
@@ -477,18 +505,23 @@ struct WarpRKC {
                 if (valid(r)) {
                     const double d = 0.8 * (y[r] - w1[r]) + 0.4 * hh * (f0[r] + fx[r]);
                     const double sc = atol + rtol * fmax(fabs(y[r]), fabs(w1[r]));
-                    const double q = d / sc;
+                    const double q = d * rcp_newton(sc);
                     acc += q * q;
                 }
-            const double err = sqrt(warp_sum(acc) * invN);
-            if (err <= 1.0) {
+            // x = ||Delta||^2; z = x^(-1/6) = err^(-1/3) (see the lane kernel)
+            const double xe = warp_sum(acc) * invN;
+            if (xe <= 1.0) {
                 nacc++;
-                const double c3 = cbrt(err);
-                double fac;
-                if (err == 0.0) fac = 10.0;
-                else if (have_prev && !last_rej && cprev > 0.0)
-                    fac = 0.8 * hh * cprev / (hprev * c3 * c3);
-                else fac = 0.8 / c3;
+                double fac, c3 = 0.0;
+                if (xe == 0.0) {
+                    fac = 10.0;
+                } else {
+                    const double z = rpow6_newton(xe), z2 = z * z;
+                    c3 = xe * (z2 * z2 * z);
+                    if (have_prev && !last_rej && cprev > 0.0)
+                        fac = 0.8 * hh * cprev * z2 * rcp_newton(hprev);
+                    else fac = 0.8 * z;
+                }
                 fac = fmin(10.0, fmax(0.1, fac));
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
@@ -506,7 +539,7 @@ struct WarpRKC {
                 h = fac * hh;
             } else {
                 nrej++;
-                double fac = isfinite(err) ? 0.8 / cbrt(err) : 0.1;
+                double fac = isfinite(xe) ? 0.8 * rpow6_newton(xe) : 0.1;
                 if (fac < 0.1) fac = 0.1;
                 last_rej = true;
                 h = fac * hh;
@@ -550,20 +583,27 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_ini
         if constexpr (!EN) {
             // rate constants (Eq. (E:rxn-const)) in permutation order; with the
             // energy equation they follow T and are formed inside f instead
+            // (for the main kernel in the workspace, and for this kernel's own
+            // evaluations in the staged copy when there is one)
             R* kc = reinterpret_cast<R*>(L.cell_k) + g * nK;
+            R* ks = W.Ks ? W.Ks : kc;
             const double lnT = log(T), invT = 1.0 / T;
             for (int q = lane; q < M.nR; q += 32) {
                 const int j = M.rxn_perm[q];
                 const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
-                kc[q] = Tab<R>::ex(a);
+                const R k = Tab<R>::ex(a);
+                kc[q] = k;
+                ks[q] = k;
                 const int fo = M.rxnp[q].fo;
                 if (fo >= 0) {
                     const double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
-                    kc[M.nR + fo] = Tab<R>::ex(a0 - a);
+                    const R k0 = Tab<R>::ex(a0 - a);
+                    kc[M.nR + fo] = k0;
+                    ks[M.nR + fo] = k0;
                 }
             }
             __syncwarp();
-            W.Kc = kc;
+            W.Kc = ks;
         }
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
@@ -643,7 +683,18 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_int
             W.atol = I.atol;
             W.rtol = I.rtol;
             W.p = p;
-            W.Kc = EN ? nullptr : reinterpret_cast<const R*>(L.cell_k) + g * nK;
+            if constexpr (EN) {
+                W.Kc = nullptr;
+            } else {
+                const R* kg = reinterpret_cast<const R*>(L.cell_k) + g * nK;
+                if (W.Ks) {  // stage the cell's k (the last f of the previous cell ended in a sync)
+                    for (int q = lane; q < nK; q += 32) W.Ks[q] = kg[q];
+                    __syncwarp();
+                    W.Kc = W.Ks;
+                } else {
+                    W.Kc = kg;
+                }
+            }
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 const int i = lane + 32 * r;
@@ -674,10 +725,10 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_int
     }
 }
 
-inline size_t warp_smem_bytes(const MechDev& M, int precision, int threads)
+template <typename R, bool EN>
+inline size_t warp_smem_bytes(const MechDev& M, int threads)
 {
-    (void)precision;  // FP64-sized in both precisions
-    return (size_t)warp_smem_elems(M) * (threads / 32) * 8;
+    return (size_t)warp_group_words<R, EN>(M) * (threads / 32) * 8;
 }
 
 // ---------------------------------------------------- RKCK, warp per cell --
@@ -697,6 +748,7 @@ struct WarpRKCK {
     const MechDev& M;
     R* C;
     R* OM;
+    R* Ks;  // the group's staged rate constants, or null
     const R* Kc;
     int lane, nV;
     unsigned mask;  // the group's lanes
@@ -708,9 +760,10 @@ struct WarpRKCK {
         : L(l), M(l.M), Kc(nullptr), lane(threadIdx.x & (G - 1)), nV(l.nV),
           mask(G == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16)))
     {
-        C = reinterpret_cast<R*>(reinterpret_cast<double*>(kin_smem) +
-                                 (size_t)(threadIdx.x / G) * warp_smem_elems(M));
+        double* base = reinterpret_cast<double*>(kin_smem) + (size_t)(threadIdx.x / G) * warp_group_words<R, EN>(M);
+        C = reinterpret_cast<R*>(base);
         OM = C + M.nS;
+        Ks = warp_k_words<R, EN>(M) ? reinterpret_cast<R*>(base + warp_smem_elems(M)) : nullptr;
     }
 
     __device__ __forceinline__ bool valid(int r) const { return lane + G * r < nV; }
@@ -766,7 +819,7 @@ struct WarpRKCK {
                 x[r] = y[r] + hh * s5;
                 if (valid(r)) {
                     const double tol = rtol * (fabs(y[r]) + fabs(hh * k[0][r])) + atol;
-                    const double q = fabs(hh * e) / tol;
+                    const double q = fabs(hh * e) * rcp_newton(tol);
                     blown |= isnan(q);
                     if (q > errmax) errmax = q;
                 }
@@ -781,7 +834,7 @@ struct WarpRKCK {
                 for (int r = 0; r < NR; ++r) y[r] = x[r];
                 if (last) return KIN_CELL_OK;
                 t += hh;
-                const double hn = errmax == 0.0 ? 5.0 * hh : 0.9 * hh * pow(errmax, -0.2);
+                const double hn = errmax == 0.0 ? 5.0 * hh : 0.9 * hh * rpow5_newton(errmax);
                 h = fmin(hn, 5.0 * hh);
                 f(y, k[0]);
                 bool fin = true;
@@ -790,7 +843,7 @@ struct WarpRKCK {
                 if (!__all_sync(mask, fin)) return KIN_CELL_NONFINITE;
             } else {
                 nrej++;
-                const double hn = isfinite(errmax) ? 0.9 * hh * pow(errmax, -0.25) : 0.1 * hh;
+                const double hn = isfinite(errmax) ? 0.9 * hh * rpow4_newton(errmax) : 0.1 * hh;
                 h = fmax(hn, 0.1 * hh);
                 if (h < 1e-20 * dt) return KIN_CELL_HMIN;
             }
@@ -821,7 +874,9 @@ __global__ void __launch_bounds__(256, NR == 8 ? 1 : 2) warp_rkck_kernel(const _
         W.p = p;
         W.nfe = 0;
         if constexpr (!EN) {
-            R* kc = reinterpret_cast<R*>(L.cell_k) + g * nK;
+            // formed straight into the staged copy when there is one (the
+            // previous cell's last f ended in a sync of the group)
+            R* kc = W.Ks ? W.Ks : reinterpret_cast<R*>(L.cell_k) + g * nK;
             const double lnT = log(T), invT = 1.0 / T;
             for (int qq = lane; qq < M.nR; qq += G) {
                 const int j = M.rxn_perm[qq];
@@ -871,15 +926,16 @@ __global__ void __launch_bounds__(256, NR == 8 ? 1 : 2) warp_rkck_kernel(const _
 
 inline int rkck_group(int nV) { return warp_cell_lanes(KIN_RKCK, nV); }
 
+template <typename R, bool EN>
 inline size_t group_smem_bytes(const MechDev& M, int threads, int G)
 {
-    return (size_t)warp_smem_elems(M) * (threads / G) * 8;
+    return (size_t)warp_group_words<R, EN>(M) * (threads / G) * 8;
 }
 
 template <typename R, int NR, bool EN, int G>
 inline cudaError_t warp_rkck_launch_nr(Launch& L, int blocks, int threads, cudaStream_t st)
 {
-    const size_t sm = group_smem_bytes(L.M, threads, G);
+    const size_t sm = group_smem_bytes<R, EN>(L.M, threads, G);
     cudaError_t e = cudaFuncSetAttribute(warp_rkck_kernel<R, NR, EN, G>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -890,7 +946,7 @@ inline cudaError_t warp_rkck_launch_nr(Launch& L, int blocks, int threads, cudaS
 template <typename R, int NR, bool EN, int G>
 inline cudaError_t warp_rkck_occ_nr(const MechDev& M, int threads, int* bps)
 {
-    const size_t sm = group_smem_bytes(M, threads, G);
+    const size_t sm = group_smem_bytes<R, EN>(M, threads, G);
     cudaError_t e = cudaFuncSetAttribute(warp_rkck_kernel<R, NR, EN, G>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -900,7 +956,7 @@ inline cudaError_t warp_rkck_occ_nr(const MechDev& M, int threads, int* bps)
 template <typename R, int NR, int OCC, bool EN>
 inline cudaError_t warp_launch_nr(Launch& L, int blocks, int threads, cudaStream_t st)
 {
-    const size_t sm = warp_smem_bytes(L.M, L.precision, threads);
+    const size_t sm = warp_smem_bytes<R, EN>(L.M, threads);
     cudaError_t e = cudaFuncSetAttribute(warp_init_kernel<R, NR, OCC, EN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
@@ -917,7 +973,7 @@ inline cudaError_t warp_launch_nr(Launch& L, int blocks, int threads, cudaStream
 template <typename R, int NR, int OCC, bool EN>
 inline cudaError_t warp_occ_nr(const MechDev& M, int precision, int threads, int* bps)
 {
-    const size_t sm = warp_smem_bytes(M, precision, threads);
+    const size_t sm = warp_smem_bytes<R, EN>(M, threads);
     cudaError_t e = cudaFuncSetAttribute(warp_integrate_kernel<R, NR, OCC, EN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
