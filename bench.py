@@ -49,13 +49,15 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture (profiles/), valid only for the kernel sources whose hash is the
-# key: workload -> (bytes, cells in the captured launch). A capture on fewer
-# cells than the benchmarked workload is scaled by the cell count.
+# capture (profiles/), valid only for the kernel sources whose hash is the key
+# and for the captured launch shape (block threads, blocks per SM, staging,
+# register budget, layout): (workload, shape) -> (bytes, cells in the captured
+# launch). A capture on fewer cells than the benchmarked workload is scaled by
+# the cell count.
 TRAFFIC = {
-    "2b7b28e9ce63": {
-        "h2co_13sp_rkc": (111.619817e9 + 92.057219e9, 262144),
-        "ch4_53sp_rkc_mixed": (270.663680e6 + 24.430848e6, 65536),
+    "b667e9f0eb0a": {
+        ("h2co_13sp_rkc", (32, 24, 0, 1, 1)): (111.008889e9 + 91.740372e9, 262144),
+        ("ch4_53sp_rkc_mixed", (256, 3, 0, 1, 2)): (272.683264e6 + 26.583040e6, 65536),
     },
 }
 
@@ -398,7 +400,9 @@ def run_kin(args):
     bind64 = t64 >= t32
     achieved = (ops64 if bind64 else ops32) / (kavg * 1e-3) / 1e9
     peak = peak64 if bind64 else peak32
-    tr = TRAFFIC.get(kernel_hash(), {}).get(name)
+    shape_key = tuple(int(shape[k]) for k in ("block_threads", "blocks_per_sm", "staging", "occupancy",
+                                                 "layout"))
+    tr = TRAFFIC.get(kernel_hash(), {}).get((name, shape_key))
     if tr is not None:
         tr = tr[0] * cells / tr[1]
 
