@@ -457,12 +457,16 @@ def run_kin(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32+f64",
             "data": "synthetic (seeded generator standing in for the paper's mechanisms and states)",
-            "config": dict(workload_config(name, cells, sigma, args.order), launch_shape=shape),
+            "config": dict(workload_config(name, cells, sigma, args.order), launch_shape=shape,
+                           f_evaluation=feval_name(km, prec, shape, cells, energy,
+                                                   layout_name(km, method, shape, cells))),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "G %s lane-ops/s" % ("FP64" if bind64 else "FP32"),
                          "frac": achieved / peak, "traffic": tr,
-                         "kernel": "kin_integrate launch (init + sort + integrate kernels, %s layout)"
-                                   % layout_name(km, method, shape, cells),
+                         "kernel": "kin_integrate launch (init + sort + integrate kernels, %s layout, "
+                                   "%s f)" % (layout_name(km, method, shape, cells),
+                                              feval_name(km, prec, shape, cells, energy,
+                                                         layout_name(km, method, shape, cells))),
                          "peak_basis": "derived: %d %s lanes/SM/clk x 152 SMs x 2070 MHz"
                                        % ((FP64_LANES_PER_SM, "FP64") if bind64 else (FP32_LANES_PER_SM, "FP32")),
                          "kernel_ms": kavg, "fp64_ops_per_launch": ops64,
@@ -667,6 +671,17 @@ def run_divergence(args):
                       **out}))
     km.close()
     return 0
+
+
+def feval_name(km, prec, shape, cells, energy, layout):
+    """'generated' where the library's automatic choice takes the generated f
+    (lane layout, FP64, isothermal, staging 0, a small mechanism, a large
+    call), else 'tables'."""
+    from paper_1309_2710_gb300 import kin
+    gen = (layout == "lane-per-cell" and prec == synth.FP64 and not energy
+           and shape.get("staging", 0) == kin.STAGE_GLOBAL and km.n_species <= kin.GEN_MAX_SPECIES
+           and km.n_reactions <= kin.GEN_MAX_REACTIONS and cells >= kin.GEN_MIN_CELLS)
+    return "generated" if gen else "tables"
 
 
 def layout_name(km, method, shape, cells):

@@ -90,6 +90,26 @@ extern "C" {
 #define KIN_WARP_MIN_REACTIONS 256
 #define KIN_WARP_MAX_CELLS_PER_SM 64
 
+/* how the lane-per-cell layout evaluates f (kin_opts.feval) */
+#define KIN_FEVAL_AUTO 0      /* the generated f for a call of at least KIN_GEN_MIN_CELLS
+                                 cells that it serves (below), else the tables: the
+                                 one-time compilation pays for itself on large calls */
+#define KIN_FEVAL_TABLE 1     /* one kernel for every mechanism: f reads the mechanism's
+                                 device tables, its concentrations and rates of progress
+                                 sit in per-lane arrays */
+#define KIN_FEVAL_GENERATED 2 /* f for this mechanism as straight-line FP64 code (species
+                                 indices, efficiencies and coefficients as literals,
+                                 concentrations and production rates in registers),
+                                 compiled with NVRTC on first use and cached per device and
+                                 mechanism. Serves KIN_FP64, isothermal, KIN_LAYOUT_LANE,
+                                 KIN_STAGE_GLOBAL and mechanisms of at most
+                                 KIN_GEN_MAX_SPECIES species and KIN_GEN_MAX_REACTIONS
+                                 reactions; KIN_EUNSUPPORTED otherwise or without NVRTC,
+                                 KIN_ECUDA if the compilation fails */
+#define KIN_GEN_MAX_SPECIES 32
+#define KIN_GEN_MAX_REACTIONS 256
+#define KIN_GEN_MIN_CELLS 65536
+
 /* per-cell status */
 #define KIN_CELL_OK 0
 #define KIN_CELL_MAXSTEPS 1  /* attempted-step limit reached */
@@ -162,6 +182,10 @@ typedef struct {
                               of the state (error norm, spectral radius) and is
                               written back to T. Needs the mechanism's cp and Hf
                               (else KIN_EUNSUPPORTED) */
+    int32_t feval;         /* KIN_FEVAL_*: tables or generated f (lane layout). Both follow
+                              the same method and decisions; the generated f rounds its
+                              sums in another order (results agree within the
+                              integration tolerance, not bit for bit) */
     void *stream;          /* cudaStream_t */
 } kin_opts;
 
@@ -281,6 +305,15 @@ int kin_integrate_noalloc(const kin_mech *m, int64_t cells, double *T, const dou
 int kin_rates(const kin_mech *m, int64_t cells, const double *T, const double *p,
               const double *Y, int64_t ldY, double *dYdt, int32_t precision, void *stream,
               void *workspace, int64_t workspace_bytes);
+
+/* The CUDA source of the generated f (KIN_FEVAL_GENERATED) for a mechanism
+ * description: straight-line FP64 code of Eqs. (E:mass), (E:spec-rate) and
+ * (E:rxn-rate) with the mechanism's indices and constants as literals. Host
+ * only (no device needed). Writes at most cap - 1 characters and a NUL to buf
+ * (buf may be NULL when cap is 0) and returns the full length, so a call with
+ * cap 0 sizes the buffer. KIN_EINVAL for an invalid description,
+ * KIN_EUNSUPPORTED beyond KIN_GEN_MAX_SPECIES / KIN_GEN_MAX_REACTIONS. */
+int64_t kin_generated_f_source(const kin_mech_desc *desc, char *buf, int64_t cap);
 
 /* Library version string. */
 const char *kin_version(void);

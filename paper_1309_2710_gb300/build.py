@@ -14,7 +14,12 @@ SOURCES = ["kernels.cu", "abi.cu", "no_alloc.cu", "inst_rkc_f64.cu", "inst_rkc_f
            "inst_rkck_f64.cu", "inst_rkck_f32.cu", "inst_warp_f64.cu", "inst_warp_f32.cu",
            "inst_warp_f64_hi.cu", "inst_warp_f32_hi.cu", "inst_energy_f64.cu", "inst_energy_f32.cu",
            "inst_warp_energy_f64.cu", "inst_warp_energy_f32.cu", "inst_warp_energy_f64_hi.cu",
-           "inst_warp_energy_f32_hi.cu", "inst_warp_rkck_f64.cu", "inst_warp_rkck_f32.cu"]
+           "inst_warp_energy_f32_hi.cu", "inst_warp_rkck_f64.cu", "inst_warp_rkck_f32.cu", "codegen.cu"]
+# sources that the run-time compilation of a generated f includes, embedded
+# in the library as strings: (C identifier, path)
+EMBEDDED = [("kin_src_kernels", os.path.join(CSRC, "kernels.cuh")),
+            ("kin_src_dev", os.path.join(CSRC, "kin_dev.cuh")),
+            ("kin_src_api", os.path.join(HERE, "..", "include", "kin.h"))]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,14 +43,31 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
+def write_embedded() -> str:
+    """_build/kin_embedded.h: the kernel headers as raw string literals."""
+    out = os.path.join(OUT_DIR, "kin_embedded.h")
+    parts = ["// written by build.py: sources for the run-time compilation of a generated f\n#pragma once\n"]
+    for name, path in EMBEDDED:
+        text = open(path).read()
+        if ")KINSRC\"" in text:
+            raise RuntimeError("%s contains the raw-string delimiter" % path)
+        parts.append('static const char* const %s = R"KINSRC(%s)KINSRC";\n' % (name, text))
+    body = "".join(parts)
+    if not os.path.exists(out) or open(out).read() != body:
+        with open(out, "w") as f:
+            f.write(body)
+    return out
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile every translation unit in parallel and link libkin.so."""
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
+    write_embedded()
     nvcc = _nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                     "-I", os.path.join(HERE, "..", "include")]
+                     "-I", os.path.join(HERE, "..", "include"), "-I", OUT_DIR]
     if verbose:
         common += ["-Xptxas", "-v"]
 
@@ -62,7 +84,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stderr)

@@ -8,8 +8,10 @@
 #include <cstdio>
 #include <climits>
 #include <cstring>
+#include <string>
 #include <vector>
 
+#include "codegen.h"
 #include "kin_dev.cuh"
 
 using namespace kin;
@@ -19,7 +21,8 @@ struct kin_mech {
     void* buf;
     int device;
     int nS, nR, nM;
-    bool thermo;  // cp and Hf given (energy equation available)
+    bool thermo;          // cp and Hf given (energy equation available)
+    std::string gen_src;  // the generated f (empty when the mechanism is too large for it)
 };
 
 namespace {
@@ -149,6 +152,8 @@ int check_opts(const kin_opts* o)
     if (o->layout != KIN_LAYOUT_AUTO && o->layout != KIN_LAYOUT_LANE && o->layout != KIN_LAYOUT_WARP)
         return fail(KIN_EINVAL, "unknown layout %d", o->layout);
     if (o->energy != 0 && o->energy != 1) return fail(KIN_EINVAL, "energy must be 0 or 1");
+    if (o->feval != KIN_FEVAL_AUTO && o->feval != KIN_FEVAL_TABLE && o->feval != KIN_FEVAL_GENERATED)
+        return fail(KIN_EINVAL, "unknown feval %d", o->feval);
     return KIN_OK;
 }
 
@@ -169,7 +174,45 @@ extern "C" {
 
 const char* kin_last_error(void) { return g_err; }
 
-const char* kin_version(void) { return "kin 0.2 (sm_103a)"; }
+const char* kin_version(void) { return "kin 0.3 (sm_103a)"; }
+
+int64_t kin_generated_f_source(const kin_mech_desc* d, char* buf, int64_t cap)
+{
+    g_err[0] = 0;
+    if (!d) return fail(KIN_EINVAL, "desc is NULL");
+    if (cap < 0 || (cap > 0 && !buf)) return fail(KIN_EINVAL, "buf is NULL or cap < 0");
+    const int nS = d->n_species, nR = d->n_reactions;
+    if (nS < 1 || nS > KIN_MAX_SPECIES || nR < 0 || nR > KIN_MAX_REACTIONS)
+        return fail(KIN_EINVAL, "n_species %d / n_reactions %d out of range", nS, nR);
+    if (!gen_eligible(nS, nR))
+        return fail(KIN_EUNSUPPORTED, "the generated f covers at most %d species and %d reactions",
+                    KIN_GEN_MAX_SPECIES, KIN_GEN_MAX_REACTIONS);
+    if (!d->W || (nR > 0 && (!d->reac || !d->prod || !d->type)))
+        return fail(KIN_EINVAL, "W, reac, prod and type must be non-NULL");
+    int rows = 0;
+    for (int i = 0; i < nS; ++i)
+        if (!finite_pos(d->W[i])) return fail(KIN_EINVAL, "W[%d] must be finite and > 0", i);
+    for (int j = 0; j < nR; ++j) {
+        const int t = d->type[j];
+        if (t != KIN_RXN_PLAIN && t != KIN_RXN_THIRD_BODY && t != KIN_RXN_FALLOFF)
+            return fail(KIN_EINVAL, "reaction %d: unknown type %d", j, t);
+        for (int k = 0; k < 2; ++k)
+            if (d->reac[2 * j + k] < -1 || d->reac[2 * j + k] >= nS || d->prod[2 * j + k] < -1 ||
+                d->prod[2 * j + k] >= nS)
+                return fail(KIN_EINVAL, "reaction %d: species index out of range", j);
+        rows += t != KIN_RXN_PLAIN;
+    }
+    if (rows > 0 && !d->eff) return fail(KIN_EINVAL, "eff is NULL but %d reactions need efficiencies", rows);
+    for (int64_t k = 0; k < (int64_t)rows * nS; ++k)
+        if (!std::isfinite(d->eff[k])) return fail(KIN_EINVAL, "non-finite efficiency");
+    const std::string src = gen_f_source(d);
+    if (cap > 0) {
+        const int64_t n = std::min<int64_t>(cap - 1, (int64_t)src.size());
+        memcpy(buf, src.data(), (size_t)n);
+        buf[n] = 0;
+    }
+    return (int64_t)src.size();
+}
 
 int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
 {
@@ -344,6 +387,7 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     M.Hf = thermo ? (const double*)(b + oHf) : nullptr;
     m->nS = nS; m->nR = nR; m->nM = nM;
     m->thermo = thermo;
+    if (gen_eligible(nS, nR)) m->gen_src = gen_f_source(d);
     e = launch_rkc_table((double*)(b + oTab), 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { cudaFree(m->buf); delete m; return cuda_fail(e, "RKC table"); }
@@ -453,6 +497,24 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     P.cell_st = (uint8_t*)(base + w.st);
     P.order = (int32_t*)(base + w.order);
     if (total > INT32_MAX) return fail(KIN_EINVAL, "more than 2^31-1 cells in one call");
+    // f: tables, or the mechanism's generated code (lane layout, FP64, isothermal)
+    bool gen = false;
+    GenKernels gk{};
+    if (o->feval == KIN_FEVAL_GENERATED || (o->feval == KIN_FEVAL_AUTO && total >= KIN_GEN_MIN_CELLS)) {
+        const bool serves = g.layout == KIN_LAYOUT_LANE && o->precision == KIN_FP64 && !o->energy &&
+                            o->staging == KIN_STAGE_GLOBAL && !m->gen_src.empty();
+        if (serves) {
+            std::string log;
+            const int grc = gen_kernels(m->device, m->gen_src, &gk, &log);
+            if (grc == KIN_OK) gen = true;
+            else if (o->feval == KIN_FEVAL_GENERATED)
+                return fail(grc, "generated f: %.400s", log.c_str());
+        } else if (o->feval == KIN_FEVAL_GENERATED) {
+            return fail(KIN_EUNSUPPORTED, "the generated f serves the lane layout, KIN_FP64, no energy "
+                                          "equation, KIN_STAGE_GLOBAL and at most %d species / %d reactions",
+                        KIN_GEN_MAX_SPECIES, KIN_GEN_MAX_REACTIONS);
+        }
+    }
     cudaStream_t st = (cudaStream_t)o->stream;
     cudaError_t e = cudaMemsetAsync(base + w.header, 0, 512, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -467,6 +529,8 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
             {{launch_warp_f64_en_o0, launch_warp_f64_en_o1}, {launch_warp_f32_en_o0, launch_warp_f32_en_o1}}};
         e = fns[o->energy][o->precision == KIN_MIXED][o->occupancy ? 1 : 0](P, blocks, g.threads, st);
     }
+    else if (gen)
+        e = gen_launch(gk, P, o->occupancy, blocks, g.threads, st);
     else
         e = launch_integrate(P, o->energy ? KIN_STAGE_GLOBAL : o->staging, o->occupancy, blocks,
                              g.threads, st);
@@ -543,7 +607,8 @@ int kin_rates(const kin_mech* m, int64_t cells, const double* T, const double* p
     if (ldY > INT32_MAX) return fail(KIN_EINVAL, "ldY >= 2^31");
     if (!is_device_ptr(T) || !is_device_ptr(p) || !is_device_ptr(Y) || !is_device_ptr(dYdt))
         return fail(KIN_EINVAL, "T, p, Y and dYdt must be device memory");
-    kin_opts o{KIN_RKC, precision, 0, 0, 0, KIN_STAGE_GLOBAL, KIN_OCC_DEFAULT, 0, KIN_LAYOUT_LANE, 0, stream};
+    kin_opts o{KIN_RKC, precision, 0, 0, 0, KIN_STAGE_GLOBAL, KIN_OCC_DEFAULT, 0, KIN_LAYOUT_LANE, 0,
+               KIN_FEVAL_TABLE, stream};
     Grid g;
     int rc = grid_for(m, &o, cells, &g);
     if (rc) return rc;

@@ -30,10 +30,12 @@
 //  * No tensor cores: the stoichiometric contraction is sparse (about four
 //    nonzeros per reaction).
 #pragma once
+#ifndef __CUDACC_RTC__  // run-time compilation (generated f) brings its own definitions
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
+#endif
 
 #include "kin_dev.cuh"
 
@@ -491,24 +493,39 @@ __device__ __forceinline__ bool power_post(int nS, Lane<double> Y, Lane<double> 
     return false;
 }
 
+// How the lane kernels evaluate the isothermal f: a policy class F with
+// F::eval<R, KT>(M, Ctot, invCtot, K, KR, C, OM, x, out). TableF is feval
+// over the mechanism's device tables (any mechanism, either precision); a
+// generated policy (FP64 only) is f for one mechanism as straight-line code,
+// compiled at run time, with the same arguments.
+struct TableF {
+    template <typename R, typename KT>
+    __device__ __forceinline__ static void eval(const MechDev& M, double Ctot, double invCtot, Lane<KT> K,
+                                                Lane<KT> KR, Lane<R> C, Lane<R> OM, Lane<double> x,
+                                                Lane<double> out)
+    {
+        feval<R, KT>(M, Ctot, invCtot, K, KR, C, OM, x, out);
+    }
+};
+
 // f in FP64 for a spectral-radius estimate: the lane's rate scratch in the
 // FP64 path, the separate FP64 scratch in the mixed-precision path (whose
 // rate constants are the same FP32 values, promoted).
-template <typename R, int STG>
+template <typename R, int STG, typename F>
 __device__ __forceinline__ void feval_sig(const Views<R, STG>& W, double Ctot, double invCtot,
                                           Lane<R> K, Lane<R> KR, Lane<double> x, Lane<double> out)
 {
     if constexpr (sizeof(R) == 4)
-        feval<double>(W.M, Ctot, invCtot, K, KR, W.C64, W.OM64, x, out);
+        F::template eval<double, R>(W.M, Ctot, invCtot, K, KR, W.C64, W.OM64, x, out);
     else
-        feval<double>(W.M, Ctot, invCtot, K, KR, W.C, W.OM, x, out);
+        F::template eval<double, R>(W.M, Ctot, invCtot, K, KR, W.C, W.OM, x, out);
 }
 
 // ------------------------------------------------------------- pre-pass --
 // For every cell g (grid-stride, uniform across lanes): rate constants, f(y0),
 // and for RKC the spectral radius (Section 2.3) and the initial step
 // h1 = 0.1 h0 / ||Delta_0||^(1/2), h0 = 1/sigma.
-template <int METHOD, typename R, int STG, bool EN>
+template <int METHOD, typename R, int STG, bool EN, typename F = TableF>
 __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launch L)
 {
     const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -527,14 +544,14 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
         // f in the rate type, and f in FP64 for the spectral radius
         auto frate = [&](Lane<double> x, Lane<double> o) {
             if constexpr (EN) feval_energy<R>(M, p, W.C, W.OM, x, o);
-            else feval<R>(M, Ctot, invCtot, K, KR, W.C, W.OM, x, o);
+            else F::template eval<R, R>(M, Ctot, invCtot, K, KR, W.C, W.OM, x, o);
         };
         auto fsig = [&](Lane<double> x, Lane<double> o) {
             if constexpr (EN) {
                 if constexpr (sizeof(R) == 4) feval_energy<double>(M, p, W.C64, W.OM64, x, o);
                 else feval_energy<double>(M, p, W.C, W.OM, x, o);
             } else {
-                feval_sig(W, Ctot, invCtot, K, KR, x, o);
+                feval_sig<R, STG, F>(W, Ctot, invCtot, K, KR, x, o);
             }
         };
         Lane<double> Y = W.V(V_Y), F0 = W.F0cell(g), X = W.V(V_X), FX = W.V(V_FX), RS = W.V(V_RS);
@@ -666,7 +683,7 @@ struct LaneState {
     PowerState P;     // RKC power-method sigma in progress
 };
 
-template <int METHOD, typename R, int STG, bool EN>
+template <int METHOD, typename R, int STG, bool EN, typename F = TableF>
 struct Integrator {
     Views<R, STG> W;
     const Launch& L;
@@ -1097,9 +1114,10 @@ struct Integrator {
                 else
                     feval_energy<double>(M, S.p, W.C, W.OM, V(S.in_v), V(S.out_v));
             } else if (sizeof(R) == 4 && sig) {
-                feval<double>(M, S.Ctot, S.invCtot, K, KR, W.C64, W.OM64, V(S.in_v), V(S.out_v));
+                F::template eval<double, R>(M, S.Ctot, S.invCtot, K, KR, W.C64, W.OM64, V(S.in_v),
+                                            V(S.out_v));
             } else {
-                feval<R>(M, S.Ctot, S.invCtot, K, KR, W.C, W.OM, V(S.in_v), V(S.out_v));
+                F::template eval<R, R>(M, S.Ctot, S.invCtot, K, KR, W.C, W.OM, V(S.in_v), V(S.out_v));
             }
             S.nfe++;
             S.nfs += sig;
@@ -1115,14 +1133,16 @@ struct Integrator {
 // OCC selects the register budget: 0 = at most 128 registers (16 resident
 // warps per SM), 1 = at most 85 (24 resident warps per SM; the rarely used
 // state spills to L1-backed local memory).
-template <int METHOD, typename R, int STG, int OCC, bool EN>
+template <int METHOD, typename R, int STG, int OCC, bool EN, typename F = TableF>
 __global__ void __launch_bounds__(128, OCC ? 6 : 4) integrate_kernel(const __grid_constant__ Launch L)
 {
     const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= L.nslots) return;
-    Integrator<METHOD, R, STG, EN> I(L, slot);
+    Integrator<METHOD, R, STG, EN, F> I(L, slot);
     I.run();
 }
+
+#ifndef __CUDACC_RTC__
 
 // ------------------------------------------------------- launch templates --
 template <int METHOD, typename R, int STG, int OCC, bool EN>
@@ -1203,5 +1223,7 @@ inline cudaError_t occ_energy(int occ, int threads, size_t sm, int* bps)
     return occ ? occ_one<METHOD, R, 0, 1, true>(threads, sm, bps)
                : occ_one<METHOD, R, 0, 0, true>(threads, sm, bps);
 }
+
+#endif  // __CUDACC_RTC__
 
 }  // namespace kin

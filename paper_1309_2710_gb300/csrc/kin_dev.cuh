@@ -5,7 +5,9 @@
 // ([element][lane] or [element][cell]) so that the 32 lanes of a warp touching
 // element e of their own cells hit consecutive words.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 #include "../../include/kin.h"
 
@@ -110,6 +112,7 @@ struct WsLayout {
 WsLayout ws_layout(const MechDev& M, int precision, int sigma_method, int energy, int64_t nslots,
                    int64_t cells);
 
+#ifndef __CUDACC_RTC__  // host-side declarations (absent from run-time compiled code)
 // Host-side helpers implemented in kernels.cu.
 cudaError_t launch_integrate(Launch& L, int staging, int occupancy, int blocks, int threads,
                              cudaStream_t st);
@@ -173,5 +176,6 @@ inline int warp_cell_lanes(int method, int nV) { return method == KIN_RKCK && nV
 int set_last_error(int code, const char* fmt, ...);
 cudaError_t integrate_occupancy(const MechDev& M, int method, int precision, int staging,
                                 int occupancy, int energy, int threads, int* blocks_per_sm);
+#endif  // __CUDACC_RTC__
 
 }  // namespace kin

@@ -26,6 +26,8 @@ SIGMA_GERSHGORIN, SIGMA_POWER = 0, 1
 LAYOUT_AUTO, LAYOUT_LANE, LAYOUT_WARP = 0, 1, 2
 WARP_MIN_REACTIONS = 256
 WARP_MAX_CELLS_PER_SM = 64
+FEVAL_AUTO, FEVAL_TABLE, FEVAL_GENERATED = 0, 1, 2
+GEN_MAX_SPECIES, GEN_MAX_REACTIONS, GEN_MIN_CELLS = 32, 256, 65536
 MAX_INSTANCES = 128
 NSTATS = 5  # per-cell statistics: f evals, accepted, rejected, sigma estimates, f evals in them
 
@@ -51,7 +53,7 @@ class Opts(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("staging", ctypes.c_int32),
                 ("occupancy", ctypes.c_int32), ("sigma", ctypes.c_int32),
                 ("layout", ctypes.c_int32), ("energy", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("feval", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class Instance(ctypes.Structure):
@@ -77,6 +79,7 @@ _SIGNATURES = {
                                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "kin_version": (ctypes.c_char_p, []),
+    "kin_generated_f_source": (ctypes.c_int64, [ctypes.POINTER(MechDesc), ctypes.c_char_p, ctypes.c_int64]),
     "kin_integrate_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -129,6 +132,39 @@ def _stream_handle(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(int(stream))
 
 
+def _mech_desc(desc):
+    """kin_mech_desc of a mechanism object (array attributes W, lnA, beta, Ea,
+    reac, prod, rtype, eff, lnA0, beta0, Ea0 and optionally cp, Hf), and the
+    arrays it points into (keep them alive while the description is used)."""
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    a = dict(W=f64(desc.W), lnA=f64(desc.lnA), beta=f64(desc.beta), Ea=f64(desc.Ea),
+             reac=np.ascontiguousarray(desc.reac, dtype=np.int32),
+             prod=np.ascontiguousarray(desc.prod, dtype=np.int32),
+             type=np.ascontiguousarray(desc.rtype, dtype=np.int8),
+             eff=f64(np.asarray(desc.eff).reshape(-1)), lnA0=f64(desc.lnA0),
+             beta0=f64(desc.beta0), Ea0=f64(desc.Ea0))
+    if getattr(desc, "cp", None) is not None:
+        a.update(cp=f64(desc.cp), Hf=f64(desc.Hf))
+    d = MechDesc(int(len(desc.W)), int(len(desc.lnA)),
+                 *[a[k].ctypes.data if k in a and a[k].size else None
+                   for k in ("W", "lnA", "beta", "Ea", "reac", "prod", "type", "eff",
+                             "lnA0", "beta0", "Ea0", "cp", "Hf")])
+    return d, a
+
+
+def generated_f_source(desc) -> str:
+    """The CUDA source of the generated f for a mechanism
+    (kin_generated_f_source; host only)."""
+    d, keep = _mech_desc(desc)
+    n = lib().kin_generated_f_source(ctypes.byref(d), None, 0)
+    if n < 0:
+        _check(int(n))
+    buf = ctypes.create_string_buffer(int(n) + 1)
+    lib().kin_generated_f_source(ctypes.byref(d), buf, int(n) + 1)
+    del keep
+    return buf.value.decode()
+
+
 class Mechanism:
     """Device-resident mechanism tables (kin_create_mechanism). `desc` has the
     array attributes W, lnA, beta, Ea, reac, prod, rtype, eff, lnA0, beta0, Ea0
@@ -137,22 +173,8 @@ class Mechanism:
     def __init__(self, desc):
         self.n_species = int(len(desc.W))
         self.n_reactions = int(len(desc.lnA))
-        f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
-        self._arrays = dict(
-            W=f64(desc.W), lnA=f64(desc.lnA), beta=f64(desc.beta), Ea=f64(desc.Ea),
-            reac=np.ascontiguousarray(desc.reac, dtype=np.int32),
-            prod=np.ascontiguousarray(desc.prod, dtype=np.int32),
-            type=np.ascontiguousarray(desc.rtype, dtype=np.int8),
-            eff=f64(np.asarray(desc.eff).reshape(-1)), lnA0=f64(desc.lnA0),
-            beta0=f64(desc.beta0), Ea0=f64(desc.Ea0))
-        self.has_thermo = getattr(desc, "cp", None) is not None
-        if self.has_thermo:
-            self._arrays.update(cp=f64(desc.cp), Hf=f64(desc.Hf))
-        a = self._arrays
-        d = MechDesc(self.n_species, self.n_reactions,
-                     *[a[k].ctypes.data if k in a and a[k].size else None
-                       for k in ("W", "lnA", "beta", "Ea", "reac", "prod", "type", "eff",
-                                 "lnA0", "beta0", "Ea0", "cp", "Hf")])
+        d, self._arrays = _mech_desc(desc)
+        self.has_thermo = "cp" in self._arrays
         h = ctypes.c_void_p()
         _check(lib().kin_create_mechanism(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -171,7 +193,8 @@ class Mechanism:
     def workspace_bytes(self, method=RKC, precision=FP64, cells=0, block_threads=0,
                         blocks_per_sm=0, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT,
                         sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0) -> int:
-        o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, sigma, layout, energy, None)
+        o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, sigma, layout, energy,
+                 FEVAL_AUTO, None)
         n = lib().kin_workspace_bytes(self.handle, ctypes.byref(o), int(cells))
         if n < 0:
             _check(int(n))
@@ -225,7 +248,7 @@ class Cells:
 def integrate(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP64,
               status=None, stats=None, workspace=None, stream=None, max_steps=0,
               block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT,
-              sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0):
+              sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0, feval=FEVAL_AUTO):
     """Integrate every cell over dt in place (kin_integrate)."""
     cells, ld = _check_state(mech, T, p, Y)
     _check_outputs(cells, status, stats)
@@ -233,7 +256,7 @@ def integrate(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP
         workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm, Y.device,
                                    staging, occupancy, sigma, layout, energy)
     o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging, occupancy, sigma,
-             layout, energy, _stream_handle(stream))
+             layout, energy, feval, _stream_handle(stream))
     _check(lib().kin_integrate(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), ld, float(dt),
                                float(rtol), float(atol), ctypes.byref(o), _ptr(status),
                                _ptr(stats), _ptr(workspace), workspace.numel()))
@@ -253,7 +276,8 @@ def make_instances(mech: Mechanism, parts: Sequence[Cells]):
 
 def integrate_batch(mech: Mechanism, parts: Sequence[Cells], method=RKC, precision=FP64,
                     workspace=None, stream=None, max_steps=0, block_threads=0, blocks_per_sm=0,
-                    staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT, sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0):
+                    staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT, sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0,
+                    feval=FEVAL_AUTO):
     """Integrate several instances in one persistent launch (kin_integrate_batch)."""
     if not 1 <= len(parts) <= MAX_INSTANCES:
         raise ValueError("1..%d instances per launch" % MAX_INSTANCES)
@@ -263,7 +287,7 @@ def integrate_batch(mech: Mechanism, parts: Sequence[Cells], method=RKC, precisi
         workspace = mech.workspace(method, precision, cells, block_threads, blocks_per_sm,
                                    parts[0].Y.device, staging, occupancy, sigma, layout, energy)
     o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging, occupancy, sigma,
-             layout, energy, _stream_handle(stream))
+             layout, energy, feval, _stream_handle(stream))
     _check(lib().kin_integrate_batch(mech.handle, len(parts), arr, ctypes.byref(o),
                                      _ptr(workspace), workspace.numel()))
 
@@ -286,9 +310,11 @@ def version() -> str:
 
 def host_buffer(mech: Mechanism, cells: int, method=RKC, precision=FP64, device=None,
                 block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL,
-                occupancy=OCC_DEFAULT, sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0) -> torch.Tensor:
+                occupancy=OCC_DEFAULT, sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0,
+                feval=FEVAL_AUTO) -> torch.Tensor:
     """Device buffer for integrate_host (kin_host_buffer_bytes)."""
-    o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, sigma, layout, energy, None)
+    o = Opts(method, precision, 0, block_threads, blocks_per_sm, staging, occupancy, sigma, layout, energy,
+             feval, None)
     n = lib().kin_host_buffer_bytes(mech.handle, ctypes.byref(o), int(cells))
     if n < 0:
         _check(int(n))
@@ -298,7 +324,7 @@ def host_buffer(mech: Mechanism, cells: int, method=RKC, precision=FP64, device=
 def integrate_host(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precision=FP64,
                    status=None, stats=None, buffer=None, stream=None, max_steps=0,
                    block_threads=0, blocks_per_sm=0, staging=STAGE_GLOBAL, occupancy=OCC_DEFAULT,
-                   sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0):
+                   sigma=SIGMA_GERSHGORIN, layout=LAYOUT_AUTO, energy=0, feval=FEVAL_AUTO):
     """kin_integrate_host: T, p, Y (in place), status, stats are CPU tensors
     (pin them for asynchronous copies). Returns after enqueueing; synchronise
     the stream before reading the results."""
@@ -311,9 +337,9 @@ def integrate_host(mech: Mechanism, T, p, Y, dt, rtol, atol, method=RKC, precisi
     _check_outputs(cells, status, stats, cuda=False)
     if buffer is None:
         buffer = host_buffer(mech, cells, method, precision, None, block_threads, blocks_per_sm,
-                             staging, occupancy, sigma, layout, energy)
+                             staging, occupancy, sigma, layout, energy, feval)
     o = Opts(method, precision, max_steps, block_threads, blocks_per_sm, staging, occupancy, sigma,
-             layout, energy, _stream_handle(stream))
+             layout, energy, feval, _stream_handle(stream))
     _check(lib().kin_integrate_host(mech.handle, cells, _ptr(T), _ptr(p), _ptr(Y), int(Y.stride(0)),
                                     float(dt), float(rtol), float(atol), ctypes.byref(o),
                                     _ptr(status), _ptr(stats), _ptr(buffer), buffer.numel()))

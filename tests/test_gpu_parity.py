@@ -265,7 +265,7 @@ def test_invalid_arguments_raise():
     h = np.zeros(8)
     rc = kin.lib().kin_integrate(km.handle, 8, ctypes.c_void_p(h.ctypes.data), kin._ptr(pd),
                                  kin._ptr(Yd), 8, 1e-6, 1e-6, 1e-10,
-                                 ctypes.byref(kin.Opts(1, 0, 0, 0, 0, 0, 0, 0, 0, 0, None)), None, None,
+                                 ctypes.byref(kin.Opts(1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, None)), None, None,
                                  kin._ptr(ws), ws.numel())
     assert rc == kin.KIN_EINVAL
 

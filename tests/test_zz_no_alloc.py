@@ -30,7 +30,7 @@ def _run(fn_name, km, T, p, Y, dt, ws=None):
     Yd = torch.as_tensor(np.ascontiguousarray(Y), device=DEV)
     st = torch.zeros(cells, dtype=torch.uint8, device=DEV)
     sta = torch.zeros((cells, kin.NSTATS), dtype=torch.int32, device=DEV)
-    o = kin.Opts(kin.RKC, kin.FP64, 0, 0, 0, 0, 0, 0, kin.LAYOUT_AUTO, 0,
+    o = kin.Opts(kin.RKC, kin.FP64, 0, 0, 0, 0, 0, 0, kin.LAYOUT_AUTO, 0, kin.FEVAL_AUTO,
                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     args = [km.handle, cells, kin._ptr(Td), kin._ptr(pd), kin._ptr(Yd), cells, dt, 1e-6, 1e-10,
             ctypes.byref(o), kin._ptr(st), kin._ptr(sta)]
@@ -59,7 +59,7 @@ def test_noalloc_rejects_cells_beyond_the_fixed_array():
     km = kin.Mechanism(m)
     one = torch.zeros(1, dtype=torch.float64, device=DEV)
     Y = torch.zeros((m.n_species, 1), dtype=torch.float64, device=DEV)
-    o = kin.Opts(kin.RKC, kin.FP64, 0, 0, 0, 0, 0, 0, kin.LAYOUT_AUTO, 0, None)
+    o = kin.Opts(kin.RKC, kin.FP64, 0, 0, 0, 0, 0, 0, kin.LAYOUT_AUTO, 0, kin.FEVAL_AUTO, None)
     # 10 million cells cannot fit in 64 MiB: refused before any launch or
     # pointer use
     rc = kin.lib().kin_integrate_noalloc(km.handle, 10_000_000, kin._ptr(one), kin._ptr(one),
