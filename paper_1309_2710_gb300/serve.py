@@ -67,8 +67,9 @@ class Request:
 class Group:
     """One mechanism/method/precision served together. `shape` is the launch
     shape of one slot's persistent launch (kin_opts fields block_threads,
-    blocks_per_sm, staging, occupancy, layout): a slot that leaves SM
-    resources free lets the other slots' launches run beside it."""
+    blocks_per_sm, staging, occupancy, layout, and the f evaluation feval): a
+    slot that leaves SM resources free lets the other slots' launches run
+    beside it."""
     mech: kin.Mechanism
     method: int
     precision: int
@@ -292,10 +293,13 @@ def percentiles(reqs: List[Request]):
 # waits for a short launch rather than a long one.
 SERVE_BATCH_CELLS = {"h2co_13sp_rkc": 131072, "ch4_53sp_rkc_mixed": 32768}
 SERVE_SLOTS = 4
+# The f evaluation is pinned per group (the automatic choice depends on the
+# launch's cell count, and a request must get the same bits in any batch).
 SERVE_SHAPES = {
     "h2co_13sp_rkc": dict(block_threads=128, blocks_per_sm=2, occupancy=kin.OCC_HIGH,
-                          layout=kin.LAYOUT_LANE),
-    "ch4_53sp_rkc_mixed": dict(block_threads=256, blocks_per_sm=1, layout=kin.LAYOUT_WARP),
+                          layout=kin.LAYOUT_LANE, feval=kin.FEVAL_GENERATED),
+    "ch4_53sp_rkc_mixed": dict(block_threads=256, blocks_per_sm=1, layout=kin.LAYOUT_WARP,
+                               feval=kin.FEVAL_TABLE),
 }
 
 

@@ -48,7 +48,8 @@ def _alone(groups, r):
     Yd = r.Y.to(d).contiguous()
     st = torch.empty(r.cells, dtype=torch.uint8, device=d)
     kin.integrate(g.mech, r.T.to(d), r.p.to(d), Yd, r.dt, r.rtol, r.atol, g.method, g.precision,
-                  status=st, sigma=g.sigma, layout=g.shape.get("layout", kin.LAYOUT_AUTO))
+                  status=st, sigma=g.sigma, layout=g.shape.get("layout", kin.LAYOUT_AUTO),
+                  feval=g.shape.get("feval", kin.FEVAL_AUTO))
     torch.cuda.synchronize()
     return Yd.cpu(), st.cpu()
 
