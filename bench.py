@@ -55,9 +55,10 @@ SM_MAX_MHZ = 2070.0
 # launch). A capture on fewer cells than the benchmarked workload is scaled by
 # the cell count.
 TRAFFIC = {
-    "b667e9f0eb0a": {
-        ("h2co_13sp_rkc", (32, 24, 0, 1, 1)): (111.008889e9 + 91.740372e9, 262144),
-        ("ch4_53sp_rkc_mixed", (256, 3, 0, 1, 2)): (272.683264e6 + 26.583040e6, 65536),
+    "0a9831263a2f": {
+        ("h2co_13sp_rkc", (32, 16, 0, 0, 1)): (3.765802e9 + 5.394754e9, 262144),
+        ("h2co_13sp_rkc", (32, 20, 0, 1, 1)): (60.121252864e9 + 41.039460096e9, 262144),
+        ("ch4_53sp_rkc_mixed", (256, 3, 0, 1, 2)): (271517696 + 26934272, 65536),
     },
 }
 
