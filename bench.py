@@ -55,12 +55,30 @@ SM_MAX_MHZ = 2070.0
 # launch). A capture on fewer cells than the benchmarked workload is scaled by
 # the cell count.
 TRAFFIC = {
-    "0a9831263a2f": {
-        ("h2co_13sp_rkc", (32, 16, 0, 0, 1)): (3.765802e9 + 5.394754e9, 262144),
-        ("h2co_13sp_rkc", (32, 20, 0, 1, 1)): (60.121252864e9 + 41.039460096e9, 262144),
-        ("ch4_53sp_rkc_mixed", (256, 3, 0, 1, 2)): (271517696 + 26934272, 65536),
+    "529606db80a6": {
+        ("h2co_13sp_rkc", (32, 16, 0, 0, 1)): (3829669632 + 5481403648, 262144),
+        ("h2co_13sp_rkc", (32, 20, 0, 1, 1)): (59821390080 + 40944381440, 262144),
+        ("ch4_53sp_rkc_mixed", (256, 3, 0, 1, 2)): (272005888 + 26279680, 65536),
     },
 }
+
+
+def traffic_for(name, shape_key, cells):
+    """DRAM bytes per launch for this workload and launch shape: the capture of
+    the same shape, else of the same kernel variant (staging, register budget,
+    layout) with the same resident lanes per SM; scaled to `cells`. Returns
+    (bytes or None, captured shape or None)."""
+    tab = TRAFFIC.get(kernel_hash(), {})
+    hit = tab.get((name, shape_key))
+    cap = shape_key
+    if hit is None:
+        for (nm, sk), v in tab.items():
+            if nm == name and sk[2:] == shape_key[2:] and sk[0] * sk[1] == shape_key[0] * shape_key[1]:
+                hit, cap = v, sk
+                break
+    if hit is None:
+        return None, None
+    return hit[0] * cells / hit[1], list(cap)
 
 
 def kernel_hash() -> str:
@@ -403,9 +421,7 @@ def run_kin(args):
     peak = peak64 if bind64 else peak32
     shape_key = tuple(int(shape[k]) for k in ("block_threads", "blocks_per_sm", "staging", "occupancy",
                                                  "layout"))
-    tr = TRAFFIC.get(kernel_hash(), {}).get((name, shape_key))
-    if tr is not None:
-        tr = tr[0] * cells / tr[1]
+    tr, tr_shape = traffic_for(name, shape_key, cells)
 
     # end to end: host (pinned) buffers through the public API, copies timed
     e2e = None
@@ -459,14 +475,14 @@ def run_kin(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32+f64",
             "data": "synthetic (seeded generator standing in for the paper's mechanisms and states)",
             "config": dict(workload_config(name, cells, sigma, args.order), launch_shape=shape,
-                           f_evaluation=feval_name(km, prec, shape, cells, energy,
+                           f_evaluation=feval_name(km, prec, shape, cells,
                                                    layout_name(km, method, shape, cells))),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "G %s lane-ops/s" % ("FP64" if bind64 else "FP32"),
-                         "frac": achieved / peak, "traffic": tr,
+                         "frac": achieved / peak, "traffic": tr, "traffic_capture_shape": tr_shape,
                          "kernel": "kin_integrate launch (init + sort + integrate kernels, %s layout, "
                                    "%s f)" % (layout_name(km, method, shape, cells),
-                                              feval_name(km, prec, shape, cells, energy,
+                                              feval_name(km, prec, shape, cells,
                                                          layout_name(km, method, shape, cells))),
                          "peak_basis": "derived: %d %s lanes/SM/clk x 152 SMs x 2070 MHz"
                                        % ((FP64_LANES_PER_SM, "FP64") if bind64 else (FP32_LANES_PER_SM, "FP32")),
@@ -674,12 +690,12 @@ def run_divergence(args):
     return 0
 
 
-def feval_name(km, prec, shape, cells, energy, layout):
+def feval_name(km, prec, shape, cells, layout):
     """'generated' where the library's automatic choice takes the generated f
-    (lane layout, FP64, isothermal, staging 0, a small mechanism, a large
-    call), else 'tables'."""
+    (lane layout, FP64, staging 0, a small mechanism, a large call; with the
+    energy equation too), else 'tables'."""
     from paper_1309_2710_gb300 import kin
-    gen = (layout == "lane-per-cell" and prec == synth.FP64 and not energy
+    gen = (layout == "lane-per-cell" and prec == synth.FP64
            and shape.get("staging", 0) == kin.STAGE_GLOBAL and km.n_species <= kin.GEN_MAX_SPECIES
            and km.n_reactions <= kin.GEN_MAX_REACTIONS and cells >= kin.GEN_MIN_CELLS)
     return "generated" if gen else "tables"

@@ -101,8 +101,9 @@ extern "C" {
                                  indices, efficiencies and coefficients as literals,
                                  concentrations and production rates in registers),
                                  compiled with NVRTC on first use and cached per device and
-                                 mechanism. Serves KIN_FP64, isothermal, KIN_LAYOUT_LANE,
-                                 KIN_STAGE_GLOBAL and mechanisms of at most
+                                 mechanism; with the energy equation too (the rate
+                                 constants then follow T inside f). Serves KIN_FP64,
+                                 KIN_LAYOUT_LANE, KIN_STAGE_GLOBAL and mechanisms of at most
                                  KIN_GEN_MAX_SPECIES species and KIN_GEN_MAX_REACTIONS
                                  reactions; KIN_EUNSUPPORTED otherwise or without NVRTC,
                                  KIN_ECUDA if the compilation fails */
@@ -308,7 +309,9 @@ int kin_rates(const kin_mech *m, int64_t cells, const double *T, const double *p
 
 /* The CUDA source of the generated f (KIN_FEVAL_GENERATED) for a mechanism
  * description: straight-line FP64 code of Eqs. (E:mass), (E:spec-rate) and
- * (E:rxn-rate) with the mechanism's indices and constants as literals. Host
+ * (E:rxn-rate) with the mechanism's indices and constants as literals, and,
+ * when the description has cp and Hf, the form with the energy equation,
+ * Eq. (E:energy), whose rate constants (Eq. (E:rxn-const)) follow T. Host
  * only (no device needed). Writes at most cap - 1 characters and a NUL to buf
  * (buf may be NULL when cap is 0) and returns the full length, so a call with
  * cap 0 sizes the buffer. KIN_EINVAL for an invalid description,

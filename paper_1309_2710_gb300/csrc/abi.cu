@@ -205,6 +205,14 @@ int64_t kin_generated_f_source(const kin_mech_desc* d, char* buf, int64_t cap)
     if (rows > 0 && !d->eff) return fail(KIN_EINVAL, "eff is NULL but %d reactions need efficiencies", rows);
     for (int64_t k = 0; k < (int64_t)rows * nS; ++k)
         if (!std::isfinite(d->eff[k])) return fail(KIN_EINVAL, "non-finite efficiency");
+    if ((d->cp != nullptr) != (d->Hf != nullptr)) return fail(KIN_EINVAL, "give both cp and Hf, or neither");
+    for (int i = 0; d->cp && i < nS; ++i)
+        if (!finite_pos(d->cp[i]) || !std::isfinite(d->Hf[i]))
+            return fail(KIN_EINVAL, "species %d: cp must be finite and > 0, Hf finite", i);
+    if (nR > 0 && (!d->lnA || !d->beta || !d->Ea)) return fail(KIN_EINVAL, "Arrhenius arrays must be non-NULL");
+    for (int j = 0; j < nR; ++j)
+        if (d->type[j] == KIN_RXN_FALLOFF && (!d->lnA0 || !d->beta0 || !d->Ea0))
+            return fail(KIN_EINVAL, "falloff reaction %d needs lnA0, beta0, Ea0", j);
     const std::string src = gen_f_source(d);
     if (cap > 0) {
         const int64_t n = std::min<int64_t>(cap - 1, (int64_t)src.size());
@@ -501,17 +509,19 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     bool gen = false;
     GenKernels gk{};
     if (o->feval == KIN_FEVAL_GENERATED || (o->feval == KIN_FEVAL_AUTO && total >= KIN_GEN_MIN_CELLS)) {
-        const bool serves = g.layout == KIN_LAYOUT_LANE && o->precision == KIN_FP64 && !o->energy &&
+        // (the energy equation comes generated too: the mechanism has cp and
+        // Hf, checked above, so its source carries that form of f)
+        const bool serves = g.layout == KIN_LAYOUT_LANE && o->precision == KIN_FP64 &&
                             o->staging == KIN_STAGE_GLOBAL && !m->gen_src.empty();
         if (serves) {
             std::string log;
             const int grc = gen_kernels(m->device, m->gen_src, &gk, &log);
-            if (grc == KIN_OK) gen = true;
+            if (grc == KIN_OK && (!o->energy || gk.energy)) gen = true;
             else if (o->feval == KIN_FEVAL_GENERATED)
-                return fail(grc, "generated f: %.400s", log.c_str());
+                return fail(grc != KIN_OK ? grc : KIN_EUNSUPPORTED, "generated f: %.400s", log.c_str());
         } else if (o->feval == KIN_FEVAL_GENERATED) {
-            return fail(KIN_EUNSUPPORTED, "the generated f serves the lane layout, KIN_FP64, no energy "
-                                          "equation, KIN_STAGE_GLOBAL and at most %d species / %d reactions",
+            return fail(KIN_EUNSUPPORTED, "the generated f serves the lane layout, KIN_FP64, "
+                                          "KIN_STAGE_GLOBAL and at most %d species / %d reactions",
                         KIN_GEN_MAX_SPECIES, KIN_GEN_MAX_REACTIONS);
         }
     }

@@ -13,9 +13,10 @@
 // table f's (Eqs. (E:mass), (E:spec-rate), (E:rxn-rate)) in FP64, rounded
 // in a different order.
 //
-// Scope: FP64, isothermal, lane layout, at most KIN_GEN_MAX_SPECIES species
-// and KIN_GEN_MAX_REACTIONS reactions (a larger f would no longer fit the
-// registers). NVRTC is loaded with dlopen when first needed; without it the
+// Scope: FP64, lane layout, at most KIN_GEN_MAX_SPECIES species and
+// KIN_GEN_MAX_REACTIONS reactions (a larger f would no longer fit the
+// registers); isothermal, and with the energy equation for a mechanism that
+// carries cp and Hf (the rate constants then follow T inside f). NVRTC is loaded with dlopen when first needed; without it the
 // generated path is unavailable and the tables serve.
 #include <dlfcn.h>
 #include <nvrtc.h>
@@ -114,14 +115,16 @@ const char* kStdint =
     "typedef unsigned long long uintptr_t;\n#define INT32_MAX 2147483647\n";
 
 // Kernels compiled per mechanism: the pre-pass and the persistent integrator
-// for RKCK and RKC (FP64, staging 0, isothermal) and both register budgets.
-std::string kernel_name(bool init, int method, int occ)
+// for RKCK and RKC (FP64, staging 0), both register budgets, isothermal and
+// (for a mechanism with thermochemistry) with the energy equation.
+std::string kernel_name(bool init, int energy, int method, int occ)
 {
     char b[160];
+    const char* en = energy ? "true" : "false";
     if (init)
-        snprintf(b, sizeof(b), "kin::init_kernel<%d, double, 0, false, kin::GenF>", method);
+        snprintf(b, sizeof(b), "kin::init_kernel<%d, double, 0, %s, kin::GenF>", method, en);
     else
-        snprintf(b, sizeof(b), "kin::integrate_kernel<%d, double, 0, %d, false, kin::GenF>", method, occ);
+        snprintf(b, sizeof(b), "kin::integrate_kernel<%d, double, 0, %d, %s, kin::GenF>", method, occ, en);
     return b;
 }
 
@@ -137,17 +140,20 @@ bool gen_eligible(int n_species, int n_reactions)
     return n_species >= 1 && n_species <= KIN_GEN_MAX_SPECIES && n_reactions <= KIN_GEN_MAX_REACTIONS;
 }
 
-std::string gen_f_source(const kin_mech_desc* d)
+namespace {
+
+// The body shared by both forms of f: mixture, rates of progress accumulated
+// into the species' rates (w_i = W_i omega_i), dY/dt. Isothermal: k_j and
+// k0/kinf come in K and KR. Energy: they follow x[nS] = T at every
+// evaluation, as in the table f, and dT/dt closes the body.
+void emit_body(std::string& s, const kin_mech_desc* d, bool energy)
 {
     const int nS = d->n_species, nR = d->n_reactions;
-    std::string s;
-    appendf(s, "// f for one mechanism: %d species, %d reactions (generated).\n", nS, nR);
-    s += "namespace kin {\nstruct GenF {\n"
-         "    template <typename R, typename KT>\n"
-         "    __device__ __forceinline__ static void eval(const MechDev&, double Ctot, double invCtot, Lane<KT> K,\n"
-         "                                                Lane<KT> KR, Lane<R>, Lane<R>, Lane<double> x,\n"
-         "                                                Lane<double> out)\n    {\n"
-         "        static_assert(sizeof(R) == 8 && sizeof(KT) == 8, \"the generated f is FP64\");\n";
+    if (energy) {
+        appendf(s, "        const double T = x[%d];\n", nS);
+        s += "        const double lnT = log(T), invT = 1.0 / T;\n"
+             "        const double Ctot = p * 1e-6 * invT * (1.0 / R_GAS), invCtot = 1.0 / Ctot;\n";
+    }
     // mixture: m_k = Y_k / W_k, S = sum m_k (two partial sums), rho = Ctot / S
     for (int i = 0; i < nS; ++i) appendf(s, "        const double m%d = x[%d] * %s;\n", i, i, lit(1.0 / d->W[i]).c_str());
     std::string ev, od;
@@ -183,14 +189,27 @@ std::string gen_f_source(const kin_mech_desc* d)
     }
     for (int i = 0; i < nS; ++i)
         if (used[i]) appendf(s, "        double w%d = 0.0;\n", i);
+    // Arrhenius exponent ln A + beta ln T - (Ea/R)/T with the table f's terms
+    auto exponent = [&](double lnA, double beta, double Ea) {
+        std::string a = lit(lnA);
+        if (beta != 0.0) a += " + " + lit(beta) + " * lnT";
+        if (Ea != 0.0) a += " - " + lit(Ea / R_GAS) + " * invT";
+        return a;
+    };
     int row = 0, fo = 0;
     for (int j = 0; j < nR; ++j) {
         const int t = d->type[j];
+        appendf(s, "        {  // reaction %d\n", j);
         std::string q;
-        appendf(q, "K[%d]", j);
+        if (energy) {
+            appendf(s, "            const double a = %s;\n", exponent(d->lnA[j], d->beta[j], d->Ea[j]).c_str());
+            q = "exp(a)";
+        } else {
+            appendf(q, "K[%d]", j);
+        }
         for (int a = 0; a < 2; ++a)
             if (d->reac[2 * j + a] >= 0) appendf(q, " * c%d", d->reac[2 * j + a]);
-        appendf(s, "        {  // reaction %d\n            double q = %s;\n", j, q.c_str());
+        appendf(s, "            double q = %s;\n", q.c_str());
         if (t != KIN_RXN_PLAIN) {
             std::string a0, a1;
             int n = 0;
@@ -207,7 +226,12 @@ std::string gen_f_source(const kin_mech_desc* d)
             if (t == KIN_RXN_THIRD_BODY) {
                 s += "            q *= Mc;\n";
             } else {
-                appendf(s, "            const double Pr = KR[%d] * Mc;\n            q *= Pr / (1.0 + Pr);\n", fo);
+                if (energy)
+                    appendf(s, "            const double Pr = exp((%s) - a) * Mc;\n",
+                            exponent(d->lnA0[j], d->beta0[j], d->Ea0[j]).c_str());
+                else
+                    appendf(s, "            const double Pr = KR[%d] * Mc;\n", fo);
+                s += "            q *= Pr / (1.0 + Pr);\n";
                 ++fo;
             }
             ++row;
@@ -222,7 +246,46 @@ std::string gen_f_source(const kin_mech_desc* d)
         if (used[i]) appendf(s, "        out[%d] = w%d * invrho;\n", i, i);
         else appendf(s, "        out[%d] = 0.0;\n", i);
     }
-    s += "    }\n};\n}  // namespace kin\n";
+    if (energy) {
+        // sum_i H_i omega_i = sum_i (Hf_i / W_i + (cp_i / W_i)(T - T_REF)) w_i; cp = sum_i Y_i cp_i / W_i
+        s += "        const double dT = T - T_REF;\n        double hw = 0.0, cpm = 0.0;\n";
+        for (int i = 0; i < nS; ++i) {
+            const std::string cpW = lit(d->cp[i] / d->W[i]);
+            if (used[i])
+                appendf(s, "        hw = fma(%s + %s * dT, w%d, hw);\n", lit(d->Hf[i] / d->W[i]).c_str(),
+                        cpW.c_str(), i);
+            appendf(s, "        cpm = fma(x[%d], %s, cpm);\n", i, cpW.c_str());
+        }
+        appendf(s, "        out[%d] = -hw * invrho / cpm;\n", nS);
+    }
+}
+
+}  // namespace
+
+std::string gen_f_source(const kin_mech_desc* d)
+{
+    const int nS = d->n_species, nR = d->n_reactions;
+    const bool thermo = d->cp && d->Hf;
+    std::string s;
+    appendf(s, "// f for one mechanism: %d species, %d reactions (generated)%s.\n", nS, nR,
+            thermo ? ", isothermal and with the energy equation" : "");
+    s += "namespace kin {\nstruct GenF {\n"
+         "    template <typename R, typename KT>\n"
+         "    __device__ __forceinline__ static void eval(const MechDev&, double Ctot, double invCtot, Lane<KT> K,\n"
+         "                                                Lane<KT> KR, Lane<R>, Lane<R>, Lane<double> x,\n"
+         "                                                Lane<double> out)\n    {\n"
+         "        static_assert(sizeof(R) == 8 && sizeof(KT) == 8, \"the generated f is FP64\");\n";
+    emit_body(s, d, false);
+    s += "    }\n";
+    if (thermo) {
+        s += "    template <typename R>\n"
+             "    __device__ __forceinline__ static void eval_energy(const MechDev&, double p, Lane<R>, Lane<R>,\n"
+             "                                                       Lane<double> x, Lane<double> out)\n    {\n"
+             "        static_assert(sizeof(R) == 8, \"the generated f is FP64\");\n";
+        emit_body(s, d, true);
+        s += "    }\n";
+    }
+    s += "};\n}  // namespace kin\n";
     return s;
 }
 
@@ -243,10 +306,13 @@ int gen_compile(const std::string& f_src, std::vector<char>* cubin, std::vector<
         *log = n.err(r);
         return KIN_ECUDA;
     }
+    // per energy form: init RKCK, init RKC, integrate [method][occupancy]
     std::vector<std::string> exprs;
-    for (int init = 1; init >= 0; --init)
-        for (int method = 0; method < 2; ++method)
-            for (int occ = 0; occ < (init ? 1 : 2); ++occ) exprs.push_back(kernel_name(init, method, occ));
+    const int forms = f_src.find("eval_energy") != std::string::npos ? 2 : 1;
+    for (int en = 0; en < forms; ++en)
+        for (int init = 1; init >= 0; --init)
+            for (int method = 0; method < 2; ++method)
+                for (int occ = 0; occ < (init ? 1 : 2); ++occ) exprs.push_back(kernel_name(init, en, method, occ));
     for (auto& e : exprs) n.add_name(prog, e.c_str());
     // -default-device: the public header's host declarations become (unused)
     // device declarations instead of errors
@@ -295,11 +361,16 @@ int gen_kernels(int device, const std::string& f_src, GenKernels* out, std::stri
         cudaGetLastError();
         return KIN_ECUDA;
     }
-    // names: init RKCK, init RKC, then integrate [method][occ]
-    e = cudaLibraryGetKernel(&g.init[0], g.lib, names[0].c_str());
-    if (e == cudaSuccess) e = cudaLibraryGetKernel(&g.init[1], g.lib, names[1].c_str());
-    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
-        e = cudaLibraryGetKernel(&g.integrate[k / 2][k % 2], g.lib, names[2 + k].c_str());
+    // names per energy form: init RKCK, init RKC, then integrate [method][occ]
+    g.energy = names.size() == 12;
+    e = cudaSuccess;
+    for (int en = 0; en < (g.energy ? 2 : 1) && e == cudaSuccess; ++en) {
+        const int b = 6 * en;
+        e = cudaLibraryGetKernel(&g.init[en][0], g.lib, names[b].c_str());
+        if (e == cudaSuccess) e = cudaLibraryGetKernel(&g.init[en][1], g.lib, names[b + 1].c_str());
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            e = cudaLibraryGetKernel(&g.integrate[en][k / 2][k % 2], g.lib, names[b + 2 + k].c_str());
+    }
     if (e != cudaSuccess) {
         *log = cudaGetErrorString(e);
         cudaGetLastError();
@@ -313,15 +384,17 @@ int gen_kernels(int device, const std::string& f_src, GenKernels* out, std::stri
 
 cudaError_t gen_launch(const GenKernels& g, Launch& L, int occ, int blocks, int threads, cudaStream_t st)
 {
+    if (L.energy && !g.energy) return cudaErrorInvalidValue;  // refused by the caller before
     void* args[] = {&L};
-    const int m = L.method == KIN_RKC ? 1 : 0;
-    cudaError_t e = cudaLaunchKernel((const void*)g.init[m], dim3(blocks), dim3(threads), args, 0, st);
+    const int m = L.method == KIN_RKC ? 1 : 0, en = L.energy ? 1 : 0;
+    cudaError_t e = cudaLaunchKernel((const void*)g.init[en][m], dim3(blocks), dim3(threads), args, 0, st);
     if (e != cudaSuccess) return e;
     if (L.method == KIN_RKC) {
         e = launch_sort(L, st);
         if (e != cudaSuccess) return e;
     }
-    return cudaLaunchKernel((const void*)g.integrate[m][occ ? 1 : 0], dim3(blocks), dim3(threads), args, 0, st);
+    return cudaLaunchKernel((const void*)g.integrate[en][m][occ ? 1 : 0], dim3(blocks), dim3(threads), args, 0,
+                            st);
 }
 
 }  // namespace kin

@@ -10,12 +10,14 @@
 
 namespace kin {
 
-// Kernels of one compiled mechanism: pre-pass per method (RKCK, RKC) and the
+// Kernels of one compiled mechanism, per form of f (isothermal; with the
+// energy equation when `energy`): pre-pass per method (RKCK, RKC) and the
 // persistent integrator per method and register budget.
 struct GenKernels {
     cudaLibrary_t lib;
-    cudaKernel_t init[2];
-    cudaKernel_t integrate[2][2];
+    bool energy;
+    cudaKernel_t init[2][2];
+    cudaKernel_t integrate[2][2][2];
 };
 
 // Mechanisms small enough for a register-resident generated f.
@@ -23,8 +25,8 @@ bool gen_eligible(int n_species, int n_reactions);
 // The CUDA source of the generated f (a policy class kin::GenF) for `d`.
 std::string gen_f_source(const kin_mech_desc* d);
 // Compile f_src with the kernel templates to a cubin for sm_103a; `lowered`
-// receives the kernels' symbol names (init RKCK, init RKC, integrate
-// [method][occupancy]). Returns KIN_OK, KIN_EUNSUPPORTED (no NVRTC) or
+// receives the kernels' symbol names (per form of f: init RKCK, init RKC,
+// integrate [method][occupancy]). Returns KIN_OK, KIN_EUNSUPPORTED (no NVRTC) or
 // KIN_ECUDA (compilation failed; `log` has the compiler output).
 int gen_compile(const std::string& f_src, std::vector<char>* cubin, std::vector<std::string>* lowered,
                 std::string* log);

@@ -506,6 +506,13 @@ struct TableF {
     {
         feval<R, KT>(M, Ctot, invCtot, K, KR, C, OM, x, out);
     }
+    // f with the energy equation (x = {Y, T})
+    template <typename R>
+    __device__ __forceinline__ static void eval_energy(const MechDev& M, double p, Lane<R> C, Lane<R> OM,
+                                                       Lane<double> x, Lane<double> out)
+    {
+        feval_energy<R>(M, p, C, OM, x, out);
+    }
 };
 
 // f in FP64 for a spectral-radius estimate: the lane's rate scratch in the
@@ -543,13 +550,13 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
         if constexpr (!EN) rate_constants<R>(M, T, K, KR);
         // f in the rate type, and f in FP64 for the spectral radius
         auto frate = [&](Lane<double> x, Lane<double> o) {
-            if constexpr (EN) feval_energy<R>(M, p, W.C, W.OM, x, o);
+            if constexpr (EN) F::template eval_energy<R>(M, p, W.C, W.OM, x, o);
             else F::template eval<R, R>(M, Ctot, invCtot, K, KR, W.C, W.OM, x, o);
         };
         auto fsig = [&](Lane<double> x, Lane<double> o) {
             if constexpr (EN) {
-                if constexpr (sizeof(R) == 4) feval_energy<double>(M, p, W.C64, W.OM64, x, o);
-                else feval_energy<double>(M, p, W.C, W.OM, x, o);
+                if constexpr (sizeof(R) == 4) F::template eval_energy<double>(M, p, W.C64, W.OM64, x, o);
+                else F::template eval_energy<double>(M, p, W.C, W.OM, x, o);
             } else {
                 feval_sig<R, STG, F>(W, Ctot, invCtot, K, KR, x, o);
             }
@@ -1108,11 +1115,11 @@ struct Integrator {
             const bool sig = METHOD == KIN_RKC && S.phase >= PH_SIGBASE && S.phase <= PH_POW;
             if constexpr (EN) {
                 if (!sig)
-                    feval_energy<R>(M, S.p, W.C, W.OM, V(S.in_v), V(S.out_v));
+                    F::template eval_energy<R>(M, S.p, W.C, W.OM, V(S.in_v), V(S.out_v));
                 else if constexpr (sizeof(R) == 4)
-                    feval_energy<double>(M, S.p, W.C64, W.OM64, V(S.in_v), V(S.out_v));
+                    F::template eval_energy<double>(M, S.p, W.C64, W.OM64, V(S.in_v), V(S.out_v));
                 else
-                    feval_energy<double>(M, S.p, W.C, W.OM, V(S.in_v), V(S.out_v));
+                    F::template eval_energy<double>(M, S.p, W.C, W.OM, V(S.in_v), V(S.out_v));
             } else if (sizeof(R) == 4 && sig) {
                 F::template eval<double, R>(M, S.Ctot, S.invCtot, K, KR, W.C64, W.OM64, V(S.in_v),
                                             V(S.out_v));

@@ -1,10 +1,10 @@
 """The generated f (kin_generated_f_source) on the CPU: the library writes the
 mechanism-specific source, g++ compiles it behind a small shim of the device
 types, and every evaluation is compared with the oracle's f (Eqs. (E:mass),
-(E:spec-rate), (E:rxn-rate)) for the same state and rate constants. Runs
-without a GPU; the GPU tests run the same source inside the integrator."""
+(E:spec-rate), (E:rxn-rate)) for the same state and rate constants, and with
+the energy equation (Eq. (E:energy)) for mechanisms with thermochemistry.
+Runs without a GPU; the GPU tests run the same source inside the integrator."""
 import ctypes
-import os
 import shutil
 import subprocess
 
@@ -28,7 +28,10 @@ template <typename T> struct Lane {
 };
 template <typename R> struct Tab;
 template <> struct Tab<double> { static double inv(double a) { return 1.0 / a; } };
+constexpr double R_GAS = 8.314462618, T_REF = 298.15;
+using std::exp;
 using std::fma;
+using std::log;
 }
 #include "gen_f.inc"
 extern "C" void gen_f(double Ctot, double* K, double* KR, double* x, double* out)
@@ -36,6 +39,13 @@ extern "C" void gen_f(double Ctot, double* K, double* KR, double* x, double* out
     kin::Lane<double> k{K, 1}, kr{KR, 1}, xx{x, 1}, o{out, 1}, none{nullptr, 1};
     kin::GenF::eval<double, double>(kin::MechDev{}, Ctot, 1.0 / Ctot, k, kr, none, none, xx, o);
 }
+#ifdef GEN_ENERGY
+extern "C" void gen_f_energy(double p, double* x, double* out)
+{
+    kin::Lane<double> xx{x, 1}, o{out, 1}, none{nullptr, 1};
+    kin::GenF::eval_energy<double>(kin::MechDev{}, p, none, none, xx, o);
+}
+#endif
 """
 
 R_GAS = 8.314462618
@@ -48,10 +58,13 @@ def compile_generated(m, tmp_path):
     (tmp_path / "gen_f.inc").write_text(src)
     (tmp_path / "shim.cpp").write_text(SHIM)
     so = str(tmp_path / "gen_f.so")
-    subprocess.run(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-o", so, str(tmp_path / "shim.cpp")],
-                   check=True, capture_output=True, cwd=tmp_path)
+    energy = "eval_energy" in src
+    subprocess.run(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-o", so, str(tmp_path / "shim.cpp")]
+                   + (["-DGEN_ENERGY"] if energy else []), check=True, capture_output=True, cwd=tmp_path)
     L = ctypes.CDLL(so)
     L.gen_f.argtypes = [ctypes.c_double] + [ctypes.c_void_p] * 4
+    if energy:
+        L.gen_f_energy.argtypes = [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
     return L, src
 
 
@@ -106,6 +119,49 @@ def test_generated_f_third_body_falloff_and_inert(tmp_path):
         ref = oracle.rates(om, T, p, y)
         got = generated_rates(L, om, m, T, p, y)
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", ["h2co_13sp_rkc_energy", "h2_9sp_rkck_energy"])
+def test_generated_energy_f_equals_the_oracle(name, tmp_path):
+    """The form with the energy equation: k_j from the state's T inside f, and
+    dT/dt = -(sum_i H_i omega_i) / (rho cp) as the last component."""
+    m = synth.workload_mechanism(name)
+    om = oracle.Mech(m)
+    L, src = compile_generated(m, tmp_path)
+    assert "eval_energy" in src
+    T, p, Y = synth.workload_states(name, m, cells=48, seed_offset=82)
+    nS = len(m.W)
+    for c in range(48):
+        y = np.ascontiguousarray(np.append(Y[:, c], T[c]))
+        ref = oracle.rates_energy(om, p[c], y)
+        out = np.empty(nS + 1)
+        L.gen_f_energy(float(p[c]), y.ctypes.data, out.ctypes.data)
+        assert np.abs(out[:nS] - ref[:nS]).max() <= 1e-12 * np.abs(ref[:nS]).max(), c
+        assert abs(out[nS] - ref[nS]) <= 1e-12 * abs(ref[nS]), c
+        # and the isothermal form at this T is the same species rows
+        iso = generated_rates(L, om, m, T[c], p[c], Y[:, c])
+        assert np.abs(iso - out[:nS]).max() <= 1e-12 * np.abs(ref[:nS]).max()
+
+
+def test_generated_energy_f_falloff(tmp_path):
+    W = [2.016, 31.998, 18.015, 28.014]
+    rx = [dict(reac=[0, 0], prod=[2], A=3e9, beta=0.5, Ea=4e4),
+          dict(reac=[2], prod=[0, 1], A=2e12, beta=-0.3, Ea=1.2e5, type=2, A0=5e15, beta0=0.2, Ea0=9e4),
+          dict(reac=[0, 1], prod=[2, 2], A=1e8, type=1)]
+    m = mechs.mech(W, rx, eff_rows=[[1.0, 0.5, 2.5, 0.7], [1.3, 1.0, 0.0, 2.0]],
+                   cp=[29.0, 29.5, 33.6, 29.1], Hf=[0.0, 0.0, -2.418e5, 0.0])
+    om = oracle.Mech(m)
+    L, src = compile_generated(m, tmp_path)
+    rng = np.random.default_rng(4)
+    for _ in range(30):
+        y = rng.uniform(0.01, 1.0, 4)
+        y /= y.sum()
+        y = np.append(y, rng.uniform(900, 2500))
+        p = rng.uniform(5e4, 2e6)
+        ref = oracle.rates_energy(om, p, y)
+        out = np.empty(5)
+        L.gen_f_energy(p, y.ctypes.data, out.ctypes.data)
+        assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
 def test_generated_f_scope():

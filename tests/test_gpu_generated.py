@@ -1,9 +1,9 @@
 """GPU parity of the generated f (KIN_FEVAL_GENERATED): the mechanism's f as
 straight-line code, compiled at run time into the lane-per-cell integrator,
 against the FP64 oracle (both methods, both spectral-radius estimators,
-ragged sizes), against the table-driven kernels, through the automatic
-choice, the batched launch and a CUDA graph; and the refusals outside its
-scope."""
+ragged sizes, isothermal and with the energy equation), against the
+table-driven kernels, through the automatic choice, the batched launch and a
+CUDA graph; and the refusals outside its scope."""
 import numpy as np
 import pytest
 
@@ -139,17 +139,41 @@ def test_generated_batch_and_graph():
         assert np.array_equal(c.Y.cpu().numpy(), a[0])
 
 
-@pytest.mark.parametrize("case", ["mixed", "warp", "energy", "large", "staging"])
+@pytest.mark.parametrize("name,cells", [("h2co_13sp_rkc_energy", 211), ("h2_9sp_rkck_energy", 333)])
+def test_generated_energy_against_oracle(name, cells):
+    """The energy equation with the generated f: T is a state component, k_j
+    follows it inside f; against the FP64 oracle and the table-driven kernel."""
+    w = synth.WORKLOADS[name]
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m, cells=cells, seed_offset=95)
+
+    def go(feval):
+        Td, Yd = dev(T), dev(Y)
+        st = torch.full((cells,), 255, dtype=torch.uint8, device=DEV)
+        sta = torch.zeros((cells, kin.NSTATS), dtype=torch.int32, device=DEV)
+        kin.integrate(km, Td, dev(p), Yd, w["dt"], w["rtol"], w["atol"], w["method"], status=st, stats=sta,
+                      sigma=w["sigma"], layout=LANE, energy=1, feval=feval)
+        torch.cuda.synchronize()
+        return np.vstack([Yd.cpu().numpy(), Td.cpu().numpy()]), st.cpu().numpy(), sta.cpu().numpy()
+
+    g, t = go(GEN), go(TABLE)
+    Yo, sto, stao, _, To = oracle.integrate(om, T, p, Y, w["dt"], w["rtol"], w["atol"],
+                                            omethod(w["method"], w["sigma"]), energy=True)
+    assert np.abs(To - T).max() > 1e-3
+    frac = 0.05 if w["method"] == kin.RKC else 0.01
+    compare(g[0], np.vstack([Yo, To]), g[1], sto, g[2], stao, w["atol"], w["rtol"], max_div_frac=frac)
+    compare(g[0], t[0], g[1], t[1], g[2], t[2], w["atol"], w["rtol"], max_div_frac=frac)
+
+
+@pytest.mark.parametrize("case", ["mixed", "warp", "large", "staging"])
 def test_generated_refusals(case):
-    name = {"energy": "h2co_13sp_rkc_energy", "large": "ch4_53sp_rkc_mixed"}.get(case, "h2co_13sp_rkc")
+    name = {"large": "ch4_53sp_rkc_mixed"}.get(case, "h2co_13sp_rkc")
     m, km, om = mech(name)
     w = dict(synth.WORKLOADS[name])
     T, p, Y = synth.workload_states(name, m, cells=64)
     kw = dict(precision=kin.FP64)
     if case == "mixed":
         kw["precision"] = kin.MIXED
-    if case == "energy":
-        kw["energy"] = 1
     if case == "staging":
         kw["staging"] = kin.STAGE_SHARED
     layout = kin.LAYOUT_WARP if case == "warp" else LANE
