@@ -51,29 +51,30 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture (profiles/), valid only for the kernel sources whose hash is the key
 # and for the captured launch shape (block threads, blocks per SM, staging,
-# register budget, layout): (workload, shape) -> (bytes, cells in the captured
-# launch). A capture on fewer cells than the benchmarked workload is scaled by
+# register budget, layout) and f evaluation: (workload, shape, f) -> (bytes,
+# cells in the captured launch). A capture on fewer cells than the benchmarked workload is scaled by
 # the cell count.
 TRAFFIC = {
     "529606db80a6": {
-        ("h2co_13sp_rkc", (32, 16, 0, 0, 1)): (3829669632 + 5481403648, 262144),
-        ("h2co_13sp_rkc", (32, 20, 0, 1, 1)): (59821390080 + 40944381440, 262144),
-        ("ch4_53sp_rkc_mixed", (256, 3, 0, 1, 2)): (272005888 + 26279680, 65536),
+        ("h2co_13sp_rkc", (32, 16, 0, 0, 1), "generated"): (3829669632 + 5481403648, 262144),
+        ("h2co_13sp_rkc", (32, 20, 0, 1, 1), "generated"): (59821390080 + 40944381440, 262144),
+        ("ch4_53sp_rkc_mixed", (256, 3, 0, 1, 2), "tables"): (272005888 + 26279680, 65536),
     },
 }
 
 
-def traffic_for(name, shape_key, cells):
+def traffic_for(name, shape_key, fname, cells):
     """DRAM bytes per launch for this workload and launch shape: the capture of
     the same shape, else of the same kernel variant (staging, register budget,
     layout) with the same resident lanes per SM; scaled to `cells`. Returns
     (bytes or None, captured shape or None)."""
     tab = TRAFFIC.get(kernel_hash(), {})
-    hit = tab.get((name, shape_key))
+    hit = tab.get((name, shape_key, fname))
     cap = shape_key
     if hit is None:
-        for (nm, sk), v in tab.items():
-            if nm == name and sk[2:] == shape_key[2:] and sk[0] * sk[1] == shape_key[0] * shape_key[1]:
+        for (nm, sk, fn), v in tab.items():
+            if (nm == name and fn == fname and sk[2:] == shape_key[2:]
+                    and sk[0] * sk[1] == shape_key[0] * shape_key[1]):
                 hit, cap = v, sk
                 break
     if hit is None:
@@ -364,6 +365,8 @@ def run_kin(args):
         best = autotune.tune(km, m, T0d, pd, Y0d, w["dt"], w["rtol"], w["atol"], method, prec,
                              sigma=sigma, energy=energy)
         shape = {k: best[k] for k in shape}
+    if args.feval != "auto":
+        shape["feval"] = kin.FEVAL_TABLE if args.feval == "table" else kin.FEVAL_GENERATED
     ws = km.workspace(method, prec, cells, shape["block_threads"], shape["blocks_per_sm"], dev,
                       shape["staging"], shape["occupancy"], sigma, shape["layout"], energy)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -421,7 +424,9 @@ def run_kin(args):
     peak = peak64 if bind64 else peak32
     shape_key = tuple(int(shape[k]) for k in ("block_threads", "blocks_per_sm", "staging", "occupancy",
                                                  "layout"))
-    tr, tr_shape = traffic_for(name, shape_key, cells)
+    tr, tr_shape = traffic_for(name, shape_key,
+                               feval_name(km, prec, shape, cells, layout_name(km, method, shape, cells)),
+                               cells)
 
     # end to end: host (pinned) buffers through the public API, copies timed
     e2e = None
@@ -691,10 +696,12 @@ def run_divergence(args):
 
 
 def feval_name(km, prec, shape, cells, layout):
-    """'generated' where the library's automatic choice takes the generated f
-    (lane layout, FP64, staging 0, a small mechanism, a large call; with the
-    energy equation too), else 'tables'."""
+    """'generated' where the call runs the generated f (asked for, or the
+    library's automatic choice: lane layout, FP64, staging 0, a small
+    mechanism, a large call; with the energy equation too), else 'tables'."""
     from paper_1309_2710_gb300 import kin
+    if shape.get("feval", kin.FEVAL_AUTO) != kin.FEVAL_AUTO:
+        return "generated" if shape["feval"] == kin.FEVAL_GENERATED else "tables"
     gen = (layout == "lane-per-cell" and prec == synth.FP64
            and shape.get("staging", 0) == kin.STAGE_GLOBAL and km.n_species <= kin.GEN_MAX_SPECIES
            and km.n_reactions <= kin.GEN_MAX_REACTIONS and cells >= kin.GEN_MIN_CELLS)
@@ -735,6 +742,8 @@ def main():
     ap.add_argument("--sigma", choices=["default", "gershgorin", "power"], default="default",
                     help="RKC spectral-radius estimator (default: the workload's)")
     ap.add_argument("--scale", type=float, default=1.0, help="batched mode: instance size scale")
+    ap.add_argument("--feval", choices=["auto", "table", "generated"], default="auto",
+                    help="f evaluation of the lane layout (default: the library's choice)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="batched mode: rate precision")
     args = ap.parse_args()
