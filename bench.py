@@ -55,7 +55,7 @@ SM_MAX_MHZ = 2070.0
 # cells in the captured launch). A capture on fewer cells than the benchmarked workload is scaled by
 # the cell count.
 TRAFFIC = {
-    "529606db80a6": {
+    "d35978e6b74a": {
         ("h2co_13sp_rkc", (32, 16, 0, 0, 1), "generated"): (3829669632 + 5481403648, 262144),
         ("h2co_13sp_rkc", (32, 20, 0, 1, 1), "generated"): (59821390080 + 40944381440, 262144),
         ("ch4_53sp_rkc_mixed", (256, 3, 0, 1, 2), "tables"): (272005888 + 26279680, 65536),
@@ -82,11 +82,17 @@ def traffic_for(name, shape_key, fname, cells):
     return hit[0] * cells / hit[1], list(cap)
 
 
+# host-only sources (argument checks, launch choices): not part of the kernels
+HOST_ONLY = ("abi.cu", "no_alloc.cu")
+
+
 def kernel_hash() -> str:
+    """Hash of the sources that define kernel code (device templates, their
+    instantiations and the generator of the run-time compiled f)."""
     d = os.path.join(ROOT, "paper_1309_2710_gb300", "csrc")
     h = hashlib.sha1()
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
+        if f.endswith((".cu", ".cuh")) and f not in HOST_ONLY:
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
 
@@ -424,9 +430,8 @@ def run_kin(args):
     peak = peak64 if bind64 else peak32
     shape_key = tuple(int(shape[k]) for k in ("block_threads", "blocks_per_sm", "staging", "occupancy",
                                                  "layout"))
-    tr, tr_shape = traffic_for(name, shape_key,
-                               feval_name(km, prec, shape, cells, layout_name(km, method, shape, cells)),
-                               cells)
+    fname = feval_name(km, prec, shape, cells, layout_name(km, method, shape, cells), energy)
+    tr, tr_shape = traffic_for(name, shape_key, fname, cells)
 
     # end to end: host (pinned) buffers through the public API, copies timed
     e2e = None
@@ -480,15 +485,12 @@ def run_kin(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32+f64",
             "data": "synthetic (seeded generator standing in for the paper's mechanisms and states)",
             "config": dict(workload_config(name, cells, sigma, args.order), launch_shape=shape,
-                           f_evaluation=feval_name(km, prec, shape, cells,
-                                                   layout_name(km, method, shape, cells))),
+                           f_evaluation=fname),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "G %s lane-ops/s" % ("FP64" if bind64 else "FP32"),
                          "frac": achieved / peak, "traffic": tr, "traffic_capture_shape": tr_shape,
                          "kernel": "kin_integrate launch (init + sort + integrate kernels, %s layout, "
-                                   "%s f)" % (layout_name(km, method, shape, cells),
-                                              feval_name(km, prec, shape, cells,
-                                                         layout_name(km, method, shape, cells))),
+                                   "%s f)" % (layout_name(km, method, shape, cells), fname),
                          "peak_basis": "derived: %d %s lanes/SM/clk x 152 SMs x 2070 MHz"
                                        % ((FP64_LANES_PER_SM, "FP64") if bind64 else (FP32_LANES_PER_SM, "FP32")),
                          "kernel_ms": kavg, "fp64_ops_per_launch": ops64,
@@ -695,14 +697,14 @@ def run_divergence(args):
     return 0
 
 
-def feval_name(km, prec, shape, cells, layout):
+def feval_name(km, prec, shape, cells, layout, energy=0):
     """'generated' where the call runs the generated f (asked for, or the
-    library's automatic choice: lane layout, FP64, staging 0, a small
-    mechanism, a large call; with the energy equation too), else 'tables'."""
+    library's automatic choice: lane layout, FP64, isothermal, staging 0, a
+    small mechanism, a large call), else 'tables'."""
     from paper_1309_2710_gb300 import kin
     if shape.get("feval", kin.FEVAL_AUTO) != kin.FEVAL_AUTO:
         return "generated" if shape["feval"] == kin.FEVAL_GENERATED else "tables"
-    gen = (layout == "lane-per-cell" and prec == synth.FP64
+    gen = (layout == "lane-per-cell" and prec == synth.FP64 and not energy
            and shape.get("staging", 0) == kin.STAGE_GLOBAL and km.n_species <= kin.GEN_MAX_SPECIES
            and km.n_reactions <= kin.GEN_MAX_REACTIONS and cells >= kin.GEN_MIN_CELLS)
     return "generated" if gen else "tables"

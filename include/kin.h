@@ -91,9 +91,11 @@ extern "C" {
 #define KIN_WARP_MAX_CELLS_PER_SM 64
 
 /* how the lane-per-cell layout evaluates f (kin_opts.feval) */
-#define KIN_FEVAL_AUTO 0      /* the generated f for a call of at least KIN_GEN_MIN_CELLS
-                                 cells that it serves (below), else the tables: the
-                                 one-time compilation pays for itself on large calls */
+#define KIN_FEVAL_AUTO 0      /* the generated f for an isothermal call of at least
+                                 KIN_GEN_MIN_CELLS cells that it serves (below), else the
+                                 tables: the one-time compilation pays for itself on large
+                                 calls (with the energy equation the generated form, one
+                                 inlined exp per reaction, is slower than the tables) */
 #define KIN_FEVAL_TABLE 1     /* one kernel for every mechanism: f reads the mechanism's
                                  device tables, its concentrations and rates of progress
                                  sit in per-lane arrays */

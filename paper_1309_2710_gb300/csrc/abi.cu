@@ -508,7 +508,10 @@ int kin_integrate_batch(const kin_mech* m, int32_t n, const kin_instance* inst, 
     // f: tables, or the mechanism's generated code (lane layout, FP64, isothermal)
     bool gen = false;
     GenKernels gk{};
-    if (o->feval == KIN_FEVAL_GENERATED || (o->feval == KIN_FEVAL_AUTO && total >= KIN_GEN_MIN_CELLS)) {
+    // (the automatic choice leaves the energy equation on the tables: with a
+    // per-reaction exp inlined, the generated form measured slower)
+    if (o->feval == KIN_FEVAL_GENERATED ||
+        (o->feval == KIN_FEVAL_AUTO && total >= KIN_GEN_MIN_CELLS && !o->energy)) {
         // (the energy equation comes generated too: the mechanism has cp and
         // Hf, checked above, so its source carries that form of f)
         const bool serves = g.layout == KIN_LAYOUT_LANE && o->precision == KIN_FP64 &&
