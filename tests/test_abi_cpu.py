@@ -61,3 +61,26 @@ def test_integrate_rejects_null_mechanism(lib):
 def test_version(lib):
     lib.kin_version.restype = ctypes.c_char_p
     assert b"sm_103a" in lib.kin_version()
+
+
+def test_binding_constants_match_the_header():
+    """Every constant the binding mirrors has the header's value, and the
+    binding's option struct has the header's fields in the header's order."""
+    from paper_1309_2710_gb300 import kin
+    src = open(os.path.join(ROOT, "include", "kin.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+(KIN_\w+)\s+\(?(-?\d+)\)?", src)}
+    pairs = {"KIN_RKCK": kin.RKCK, "KIN_RKC": kin.RKC, "KIN_FP64": kin.FP64, "KIN_MIXED": kin.MIXED,
+             "KIN_LAYOUT_AUTO": kin.LAYOUT_AUTO, "KIN_LAYOUT_LANE": kin.LAYOUT_LANE,
+             "KIN_LAYOUT_WARP": kin.LAYOUT_WARP, "KIN_SIGMA_GERSHGORIN": kin.SIGMA_GERSHGORIN,
+             "KIN_SIGMA_POWER": kin.SIGMA_POWER, "KIN_FEVAL_AUTO": kin.FEVAL_AUTO,
+             "KIN_FEVAL_TABLE": kin.FEVAL_TABLE, "KIN_FEVAL_GENERATED": kin.FEVAL_GENERATED,
+             "KIN_GEN_MAX_SPECIES": kin.GEN_MAX_SPECIES, "KIN_GEN_MAX_REACTIONS": kin.GEN_MAX_REACTIONS,
+             "KIN_GEN_MIN_CELLS": kin.GEN_MIN_CELLS, "KIN_NSTATS": kin.NSTATS,
+             "KIN_WARP_MIN_REACTIONS": kin.WARP_MIN_REACTIONS,
+             "KIN_WARP_MAX_CELLS_PER_SM": kin.WARP_MAX_CELLS_PER_SM, "KIN_EUNSUPPORTED": kin.KIN_EUNSUPPORTED}
+    for name, value in pairs.items():
+        assert defs[name] == value, name
+    plain = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    end = plain.index("} kin_opts;")
+    fields = re.findall(r"\b(\w+)\s*;", plain[plain.rindex("{", 0, end) + 1:end])
+    assert fields == [f for f, _ in kin.Opts._fields_]
