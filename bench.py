@@ -504,6 +504,11 @@ def run_kin(args):
             "clocks": clk.summary(),
             "cell_status": np.bincount(status, minlength=4).tolist(),
             "mean_f_evals_per_cell": float(stats[:, 0].mean()),
+            # the timed calls one by one (CUDA events around each kin_integrate,
+            # excluding the L2 flush and the state reset between them)
+            "call_ms": {"median": float(np.median(kern_ms)), "min": float(min(kern_ms)),
+                        "max": float(max(kern_ms)), "n": len(kern_ms),
+                        "cells_per_s_at_median": world * cells / (float(np.median(kern_ms)) * 1e-3)},
         }
         print(json.dumps(line))
     if world > 1:
