@@ -52,8 +52,8 @@ SM_MAX_MHZ = 2070.0
 # capture (profiles/), valid only for the kernel sources whose hash is the key
 # and for the captured launch shape (block threads, blocks per SM, staging,
 # register budget, layout) and f evaluation: (workload, shape, f) -> (bytes,
-# cells in the captured launch). A capture on fewer cells than the benchmarked workload is scaled by
-# the cell count.
+# cells in the captured launch). A capture on fewer cells than the benchmarked
+# workload is scaled by the cell count.
 TRAFFIC = {
     "d35978e6b74a": {
         ("h2co_13sp_rkc", (32, 16, 0, 0, 1), "generated"): (3829669632 + 5481403648, 262144),
