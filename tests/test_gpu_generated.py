@@ -84,6 +84,20 @@ def test_generated_against_tables(occupancy):
     compare(a[0], b[0], a[1], b[1], a[2], b[2], w["atol"], w["rtol"])
 
 
+def test_generated_launch_shapes_bit_identical():
+    """The benchmark's candidate shapes (both register budgets, block sizes)
+    give the same bits: each cell's arithmetic does not depend on which lane
+    or launch shape integrates it."""
+    name = "h2co_13sp_rkc"
+    w = synth.WORKLOADS[name]
+    m, km, om = mech(name)
+    T, p, Y = synth.workload_states(name, m, cells=3000, seed_offset=96)
+    ref = run(km, T, p, Y, w, GEN, block_threads=32, blocks_per_sm=16, occupancy=kin.OCC_DEFAULT)
+    for bt, bps, occ in ((128, 4, kin.OCC_DEFAULT), (32, 20, kin.OCC_HIGH), (128, 6, kin.OCC_HIGH)):
+        got = run(km, T, p, Y, w, GEN, block_threads=bt, blocks_per_sm=bps, occupancy=occ)
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[2], ref[2]), (bt, bps, occ)
+
+
 def test_automatic_choice_uses_generated_for_large_calls():
     name = "h2co_13sp_rkc"
     w = synth.WORKLOADS[name]

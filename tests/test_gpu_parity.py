@@ -105,8 +105,9 @@ def test_rkc_h2co_ragged(cells):
 
 
 def test_rkc_h2co_full_size_sampled():
-    """All 262144 cells in one launch (the benchmark's configuration); the
-    oracle recomputes 1536 cells drawn at random."""
+    """All 262144 cells in one launch (the benchmark's configuration: the
+    lane layout with the generated f, which the automatic choice takes for a
+    call this large); the oracle recomputes 1536 cells drawn at random."""
     name = "h2co_13sp_rkc"
     w = synth.WORKLOADS[name]
     m, km, om = mech(name)
