@@ -173,3 +173,19 @@ def test_generated_f_scope():
     with pytest.raises(kin.KinError) as e:
         kin.generated_f_source(bad)
     assert e.value.code == kin.KIN_EINVAL
+
+
+def test_generated_f_degenerate_mechanisms(tmp_path):
+    """No reactions, and a single species: f is identically zero, and the
+    source still compiles (the mixture sums have one or no odd terms)."""
+    for W, rx in (([28.0], []), ([2.0, 32.0, 18.0], [])):
+        m = mechs.mech(W, rx)
+        om = oracle.Mech(m)
+        sub = tmp_path / ("n%d" % len(W))
+        sub.mkdir()
+        L, src = compile_generated(m, sub)
+        assert "fma(" not in src
+        y = np.full(len(W), 1.0 / len(W))
+        got = generated_rates(L, om, m, 1500.0, 101325.0, y)
+        assert np.array_equal(got, np.zeros(len(W)))
+        assert np.array_equal(oracle.rates(om, 1500.0, 101325.0, y), np.zeros(len(W)))
