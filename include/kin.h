@@ -108,7 +108,9 @@ extern "C" {
                                  KIN_LAYOUT_LANE, KIN_STAGE_GLOBAL and mechanisms of at most
                                  KIN_GEN_MAX_SPECIES species and KIN_GEN_MAX_REACTIONS
                                  reactions; KIN_EUNSUPPORTED otherwise or without NVRTC,
-                                 KIN_ECUDA if the compilation fails */
+                                 KIN_ECUDA if the compilation fails. The first such call
+                                 of a mechanism compiles and loads f on the host: make it
+                                 before capturing the call into a CUDA graph */
 #define KIN_GEN_MAX_SPECIES 32
 #define KIN_GEN_MAX_REACTIONS 256
 #define KIN_GEN_MIN_CELLS 65536
