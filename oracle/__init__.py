@@ -85,7 +85,9 @@ def bind(path: str) -> ctypes.CDLL:
     L.orc_trace_cell.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                 ctypes.c_int] + [ctypes.c_void_p] * 5 + [ctypes.c_int]
+                                 ctypes.c_int] + [ctypes.c_void_p] * 5 + [ctypes.c_int,
+                                                                          ctypes.c_void_p,
+                                                                          ctypes.c_void_p]
     L.orc_sigma_power.restype = ctypes.c_double
     L.orc_sigma_power.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -226,13 +228,19 @@ def integrate(om: Mech, T, p, Y, dt, rtol, atol, method, max_steps=0, nthreads=0
 def trace_cell(om: Mech, T, p, y, dt, rtol, atol, method, max_steps=0, cap=100000,
                energy=False):
     """Integrate one cell recording every attempt. Returns (y_new, status,
-    dict(h, err, s, accepted) arrays). With `energy`, y = (Y_1..Y_nS, T)."""
+    dict(h, err, s, accepted, sigma) arrays plus the cell's counters `stats`
+    = (f evaluations, accepted, rejected, sigma estimates, f evaluations in
+    them)). sigma is the spectral radius each RKC attempt took its stage
+    count from (0 for RKCK). With `energy`, y = (Y_1..Y_nS, T)."""
     y = np.array(y, dtype=np.float64, copy=True)
-    h = np.zeros(cap); e = np.zeros(cap)
+    h = np.zeros(cap); e = np.zeros(cap); sg = np.zeros(cap)
     s = np.zeros(cap, dtype=np.int32); a = np.zeros(cap, dtype=np.int32)
+    stats = np.zeros(5, dtype=np.int32)
     n = ctypes.c_int32(0)
     st = lib().orc_trace_cell(om.ptr, float(T), float(p), _ptr(y), float(dt), float(rtol),
                               float(atol), int(method), int(max_steps), int(cap), _ptr(h),
-                              _ptr(e), _ptr(s), _ptr(a), ctypes.byref(n), int(bool(energy)))
+                              _ptr(e), _ptr(s), _ptr(a), ctypes.byref(n), int(bool(energy)),
+                              _ptr(sg), _ptr(stats))
     k = min(n.value, cap)
-    return y, st, dict(h=h[:k], err=e[:k], s=s[:k], accepted=a[:k].astype(bool))
+    return y, st, dict(h=h[:k], err=e[:k], s=s[:k], accepted=a[:k].astype(bool), sigma=sg[:k],
+                       stats=stats)

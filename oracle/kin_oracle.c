@@ -343,21 +343,23 @@ static void rkck_step(orc_f *F, int n, const double *y, const double *f0, double
 }
 
 /* Per-cell counters, and an optional per-attempt trace (step size tried,
- * error measure, stage count or 0 for RKCK, 1 if accepted) used by tests. */
+ * error measure, stage count or 0 for RKCK, 1 if accepted, and the spectral
+ * radius the RKC stage count was taken from, 0 for RKCK) used by tests. */
 typedef struct {
     int nfe, nacc, nrej, nsig, nfs; /* nfs: f evaluations inside sigma estimates */
     int cap, len;
-    double *tr_h, *tr_err;
+    double *tr_h, *tr_err, *tr_sig;
     int *tr_s, *tr_acc;
 } orc_stats;
 
-static void trace(orc_stats *st, double h, double err, int s, int acc)
+static void trace(orc_stats *st, double h, double err, int s, int acc, double sigma)
 {
     if (st->len < st->cap) {
         st->tr_h[st->len] = h;
         st->tr_err[st->len] = err;
         st->tr_s[st->len] = s;
         st->tr_acc[st->len] = acc;
+        if (st->tr_sig) st->tr_sig[st->len] = sigma;
     }
     st->len++;
 }
@@ -384,7 +386,7 @@ static int rkck_cell(orc_f *F, int n, double *y, double dt, double rtol, double 
             if (isnan(r)) { errmax = NAN; break; } /* a blown-up component: reject */
             if (r > errmax) errmax = r;
         }
-        trace(st, hh, errmax, 0, errmax <= 1.0);
+        trace(st, hh, errmax, 0, errmax <= 1.0, 0.0);
         if (errmax <= 1.0) {
             st->nacc++;
             memcpy(y, y5, sizeof(double) * n);
@@ -674,7 +676,7 @@ static int rkc_cell(orc_f *F, int n, double *y, double dt, double rtol, double a
         attempts++;
         for (i = 0; i < n; i++) d[i] = 0.8 * (y[i] - ys[i]) + 0.4 * hh * (f0[i] + fx[i]);
         err = rms_norm(n, d, y, ys, rtol, atol);
-        trace(st, hh, err, s, err <= 1.0);
+        trace(st, hh, err, s, err <= 1.0, sigma);
         if (err <= 1.0) {
             st->nacc++;
             if (err == 0.0)
@@ -773,7 +775,7 @@ int orc_integrate(const void *mp, int64_t cells, double *Tc, const double *pc,
         double *y = (double *)xmalloc(sizeof(double) * n);
         double *k = (double *)xmalloc(sizeof(double) * 2 * m->nR);
         double *work = (double *)xmalloc(sizeof(double) * (2 * m->nS + 2 * m->nR));
-        orc_stats S = {0, 0, 0, 0, 0, 0, 0, NULL, NULL, NULL, NULL};
+        orc_stats S = {0, 0, 0, 0, 0, 0, 0, NULL, NULL, NULL, NULL, NULL};
         orc_f F;
         for (i = 0; i < m->nS; i++) y[i] = Y[(int64_t)i * ldY + c];
         if (energy) y[m->nS] = Tc[c];
@@ -800,17 +802,19 @@ int orc_integrate(const void *mp, int64_t cells, double *Tc, const double *pc,
 }
 
 /* One cell with a per-attempt trace of at most cap entries. Returns the cell
- * status; *len receives the number of attempts (may exceed cap). With
- * energy != 0, y holds nS + 1 components, T last (T is ignored). */
+ * status; *len receives the number of attempts (may exceed cap) and stats
+ * (if not NULL) the cell's five counters as in orc_integrate. tr_sig may be
+ * NULL. With energy != 0, y holds nS + 1 components, T last (T is ignored). */
 int orc_trace_cell(const void *mp, double T, double p, double *y, double dt, double rtol,
                    double atol, int method, int max_steps, int cap, double *tr_h,
-                   double *tr_err, int32_t *tr_s, int32_t *tr_acc, int32_t *len, int energy)
+                   double *tr_err, int32_t *tr_s, int32_t *tr_acc, int32_t *len, int energy,
+                   double *tr_sig, int32_t *stats)
 {
     const orc_mech *m = (const orc_mech *)mp;
     int n = m->nS + (energy ? 1 : 0), st;
     double *k = (double *)xmalloc(sizeof(double) * 2 * m->nR);
     double *work = (double *)xmalloc(sizeof(double) * (2 * m->nS + 2 * m->nR));
-    orc_stats S = {0, 0, 0, 0, 0, cap, 0, tr_h, tr_err, (int *)tr_s, (int *)tr_acc};
+    orc_stats S = {0, 0, 0, 0, 0, cap, 0, tr_h, tr_err, tr_sig, (int *)tr_s, (int *)tr_acc};
     orc_f F;
     if (energy && !m->cp) { free(k); free(work); return -1; }
     if (max_steps <= 0) max_steps = 100000;
@@ -821,6 +825,13 @@ int orc_trace_cell(const void *mp, double T, double p, double *y, double dt, dou
     st = method == 0 ? rkck_cell(&F, n, y, dt, rtol, atol, max_steps, &S)
                      : rkc_cell(&F, n, y, dt, rtol, atol, max_steps, &S, method);
     *len = S.len;
+    if (stats) {
+        stats[0] = (int32_t)F.nfe;
+        stats[1] = S.nacc;
+        stats[2] = S.nrej;
+        stats[3] = S.nsig;
+        stats[4] = S.nfs;
+    }
     free(k); free(work);
     return st;
 }

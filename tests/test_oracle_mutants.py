@@ -70,6 +70,26 @@ MUTANTS = [
     ("rates at a fixed temperature", "rho = production(m, T, p, k, k0, y, omega, C);",
      "rho = production(m, 1000.0, p, k, k0, y, omega, C);",
      [pins.test_energy_species_part_is_the_isothermal_f_at_the_state_temperature]),
+    ("sigma refreshed every 20 steps", "if (since_sigma >= 25 || (last_rejected && !sigma_here)) {",
+     "if (since_sigma >= 20 || (last_rejected && !sigma_here)) {",
+     [pins.test_rkc_sigma_refresh_schedule]),
+    ("no sigma refresh after a rejection", "if (since_sigma >= 25 || (last_rejected && !sigma_here)) {",
+     "if (since_sigma >= 25) {",
+     [pins.test_rkc_sigma_refresh_schedule]),
+    ("sigma age never reset", "            since_sigma = 0;\n", "",
+     [pins.test_rkc_sigma_refresh_schedule]),
+    ("stage cap dropped",
+     "            s = ORC_SMAX;\n            hh = ((ORC_SMAX - 1.0) * (ORC_SMAX - 1.0) - 1.0) / (1.54 * sigma);\n"
+     "            last = 0;\n", "",
+     [pins.test_rkc_stage_cap_on_stiff_linear_decay]),
+    ("stage-cap step reset off by one", "hh = ((ORC_SMAX - 1.0) * (ORC_SMAX - 1.0) - 1.0) / (1.54 * sigma);",
+     "hh = (ORC_SMAX * ORC_SMAX - 1.0) / (1.54 * sigma);",
+     [pins.test_rkc_stage_cap_on_stiff_linear_decay]),
+    ("RKCK minimum step", "double t = 0.0, h = dt, hmin = 1e-20 * dt;",
+     "double t = 0.0, h = dt, hmin = 1e-22 * dt;",
+     [pins.test_status_step_size_underflow]),
+    ("RKC minimum step", "double t = 0.0, hmin = 1e-20 * dt, sigma,", "double t = 0.0, hmin = 1e-22 * dt, sigma,",
+     [pins.test_status_step_size_underflow]),
 ]
 
 

@@ -418,34 +418,36 @@ def test_gershgorin_on_linear_chain():
     assert sig == pytest.approx(exact, rel=1e-6, abs=0)
 
 
-def test_rkc_controller_trace_on_linear_decay():
-    """Hand-worked trace of RKC on A -> B (sigma = k exactly), every attempt to
-    the end of the flow step: initial step from h0 = 1/sigma and Delta_0 (both
-    in closed form), the stage count rule, the step factor P_s(-k h) from numpy
+def _rkc_linear_decay_replay(k, dt, rtol, atol, ya, yb, tr):
+    """Replay, by hand, RKC on A -> B (sigma = k exactly) against an oracle
+    trace: initial step from h0 = 1/sigma and Delta_0 (both in closed form),
+    the stage count rule with its cap at 250 stages and the step reset
+    h = ((250 - 1)^2 - 1)/(1.54 sigma), the step factor P_s(-k h) from numpy
     Chebyshev, the error estimate, and the step factors (0.8/err^(1/3) first
-    and after a rejection, the predictive form otherwise)."""
-    k = 2.0e8
-    om = oracle.Mech(mechs.a_to_b(k))
-    dt, rtol, atol = 1e-6, 1e-6, 1e-10
-    ya, yb = 0.7, 0.3
-    _, st, tr = oracle.trace_cell(om, 1000.0, 1e5, np.array([ya, yb]), dt, rtol, atol, method=1)
-    assert st == 0
+    and after a rejection, the predictive form otherwise). Returns the
+    attempts' stage counts."""
     sigma = k  # rows of J = [[-k, 0], [k, 0]] both sum to k
-    h0 = 1.0 / sigma
-    # Delta_0 = h0 (f(y + h0 f0) - f0): A component = ya, B component = -ya
-    d0 = math.sqrt(0.5 * ((ya / (atol + rtol * ya)) ** 2 + (ya / (atol + rtol * yb)) ** 2))
+    h0 = min(1.0 / sigma, dt)
+    # Delta_0 = h0 (f(y + h0 f0) - f0): A component = k h0 ya, B = -k h0 ya
+    d = k * h0 * ya
+    d0 = math.sqrt(0.5 * ((d / (atol + rtol * ya)) ** 2 + (d / (atol + rtol * yb)) ** 2))
     h = min(0.1 * h0 / math.sqrt(d0), dt)
     t = 0.0
     prev = None
     rejected = False
     n_att = len(tr["h"])
-    assert n_att > 10
+    stages = []
     for n in range(n_att):
         hh = min(h, dt - t)
-        assert tr["h"][n] == pytest.approx(hh, rel=1e-9, abs=0)
-        hh = tr["h"][n]
         s = max(2, int(math.floor(1 + math.sqrt(1 + 1.54 * hh * sigma))))
-        assert tr["s"][n] == s
+        if s > 250:  # the cap: 250 stages and the longest step they keep stable
+            s = 250
+            hh = ((250 - 1.0) ** 2 - 1.0) / (1.54 * sigma)
+        assert tr["h"][n] == pytest.approx(hh, rel=1e-9, abs=0), n
+        hh = tr["h"][n]
+        assert tr["s"][n] == s, n
+        assert tr["sigma"][n] == pytest.approx(sigma, rel=1e-6, abs=0)
+        stages.append(s)
         g = _stability_poly(s, -k * hh)
         na = g * ya
         nb = yb + (1 - g) * ya
@@ -455,9 +457,10 @@ def test_rkc_controller_trace_on_linear_decay():
         ta = atol + rtol * max(abs(ya), abs(na))
         tb = atol + rtol * max(abs(yb), abs(nb))
         err = math.sqrt(0.5 * ((da / ta) ** 2 + (db / tb) ** 2))
-        # the estimate cancels terms of size |y|: allow their rounding
-        cancel = 4e-16 * (abs(ya) + abs(na) + abs(hh * fa0)) / min(ta, tb)
-        assert tr["err"][n] == pytest.approx(err, rel=1e-8, abs=cancel)
+        # the estimate cancels terms of size |y|: allow their rounding (and,
+        # at the cap, that of a 250-stage recursion)
+        cancel = (4e-16 if s < 250 else 1e-13) * (abs(ya) + abs(na) + abs(hh * fa0)) / min(ta, tb)
+        assert tr["err"][n] == pytest.approx(err, rel=1e-8, abs=cancel), n
         err = tr["err"][n]
         assert tr["accepted"][n] == (err <= 1.0)
         if err <= 1.0:
@@ -476,7 +479,143 @@ def test_rkc_controller_trace_on_linear_decay():
             rejected = True
         h = min(10.0, max(0.1, fac)) * hh
     assert t == pytest.approx(dt, rel=1e-12, abs=0)
-    assert max(tr["s"]) >= 10  # the stage rule is exercised beyond s = 2
+    return stages
+
+
+def test_rkc_controller_trace_on_linear_decay():
+    """Hand-worked RKC trace on A -> B (k dt = 200), every attempt to the
+    end of the flow step."""
+    k = 2.0e8
+    om = oracle.Mech(mechs.a_to_b(k))
+    dt, rtol, atol = 1e-6, 1e-6, 1e-10
+    _, st, tr = oracle.trace_cell(om, 1000.0, 1e5, np.array([0.7, 0.3]), dt, rtol, atol, method=1)
+    assert st == 0
+    stages = _rkc_linear_decay_replay(k, dt, rtol, atol, 0.7, 0.3, tr)
+    assert len(stages) > 10
+    assert max(stages) >= 10  # the stage rule is exercised beyond s = 2
+
+
+def test_rkc_stage_cap_on_stiff_linear_decay():
+    """k dt = 2e5: once the transient has decayed the stage rule asks for more
+    than 250 stages. The cap (Section 2.3 gives the rule s = 1 + sqrt(1 +
+    1.54 h sigma); the cap is this build's reading) keeps s = 250 and takes
+    the step that 250 stages keep stable; the hand replay follows every
+    attempt, including the capped ones and the rejection."""
+    k = 2.0e11
+    om = oracle.Mech(mechs.a_to_b(k))
+    dt, rtol, atol = 1e-6, 1e-6, 1e-10
+    _, st, tr = oracle.trace_cell(om, 1000.0, 1e5, np.array([0.7, 0.3]), dt, rtol, atol, method=1)
+    assert st == 0
+    stages = _rkc_linear_decay_replay(k, dt, rtol, atol, 0.7, 0.3, tr)
+    assert stages.count(250) >= 2
+    assert (~tr["accepted"]).sum() >= 1
+
+
+def _autocatalytic(k, W=20.0):
+    """A + B -> B + B with equal molar masses."""
+    return mechs.mech([W, W], [dict(reac=[0, 1], prod=[1, 1], A=k)])
+
+
+def _sigma_schedule(accepted):
+    """Attempts before which the spectral radius is estimated, by the rule of
+    Section 2.3 as read here: before the first attempt, before the attempt
+    that follows 25 accepted steps since the last estimate, and before the
+    attempt that follows a rejection when the last estimate was made at an
+    earlier point (an estimate at the same point would repeat itself)."""
+    est, since, fresh, after_reject = [], 0, False, False
+    for n, acc in enumerate(accepted):
+        if n == 0 or since >= 25 or (after_reject and not fresh):
+            est.append(n)
+            since, fresh = 0, True
+        if acc:
+            since, fresh, after_reject = since + 1, False, False
+        else:
+            after_reject = True
+    return est
+
+
+def test_rkc_sigma_refresh_schedule():
+    """A + B -> B + B, equal molar masses. With Y_A + Y_B = 1 the density is
+    p W/(R T), dY_B/dt = k P Y_A Y_B with P = p/(R T) [mol/cm^3] (a logistic
+    curve), and the Jacobian of f with each Y_k perturbed alone (the density
+    moves with it) has rows +-k P (Y_B^2, Y_A^2): its Gershgorin bound is
+    sigma = k P (Y_A^2 + Y_B^2), which falls to half and rises again as B
+    takes over. The spectral radius each attempt used must change exactly at
+    the attempts the schedule names and equal the closed form at the exact
+    state of that moment; the counters must equal the hand count."""
+    k, T, p = 1e12, 1000.0, 1e5
+    P = p * 1e-6 / (R_GAS * T)
+    r = k * P
+    om = oracle.Mech(_autocatalytic(k))
+    dt, rtol, atol, yb0 = 1e-6, 1e-6, 1e-10, 1e-3
+    y, st, tr = oracle.trace_cell(om, T, p, np.array([1 - yb0, yb0]), dt, rtol, atol, method=oracle.RKC)
+    assert st == 0
+    acc, sig, h = tr["accepted"], tr["sigma"], tr["h"]
+    est = _sigma_schedule(acc)
+    since_counts = set()
+    for n in range(1, len(acc)):
+        if n in est:
+            assert sig[n] != sig[n - 1], n
+        else:
+            assert sig[n] == sig[n - 1], n
+    t = np.concatenate([[0.0], np.cumsum(np.where(acc, h, 0.0))])[:-1]  # start time of each attempt
+    for i, n in enumerate(est):
+        yb = 1.0 / (1.0 + (1.0 / yb0 - 1.0) * math.exp(-r * t[n]))
+        exact = r * ((1.0 - yb) ** 2 + yb ** 2)
+        assert sig[n] == pytest.approx(exact, rel=1e-4, abs=0), n
+        if i:
+            since_counts.add(int(acc[est[i - 1]:n].sum()))
+    assert 25 in since_counts  # refreshed for age ...
+    assert any(c < 25 for c in since_counts)  # ... and after a rejection
+    assert sig.max() / sig.min() > 1.8  # sigma does move along the trajectory
+    nfe, nacc, nrej, nsig, nfs = tr["stats"]
+    assert (nacc, nrej) == (int(acc.sum()), int((~acc).sum()))
+    assert nsig == len(est)
+    assert nfs == 2 * len(est)  # two Gershgorin columns per estimate
+    # f(y0), the estimates, the initial-step probe, and s evaluations per attempt
+    assert nfe == 1 + nfs + 1 + int(tr["s"].sum())
+    assert y[1] == pytest.approx(1.0 / (1.0 + (1.0 / yb0 - 1.0) * math.exp(-r * dt)), rel=1e-4)
+
+
+def test_status_step_size_underflow():
+    """Status 2 (the step size fell below 1e-20 dt), with the state left at the
+    last accepted one (here the initial one).
+    RKCK on A -> B with k = 1e300: every trial step overflows, each rejection
+    divides the step by 10, and the call stops at the first step below
+    1e-20 dt: 21 attempts from dt, 1 + 5 evaluations of f each.
+    RKC: sigma = k, h0 = 1/k, and the initial-step probe gives
+    h1 = 0.1 h0/||Delta_0||^(1/2) (closed form) below 1e-20 dt for k = 1e23,
+    so the call stops before any attempt; for k = 2.5e21, h1 lies above the
+    bound and the call runs until its step limit."""
+    dt, rtol, atol = 1e-6, 1e-6, 1e-10
+    y0 = np.array([0.7, 0.3])
+    om = oracle.Mech(mechs.a_to_b(1e300))
+    y, st, tr = oracle.trace_cell(om, 1000.0, 1e5, y0, dt, rtol, atol, method=oracle.RKCK)
+    h, n = dt, 0
+    while True:  # the same IEEE operations as the integrator's
+        n += 1
+        h = 0.1 * h
+        if h < 1e-20 * dt:
+            break
+    assert st == 2
+    assert len(tr["h"]) == n == 21 and not tr["accepted"].any()
+    assert list(tr["stats"]) == [1 + 5 * n, 0, n, 0, 0]
+    assert np.array_equal(y, y0)
+
+    def h1(k):  # closed form of the RKC initial step on A -> B (sigma = k)
+        d0 = math.sqrt(0.5 * ((0.7 / (atol + rtol * 0.7)) ** 2 + (0.7 / (atol + rtol * 0.3)) ** 2))
+        return 0.1 / k / math.sqrt(d0)
+
+    assert h1(1e23) < 1e-20 * dt < h1(2.5e21)
+    y, st, tr = oracle.trace_cell(oracle.Mech(mechs.a_to_b(1e23)), 1000.0, 1e5, y0, dt, rtol, atol,
+                                  method=oracle.RKC)
+    assert st == 2 and len(tr["h"]) == 0
+    assert list(tr["stats"]) == [4, 0, 0, 1, 2]  # f(y0), two columns, the probe
+    assert np.array_equal(y, y0)
+    y, st, tr = oracle.trace_cell(oracle.Mech(mechs.a_to_b(2.5e21)), 1000.0, 1e5, y0, dt, rtol, atol,
+                                  method=oracle.RKC, max_steps=5)
+    assert st == 1 and len(tr["h"]) == 5
+    assert tr["h"][0] == pytest.approx(h1(2.5e21), rel=1e-9)
 
 
 # ------------------------------------------------------ whole integrator ---
