@@ -281,20 +281,27 @@ int kin_integrate_host(const kin_mech *m, int64_t cells, double *T, const double
  * device, or code running where allocation is not allowed). Same arguments,
  * meaning and errors as kin_integrate, minus the workspace: the working memory
  * comes from a fixed array of KIN_NOALLOC_SCRATCH_BYTES that the library
- * reserves on every device where it is loaded and keeps until the process
- * exits. The call itself allocates nothing.
- *  - The first call on a device looks up that array's device address (with
- *    the device current); make that first call before any stream capture.
+ * reserves on every device where it is used and keeps until the process
+ * exits. After its first call on a device, the call allocates nothing.
+ *  - The first call on a device loads that array (64 MiB of device memory)
+ *    and looks up its device address with the device current: make it at
+ *    start-up, before any stream capture. If the device has no room for the
+ *    array, that call fails with KIN_ENOMEM.
  *  - The array is shared by all calls on a device and keeps the last call's
  *    contents; each call clears what must start at zero. Calls that overlap
  *    on the GPU (on different streams, or from different threads) race on it:
  *    serialise them.
- *  - The working memory grows with the cell count: a call fits when
- *    kin_workspace_bytes(m, opts with blocks_per_sm = 1, cells) is at most
- *    KIN_NOALLOC_SCRATCH_BYTES (for a 13-species / 54-reaction mechanism in
- *    FP64 on a 152-SM GPU, about 57,000 cells). A call that does not fit fails
- *    with KIN_ENOMEM and launches nothing. Fewer persistent blocks per SM
- *    than requested are used when that makes the call fit.
+ *  - The working memory grows with the cell count and the persistent blocks
+ *    per SM. blocks_per_sm is resolved as in kin_integrate (0: as many as
+ *    fit); when that workspace exceeds the array, the call steps down to the
+ *    largest count that fits. A call that does not fit even at one block per
+ *    SM (for a 13-species / 54-reaction mechanism in FP64 on a 152-SM GPU,
+ *    about 57,000 cells) fails with KIN_ENOMEM and launches nothing.
+ *  - It never compiles a generated f (KIN_FEVAL_GENERATED), because the
+ *    compilation and the library load allocate. With KIN_FEVAL_AUTO it uses
+ *    the tables unless an earlier call loaded the mechanism's generated f on
+ *    this device (then it chooses as kin_integrate does); KIN_FEVAL_GENERATED
+ *    fails with KIN_EUNSUPPORTED until such a call has loaded it.
  * The paper has no counterpart of this entry point. */
 int kin_integrate_noalloc(const kin_mech *m, int64_t cells, double *T, const double *p,
                           double *Y, int64_t ldY, double dt, double rtol, double atol,

@@ -170,6 +170,50 @@ int kin::set_last_error(int code, const char* fmt, ...)
     return code;
 }
 
+int kin::noalloc_opts(const kin_mech* m, const kin_opts* in, int64_t cells, int64_t cap,
+                      kin_opts* out)
+{
+    g_err[0] = 0;
+    if (!m) return fail(KIN_EINVAL, "mechanism is NULL");
+    if (cells < 0) return fail(KIN_EINVAL, "cells < 0");
+    int rc = check_opts(in);
+    if (rc) return rc;
+    kin_opts o = *in;
+    // Never compile here: NVRTC and loading the compiled library allocate
+    // device memory. The generated f runs only where an earlier call loaded
+    // it on this device; otherwise the automatic choice falls back to the
+    // tables and a forced one is refused.
+    if (o.feval != KIN_FEVAL_TABLE && (m->gen_src.empty() || !gen_loaded(m->device, m->gen_src))) {
+        if (o.feval == KIN_FEVAL_GENERATED)
+            return fail(KIN_EUNSUPPORTED,
+                        "kin_integrate_noalloc: the generated f of this mechanism is not loaded on "
+                        "device %d (a kin_integrate call with KIN_FEVAL_GENERATED compiles and loads "
+                        "it, which allocates)", m->device);
+        o.feval = KIN_FEVAL_TABLE;
+    }
+    Grid g;
+    rc = grid_for(m, &o, cells, &g);  // resolves blocks_per_sm = 0 to "as many as fit"
+    if (rc) return rc;
+    int nsm = 1;
+    cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    int64_t need = 0;
+    for (int bps = g.blocks / nsm; bps >= 1; --bps) {
+        o.blocks_per_sm = bps;
+        rc = grid_for(m, &o, cells, &g);
+        if (rc) return rc;
+        need = ws_bytes(m, &o, g, cells);
+        if (need <= cap) {
+            *out = o;
+            return KIN_OK;
+        }
+    }
+    return fail(KIN_ENOMEM,
+                "kin_integrate_noalloc: %lld cells need %lld bytes of working memory even at one "
+                "block per SM, more than the %lld-byte fixed array",
+                (long long)cells, (long long)need, (long long)cap);
+}
+
 extern "C" {
 
 const char* kin_last_error(void) { return g_err; }

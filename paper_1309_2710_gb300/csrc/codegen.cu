@@ -382,6 +382,12 @@ int gen_kernels(int device, const std::string& f_src, GenKernels* out, std::stri
     return KIN_OK;
 }
 
+bool gen_loaded(int device, const std::string& f_src)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_cache.count(std::make_pair(device, f_src)) > 0;
+}
+
 cudaError_t gen_launch(const GenKernels& g, Launch& L, int occ, int blocks, int threads, cudaStream_t st)
 {
     if (L.energy && !g.energy) return cudaErrorInvalidValue;  // refused by the caller before

@@ -32,6 +32,9 @@ int gen_compile(const std::string& f_src, std::vector<char>* cubin, std::vector<
                 std::string* log);
 // Compile (once per device and source) and load the kernels.
 int gen_kernels(int device, const std::string& f_src, GenKernels* out, std::string* log);
+// Whether gen_kernels has already compiled and loaded f_src on `device` (a
+// lookup: compiles nothing, allocates nothing).
+bool gen_loaded(int device, const std::string& f_src);
 // Pre-pass, longest-first sort (RKC) and integrator of one call.
 cudaError_t gen_launch(const GenKernels& g, Launch& L, int occ, int blocks, int threads, cudaStream_t st);
 

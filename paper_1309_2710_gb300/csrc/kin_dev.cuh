@@ -174,6 +174,14 @@ inline int warp_cell_lanes(int method, int nV) { return method == KIN_RKCK && nV
 // Record `code` and a printf-style message as the calling thread's last
 // error (kin_last_error); returns `code`.
 int set_last_error(int code, const char* fmt, ...);
+// Options under which a call of `cells` cells runs in a fixed working array of
+// `cap_bytes` without allocating (abi.cu): the f evaluation never compiles
+// (the generated f only where it is already loaded on the device), and the
+// requested blocks per SM (0: as many as fit) step down to the largest count
+// whose workspace fits. KIN_ENOMEM if none fits; other errors as
+// kin_workspace_bytes.
+int noalloc_opts(const kin_mech* m, const kin_opts* in, int64_t cells, int64_t cap_bytes,
+                 kin_opts* out);
 cudaError_t integrate_occupancy(const MechDev& M, int method, int precision, int staging,
                                 int occupancy, int energy, int threads, int* blocks_per_sm);
 #endif  // __CUDACC_RTC__

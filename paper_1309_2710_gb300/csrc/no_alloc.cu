@@ -6,11 +6,10 @@
 // that must not grow the device footprint after start-up. For them,
 // kin_integrate_noalloc takes the integrator's working memory from a fixed
 // array that the library reserves once per device, instead of a caller
-// workspace.
+// workspace, and never compiles a generated f (NVRTC and the library load
+// behind it allocate).
 #include <cuda_runtime.h>
 
-#include <climits>
-#include <cstdio>
 #include <mutex>
 
 #include "kin_dev.cuh"
@@ -18,7 +17,9 @@
 namespace {
 
 // Fixed working memory. Every GPU that loads the library holds it until the
-// process exits.
+// process exits. The module that holds it is loaded, and the memory taken,
+// at the first address lookup on a device (lazy module loading), so the
+// first call on each device is where a lack of memory shows.
 constexpr int64_t kStaticBytes = (int64_t)KIN_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_scratch[KIN_NOALLOC_SCRATCH_BYTES];
 
@@ -53,35 +54,18 @@ extern "C" int kin_integrate_noalloc(const kin_mech* m, int64_t cells, double* T
                                      double rtol, double atol, const kin_opts* opts,
                                      uint8_t* status, int32_t* stats)
 {
-    if (!m || !opts)  // let the regular entry point report the argument error
-        return kin_integrate(m, cells, T, p, Y, ldY, dt, rtol, atol, opts, status, stats, nullptr, 0);
-    // Fewer persistent blocks per SM shrink the per-lane part of the working
-    // memory: take the largest count (up to the requested one) that fits.
-    kin_opts o = *opts;
-    o.blocks_per_sm = 1;
-    int64_t need = kin_workspace_bytes(m, &o, cells);
-    if (need < 0) return (int)need;  // invalid options or cell count; message set
-    if (need > kStaticBytes)
-        return kin::set_last_error(KIN_ENOMEM,
-                                   "kin_integrate_noalloc: %lld cells need %lld bytes of working "
-                                   "memory, more than the %lld-byte fixed array",
-                                   (long long)cells, (long long)need, (long long)kStaticBytes);
-    const int top = opts->blocks_per_sm > 0 ? opts->blocks_per_sm : 4;
-    for (int bps = top; bps > 1; --bps) {
-        kin_opts t = *opts;
-        t.blocks_per_sm = bps;
-        const int64_t n = kin_workspace_bytes(m, &t, cells);
-        if (n >= 0 && n <= kStaticBytes) {
-            o = t;
-            break;
-        }
-    }
+    // the caller's options, with the f evaluation and the blocks per SM
+    // chosen so that the call neither compiles nor outgrows the array
+    kin_opts o;
+    const int rc = kin::noalloc_opts(m, opts, cells, kStaticBytes, &o);
+    if (rc) return rc;
     void* ws = nullptr;
     const cudaError_t e = scratch_address(&ws);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return kin::set_last_error(KIN_ECUDA, "kin_integrate_noalloc: cudaGetSymbolAddress: %s",
-                                   cudaGetErrorString(e));
+        return kin::set_last_error(e == cudaErrorMemoryAllocation ? KIN_ENOMEM : KIN_ECUDA,
+                                   "kin_integrate_noalloc: loading the %lld-byte fixed array: %s",
+                                   (long long)kStaticBytes, cudaGetErrorString(e));
     }
     return kin_integrate(m, cells, T, p, Y, ldY, dt, rtol, atol, &o, status, stats, ws, kStaticBytes);
 }
