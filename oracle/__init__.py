@@ -22,14 +22,15 @@ _lib = None
 RKCK, RKC, RKC_POWER = 0, 1, 2  # method: RKC_POWER = RKC with the power-method sigma
 
 
-def compile_source(src: str, out: str) -> str:
+def compile_source(src: str, out: str, extra=()) -> str:
     """gcc the oracle source ``src`` into the shared library ``out`` (no
     fast-math, no FMA contraction, so it rounds the same on x86-64 and
-    aarch64)."""
+    aarch64). ``extra`` flags come last (the tests' rounding variants use
+    them to allow contraction)."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
     tmp = out + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", src, "-o", tmp, "-lm"]
+           "-ffp-contract=off", "-fno-fast-math"] + list(extra) + [src, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out

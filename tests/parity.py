@@ -1,6 +1,17 @@
 """Helpers for GPU-vs-oracle parity (no GPU or oracle calls at import)."""
 import numpy as np
 
+# The FP64 target in the hot-path contract's metric, |dY| / max(|Y|, atol).
+SURVEY_TOL = 1e-8
+# Allowed multiple of the oracle's own rounding noise floor in that metric
+# (tests/oracle_variants.py). The CUDA path differs from the oracle in more
+# roundings at once than any one variant does (CUDA's exp, tree-ordered warp
+# sums, the generated f's accumulation order, Newton-refined step-control
+# helpers), and the integrator responds linearly to such perturbations, so
+# its distance is a small multiple of the variants' distance, not a new
+# scale. Fixed before the GPU measurements this bound is checked on.
+FLOOR_K = 10
+
 
 def rel_err(Yg, Yo, atol):
     """Per-element |Y_gpu - Y_ref| / max(|Y_ref|, atol)."""
@@ -17,7 +28,7 @@ def tol_rel_err(Yg, Yo, atol, rtol):
 
 
 def compare(Yg, Yo, st_g, st_o, sta_g, sta_o, atol, rtol, tol=1e-8, div_tol=None,
-            max_div_frac=0.01):
+            max_div_frac=0.01, floor=None):
     """Compare GPU and oracle states of the same cells.
 
     The adaptive integrators take discrete decisions (accept/reject, the
@@ -27,19 +38,30 @@ def compare(Yg, Yo, st_g, st_o, sta_g, sta_o, atol, rtol, tol=1e-8, div_tol=None
     (f evaluations, accepted and rejected steps, spectral-radius estimates)
     matches the oracle must agree to `tol` in `tol_rel_err`; the rest must be
     a small fraction and agree to `div_tol` (default 10 rtol). Status codes
-    must match. Returns a summary dict (it also reports the error relative to
-    max(|Y|, atol)).
+    must match.
+
+    With `floor` (the oracle's rounding noise floor on the same cells, from
+    tests.oracle_variants.reference), trace-identical cells must also meet
+    the contract's metric rel_err: at most max(SURVEY_TOL, FLOOR_K floor).
+    Returns a summary dict with both metrics.
     """
     div_tol = 10 * rtol if div_tol is None else div_tol
     assert np.array_equal(st_g, st_o), "status differs: %s vs %s" % (
         np.bincount(st_g, minlength=4), np.bincount(st_o, minlength=4))
     rel = tol_rel_err(Yg, Yo, atol, rtol).max(axis=0)
+    rel_a = rel_err(Yg, Yo, atol).max(axis=0)
     same = (sta_g == sta_o).all(axis=1)
     out = dict(cells=int(len(same)), trace_divergent=int((~same).sum()),
                max_err_same=float(rel[same].max()) if same.any() else 0.0,
                max_err_divergent=float(rel[~same].max()) if (~same).any() else 0.0,
-               max_err_atol_floor=float(rel_err(Yg, Yo, atol).max()))
+               max_err_atol_floor=float(rel_a.max()),
+               max_err_atol_floor_same=float(rel_a[same].max()) if same.any() else 0.0)
+    if floor is not None:
+        out["noise_floor"] = float(floor)
+        out["atol_floor_bound"] = max(SURVEY_TOL, FLOOR_K * float(floor))
     assert out["max_err_same"] <= tol, out
     assert (~same).mean() <= max_div_frac, out
     assert out["max_err_divergent"] <= div_tol, out
+    if floor is not None:
+        assert out["max_err_atol_floor_same"] <= out["atol_floor_bound"], out
     return out
