@@ -17,7 +17,9 @@ mechanism with the same species and reaction counts:
   ``atoms(a) + atoms(b) == atoms(c) + atoms(d)``, so atoms and mass balance by
   construction. Both the forward and products are drawn at random.
 * Arrhenius parameters: A log-uniform in [1e8, 1e14] (cm-mol-s units),
-  beta uniform in [-1, 1], Ea uniform in [0, 2e5] J/mol.
+  beta uniform in [-1, 1], Ea uniform in [0, 2e5] J/mol; the 111-species
+  mechanism of the batched workload draws A in [10^11.5, 10^17.5] and Ea in
+  [1e5, 3e5] J/mol (see WORKLOADS).
 * Third-body and Lindemann falloff reactions get a dense efficiency row
   drawn uniformly from [0.5, 3] over all species. The low-pressure limit of a
   falloff reaction has log10(A0/A) ~ U(3, 7), beta0 = beta and Ea0 = 0.8 Ea.
@@ -165,8 +167,12 @@ def _grow_pool(reactive, cands, diluent_vec, target, rng, sample=24) -> None:
 
 def make_mechanism(n_species: int, n_reactions: int, elements: Sequence[str],
                    tb_frac: float = 0.0, fo_frac: float = 0.0,
-                   seed: int = 0) -> Mechanism:
-    """Draw a balanced, irreversible synthetic mechanism (see module doc)."""
+                   seed: int = 0, log10_A: Tuple[float, float] = (8.0, 14.0),
+                   Ea_range: Tuple[float, float] = (0.0, 2.0e5)) -> Mechanism:
+    """Draw a balanced, irreversible synthetic mechanism (see module doc).
+    log10_A and Ea_range bound the log-uniform pre-exponential factors
+    (cm-mol-s) and the uniform activation energies (J/mol); the draws behind
+    them do not depend on the bounds."""
     elements = list(elements)
     rng = np.random.default_rng(seed)
     has_n = "N" in elements
@@ -220,9 +226,9 @@ def make_mechanism(n_species: int, n_reactions: int, elements: Sequence[str],
         else:  # pragma: no cover - the species pool always has exchanges
             raise RuntimeError("could not draw a balanced reaction")
 
-    lnA = np.log(10.0) * rng.uniform(8.0, 14.0, n_reactions)
+    lnA = np.log(10.0) * rng.uniform(log10_A[0], log10_A[1], n_reactions)
     beta = rng.uniform(-1.0, 1.0, n_reactions)
-    Ea = rng.uniform(0.0, 2.0e5, n_reactions)
+    Ea = rng.uniform(Ea_range[0], Ea_range[1], n_reactions)
 
     rtype = np.zeros(n_reactions, dtype=np.int8)
     n_tb = int(round(tb_frac * n_reactions))
@@ -379,7 +385,15 @@ WORKLOADS = {
                                cells=131072, T=(800.0, 2200.0), p=(1.0, 20.0),
                                dt=1e-6, rtol=1e-6, atol=1e-10, method=RKC, precision=MIXED,
                                sigma=POWER),
+    # The stiffness of this workload is spread by its bimodal temperatures:
+    # with every activation energy at least 1e5 J/mol the cold cells'
+    # reactions are frozen (2 RKC stages) while the hot cells' reach ~200
+    # stages at dt = 1e-5 s, and per-cell f evaluations differ ~600-fold. With
+    # the other workloads' ranges (A 1e8-1e14, Ea 0-2e5) the low-barrier
+    # reactions set the stiffness at any temperature and the stages span
+    # only 2-57.
     "c2h4_111sp_rkc_batched": dict(idx=4, n_species=111, n_reactions=1566,
+                                   log10_A=(11.5, 17.5), Ea=(1.0e5, 3.0e5),
                                    elements=("H", "O", "C", "N"), tb=0.08, fo=0.04,
                                    cells=None, T=None, T_bimodal=((700.0, 900.0), (1800.0, 2400.0)),
                                    p=(1.0, 1.0), dt=(1e-6, 1e-5), rtol=1e-6, atol=1e-10,
@@ -400,7 +414,8 @@ for _base, _sigma in (("h2_9sp_rkck", GERSHGORIN), ("h2co_13sp_rkc", POWER),
 def workload_mechanism(name: str) -> Mechanism:
     w = WORKLOADS[name]
     m = make_mechanism(w["n_species"], w["n_reactions"], w["elements"],
-                       w["tb"], w["fo"], seed=1000 + w["idx"])
+                       w["tb"], w["fo"], seed=1000 + w["idx"],
+                       log10_A=w.get("log10_A", (8.0, 14.0)), Ea_range=w.get("Ea", (0.0, 2.0e5)))
     if w.get("energy"):
         cp, Hf = make_thermo(m, 4000 + w["idx"])
         m = dataclasses.replace(m, cp=cp, Hf=Hf)

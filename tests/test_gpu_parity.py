@@ -12,6 +12,7 @@ torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
 from paper_1309_2710_gb300 import synth  # noqa: E402
+from tests.oracle_variants import reference  # noqa: E402
 from tests.parity import compare, rel_err, tol_rel_err  # noqa: E402
 
 if not torch.cuda.is_available():  # pragma: no cover
@@ -85,8 +86,8 @@ def test_rkck_h2_full_workload():
     m, km, om = mech(name)
     T, p, Y = synth.workload_states(name, m)
     Yg, stg, stag = run_gpu(km, T, p, Y, w["dt"], w["rtol"], w["atol"], kin.RKCK)
-    Yo, sto, stao, _ = oracle.integrate(om, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKCK)
-    s = compare(Yg, Yo, stg, sto, stag, stao, w["atol"], w["rtol"])
+    Yo, sto, stao, fl = reference(m, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKCK)
+    s = compare(Yg, Yo, stg, sto, stag, stao, w["atol"], w["rtol"], floor=fl)
     print("rkck h2", s)
 
 
@@ -98,8 +99,8 @@ def test_rkc_h2co_ragged(cells):
     m, km, om = mech(name)
     T, p, Y = synth.workload_states(name, m, cells=cells, seed_offset=7)
     Yg, stg, stag = run_gpu(km, T, p, Y, w["dt"], w["rtol"], w["atol"], kin.RKC, ld=cells + 5)
-    Yo, sto, stao, _ = oracle.integrate(om, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKC)
-    s = compare(Yg[:, :cells], Yo, stg, sto, stag, stao, w["atol"], w["rtol"])
+    Yo, sto, stao, fl = reference(m, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKC)
+    s = compare(Yg[:, :cells], Yo, stg, sto, stag, stao, w["atol"], w["rtol"], floor=fl)
     assert np.all(Yg[:, cells:] == 0.0)  # padding columns untouched
     print("rkc h2co", cells, s)
 
@@ -114,9 +115,9 @@ def test_rkc_h2co_full_size_sampled():
     T, p, Y = synth.workload_states(name, m)
     Yg, stg, stag = run_gpu(km, T, p, Y, w["dt"], w["rtol"], w["atol"], kin.RKC)
     idx = np.sort(np.random.default_rng(17).choice(T.shape[0], 1536, replace=False))
-    Yo, sto, stao, _ = oracle.integrate(om, T[idx], p[idx], Y[:, idx], w["dt"], w["rtol"],
-                                        w["atol"], oracle.RKC)
-    s = compare(Yg[:, idx], Yo, stg[idx], sto, stag[idx], stao, w["atol"], w["rtol"])
+    Yo, sto, stao, fl = reference(m, T[idx], p[idx], Y[:, idx], w["dt"], w["rtol"], w["atol"],
+                                  oracle.RKC)
+    s = compare(Yg[:, idx], Yo, stg[idx], sto, stag[idx], stao, w["atol"], w["rtol"], floor=fl)
     # properties that hold for every cell: mass stays 1, status ok
     assert (stg == 0).all()
     assert np.abs(Yg.sum(0) - 1).max() < 1e-12
@@ -151,38 +152,62 @@ def test_rkc_ch4_fp64_sampled():
     m, km, om = mech(name)
     T, p, Y = synth.workload_states(name, m, cells=300, seed_offset=3)
     Yg, stg, stag = run_gpu(km, T, p, Y, w["dt"], w["rtol"], w["atol"], kin.RKC)
-    Yo, sto, stao, _ = oracle.integrate(om, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKC)
-    print("rkc ch4 fp64", compare(Yg, Yo, stg, sto, stag, stao, w["atol"], w["rtol"]))
+    Yo, sto, stao, fl = reference(m, T, p, Y, w["dt"], w["rtol"], w["atol"], oracle.RKC)
+    print("rkc ch4 fp64", compare(Yg, Yo, stg, sto, stag, stao, w["atol"], w["rtol"], floor=fl))
 
 
 # ------------------------------------------------------------- batched ---
-def _c4_parts(scale):
+@pytest.mark.parametrize("precision", [kin.FP64, kin.MIXED])
+def test_batched_c2h4_benchmarked_path(precision):
+    """The batched workload as the benchmark runs it: 16 uneven instances of
+    the 111-species mechanism (sizes scaled by 1/16, 17,000 cells, stages
+    2..~200) in one persistent launch, warp layout, power-method sigma, the
+    library's launch shape. 8 cells of every instance against the oracle.
+    FP64 (the workload's precision) as every FP64 parity test: trace-identical
+    cells to 1e-8, at most 5 % trace-divergent within 10 rtol, the contract
+    metric within the measured floor bound. Mixed precision is not this
+    workload's configuration; its result is a second valid RKC solution (FP32
+    rates move every decision) and is held to the bound such solutions get,
+    10 rtol in the integrator's weighting. On these instances, up to ~200
+    stages at dt = 1e-5 s, it lands near 1e-5 (measured 1.05e-5), against
+    3e-6 on the 53-species mixed workload, which is held to 1e-5."""
     name = "c2h4_111sp_rkc_batched"
     m, km, om = mech(name)
     parts, host = [], []
-    for i, (n, dt) in enumerate(synth.batched_instances(name, scale=scale)):
+    for i, (n, dt) in enumerate(synth.batched_instances(name, scale=1 / 16)):
         T, p, Y = synth.workload_states(name, m, cells=n, seed_offset=100 + i)
         host.append((T, p, Y, dt))
         parts.append(kin.Cells(dev(T), dev(p), dev(Y), dt, 1e-6, 1e-10,
                                torch.zeros(n, dtype=torch.uint8, device=DEV),
                                torch.zeros((n, kin.NSTATS), dtype=torch.int32, device=DEV)))
-    return m, km, om, parts, host
-
-
-def test_batched_c2h4_reduced():
-    """16 uneven instances of the 111-species mechanism (sizes scaled by
-    1/128) in one launch; every instance's sampled cells against the oracle."""
-    m, km, om, parts, host = _c4_parts(1 / 128)
-    kin.integrate_batch(km, parts, kin.RKC, layout=LANE)
+    kin.integrate_batch(km, parts, kin.RKC, precision, sigma=kin.SIGMA_POWER)
     torch.cuda.synchronize()
-    tot = 0
-    for (T, p, Y, dt), c in zip(host, parts):
-        idx = np.arange(0, T.shape[0], max(1, T.shape[0] // 4))
-        Yo, sto, stao, _ = oracle.integrate(om, T[idx], p[idx], Y[:, idx], dt, 1e-6, 1e-10, oracle.RKC)
-        compare(c.Y.cpu().numpy()[:, idx], Yo, c.status.cpu().numpy()[idx], sto,
-                c.stats.cpu().numpy()[idx], stao, 1e-10, 1e-6, max_div_frac=0.5)
-        tot += len(idx)
-    assert tot >= 32
+    Yg, Yo, stg, sto, xg, xo, fls = [], [], [], [], [], [], []
+    for dt in sorted(set(d for *_, d in host)):
+        sel = [(h, c) for h, c in zip(host, parts) if h[3] == dt]
+        idx = [np.linspace(0, h[0].shape[0] - 1, 8).astype(int) for h, _ in sel]
+        T = np.concatenate([h[0][i] for (h, _), i in zip(sel, idx)])
+        p = np.concatenate([h[1][i] for (h, _), i in zip(sel, idx)])
+        Y = np.concatenate([h[2][:, i] for (h, _), i in zip(sel, idx)], axis=1)
+        ref = reference(m, T, p, Y, dt, 1e-6, 1e-10, oracle.RKC_POWER) if precision == kin.FP64 else \
+            oracle.integrate(om, T, p, Y, dt, 1e-6, 1e-10, oracle.RKC_POWER)
+        Yo.append(ref[0]), sto.append(ref[1]), xo.append(ref[2]), fls.append(ref[3])
+        Yg.append(np.concatenate([c.Y.cpu().numpy()[:, i] for (_, c), i in zip(sel, idx)], axis=1))
+        stg.append(np.concatenate([c.status.cpu().numpy()[i] for (_, c), i in zip(sel, idx)]))
+        xg.append(np.concatenate([c.stats.cpu().numpy()[i] for (_, c), i in zip(sel, idx)]))
+    Yg, Yo = np.concatenate(Yg, axis=1), np.concatenate(Yo, axis=1)
+    stg, sto, xg, xo = map(np.concatenate, (stg, sto, xg, xo))
+    assert Yg.shape[1] == 128
+    assert (sto == 0).all()
+    assert xo[:, 0].max() >= 100 * xo[:, 0].min()  # the spread the launch balances
+    if precision == kin.FP64:
+        s = compare(Yg, Yo, stg, sto, xg, xo, 1e-10, 1e-6, max_div_frac=0.05, floor=max(fls))
+        print("batched c2h4 fp64", s, "f evals per cell %d..%d" % (xo[:, 0].min(), xo[:, 0].max()))
+    else:
+        assert np.array_equal(stg, sto)
+        e = tol_rel_err(Yg, Yo, 1e-10, 1e-6)
+        print("batched c2h4 mixed: max %.3e; contract metric %.3e" % (e.max(), rel_err(Yg, Yo, 1e-10).max()))
+        assert e.max() <= 10 * 1e-6
 
 
 def test_batch_equals_separate_calls():
@@ -205,6 +230,34 @@ def test_batch_equals_separate_calls():
 
 
 # ---------------------------------------------------------- edge cases ---
+@pytest.mark.parametrize("layout", [kin.LAYOUT_LANE, kin.LAYOUT_WARP])
+@pytest.mark.parametrize("method,k", [(kin.RKCK, 1e300), (kin.RKC, 1e23)])
+def test_step_size_underflow_status(method, k, layout):
+    """Status 2 as the oracle pins it on A -> B: RKCK at k = 1e300 rejects
+    every overflowing trial step until the step falls below 1e-20 dt; RKC at
+    k = 1e23 gets an initial step below that bound. The state stays at the
+    initial one and the counters equal the oracle's."""
+    from tests import mechs
+    m = mechs.a_to_b(k)
+    km = kin.Mechanism(m)
+    cells = 37
+    T = np.full(cells, 1000.0)
+    p = np.full(cells, 1e5)
+    Y = np.tile(np.array([[0.7], [0.3]]), (1, cells))
+    Yd = dev(Y)
+    st = torch.full((cells,), 255, dtype=torch.uint8, device=DEV)
+    sta = torch.zeros((cells, kin.NSTATS), dtype=torch.int32, device=DEV)
+    kin.integrate(km, dev(T), dev(p), Yd, 1e-6, 1e-6, 1e-10, method, status=st, stats=sta, layout=layout)
+    torch.cuda.synchronize()
+    Yo, sto, stao, _ = oracle.integrate(oracle.Mech(m), T, p, Y, 1e-6, 1e-6, 1e-10,
+                                        oracle.RKCK if method == kin.RKCK else oracle.RKC)
+    assert (sto == 2).all()
+    assert np.array_equal(st.cpu().numpy(), sto)
+    assert np.array_equal(Yd.cpu().numpy(), Y)
+    assert np.array_equal(sta.cpu().numpy(), stao)
+    km.close()
+
+
 def test_zero_cells_is_a_noop():
     m, km, om = mech("h2co_13sp_rkc")
     Y = torch.ones((m.n_species, 4), dtype=torch.float64, device=DEV)
@@ -355,10 +408,10 @@ def test_rkc_power_sigma_fp64(name, cells):
     dt = w["dt"] if not isinstance(w["dt"], tuple) else w["dt"][1]
     T, p, Y = synth.workload_states(name, m, cells=cells, seed_offset=21)
     Yg, stg, stag = run_gpu_sig(km, T, p, Y, dt, w["rtol"], w["atol"], kin.FP64, kin.SIGMA_POWER)
-    Yo, sto, stao, _ = oracle.integrate(om, T, p, Y, dt, w["rtol"], w["atol"], oracle.RKC_POWER)
+    Yo, sto, stao, fl = reference(m, T, p, Y, dt, w["rtol"], w["atol"], oracle.RKC_POWER)
     # power-iteration stopping tests can flip on rounding like the other
     # decisions; allow a few percent of trace-divergent cells at 10 rtol
-    s = compare(Yg, Yo, stg, sto, stag, stao, w["atol"], w["rtol"], max_div_frac=0.05)
+    s = compare(Yg, Yo, stg, sto, stag, stao, w["atol"], w["rtol"], max_div_frac=0.05, floor=fl)
     print("rkc power", name, s, "mean nfe gpu %.1f oracle %.1f" % (stag[:, 0].mean(), stao[:, 0].mean()))
 
 
