@@ -36,13 +36,12 @@ METRIC = "cell-ODEs integrated over Δt per sec per GB300 at rtol 1e-6"
 UNIT = "cell-ODEs/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# The FP64 pipe binds this path. From the nominal 1.25 TFLOP/s of a GB300:
-# 2 FP64 lanes per SM per clock x 152 SMs x 2070 MHz = 629.3 G lane-ops/s
-# (1258.6 GFLOP/s counting an FMA as 2 flops). Every FP64 add, multiply,
-# divide or FMA occupies one lane-op of that pipe, so the roofline is stated
-# in operations. The FP32 pipe (128 lanes per SM per clock, 40.3 T lane-ops/s)
-# runs the mixed path's rate arithmetic concurrently; the pipe with the
-# larger operations / peak binds.
+# The FP64 pipe binds this path (the FP32 pipe can bind the mixed path's
+# rate arithmetic; the pipe with the larger operations / peak binds). The
+# peaks are measured in every run by the dependent-FMA probe of
+# include/kin_peaks.h on the GPU being timed (measure_peaks). Only if that
+# probe fails do the nominal figures below stand in, and the line says so:
+# 2 FP64 and 128 FP32 FMA lanes per SM per clock x 152 SMs x 2070 MHz.
 FP64_LANES_PER_SM = 2
 FP32_LANES_PER_SM = 128
 SM_COUNT = 152
@@ -171,6 +170,79 @@ def algorithmic_work(m, method, precision, sigma, stats, energy=False):
     return float(ops64), float(ops32), exact
 
 
+def survey_flops(m, method, precision, stats, energy=False):
+    """Algorithmic flops of one call in the hot-path contract's count (an FMA
+    is 2 flops), from the per-cell counters. Per f evaluation
+    F = 4 nS + 2 nR + 2 nS nM + 6 nFO + 8 nR + 2 nS (mixture and
+    concentrations, rates of progress, third-body sums over the nM
+    third-body and falloff reactions, falloff blending, the stoichiometric
+    gather, dY/dt); RKC adds 10 nS per stage, 14 nS per attempt and 2 nS^2
+    per spectral-radius estimate, RKCK 60 nS per attempt. Returns (FP64
+    flops, FP32 flops): in the mixed path a rate evaluation is FP32 but for
+    its final 2 nS, and every spectral-radius evaluation is FP64. With the
+    energy equation nS counts T too and the per-evaluation rate constants
+    are not counted (a lower bound)."""
+    nS = m.n_species + (1 if energy else 0)
+    nR = m.n_reactions
+    n_m = int(np.count_nonzero(m.rtype != synth.PLAIN))
+    n_fo = int(np.count_nonzero(m.rtype == synth.FALLOFF))
+    F = 4 * nS + 2 * nR + 2 * nS * n_m + 6 * n_fo + 8 * nR + 2 * nS
+    nfe = stats[:, 0].astype(np.float64)
+    att = (stats[:, 1] + stats[:, 2]).astype(np.float64)
+    nsig = stats[:, 3].astype(np.float64)
+    sig_evals = stats[:, 4].astype(np.float64)
+    mixed = precision == synth.MIXED
+    if method != synth.RKC:
+        rate = nfe * F
+        vec = att * 60 * nS
+    else:
+        rate = (nfe - sig_evals) * F
+        stages = nfe - sig_evals - 2  # f(y0) and the initial-step probe are not stages
+        vec = stages * 10 * nS + att * 14 * nS + nsig * 2 * nS * nS + sig_evals * F
+    f32 = (rate - (nfe - sig_evals if method == synth.RKC else nfe) * 2 * nS) if mixed else 0.0 * rate
+    f64 = rate + vec - f32
+    return float(f64.sum()), float(f32.sum())
+
+
+def measure_peaks(gpu_index, stream=None):
+    """FP64 and FP32 FMA rates of this GPU from the dependent-FMA probe
+    (include/kin_peaks.h), each the best of three ~0.3 s runs, with the SM
+    clock sampled while it runs. Returns a dict (rates in FMA/s), or None if
+    the probe is not available."""
+    try:
+        from paper_1309_2710_gb300 import peaks
+        with ClockSampler(gpu_index) as clk:
+            peaks.fma_rate(peaks.FP64, 20000)
+            r64 = max(peaks.fma_rate(peaks.FP64, 150000)[1] for _ in range(3))
+            r32 = max(peaks.fma_rate(peaks.FP32, 10000000)[1] for _ in range(3))
+        return {"fp64_fma_per_s": r64, "fp32_fma_per_s": r32, "clocks": clk.summary()}
+    except Exception as e:  # noqa: BLE001 - the line then says the peaks are nominal
+        print("peak probe failed: %s" % e, file=sys.stderr)
+        return None
+
+
+def accuracy(m, Yg, Yo, stg, sto, stag, stao, atol, rtol, Tg=None, To=None):
+    """Errors of the GPU result against the FP64 oracle on the same cells:
+    per species the maximum of |dY| / max(|Y_ref|, atol) (the hot-path
+    contract's metric) and of |dY| / max(|Y_ref|, atol/rtol) (the
+    integrator's own weighting), over all cells and over the cells whose
+    decision trace equals the oracle's."""
+    e_a = np.abs(Yg - Yo) / np.maximum(np.abs(Yo), atol)
+    e_t = np.abs(Yg - Yo) / np.maximum(np.abs(Yo), atol / rtol)
+    same = (stag == stao).all(axis=1)
+    out = {"cells": int(Yo.shape[1]), "trace_divergent_cells": int((~same).sum()),
+           "status_equal": bool(np.array_equal(stg, sto)),
+           "max_err": float(e_a.max()), "max_err_tol_weighted": float(e_t.max()),
+           "max_err_trace_identical": float(e_a[:, same].max()) if same.any() else None,
+           "per_species_max_err": [float(x) for x in e_a.max(axis=1)],
+           "per_species_max_err_tol_weighted": [float(x) for x in e_t.max(axis=1)],
+           "species": list(m.names),
+           "metric": "|Y_gpu - Y_oracle| / max(|Y_oracle|, atol); tol_weighted: / max(|Y_oracle|, atol/rtol)"}
+    if Tg is not None:
+        out["T_max_rel_err"] = float((np.abs(Tg - To) / To).max())
+    return out
+
+
 # ------------------------------------------------------------- clocks ---
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons every 200 ms while running."""
@@ -237,16 +309,20 @@ def oracle_method(w):
     return 2 if w["sigma"] == synth.POWER else 1
 
 
-def oracle_rate(name, cells_target_s=10.0, max_cells=None, seed_offset=0, nthreads=0):
+def oracle_rate(name, cells_target_s=10.0, max_cells=None, seed_offset=0, nthreads=0, result=None,
+                cells=None, order="random"):
     """Time the FP64 oracle on the host cores (all of them, or `nthreads`) on
-    a bounded sample of the workload. Returns (cells/s, threads, sample
-    description)."""
+    a bounded sample of the workload: the first n cells of the same states.
+    Returns (cells/s, threads, sample description); with a `result` dict,
+    stores the sample's n and the oracle's outputs there (Y, status, stats
+    and, with the energy equation, T)."""
     import oracle
     w = synth.WORKLOADS[name]
     m = synth.workload_mechanism(name)
     om = oracle.Mech(m)
-    total = w["cells"]
-    T, p, Y = synth.workload_states(name, m, seed_offset=seed_offset)
+    total = cells or w["cells"]
+    T, p, Y = synth.workload_states(name, m, cells=total, seed_offset=seed_offset,
+                                    sort_by_T=order == "sorted")
     probe = min(2048 if nthreads == 0 else 64, total)
     t0 = time.perf_counter()
     meth = oracle_method(w)
@@ -256,9 +332,12 @@ def oracle_rate(name, cells_target_s=10.0, max_cells=None, seed_offset=0, nthrea
     per_cell = (time.perf_counter() - t0) / probe
     n = int(min(total if max_cells is None else max_cells, max(probe, cells_target_s / per_cell)))
     t0 = time.perf_counter()
-    nt = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], meth,
-                          nthreads=nthreads, energy=en)[3]
+    r = oracle.integrate(om, T[:n], p[:n], Y[:, :n], w["dt"], w["rtol"], w["atol"], meth,
+                         nthreads=nthreads, energy=en)
     el = time.perf_counter() - t0
+    nt = r[3]
+    if result is not None:
+        result.update(n=n, Y=r[0], status=r[1], stats=r[2], T=r[4] if en else None)
     return n / el, nt, "first %d of the %d cells of %s (same seeds), %.1f s wall" % (n, total, name, el)
 
 
@@ -324,6 +403,55 @@ def workload_config(name, cells, sigma=None, order="random"):
 
 
 # ------------------------------------------------------------ GPU arm ---
+def rank_states(name, m, cells_per_rank, world, rank, order="random"):
+    """This rank's block of the whole job. The job is world x cells_per_rank
+    cells of one seeded draw (so the per-GPU work stays fixed as ranks are
+    added: weak scaling); the cells are independent (Section 2.1), so each
+    rank takes its contiguous block (shard.shard_cells) and integrates it
+    with no exchange. Returns (start, stop, T, p, Y)."""
+    from paper_1309_2710_gb300 import shard
+    total = world * cells_per_rank
+    T, p, Y = synth.workload_states(name, m, cells=total, sort_by_T=order == "sorted")
+    a, b = shard.shard_cells(total, world, rank)
+    return a, b, T[a:b], p[a:b], np.ascontiguousarray(Y[:, a:b])
+
+
+def roofline(m, method, prec, sigma, stats, energy, kernel_ms, pk, world=1):
+    """The dominant launch against the binding arithmetic pipe, in two
+    counts: the hot-path contract's flops (FMA = 2; survey_flops) against
+    twice the measured FMA rate, and this build's lane operations (an FMA,
+    add, multiply or divide is one; algorithmic_work) against the FMA rate.
+    The FP64 and FP32 pipes run concurrently; the one with the larger work /
+    peak binds."""
+    ops64, ops32, exact = algorithmic_work(m, method, prec, sigma, stats, energy)
+    fl64, fl32 = survey_flops(m, method, prec, stats, energy)
+    if pk:
+        f64, f32 = pk["fp64_fma_per_s"], pk["fp32_fma_per_s"]
+        basis = ("measured: dependent-FMA probe (include/kin_peaks.h) on this GPU in this run, "
+                 "median SM clock %s MHz" % pk["clocks"].get("sm_mhz"))
+    else:
+        f64 = FP64_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6
+        f32 = FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6
+        basis = "nominal (the probe failed): 2 FP64 / 128 FP32 FMA lanes/SM/clk x 152 SMs x 2070 MHz"
+    t = kernel_ms * 1e-3
+    b64 = fl64 / f64 >= fl32 / f32
+    ach = world * (fl64 if b64 else fl32) / t / 1e9
+    peak = world * 2 * (f64 if b64 else f32) / 1e9
+    l64 = ops64 / f64 >= ops32 / f32
+    lach = world * (ops64 if l64 else ops32) / t / 1e9
+    lpeak = world * (f64 if l64 else f32) / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": peak,
+            "unit": "GFLOP/s %s (FMA = 2 flops)" % ("FP64" if b64 else "FP32"), "frac": ach / peak,
+            "count": "hot-path contract: per f 4nS+2nR+2nS*nM+6nFO+8nR+2nS; RKC 10nS/stage, 14nS/attempt, "
+                     "2nS^2/sigma estimate; RKCK 60nS/attempt; oracle-equal per-cell counters",
+            "peak_basis": basis, "kernel_ms": kernel_ms, "fp64_flops_per_launch": fl64,
+            "fp32_flops_per_launch": fl32,
+            "lane_ops": {"achieved": lach, "peak": lpeak, "frac": lach / lpeak,
+                         "unit": "G %s lane-ops/s (FMA, add, multiply, divide = 1)" % ("FP64" if l64 else "FP32"),
+                         "fp64_ops_per_launch": ops64, "fp32_ops_per_launch": ops32,
+                         "count": "exact" if exact else "lower bound"}}
+
+
 def run_kin(args):
     import torch
     import torch.distributed as dist
@@ -342,10 +470,9 @@ def run_kin(args):
     name = args.workload
     w = synth.WORKLOADS[name]
     m = synth.workload_mechanism(name)
-    cells = args.cells or w["cells"]
-    # weak scaling: every rank integrates its own full-size problem (own seeds)
-    T, p, Y0 = synth.workload_states(name, m, cells=cells, seed_offset=1000 * rank,
-                                     sort_by_T=args.order == "sorted")
+    cells_per_rank = args.cells or w["cells"]
+    a0, b0, T, p, Y0 = rank_states(name, m, cells_per_rank, world, rank, args.order)
+    cells = b0 - a0
     km = kin.Mechanism(m)
     method, prec = w["method"], w["precision"]
     sigma = w["sigma"] if args.sigma == "default" else (synth.POWER if args.sigma == "power"
@@ -394,6 +521,8 @@ def run_kin(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # the arithmetic peaks of this GPU, measured before the timed region
+    pk = measure_peaks(local)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
@@ -411,27 +540,25 @@ def run_kin(args):
         dist.barrier()
     ms_total = t_start.elapsed_time(t_end)
     kern_ms = [a.elapsed_time(b) for a, b in evs]
-    tmax = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+    tmax = torch.tensor([ms_total, float(np.mean(kern_ms))], device=dev, dtype=torch.float64)
     if world > 1:
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_step = float(tmax.item()) / args.steps
-    value = world * cells / (ms_step * 1e-3)
+    ms_step = float(tmax[0].item()) / args.steps
+    value = world * cells_per_rank / (ms_step * 1e-3)
 
     stats = sta.cpu().numpy()
     status = st.cpu().numpy()
-    ops64, ops32, exact = algorithmic_work(m, method, prec, sigma, stats, energy)
-    kavg = sum(kern_ms) / len(kern_ms)
-    peak64 = FP64_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
-    peak32 = FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
-    # the two pipes run concurrently: the binding one sets the time bound
-    t64, t32 = ops64 / peak64, ops32 / peak32
-    bind64 = t64 >= t32
-    achieved = (ops64 if bind64 else ops32) / (kavg * 1e-3) / 1e9
-    peak = peak64 if bind64 else peak32
+    kavg = float(tmax[1].item())
+    roof = roofline(m, method, prec, sigma, stats, energy, kavg, pk, world)
     shape_key = tuple(int(shape[k]) for k in ("block_threads", "blocks_per_sm", "staging", "occupancy",
                                                  "layout"))
     fname = feval_name(km, prec, shape, cells, layout_name(km, method, shape, cells), energy)
     tr, tr_shape = traffic_for(name, shape_key, fname, cells)
+    roof.update(traffic=tr, traffic_capture_shape=tr_shape,
+                kernel="kin_integrate launch (init + sort + integrate kernels, %s layout, %s f)"
+                       % (layout_name(km, method, shape, cells), fname))
+    Yg = Yd.cpu().numpy()
+    Tg = Td.cpu().numpy() if energy else None
 
     # end to end: host (pinned) buffers through the public API, copies timed
     e2e = None
@@ -466,17 +593,25 @@ def run_kin(args):
         te = torch.tensor([el], device=dev, dtype=torch.float64)
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * cells * ne / float(te.item()), "unit": UNIT,
+        e2e = {"value": world * cells_per_rank * ne / float(te.item()), "unit": UNIT,
                "h2d_bytes_per_step": int(Th.numel() * 8 + ph.numel() * 8 + Yh.numel() * 8),
                "d2h_bytes_per_step": int(Yh.numel() * 8 + sth.numel() + (Th.numel() * 8 if energy else 0)),
                "api": "kin_integrate_host (pinned host buffers)"}
 
-    cpu = None
+    cpu = acc = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, nt, sample = oracle_rate(name, cells_target_s=args.cpu_seconds)
+        ref = {}
+        v, nt, sample = oracle_rate(name, cells_target_s=args.cpu_seconds, max_cells=cells, result=ref,
+                                    cells=cells, order=args.order)
         cpu = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": sample}
         v1, _, sample1 = oracle_rate(name, cells_target_s=args.cpu_seconds / 2, nthreads=1)
         cpu["single_core"] = {"value": v1, "unit": UNIT, "cores": 1, "sample": sample1}
+        # the GPU's own results on those cells (the last timed call) against
+        # the oracle's: the error per result that the precision target names
+        n = ref["n"]
+        acc = accuracy(m, Yg[:, :n], ref["Y"], status[:n], ref["status"], stats[:n], ref["stats"],
+                       w["atol"], w["rtol"], None if Tg is None else Tg[:n], ref["T"])
+        acc["sample"] = "the cpu_baseline cells: " + sample
 
     if rank == 0:
         line = {
@@ -484,37 +619,52 @@ def run_kin(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == synth.FP64 else "f32+f64",
             "data": "synthetic (seeded generator standing in for the paper's mechanisms and states)",
-            "config": dict(workload_config(name, cells, sigma, args.order), launch_shape=shape,
-                           f_evaluation=fname),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "G %s lane-ops/s" % ("FP64" if bind64 else "FP32"),
-                         "frac": achieved / peak, "traffic": tr, "traffic_capture_shape": tr_shape,
-                         "kernel": "kin_integrate launch (init + sort + integrate kernels, %s layout, "
-                                   "%s f)" % (layout_name(km, method, shape, cells), fname),
-                         "peak_basis": "derived: %d %s lanes/SM/clk x 152 SMs x 2070 MHz"
-                                       % ((FP64_LANES_PER_SM, "FP64") if bind64 else (FP32_LANES_PER_SM, "FP32")),
-                         "kernel_ms": kavg, "fp64_ops_per_launch": ops64,
-                         "fp32_ops_per_launch": ops32, "ops_count": "exact" if exact else "lower bound",
-                         "fp64_frac": t64 / (kavg * 1e-3 * 1e9), "fp32_frac": t32 / (kavg * 1e-3 * 1e9)},
+            "config": dict(workload_config(name, cells_per_rank, sigma, args.order), launch_shape=shape,
+                           f_evaluation=fname, cells_total=world * cells_per_rank,
+                           parallelism="%d rank(s), one contiguous block of cells each "
+                                       "(shard.shard_cells), no exchange" % world),
+            "roofline": roof,
             "cpu_baseline": cpu,
+            "accuracy_vs_oracle": acc,
             "e2e": e2e,
             "gpu_launches": args.steps * (5 if method == synth.RKC else
                                           (1 if layout_name(km, method, shape, cells) == "warp-per-cell"
                                            else 2)),
             "clocks": clk.summary(),
+            "peak_probe": pk,
             "cell_status": np.bincount(status, minlength=4).tolist(),
             "mean_f_evals_per_cell": float(stats[:, 0].mean()),
             # the timed calls one by one (CUDA events around each kin_integrate,
             # excluding the L2 flush and the state reset between them)
             "call_ms": {"median": float(np.median(kern_ms)), "min": float(min(kern_ms)),
                         "max": float(max(kern_ms)), "n": len(kern_ms),
-                        "cells_per_s_at_median": world * cells / (float(np.median(kern_ms)) * 1e-3)},
+                        "cells_per_s_at_median": world * cells_per_rank / (float(np.median(kern_ms)) * 1e-3)},
         }
+        if args.serve_requests > 0 and world == 1:
+            line["serve"] = run_serve_leg(args)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     km.close()
     return 0
+
+
+def run_serve_leg(args):
+    """The serving workload on this GPU: Poisson requests of 1,024-65,536
+    cells (13-species FP64 or 53-species mixed, dt log-uniform 1e-7-1e-5 s),
+    continuous batching against one launch per request at 0.8 of the
+    saturated continuous-batching throughput, with p50/p99 latency and
+    throughput of each (serve.benchmark), and the SM clocks sampled over it."""
+    from paper_1309_2710_gb300 import serve
+    n = args.serve_requests
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        out = serve.benchmark(requests=n, loads=(0.8,), saturation_requests=max(50, n // 2))
+    out["clocks"] = clk.summary()
+    out["workload"] = ("%d Poisson requests at 0.8 load (saturation measured on %d requests at t = 0); "
+                       "continuous batching: %d slots per mechanism, per-launch cell caps %s; "
+                       "latency = arrival to result in pinned host memory"
+                       % (n, max(50, n // 2), out["slots_per_group"], out["batch_cells_cap"]))
+    return out
 
 
 # ------------------------------------------------------- batched mode ---
@@ -581,6 +731,7 @@ def run_batched(args):
     with torch.cuda.graph(g, stream=stream):
         kin.integrate_batch(km, parts, kin.RKC, prec, workspace=ws, sigma=sigma, **shape)
     out = {}
+    pk = measure_peaks(torch.cuda.current_device())
     for label, fn in (("persistent_graph", g.replay), ("separate_launches", separate)):
         for _ in range(args.warmup):
             with torch.cuda.stream(stream):
@@ -588,37 +739,84 @@ def run_batched(args):
                 fn()
         torch.cuda.synchronize()
         ms = []
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                reset()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                fn()
-                e1.record(stream)
-            torch.cuda.synchronize()
-            ms.append(e0.elapsed_time(e1))
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for _ in range(args.steps):
+                with torch.cuda.stream(stream):
+                    reset()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
         st = torch.cat([c.status for c in parts]).cpu().numpy()
         out[label] = {"ms": float(np.median(ms)), "cells_per_s": total / (np.median(ms) * 1e-3),
-                      "status": np.bincount(st, minlength=4).tolist()}
+                      "status": np.bincount(st, minlength=4).tolist(), "clocks": clk.summary()}
     stats = torch.cat([c.stats for c in parts]).cpu().numpy()
     nfe = float(stats[:, 0].mean())
-    ops64, ops32, exact = algorithmic_work(m, synth.RKC, prec, sigma, stats)
-    peak64 = FP64_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
-    peak32 = FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e9
-    kms = out["persistent_graph"]["ms"]
-    bind64 = ops64 / peak64 >= ops32 / peak32
-    ach = (ops64 if bind64 else ops32) / (kms * 1e-3) / 1e9
-    pk = peak64 if bind64 else peak32
-    roof = {"bound": "alu", "achieved": ach, "peak": pk, "frac": ach / pk,
-            "unit": "G %s lane-ops/s" % ("FP64" if bind64 else "FP32"),
-            "ops_count": "exact" if exact else "lower bound", "kernel_ms": kms,
-            "fp64_ops": ops64, "fp32_ops": ops32}
+    roof = roofline(m, synth.RKC, prec, sigma, stats, 0, out["persistent_graph"]["ms"], pk)
+    cpu = None if args.no_cpu_baseline else oracle_batched_sample(name, m, inst, args.stage_sample)
     print(json.dumps({"mode": "batched", "workload": name, "instances": len(inst), "cells": total,
+                      "cpu_baseline": cpu, "gpu_f_evals_per_cell": {
+                          "min": int(stats[:, 0].min()), "median": float(np.median(stats[:, 0])),
+                          "max": int(stats[:, 0].max())},
                       "scale": args.scale, "precision": args.precision, "mean_f_evals": nfe,
                       "sigma": "power" if sigma == synth.POWER else "gershgorin",
                       "sizes": [n for n, _ in inst], "launch_shape": shape, **out, "roofline": roof,
                       "speedup": out["separate_launches"]["ms"] / out["persistent_graph"]["ms"]}))
     return 0
+
+
+def oracle_batched_sample(name, m, inst, per_dt):
+    """The CPU leg of the batched line: the FP64 oracle on a bounded sample
+    of the batched workload, `per_dt` cells for each dt (taken in turn from
+    the instances with that dt, the same states as the GPU run), timed on the
+    host cores, with the RKC stage count of every attempt traced: the
+    workload's stiffness spread that the persistent launch balances."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    w = synth.WORKLOADS[name]
+    om = oracle.Mech(m)
+    sample, stages = [], {}
+    for dt in sorted(set(d for _, d in inst)):
+        picks = [(i, n) for i, (n, d) in enumerate(inst) if d == dt]
+        states = [synth.workload_states(name, m, cells=n, seed_offset=100 + i) for i, n in picks]
+        cells, k = [], 0
+        while len(cells) < per_dt and k < max(n for _, n in picks):
+            for j, (i, n) in enumerate(picks):
+                if k < n and len(cells) < per_dt:
+                    T, p, Y = states[j]
+                    cells.append((T[k], p[k], Y[:, k].copy()))
+            k += 1
+        sample.append((dt, cells))
+    threads = os.cpu_count() or 1
+
+    def one(args):
+        dt, (T, p, y) = args
+        _, st, tr = oracle.trace_cell(om, T, p, y, dt, w["rtol"], w["atol"], oracle_method(w), cap=200000)
+        return dt, st, tr["s"], int(tr["stats"][0])
+
+    jobs = [(dt, c) for dt, cells in sample for c in cells]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:  # the oracle's C code runs without the GIL
+        res = list(ex.map(one, jobs))
+    el = time.perf_counter() - t0
+    for dt in sorted(set(r[0] for r in res)):
+        rr = [r for r in res if r[0] == dt]
+        s_all = np.concatenate([r[2] for r in rr])
+        smax = np.array([r[2].max() for r in rr])
+        nfe = np.array([r[3] for r in rr])
+        stages["%g" % dt] = {
+            "cells": len(rr), "status": np.bincount([r[1] for r in rr], minlength=4).tolist(),
+            "stages_per_attempt": {"min": int(s_all.min()), "p50": float(np.percentile(s_all, 50)),
+                                   "p90": float(np.percentile(s_all, 90)), "p99": float(np.percentile(s_all, 99)),
+                                   "max": int(s_all.max())},
+            "max_stages_per_cell": {"min": int(smax.min()), "p50": float(np.median(smax)), "max": int(smax.max())},
+            "f_evals_per_cell": {"min": int(nfe.min()), "p50": float(np.median(nfe)), "max": int(nfe.max())},
+            "histogram_stages_by_25": np.bincount(np.minimum(s_all, 250) // 25, minlength=11).tolist()}
+    return {"value": len(jobs) / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d cells per dt, the first cells of the instances with that dt in turn, %.1f s wall"
+                      % (per_dt, el), "stage_counts": stages}
 
 
 def run_divergence(args):
@@ -726,6 +924,14 @@ def layout_name(km, method, shape, cells):
     return "warp-per-cell" if lay == kin.LAYOUT_WARP else "lane-per-cell"
 
 
+def launcher_cmd(argv, n_gpus, port):
+    """The command that runs this benchmark as n_gpus ranks on one node,
+    one process per GPU (rendezvous on 127.0.0.1)."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+            "--nproc-per-node", str(n_gpus), "--master-addr", "127.0.0.1", "--master-port", str(port),
+            os.path.abspath(__file__)] + list(argv)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -753,7 +959,18 @@ def main():
                     help="f evaluation of the lane layout (default: the library's choice)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="batched mode: rate precision")
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests of the serving leg on the headline line (0: no serving leg)")
+    ap.add_argument("--stage-sample", type=int, default=96,
+                    help="batched mode: cells per dt whose RKC stage counts the oracle traces")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: re-run this command under torch.distributed.run
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        return subprocess.call(launcher_cmd(sys.argv[1:], args.gpus, port))
     if args.mode == "batched":
         return run_batched(args)
     if args.mode == "divergence":

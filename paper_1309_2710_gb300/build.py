@@ -10,6 +10,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkin.so")
+# the arithmetic-peak probe behind include/kin_peaks.h: its own library, not
+# part of the integrator
+LIB_PEAKS = os.path.join(OUT_DIR, "libkin_peaks.so")
+PEAKS_SOURCE = "peaks.cu"
 SOURCES = ["kernels.cu", "abi.cu", "no_alloc.cu", "inst_rkc_f64.cu", "inst_rkc_f32.cu",
            "inst_rkck_f64.cu", "inst_rkck_f32.cu", "inst_warp_f64.cu", "inst_warp_f32.cu",
            "inst_warp_f64_hi.cu", "inst_warp_f32_hi.cu", "inst_energy_f64.cu", "inst_energy_f32.cu",
@@ -37,9 +41,9 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(LIB_PEAKS):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(LIB_PEAKS))
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
@@ -81,14 +85,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-ldl"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed:\n" + r.stderr)
-    os.replace(tmp, LIB)
+    with cf.ThreadPoolExecutor(len(SOURCES) + 1) as ex:
+        objs = list(ex.map(compile_one, SOURCES + [PEAKS_SOURCE]))
+    for lib, parts in ((LIB, objs[:-1] + ["-ldl"]), (LIB_PEAKS, objs[-1:])):
+        tmp = lib + ".%d.tmp" % os.getpid()
+        cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + parts
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n" + r.stderr)
+        os.replace(tmp, lib)
     return LIB
 
 

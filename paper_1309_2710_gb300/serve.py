@@ -4,7 +4,9 @@ A request is one CFD subdomain: its cells' (T, p, Y), the flow step dt and
 the tolerances, for one of the registered mechanisms. The server
 
 * admits arrived requests in FIFO order while their device state fits a
-  memory budget, and keeps that state resident until the result is back;
+  memory budget, and keeps that state resident until the result is back; the
+  budget also holds the slots' workspaces, sized once per run for the
+  largest launch a slot can make;
 * groups admitted requests by mechanism/method/precision and launches each
   group's waiting requests as ONE persistent kin_integrate_batch launch on one
   of the group's stream slots as soon as a slot is free, so requests that
@@ -106,7 +108,30 @@ class Server:
         self.device = device or torch.device("cuda")
         self.slots = {g: [_Slot(torch.cuda.Stream(device=self.device)) for _ in range(slots_per_group)]
                       for g in groups}
-        self.used = 0
+        self.used = 0        # device bytes of admitted requests' state
+        self.peak_used = 0   # the largest `used` seen
+        self.ws_bytes = 0    # device bytes of the slots' workspaces
+
+    def _cap(self, gname: str) -> int:
+        return self.groups[gname].max_batch_cells or self.max_batch_cells
+
+    def _size_workspaces(self, requests: List[Request]):
+        """Allocate every slot's workspace once, for the largest launch it can
+        make in this run: the group's per-launch cell cap (or all of the
+        group's cells, if fewer), or a single larger request."""
+        self.ws_bytes = 0
+        for gname, slots in self.slots.items():
+            g = self.groups[gname]
+            sizes = [r.cells for r in requests if r.group == gname]
+            cells = max(max(sizes, default=0), min(self._cap(gname), sum(sizes)))
+            sh = g.shape
+            need = g.mech.workspace_bytes(g.method, g.precision, cells, sh.get("block_threads", 0),
+                                          sh.get("blocks_per_sm", 0), sh.get("staging", 0),
+                                          sh.get("occupancy", 0), g.sigma, sh.get("layout", 0))
+            for slot in slots:
+                if slot.workspace is None or slot.workspace.numel() < need:
+                    slot.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+                self.ws_bytes += slot.workspace.numel()
 
     def request_bytes(self, r: Request) -> int:
         nS = self.groups[r.group].mech.n_species
@@ -124,17 +149,11 @@ class Server:
         r.status = torch.empty(n, dtype=torch.uint8, pin_memory=True)
         r._bytes = self.request_bytes(r)
         self.used += r._bytes
+        self.peak_used = max(self.peak_used, self.used)
         r.t_admit = now
 
     def _launch(self, gname: str, slot: _Slot, batch: List[Request], now: float):
         g = self.groups[gname]
-        cells = sum(r.cells for r in batch)
-        sh = g.shape
-        need = g.mech.workspace_bytes(g.method, g.precision, cells, sh.get("block_threads", 0),
-                                      sh.get("blocks_per_sm", 0), sh.get("staging", 0),
-                                      sh.get("occupancy", 0), g.sigma, sh.get("layout", 0))
-        if slot.workspace is None or slot.workspace.numel() < need:
-            slot.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
         with torch.cuda.stream(slot.stream):
             parts = []
             for r in batch:
@@ -166,8 +185,9 @@ class Server:
         """Serve `requests` (arrival times in seconds from the start of the
         call, in wall-clock time). Returns them with results and times."""
         todo = sorted(requests, key=lambda r: r.arrival)
+        self._size_workspaces(todo)
         for r in todo:
-            if self.request_bytes(r) > self.budget:
+            if self.ws_bytes + self.request_bytes(r) > self.budget:
                 raise ValueError("request %d needs more memory than the budget" % r.rid)
         waiting: List[Request] = []  # arrived, not admitted (FIFO)
         ready: Dict[str, List[Request]] = {g: [] for g in self.groups}
@@ -178,7 +198,7 @@ class Server:
             while nxt < len(todo) and todo[nxt].arrival <= now:
                 waiting.append(todo[nxt])
                 nxt += 1
-            while waiting and self.used + self.request_bytes(waiting[0]) <= self.budget:
+            while waiting and self.ws_bytes + self.used + self.request_bytes(waiting[0]) <= self.budget:
                 r = waiting.pop(0)
                 self._admit(r, now)
                 ready[r.group].append(r)
@@ -192,7 +212,7 @@ class Server:
                     if slot.event is None and ready[gname]:
                         batch, cells = [], 0
                         q = ready[gname]
-                        cap = self.groups[gname].max_batch_cells or self.max_batch_cells
+                        cap = self._cap(gname)
                         while q and len(batch) < self.max_instances and (
                                 not batch or cells + q[0].cells <= cap):
                             r = q.pop(0)
@@ -314,6 +334,39 @@ def default_groups():
     return groups, pools
 
 
+def benchmark(requests: int = 2000, loads=(0.5, 0.8, 0.95), budget_gb: float = 16.0,
+              slots: int = SERVE_SLOTS, saturation_requests: Optional[int] = None):
+    """The serving measurement: the saturated throughput of continuous
+    batching (every request arrives at t = 0; `saturation_requests` of them,
+    default `requests`), then at each offered load (a fraction of that
+    throughput, Poisson arrivals) `requests` requests served by continuous
+    batching and by one launch per request, with p50/p99 latency and
+    throughput of each."""
+    groups, pools = default_groups()
+    budget = int(budget_gb * (1 << 30))
+    # warm up both paths (module loads, workspaces, pinned pools)
+    warm = make_requests(8, pools, seed=7)
+    Server(groups, budget, slots).run(warm)
+    one_launch_per_request(groups, make_requests(4, pools, seed=8))
+    torch.cuda.synchronize()
+    sat_reqs = make_requests(saturation_requests or requests, pools)
+    srv = Server(groups, budget, slots)
+    sat = percentiles(srv.run(sat_reqs))
+    mean_cells = np.mean([r.cells for r in make_requests(requests, pools)])
+    out = {"saturated": sat, "budget_bytes": budget, "workspace_bytes": srv.ws_bytes,
+           "peak_state_bytes": srv.peak_used, "slots_per_group": slots,
+           "batch_cells_cap": dict(SERVE_BATCH_CELLS), "loads": []}
+    for load in loads:
+        rate = load * sat["throughput_cells_per_s"] / mean_cells
+        a = percentiles(Server(groups, budget, slots).run(make_requests(requests, pools, loads_rate=rate)))
+        b = percentiles(one_launch_per_request(groups, make_requests(requests, pools, loads_rate=rate)))
+        out["loads"].append({"load": load, "offered_requests_per_s": rate,
+                             "continuous_batching": a, "one_launch_per_request": b})
+    for g in groups.values():
+        g.mech.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description="continuous-batching serving benchmark")
     ap.add_argument("--requests", type=int, default=2000)
@@ -323,27 +376,8 @@ def main():
     args = ap.parse_args()
     from . import build as _b
     _b.build()
-    groups, pools = default_groups()
-    budget = int(args.budget_gb * (1 << 30))
-    # warm up both paths (module loads, workspaces, pinned pools)
-    warm = make_requests(8, pools, seed=7)
-    Server(groups, budget, args.slots).run(warm)
-    one_launch_per_request(groups, make_requests(4, pools, seed=8))
-    torch.cuda.synchronize()
-    # saturated throughput: everything arrives at t = 0
-    sat_reqs = make_requests(args.requests, pools)
-    srv = Server(groups, budget, args.slots)
-    sat = percentiles(srv.run(sat_reqs))
-    mean_cells = np.mean([r.cells for r in sat_reqs])
-    out = {"saturated": sat, "loads": []}
-    for load in [float(x) for x in args.loads.split(",") if x]:
-        rate = load * sat["throughput_cells_per_s"] / mean_cells
-        a = percentiles(Server(groups, budget, args.slots).run(make_requests(args.requests, pools,
-                                                                             loads_rate=rate)))
-        b = percentiles(one_launch_per_request(groups, make_requests(args.requests, pools,
-                                                                     loads_rate=rate)))
-        out["loads"].append({"load": load, "offered_requests_per_s": rate,
-                             "continuous_batching": a, "one_launch_per_request": b})
+    out = benchmark(args.requests, [float(x) for x in args.loads.split(",") if x], args.budget_gb,
+                    args.slots)
     print(json.dumps(out))
 
 

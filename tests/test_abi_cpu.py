@@ -84,3 +84,19 @@ def test_binding_constants_match_the_header():
     end = plain.index("} kin_opts;")
     fields = re.findall(r"\b(\w+)\s*;", plain[plain.rindex("{", 0, end) + 1:end])
     assert fields == [f for f, _ in kin.Opts._fields_]
+
+
+def test_peak_probe_library_exports_its_header():
+    """libkin_peaks.so exports every entry point include/kin_peaks.h declares,
+    and refuses a bad argument before any CUDA call."""
+    kbuild.build()
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "kin_peaks.h")).read(), flags=re.S)
+    names = set(re.findall(r"\b(kinpk_\w+)\s*\(", src))
+    assert names == {"kinpk_fma_rate", "kinpk_last_error"}
+    L = ctypes.CDLL(kbuild.LIB_PEAKS)
+    for name in names:
+        assert hasattr(L, name), name
+    from paper_1309_2710_gb300 import peaks
+    ms, rate = ctypes.c_double(), ctypes.c_double()
+    assert peaks.lib().kinpk_fma_rate(9, 1, 1, 32, None, ctypes.byref(ms), ctypes.byref(rate)) == -1
+    assert b"precision" in peaks.lib().kinpk_last_error()

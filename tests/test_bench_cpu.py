@@ -116,3 +116,41 @@ def test_traffic_lookup(monkeypatch):
     assert bench.traffic_for("v", (32, 16, 0, 0, 1), "generated", 10) == (None, None)
     monkeypatch.setattr(bench, "kernel_hash", lambda: "other")
     assert bench.traffic_for("w", (32, 16, 0, 0, 1), "generated", 10) == (None, None)
+
+
+def test_survey_flops_by_hand():
+    """The hot-path contract's flop count: per f evaluation
+    F = 4 nS + 2 nR + 2 nS nM + 6 nFO + 8 nR + 2 nS; RKC adds 10 nS per
+    stage, 14 nS per attempt, 2 nS^2 per spectral-radius estimate."""
+    m = small_mech()  # nS 3, nR 4, nM 2, nFO 1
+    F = 4 * 3 + 2 * 4 + 2 * 3 * 2 + 6 * 1 + 8 * 4 + 2 * 3
+    assert F == 76
+    st = stats([[40, 10, 1, 2, 6]])
+    f64, f32 = bench.survey_flops(m, synth.RKC, synth.FP64, st)
+    stages, att = 40 - 6 - 2, 11
+    assert f32 == 0
+    assert f64 == 34 * F + stages * 10 * 3 + att * 14 * 3 + 2 * 2 * 9 + 6 * F
+    st = stats([[40, 10, 1, 2, 8]])
+    f64, f32 = bench.survey_flops(m, synth.RKC, synth.MIXED, st)
+    rate = 40 - 8
+    assert f32 == rate * (F - 2 * 3)
+    assert f64 == rate * 2 * 3 + (rate - 2) * 10 * 3 + att * 14 * 3 + 2 * 2 * 9 + 8 * F
+    st = stats([[60, 8, 2, 0, 0]])
+    f64, f32 = bench.survey_flops(m, synth.RKCK, synth.FP64, st)
+    assert f64 == 60 * F + 10 * 60 * 3 and f32 == 0
+
+
+def test_survey_flops_per_evaluation_of_the_headline_mechanism():
+    # 13 species, 54 reactions, 5 third-body reactions, no falloff: 748 flops
+    m = synth.workload_mechanism("h2co_13sp_rkc")
+    assert bench.survey_flops(m, synth.RKCK, synth.FP64, stats([[1, 0, 0, 0, 0]]))[0] == 748
+
+
+def test_launcher_runs_one_process_per_gpu():
+    cmd = bench.launcher_cmd(["--gpus", "4", "--steps", "3"], 4, 29511)
+    assert cmd[1:3] == ["-m", "torch.distributed.run"]
+    i = cmd.index("--nproc-per-node")
+    assert cmd[i + 1] == "4"
+    assert cmd[cmd.index("--master-addr") + 1] == "127.0.0.1"
+    assert cmd[cmd.index("--master-port") + 1] == "29511"
+    assert cmd[-4:] == ["--gpus", "4", "--steps", "3"] and cmd[-5].endswith("bench.py")

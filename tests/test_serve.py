@@ -57,7 +57,7 @@ def _alone(groups, r):
 def test_served_equals_alone(setup):
     groups, pools = setup
     reqs = _requests(pools, 40, seed=1, rate=400.0)
-    srv = serve.Server(groups, budget_bytes=64 << 20, slots_per_group=2)
+    srv = serve.Server(groups, budget_bytes=1 << 30, slots_per_group=2)
     out = srv.run(reqs)
     assert srv.used == 0
     launched_while_busy = 0
@@ -75,16 +75,35 @@ def test_served_equals_alone(setup):
 
 
 def test_budget_limits_resident_state(setup):
+    """The budget holds the slots' workspaces plus the device state of the
+    admitted requests. With room for the largest request only, two requests
+    are resident at the same time only if both fit together, and the
+    resident bytes never exceed what the workspaces leave of the budget."""
     groups, pools = setup
     reqs = _requests(pools, 12, seed=2)
-    budget = max(serve.Server(groups, 1).request_bytes(r) for r in reqs)
-    srv = serve.Server(groups, budget_bytes=budget, slots_per_group=2)
+    probe = serve.Server(groups, 1 << 40, slots_per_group=2)
+    probe._size_workspaces(reqs)
+    ws = probe.ws_bytes
+    assert ws > 0
+    room = max(probe.request_bytes(r) for r in reqs)
+    srv = serve.Server(groups, budget_bytes=ws + room, slots_per_group=2)
     out = srv.run(reqs)
-    # with room for only the largest request, admissions serialise: a request
-    # is admitted only after the previous admitted one completed, unless both fit
     for r in out:
         assert r.status.max().item() == 0
     assert srv.used == 0
+    assert srv.ws_bytes == ws
+    assert 0 < srv.peak_used <= room
+    together = 0
+    for a in out:
+        for b in out:
+            if a.rid < b.rid and a.t_admit < b.t_done and b.t_admit < a.t_done:
+                together += 1
+                assert srv.request_bytes(a) + srv.request_bytes(b) <= room
+    # and the rule is not vacuous: some pair did not fit together
+    pairs = [(a, b) for a in out for b in out if a.rid < b.rid]
+    assert any(srv.request_bytes(a) + srv.request_bytes(b) > room for a, b in pairs)
+    with pytest.raises(ValueError):
+        serve.Server(groups, budget_bytes=ws + room - 1, slots_per_group=2).run(reqs)
 
 
 def test_one_launch_per_request_matches(setup):

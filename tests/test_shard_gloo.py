@@ -81,3 +81,39 @@ def test_two_rank_shards_equal_single_rank():
                                           w["method"], nthreads=1)
     got = np.concatenate([o[2] for o in sorted(out, key=lambda o: o[0])], axis=1)
     assert np.array_equal(got, Yref)
+
+
+def _bench_worker(rank, world, port, q):
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    name = "h2co_13sp_rkc"
+    m = synth.workload_mechanism(name)
+    a, b, T, p, Y = bench.rank_states(name, m, 37, world, rank)
+    out = [None] * world
+    dist.all_gather_object(out, (a, b, T, Y))
+    if rank == 0:
+        q.put(out)
+    dist.destroy_process_group()
+
+
+def test_benchmark_ranks_cover_the_job_once_in_order():
+    """bench.py's rank blocks under two gloo ranks: the job is 2 x 37 cells
+    of one seeded draw; the blocks tile it once, in order, and hold exactly
+    the single-rank draw's states."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_worker, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    out = q.get(timeout=120)
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    out = sorted(out, key=lambda o: o[0])
+    assert [(o[0], o[1]) for o in out] == [(0, 37), (37, 74)]
+    name = "h2co_13sp_rkc"
+    T, p, Y = synth.workload_states(name, synth.workload_mechanism(name), cells=74)
+    assert np.array_equal(np.concatenate([o[2] for o in out]), T)
+    assert np.array_equal(np.concatenate([o[3] for o in out], axis=1), Y)
