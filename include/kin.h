@@ -84,8 +84,8 @@ extern "C" {
                              reactions and species of f; the cell's concentrations and
                              rates of progress live in shared memory. staging is
                              ignored; for RKC, occupancy selects the register budget
-                             (KIN_OCC_HIGH: 80 registers for up to 64 state
-                             components, 24 warps per SM); block_threads may be up to
+                             (KIN_OCC_HIGH: 64 registers for up to 64 state
+                             components, 32 warps per SM); block_threads may be up to
                              256 */
 #define KIN_WARP_MIN_REACTIONS 256
 #define KIN_WARP_MAX_CELLS_PER_SM 64

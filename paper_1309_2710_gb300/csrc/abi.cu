@@ -393,6 +393,25 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
             nuW32[e2] = (float)cnuW[e2];
         }
     const size_t oNuW = put(cnuW.data(), 8 * nnz), oNuW32 = put(nuW32.data(), 4 * nnz);
+    // ELL copies of the gather entries for the warp layout's 32 lanes
+    int ell_base[ELL_SLOTS] = {0};
+    int ell_n = 0;
+    for (int r = 0; r * 32 < nS; ++r) {
+        int len = 0;
+        for (int i = 32 * r; i < std::min(nS, 32 * r + 32); ++i) len = std::max(len, ptr[i + 1] - ptr[i]);
+        ell_base[r] = ell_n;
+        ell_n += 32 * len;
+    }
+    std::vector<CsrW32> ell32(ell_n, CsrW32{0.0f, 0});
+    std::vector<CsrW64> ell64(ell_n, CsrW64{0.0, 0, 0});
+    for (int i = 0; i < nS; ++i)
+        for (int e2 = ptr[i]; e2 < ptr[i + 1]; ++e2) {
+            const int at = ell_base[i / 32] + 32 * (e2 - ptr[i]) + i % 32;
+            ell32[at] = CsrW32{nuW32[e2], crxp[e2]};
+            ell64[at] = CsrW64{cnuW[e2], crxp[e2], 0};
+        }
+    const size_t oEll32 = put(ell32.data(), sizeof(CsrW32) * ell_n);
+    const size_t oEll64 = put(ell64.data(), sizeof(CsrW64) * ell_n);
     const size_t oEff = put(d->eff, 8 * (size_t)nM * nS), oEff32 = put(eff32.data(), 4 * (size_t)nM * nS);
     // thermochemistry for the energy equation: cp, cp/W, Hf
     const bool thermo = d->cp && d->Hf;
@@ -427,6 +446,9 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     M.rxn_perm = (const int*)(b + oPerm);
     M.rxnp = (const Rxn*)(b + oRxp);
     M.csrp_rxn = (const int*)(b + oCrxp);
+    M.ell32 = (const CsrW32*)(b + oEll32);
+    M.ell64 = (const CsrW64*)(b + oEll64);
+    for (int r = 0; r < ELL_SLOTS; ++r) M.ell_base[r] = ell_base[r];
     M.effT = (const double*)(b + oEffT);
     M.effT32 = (const float*)(b + oEffT32);
     M.csr_ptr = (const int*)(b + oPtr); M.csr_rxn = (const int*)(b + oCrx);

@@ -29,6 +29,20 @@ struct Rxn {
     int32_t fo;      // falloff ordinal or -1
 };
 
+// Stoichiometric entry of the warp layout's gather: the net coefficient
+// times the species' molar mass, and the reaction's permutation position.
+struct CsrW32 {
+    float nuW;
+    int32_t pos;
+};
+struct CsrW64 {
+    double nuW;
+    int32_t pos, pad;
+};
+
+// Species slots of 32 in the warp layout's ELL gather tables.
+constexpr int ELL_SLOTS = (KIN_MAX_SPECIES + 31) / 32;
+
 struct MechDev {
     int nS, nR, nM, nFO, nnz;
     const double* W;       // [nS]
@@ -45,6 +59,13 @@ struct MechDev {
     const int* rxn_perm;   // [nR] reaction at each permutation position
     const Rxn* rxnp;       // [nR] descriptors in permutation order; .row indexes effT's columns
     const int* csrp_rxn;   // [nnz] permutation position of each CSR entry's reaction
+    // The same entries for a 32-lane gather, in ELL order: species i = 32 r + l
+    // keeps its k-th entry at ell[ell_base[r] + 32 k + l] (k below the row
+    // length csr_ptr[i + 1] - csr_ptr[i]), so the 32 lanes of a step read
+    // consecutive entries.
+    const CsrW32* ell32;
+    const CsrW64* ell64;
+    int ell_base[ELL_SLOTS];
     const double* effT;    // [nS][nM] efficiencies, column = non-plain reaction in permutation order
     const float* effT32;   // [nS][nM]
     const int* csr_ptr;    // [nS + 1] species -> entries

@@ -72,6 +72,17 @@ struct TabW<float> {
     __device__ static const float* effT(const MechDev& M) { return M.effT32; }
 };
 
+template <typename R>
+struct EllT;
+template <>
+struct EllT<double> {
+    __device__ static const CsrW64* tab(const MechDev& M) { return M.ell64; }
+};
+template <>
+struct EllT<float> {
+    __device__ static const CsrW32* tab(const MechDev& M) { return M.ell32; }
+};
+
 // Shared words per warp: C [nS] and Omega [nR], padded to 4, sized for FP64
 // (the mixed-precision path evaluates f in FP32 for its RK stages and in FP64
 // for its spectral-radius estimates, over the same words).
@@ -161,7 +172,11 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
         OM[q] = v;
     }
     __syncwarp(mask);
-    // W_i omega_i over the species' row (W_i folded into its coefficients)
+    // W_i omega_i over the species' row (W_i folded into its coefficients).
+    // With 32 lanes per cell the row is read from the ELL copy, where the
+    // lanes of a step read consecutive entries (one or two cache lines per
+    // load instead of one line per lane); the entries and their order are
+    // those of the species-major rows.
     const R* __restrict__ nuW = Tab<R>::nuW(M);
     const double invrho = (double)s * invCtot;
 #pragma unroll
@@ -170,13 +185,28 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
         double o = 0.0;
         if (i < nS) {
             R w0 = R(0), w1 = R(0);
-            const int e1 = M.csr_ptr[i + 1];
-            int e = M.csr_ptr[i];
-            for (; e + 1 < e1; e += 2) {
-                w0 += nuW[e] * OM[M.csrp_rxn[e]];
-                w1 += nuW[e + 1] * OM[M.csrp_rxn[e + 1]];
+            if constexpr (G == 32) {
+                const int len = M.csr_ptr[i + 1] - M.csr_ptr[i];
+                const auto* __restrict__ p = EllT<R>::tab(M) + M.ell_base[r] + lane;
+                int k = 0;
+                for (; k + 1 < len; k += 2) {
+                    const auto a = p[32 * k], b = p[32 * (k + 1)];
+                    w0 += a.nuW * OM[a.pos];
+                    w1 += b.nuW * OM[b.pos];
+                }
+                if (k < len) {
+                    const auto a = p[32 * k];
+                    w0 += a.nuW * OM[a.pos];
+                }
+            } else {
+                const int e1 = M.csr_ptr[i + 1];
+                int e = M.csr_ptr[i];
+                for (; e + 1 < e1; e += 2) {
+                    w0 += nuW[e] * OM[M.csrp_rxn[e]];
+                    w1 += nuW[e + 1] * OM[M.csrp_rxn[e + 1]];
+                }
+                if (e < e1) w0 += nuW[e] * OM[M.csrp_rxn[e]];
             }
-            if (e < e1) w0 += nuW[e] * OM[M.csrp_rxn[e]];
             o = (double)(w0 + w1) * invrho;
         }
         out[r] = o;
@@ -550,12 +580,15 @@ struct WarpRKC {
 };
 
 // Register budget at 256 threads per block. OCC 0: 128 registers (no spills
-// for up to 4 vector slots; 16 resident warps per SM); OCC 1: 80 registers
-// for 2 or fewer slots (24 warps per SM; a few values spill to local memory),
-// 128 for 4 and 8 slots.
+// for up to 4 vector slots; 16 resident warps per SM); OCC 1: 64 registers
+// for 2 or fewer slots (32 warps per SM; some values spill to local memory),
+// 128 for 4 and 8 slots. The f evaluation of these mechanisms waits on L1 and
+// shared-memory round trips, and more resident warps hide more of that
+// latency: on 53 species / 634 reactions, mixed precision, 32 warps per SM
+// measured 195 K cells/s against 178 K at 24 (80 registers).
 template <int NR, int OCC>
 struct WarpBounds {
-    static constexpr int min_blocks = NR == 8 ? (OCC ? 2 : 1) : (OCC && NR <= 2 ? 3 : 2);
+    static constexpr int min_blocks = NR == 8 ? (OCC ? 2 : 1) : (OCC && NR <= 2 ? 4 : 2);
 };
 
 // Pre-pass, one warp per cell (grid-stride over cells): the cell's rate
