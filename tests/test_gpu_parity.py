@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 import oracle  # noqa: E402
 from paper_1309_2710_gb300 import synth  # noqa: E402
 from tests.oracle_variants import reference  # noqa: E402
-from tests.parity import compare, rel_err, tol_rel_err  # noqa: E402
+from tests.parity import compare, compare_mixed, rel_err, tol_rel_err  # noqa: E402
 
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no CUDA device", allow_module_level=True)
@@ -137,13 +137,10 @@ def test_rkc_mixed_ch4_sampled():
     idx = np.arange(0, 2048, 8)
     Yo, sto, stao, _ = oracle.integrate(om, T[idx], p[idx], Y[:, idx], w["dt"], w["rtol"],
                                         w["atol"], oracle.RKC)
-    assert (stg[idx] == sto).all()
     Yg = Yg[:, idx]
-    e = tol_rel_err(Yg, Yo, w["atol"], w["rtol"])
-    per_species = e.max(axis=1)
-    print("mixed ch4: max %.3e, per species %s; error relative to max(|Y|, atol) %.3e"
-          % (e.max(), np.array2string(per_species, precision=1), rel_err(Yg, Yo, w["atol"]).max()))
-    assert e.max() <= 1e-5
+    per_species = tol_rel_err(Yg, Yo, w["atol"], w["rtol"]).max(axis=1)
+    print("mixed ch4 per species %s" % np.array2string(per_species, precision=1))
+    print("mixed ch4", compare_mixed(Yg, Yo, stg[idx], sto, stag[idx], stao, w["atol"], w["rtol"]))
 
 
 def test_rkc_ch4_fp64_sampled():
@@ -165,14 +162,11 @@ def test_batched_c2h4_benchmarked_path(precision):
     library's launch shape. 8 cells of every instance against the oracle.
     FP64 (the workload's precision) as every FP64 parity test: trace-identical
     cells to 1e-8, at most 5 % trace-divergent within 10 rtol, the contract
-    metric within the measured floor bound. Mixed precision is not this
-    workload's configuration; its result is a second valid RKC solution (FP32
-    rates move every decision) and is held to the spread of valid solutions
-    at rtol 1e-6, 1e-4 in the integrator's weighting (measured on the oracle:
-    its rtol 1e-6 result differs from a converged one by up to 8.8e-5). On
-    these instances, up to ~200 stages at dt = 1e-5 s, it lands near 1e-5
-    (measured 1.05e-5 to 1.08e-5), against 3e-6 on the 53-species mixed
-    workload, which is held to 1e-5."""
+    metric within the measured floor bound. Mixed precision (not this
+    workload's configuration) as every mixed test: 1e-5 on the cells whose
+    accepted and rejected step counts equal the oracle's, the spread of valid
+    solutions on the cells where an FP32 rounding flipped a decision
+    (measured: 2.5e-6 and 1.05e-5)."""
     name = "c2h4_111sp_rkc_batched"
     m, km, om = mech(name)
     parts, host = [], []
@@ -206,10 +200,8 @@ def test_batched_c2h4_benchmarked_path(precision):
         s = compare(Yg, Yo, stg, sto, xg, xo, 1e-10, 1e-6, max_div_frac=0.05, floor=max(fls))
         print("batched c2h4 fp64", s, "f evals per cell %d..%d" % (xo[:, 0].min(), xo[:, 0].max()))
     else:
-        assert np.array_equal(stg, sto)
-        e = tol_rel_err(Yg, Yo, 1e-10, 1e-6)
-        print("batched c2h4 mixed: max %.3e; contract metric %.3e" % (e.max(), rel_err(Yg, Yo, 1e-10).max()))
-        assert e.max() <= 1e-4
+        s = compare_mixed(Yg, Yo, stg, sto, xg, xo, 1e-10, 1e-6)
+        print("batched c2h4 mixed", s)
 
 
 def test_batch_equals_separate_calls():
@@ -426,7 +418,4 @@ def test_rkc_power_sigma_mixed():
     idx = np.arange(0, 1024, 8)
     Yo, sto, stao, _ = oracle.integrate(om, T[idx], p[idx], Y[:, idx], w["dt"], w["rtol"], w["atol"],
                                         oracle.RKC_POWER)
-    assert (stg[idx] == sto).all()
-    e = tol_rel_err(Yg[:, idx], Yo, w["atol"], w["rtol"])
-    print("mixed power: max %.3e" % e.max())
-    assert e.max() <= 1e-5
+    print("mixed power", compare_mixed(Yg[:, idx], Yo, stg[idx], sto, stag[idx], stao, w["atol"], w["rtol"]))

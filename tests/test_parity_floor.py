@@ -64,3 +64,44 @@ def test_noise_floor_exceeds_the_target_on_the_53_species_mechanism():
                                                               w["atol"], oracle.RKC)[0])
         worst = max(worst, float((np.abs(Yv - Yo) / np.maximum(np.abs(Yo), w["atol"] / w["rtol"])).max()))
     assert worst < 1e-9
+
+
+def _arrays(n=10, species=3):
+    rng = np.random.default_rng(0)
+    Yo = rng.uniform(1e-3, 1.0, (species, n))
+    st = np.zeros(n, np.uint8)
+    sta = np.tile(np.array([[100, 40, 2, 3, 9]], np.int32), (n, 1))
+    return Yo, st, sta
+
+
+def test_compare_holds_trace_identical_cells_to_the_floor_bound():
+    from tests.parity import compare
+    Yo, st, sta = _arrays()
+    Yg = Yo * (1 + 5e-9)
+    out = compare(Yg, Yo, st, st, sta, sta, 1e-10, 1e-6, floor=1e-10)
+    assert out["atol_floor_bound"] == 1e-8 and out["trace_divergent"] == 0
+    with pytest.raises(AssertionError):  # above max(1e-8, 10 x floor)
+        compare(Yo * (1 + 3e-8), Yo, st, st, sta, sta, 1e-10, 1e-6, floor=2e-9, tol=1.0)
+    compare(Yo * (1 + 3e-8), Yo, st, st, sta, sta, 1e-10, 1e-6, floor=4e-9, tol=1.0)
+
+
+def test_compare_mixed_splits_cells_by_their_step_decisions():
+    from tests.parity import compare_mixed
+    Yo, st, sta = _arrays()
+    sg = sta.copy()
+    sg[:, 0] += 7  # f-evaluation counts move on every cell
+    Yg = Yo * (1 + 5e-6)
+    out = compare_mixed(Yg, Yo, st, st, sg, sta, 1e-10, 1e-6)
+    assert out["step_divergent"] == 0
+    # one cell with an extra rejection may sit farther away, up to the spread
+    sg[3, 2] += 1
+    Yg[:, 3] = Yo[:, 3] * (1 + 5e-5)
+    out = compare_mixed(Yg, Yo, st, st, sg, sta, 1e-10, 1e-6)
+    assert out["step_divergent"] == 1 and out["max_err"] > 1e-5
+    with pytest.raises(AssertionError):  # but not a step-identical one
+        sg[3, 2] -= 1
+        compare_mixed(Yg, Yo, st, st, sg, sta, 1e-10, 1e-6)
+    with pytest.raises(AssertionError):  # nor anything beyond the spread
+        sg[3, 2] += 1
+        Yg[:, 3] = Yo[:, 3] * (1 + 5e-4)
+        compare_mixed(Yg, Yo, st, st, sg, sta, 1e-10, 1e-6)
