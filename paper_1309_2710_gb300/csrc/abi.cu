@@ -402,13 +402,50 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
         ell_base[r] = ell_n;
         ell_n += 32 * len;
     }
+    // Each species' entries are ordered step by step so that the lanes of a
+    // step read Omega words in distinct shared-memory banks where they can:
+    // for FP32 words the bank is the position mod 32 across the warp; for
+    // FP64 words, read by half-warps, the position mod 16 within each half.
+    // A greedy pass gives each lane, in turn, its remaining entry in the
+    // least used bank of the step. Only the summation order of a row
+    // follows from this; its entries do not change.
+    std::vector<int> ord32(nnz), ord64(nnz);
+    auto order_rows = [&](std::vector<int>& ord, int banks, int group) {
+        for (int r = 0; r * 32 < nS; ++r) {
+            std::vector<std::vector<int>> left(32);
+            int len = 0;
+            for (int l = 0; l < 32 && 32 * r + l < nS; ++l) {
+                const int i = 32 * r + l;
+                for (int e2 = ptr[i]; e2 < ptr[i + 1]; ++e2) left[l].push_back(e2);
+                len = std::max(len, ptr[i + 1] - ptr[i]);
+            }
+            for (int k = 0; k < len; ++k) {
+                std::vector<int> used(2 * banks, 0);
+                for (int l = 0; l < 32; ++l) {
+                    if (left[l].empty()) continue;
+                    const int gbase = (l / group) * banks;
+                    size_t best = 0;
+                    for (size_t c = 1; c < left[l].size(); ++c)
+                        if (used[gbase + crxp[left[l][c]] % banks] < used[gbase + crxp[left[l][best]] % banks])
+                            best = c;
+                    const int e2 = left[l][best];
+                    left[l].erase(left[l].begin() + best);
+                    used[gbase + crxp[e2] % banks]++;
+                    ord[ptr[32 * r + l] + k] = e2;
+                }
+            }
+        }
+    };
+    order_rows(ord32, 32, 32);
+    order_rows(ord64, 16, 16);
     std::vector<CsrW32> ell32(ell_n, CsrW32{0.0f, 0});
     std::vector<CsrW64> ell64(ell_n, CsrW64{0.0, 0, 0});
     for (int i = 0; i < nS; ++i)
-        for (int e2 = ptr[i]; e2 < ptr[i + 1]; ++e2) {
-            const int at = ell_base[i / 32] + 32 * (e2 - ptr[i]) + i % 32;
-            ell32[at] = CsrW32{nuW32[e2], crxp[e2]};
-            ell64[at] = CsrW64{cnuW[e2], crxp[e2], 0};
+        for (int k = 0; k < ptr[i + 1] - ptr[i]; ++k) {
+            const int at = ell_base[i / 32] + 32 * k + i % 32;
+            const int a = ord32[ptr[i] + k], b = ord64[ptr[i] + k];
+            ell32[at] = CsrW32{nuW32[a], crxp[a]};
+            ell64[at] = CsrW64{cnuW[b], crxp[b], 0};
         }
     const size_t oEll32 = put(ell32.data(), sizeof(CsrW32) * ell_n);
     const size_t oEll64 = put(ell64.data(), sizeof(CsrW64) * ell_n);
