@@ -72,12 +72,16 @@ MUTANTS = [
      [pins.test_energy_species_part_is_the_isothermal_f_at_the_state_temperature]),
     ("sigma refreshed every 20 steps", "if (since_sigma >= 25 || (last_rejected && !sigma_here)) {",
      "if (since_sigma >= 20 || (last_rejected && !sigma_here)) {",
-     [pins.test_rkc_sigma_refresh_schedule]),
+     [lambda: pins.test_rkc_sigma_refresh_schedule(12.0, 1e-3)]),
     ("no sigma refresh after a rejection", "if (since_sigma >= 25 || (last_rejected && !sigma_here)) {",
      "if (since_sigma >= 25) {",
-     [pins.test_rkc_sigma_refresh_schedule]),
+     [lambda: pins.test_rkc_sigma_refresh_schedule(12.0, 1e-3)]),
     ("sigma age never reset", "            since_sigma = 0;\n", "",
-     [pins.test_rkc_sigma_refresh_schedule]),
+     [lambda: pins.test_rkc_sigma_refresh_schedule(12.0, 1e-3)]),
+    ("sigma re-estimated at the point just estimated",
+     "if (since_sigma >= 25 || (last_rejected && !sigma_here)) {",
+     "if (since_sigma >= 25 || last_rejected) {",
+     [lambda: pins.test_rkc_sigma_refresh_schedule(40.0, 1e-16)]),
     ("stage cap dropped",
      "            s = ORC_SMAX;\n            hh = ((ORC_SMAX - 1.0) * (ORC_SMAX - 1.0) - 1.0) / (1.54 * sigma);\n"
      "            last = 0;\n", "",

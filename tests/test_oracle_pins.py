@@ -534,7 +534,8 @@ def _sigma_schedule(accepted):
     return est
 
 
-def test_rkc_sigma_refresh_schedule():
+@pytest.mark.parametrize("kPdt,yb0", [(12.0, 1e-3), (40.0, 1e-16)])
+def test_rkc_sigma_refresh_schedule(kPdt, yb0):
     """A + B -> B + B, equal molar masses. With Y_A + Y_B = 1 the density is
     p W/(R T), dY_B/dt = k P Y_A Y_B with P = p/(R T) [mol/cm^3] (a logistic
     curve), and the Jacobian of f with each Y_k perturbed alone (the density
@@ -542,12 +543,21 @@ def test_rkc_sigma_refresh_schedule():
     sigma = k P (Y_A^2 + Y_B^2), which falls to half and rises again as B
     takes over. The spectral radius each attempt used must change exactly at
     the attempts the schedule names and equal the closed form at the exact
-    state of that moment; the counters must equal the hand count."""
-    k, T, p = 1e12, 1000.0, 1e5
+    state of that moment; the counters must equal the hand count.
+    k P dt = 12 from Y_B = 1e-3 refreshes for age and after rejections; k P dt
+    = 40 from Y_B = 1e-16 rejects the very first attempt (the initial-step
+    probe sees almost no change, and the first step spans an e^40 growth), so
+    no second estimate may follow at the same point. In that second case B
+    stays below atol for most of the step, where the error test does not
+    follow it, so the integrated state lags the exact curve: its estimates are
+    checked against the bounds k P / 2 <= sigma <= k P instead of the closed
+    form at the exact state."""
+    T, p = 1000.0, 1e5
     P = p * 1e-6 / (R_GAS * T)
+    dt, rtol, atol = 1e-6, 1e-6, 1e-10
+    k = kPdt / (P * dt)
     r = k * P
     om = oracle.Mech(_autocatalytic(k))
-    dt, rtol, atol, yb0 = 1e-6, 1e-6, 1e-10, 1e-3
     y, st, tr = oracle.trace_cell(om, T, p, np.array([1 - yb0, yb0]), dt, rtol, atol, method=oracle.RKC)
     assert st == 0
     acc, sig, h = tr["accepted"], tr["sigma"], tr["h"]
@@ -559,22 +569,31 @@ def test_rkc_sigma_refresh_schedule():
         else:
             assert sig[n] == sig[n - 1], n
     t = np.concatenate([[0.0], np.cumsum(np.where(acc, h, 0.0))])[:-1]  # start time of each attempt
+    follows_exact = kPdt < 20
     for i, n in enumerate(est):
-        yb = 1.0 / (1.0 + (1.0 / yb0 - 1.0) * math.exp(-r * t[n]))
-        exact = r * ((1.0 - yb) ** 2 + yb ** 2)
-        assert sig[n] == pytest.approx(exact, rel=1e-4, abs=0), n
+        if follows_exact:
+            yb = 1.0 / (1.0 + (1.0 / yb0 - 1.0) * math.exp(-r * t[n]))
+            exact = r * ((1.0 - yb) ** 2 + yb ** 2)
+            assert sig[n] == pytest.approx(exact, rel=1e-4, abs=0), n
+        else:
+            assert 0.5 * r * (1 - 1e-6) <= sig[n] <= r * (1 + 1e-6), n
         if i:
             since_counts.add(int(acc[est[i - 1]:n].sum()))
-    assert 25 in since_counts  # refreshed for age ...
-    assert any(c < 25 for c in since_counts)  # ... and after a rejection
-    assert sig.max() / sig.min() > 1.8  # sigma does move along the trajectory
+    assert any(c < 25 for c in since_counts)  # refreshed after a rejection
+    if follows_exact:
+        assert 25 in since_counts  # ... and for age
+        assert sig.max() / sig.min() > 1.8  # sigma does move along the trajectory
+    else:
+        assert not acc[0] and 1 not in est  # no second estimate at the same point
     nfe, nacc, nrej, nsig, nfs = tr["stats"]
     assert (nacc, nrej) == (int(acc.sum()), int((~acc).sum()))
     assert nsig == len(est)
     assert nfs == 2 * len(est)  # two Gershgorin columns per estimate
     # f(y0), the estimates, the initial-step probe, and s evaluations per attempt
     assert nfe == 1 + nfs + 1 + int(tr["s"].sum())
-    assert y[1] == pytest.approx(1.0 / (1.0 + (1.0 / yb0 - 1.0) * math.exp(-r * dt)), rel=1e-4)
+    if follows_exact:
+        assert y[1] == pytest.approx(1.0 / (1.0 + (1.0 / yb0 - 1.0) * math.exp(-r * dt)), rel=1e-4)
+    assert y[0] == pytest.approx(1.0 - y[1], abs=1e-12)
 
 
 def test_status_step_size_underflow():
