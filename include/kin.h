@@ -84,9 +84,10 @@ extern "C" {
                              reactions and species of f; the cell's concentrations and
                              rates of progress live in shared memory. staging is
                              ignored; for RKC, occupancy selects the register budget
-                             (KIN_OCC_HIGH: 64 registers for up to 64 state
-                             components, 32 warps per SM); block_threads may be up to
-                             256 */
+                             (KIN_OCC_HIGH: for up to 64 state components 64
+                             registers and 32 warps per SM, or 80 registers and 24
+                             warps with the energy equation); block_threads may be up
+                             to 256 */
 #define KIN_WARP_MIN_REACTIONS 256
 #define KIN_WARP_MAX_CELLS_PER_SM 64
 

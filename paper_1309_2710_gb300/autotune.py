@@ -100,7 +100,7 @@ def tune(mech: kin.Mechanism, desc, T, p, Y, dt, rtol, atol, method, precision,
     """Best launch shape for this mechanism on the current GPU, timed on the
     given (device) cells: pass the cells of a representative call, since the
     persistent grid's tail depends on the cell count."""
-    key = _key(mech, method, precision, desc) + "|%d|%d|%d|v3" % (int(T.numel()), sigma, energy)
+    key = _key(mech, method, precision, desc) + "|%d|%d|%d|v4" % (int(T.numel()), sigma, energy)
     cache = {}
     if use_cache and os.path.exists(CACHE):
         with open(CACHE) as f:

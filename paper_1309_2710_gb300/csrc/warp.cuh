@@ -580,22 +580,25 @@ struct WarpRKC {
 };
 
 // Register budget at 256 threads per block. OCC 0: 128 registers (no spills
-// for up to 4 vector slots; 16 resident warps per SM); OCC 1: 64 registers
-// for 2 or fewer slots (32 warps per SM; some values spill to local memory),
-// 128 for 4 and 8 slots. The f evaluation of these mechanisms waits on L1 and
-// shared-memory round trips, and more resident warps hide more of that
-// latency: on 53 species / 634 reactions, mixed precision, 32 warps per SM
-// measured 195 K cells/s against 178 K at 24 (80 registers).
-template <int NR, int OCC>
+// for up to 4 vector slots; 16 resident warps per SM); OCC 1, for 2 or fewer
+// slots: 64 registers (32 warps per SM; some values spill to local memory),
+// or 80 (24 warps) with the energy equation, whose f holds more live values;
+// 128 for 4 and 8 slots. The isothermal f evaluation of these mechanisms
+// waits on L1 and shared-memory round trips, and more resident warps hide
+// more of that latency: on 53 species / 634 reactions, mixed precision, 32
+// warps per SM measured 195 K cells/s against 178 K at 24 (80 registers).
+// With the energy equation the same shape measured 72.1 K against 74.1 K at
+// 80 registers.
+template <int NR, int OCC, bool EN>
 struct WarpBounds {
-    static constexpr int min_blocks = NR == 8 ? (OCC ? 2 : 1) : (OCC && NR <= 2 ? 4 : 2);
+    static constexpr int min_blocks = NR == 8 ? (OCC ? 2 : 1) : (OCC && NR <= 2 ? (EN ? 3 : 4) : 2);
 };
 
 // Pre-pass, one warp per cell (grid-stride over cells): the cell's rate
 // constants (stored cell-major for the main kernel), f(y0), sigma and the
 // initial step h1 (Section 2.3).
 template <typename R, int NR, int OCC, bool EN>
-__global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_init_kernel(const __grid_constant__ Launch L)
+__global__ void __launch_bounds__(256, WarpBounds<NR, OCC, EN>::min_blocks) warp_init_kernel(const __grid_constant__ Launch L)
 {
     WarpRKC<R, NR, EN> W(L);
     const MechDev& M = L.M;
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_ini
 // Persistent main kernel: each warp takes cells from the queue in the
 // longest-first order and integrates them one after another.
 template <typename R, int NR, int OCC, bool EN>
-__global__ void __launch_bounds__(256, WarpBounds<NR, OCC>::min_blocks) warp_integrate_kernel(const __grid_constant__ Launch L)
+__global__ void __launch_bounds__(256, WarpBounds<NR, OCC, EN>::min_blocks) warp_integrate_kernel(const __grid_constant__ Launch L)
 {
     WarpRKC<R, NR, EN> W(L);
     const MechDev& M = L.M;
