@@ -44,7 +44,7 @@ def warp_candidates(full: bool = False, method: int = kin.RKC):
     # the register budget is a choice of the RKC warp kernels only
     for occupancy in ((kin.OCC_DEFAULT, kin.OCC_HIGH) if method == kin.RKC else (kin.OCC_DEFAULT,)):
         for threads in ((64, 128, 256) if full else (128, 256)):
-            for warps in ((8, 12, 16, 24, 32) if full else (8, 16, 24, 32)):
+            for warps in ((8, 12, 16, 24, 32, 40) if full else (8, 16, 24, 32, 40)):
                 bps = warps * 32 // threads
                 if bps >= 1:
                     yield dict(block_threads=threads, blocks_per_sm=bps, staging=kin.STAGE_GLOBAL,
@@ -100,7 +100,7 @@ def tune(mech: kin.Mechanism, desc, T, p, Y, dt, rtol, atol, method, precision,
     """Best launch shape for this mechanism on the current GPU, timed on the
     given (device) cells: pass the cells of a representative call, since the
     persistent grid's tail depends on the cell count."""
-    key = _key(mech, method, precision, desc) + "|%d|%d|%d|v4" % (int(T.numel()), sigma, energy)
+    key = _key(mech, method, precision, desc) + "|%d|%d|%d|v5" % (int(T.numel()), sigma, energy)
     cache = {}
     if use_cache and os.path.exists(CACHE):
         with open(CACHE) as f:

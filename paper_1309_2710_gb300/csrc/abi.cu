@@ -13,6 +13,7 @@
 
 #include "codegen.h"
 #include "kin_dev.cuh"
+#include "seg_tables.h"
 
 using namespace kin;
 
@@ -371,17 +372,29 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     }
     std::vector<int> crxp(nnz);
     for (int e2 = 0; e2 < nnz; ++e2) crxp[e2] = pos[crx[e2]];
-    std::vector<double> effT((size_t)nM * nS);
-    std::vector<float> effT32((size_t)nM * nS);
+    std::vector<double> effV64((size_t)(nS + 1) / 2 * nM * 2, 0.0);
+    std::vector<float> effV32((size_t)(nS + 3) / 4 * nM * 4, 0.0f);
     for (int q = nPlain; q < nR; ++q)
         for (int k = 0; k < nS; ++k) {
             const double a = d->eff[(size_t)rxn[perm[q]].row * nS + k];
-            effT[(size_t)k * nM + (q - nPlain)] = a;
-            effT32[(size_t)k * nM + (q - nPlain)] = (float)a;
+            const int row = q - nPlain;
+            effV64[((size_t)(k / 2) * nM + row) * 2 + k % 2] = a;
+            effV32[((size_t)(k / 4) * nM + row) * 4 + k % 4] = (float)a;
         }
+    // the warp f derives a reaction's efficiency row and falloff ordinal from
+    // its permutation position
+    std::vector<uint32_t> rxw(nR);
+    for (int q = 0; q < nR; ++q) {
+        const Rxn& x = rxnp[q];
+        if ((x.type != KIN_RXN_PLAIN) != (q >= nPlain) || (x.type != KIN_RXN_PLAIN && x.row != q - nPlain) ||
+            (x.type == KIN_RXN_FALLOFF) != (q >= nR - nFO) || (x.type == KIN_RXN_FALLOFF && x.fo != q - (nR - nFO)))
+            return fail(KIN_EUNSUPPORTED, "reaction permutation out of order at %d", q);
+        rxw[q] = (uint32_t)(x.r0 + 1) | ((uint32_t)(x.r1 + 1) << 16);
+    }
     const size_t oPerm = put(perm.data(), 4 * nR), oRxp = put(rxnp.data(), sizeof(Rxn) * nR);
+    const size_t oRxw = put(rxw.data(), 4 * nR);
     const size_t oCrxp = put(crxp.data(), 4 * nnz);
-    const size_t oEffT = put(effT.data(), 8 * effT.size()), oEffT32 = put(effT32.data(), 4 * effT32.size());
+    const size_t oEffV64 = put(effV64.data(), 8 * effV64.size()), oEffV32 = put(effV32.data(), 4 * effV32.size());
     const size_t oPtr = put(ptr.data(), 4 * (nS + 1)), oCrx = put(crx.data(), 4 * nnz);
     const size_t oNu = put(cnu.data(), 8 * nnz), oNu32 = put(nu32.data(), 4 * nnz);
     // the species' molar mass folded into its row (a common factor of the row)
@@ -449,6 +462,16 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
         }
     const size_t oEll32 = put(ell32.data(), sizeof(CsrW32) * ell_n);
     const size_t oEll64 = put(ell64.data(), sizeof(CsrW64) * ell_n);
+    // the segmented FP32 gather of the 32-lane isothermal f, where the packed
+    // entries apply and its partial sums fit in the FP32 half of the warp's
+    // shared words, past C and Omega
+    SegTables seg;
+    const int group_floats = 2 * ((nS + nR + 3) & ~3);
+    const bool use_seg = build_seg_tables(nS, nR, ptr.data(), crxp.data(), cnu.data(), seg) &&
+                         nS + nR + seg.nslots <= group_floats;
+    const size_t oSegE = use_seg ? put(seg.ent.data(), 4 * seg.ent.size()) : 0;
+    const size_t oSegF = use_seg ? put(seg.slot0.data(), 4 * seg.slot0.size()) : 0;
+    const size_t oSegP = use_seg ? put(seg.part.data(), 4 * seg.part.size()) : 0;
     const size_t oEff = put(d->eff, 8 * (size_t)nM * nS), oEff32 = put(eff32.data(), 4 * (size_t)nM * nS);
     // thermochemistry for the energy equation: cp, cp/W, Hf
     const bool thermo = d->cp && d->Hf;
@@ -486,8 +509,13 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     M.ell32 = (const CsrW32*)(b + oEll32);
     M.ell64 = (const CsrW64*)(b + oEll64);
     for (int r = 0; r < ELL_SLOTS; ++r) M.ell_base[r] = ell_base[r];
-    M.effT = (const double*)(b + oEffT);
-    M.effT32 = (const float*)(b + oEffT32);
+    M.seg_ent = use_seg ? (const uint32_t*)(b + oSegE) : nullptr;
+    M.seg_slot0 = use_seg ? (const int32_t*)(b + oSegF) : nullptr;
+    M.seg_part = use_seg ? (const int32_t*)(b + oSegP) : nullptr;
+    M.seg_K = use_seg ? seg.K : 0;
+    M.effV64 = (const double*)(b + oEffV64);
+    M.effV32 = (const float*)(b + oEffV32);
+    M.rxw = (const uint32_t*)(b + oRxw);
     M.csr_ptr = (const int*)(b + oPtr); M.csr_rxn = (const int*)(b + oCrx);
     M.csr_nu = (const double*)(b + oNu); M.csr_nu32 = (const float*)(b + oNu32);
     M.csr_nuW = (const double*)(b + oNuW); M.csr_nuW32 = (const float*)(b + oNuW32);

@@ -66,8 +66,20 @@ struct MechDev {
     const CsrW32* ell32;
     const CsrW64* ell64;
     int ell_base[ELL_SLOTS];
-    const double* effT;    // [nS][nM] efficiencies, column = non-plain reaction in permutation order
-    const float* effT32;   // [nS][nM]
+    // The segmented FP32 gather of the 32-lane isothermal f (seg_tables.h):
+    // the nonzeros cut into 32 equal chunks of seg_K packed entries, one per
+    // lane. Null where the packed form does not apply (the ELL gather runs).
+    const uint32_t* seg_ent;   // [seg_K][32] nu's FP32 bits | flush flag | position
+    const int32_t* seg_slot0;  // [32] first partial slot of each lane
+    const int32_t* seg_part;   // [nS] first slot << 8 | slot count; -1: empty row
+    int seg_K;
+    // efficiencies by non-plain reaction in permutation order (row), species
+    // in 16-byte groups: [k / V][row][k % V], V = 2 (FP64) or 4 (FP32), the
+    // last group zero-padded
+    const double* effV64;
+    const float* effV32;
+    // reactants of each reaction in permutation order: (r0 + 1) | (r1 + 1) << 16
+    const uint32_t* rxw;
     const int* csr_ptr;    // [nS + 1] species -> entries
     const int* csr_rxn;    // [nnz] reaction of each entry (ascending per species)
     const double* csr_nu;  // [nnz] net coefficient nu'' - nu' of the species

@@ -25,6 +25,7 @@
 // kernel (Section 2.3 and the readings listed with it).
 #pragma once
 #include "kernels.cuh"
+#include "seg_tables.h"
 
 namespace kin {
 
@@ -62,17 +63,6 @@ __device__ __forceinline__ double warp_max(double v)
 }
 
 template <typename R>
-struct TabW;
-template <>
-struct TabW<double> {
-    __device__ static const double* effT(const MechDev& M) { return M.effT; }
-};
-template <>
-struct TabW<float> {
-    __device__ static const float* effT(const MechDev& M) { return M.effT32; }
-};
-
-template <typename R>
 struct EllT;
 template <>
 struct EllT<double> {
@@ -82,6 +72,55 @@ template <>
 struct EllT<float> {
     __device__ static const CsrW32* tab(const MechDev& M) { return M.ell32; }
 };
+
+// The third-body concentration of efficiency row `row`, [M] = sum_k eff_k C_k
+// (Eq. (E:rxn-rate)), summed as two interleaved partial sums (even k, odd k).
+// The rows are stored 16 bytes per species group, [k / V][row][k % V] with V =
+// 4 (FP32) or 2 (FP64), so that a lane reads V efficiencies with one load and
+// the warp's broadcast concentrations with another; lanes of a round take
+// consecutive rows, so a warp's efficiency load is one contiguous span.
+template <typename R>
+__device__ __forceinline__ R eff_dot(const MechDev& M, int row, const R* C);
+
+template <>
+__device__ __forceinline__ float eff_dot<float>(const MechDev& M, int row, const float* C)
+{
+    const int nS = M.nS, nM = M.nM, n4 = nS >> 2;
+    const float4* __restrict__ a = reinterpret_cast<const float4*>(M.effV32) + row;
+    const float4* c = reinterpret_cast<const float4*>(C);
+    float m0 = 0.0f, m1 = 0.0f;
+    for (int k = 0; k < n4; ++k) {
+        const float4 e = a[(int64_t)k * nM], x = c[k];
+        m0 += e.x * x.x;
+        m1 += e.y * x.y;
+        m0 += e.z * x.z;
+        m1 += e.w * x.w;
+    }
+    if (nS & 3) {
+        const float4 e = a[(int64_t)n4 * nM];
+        const int k = n4 << 2, t = nS & 3;
+        m0 += e.x * C[k];
+        if (t > 1) m1 += e.y * C[k + 1];
+        if (t > 2) m0 += e.z * C[k + 2];
+    }
+    return m0 + m1;
+}
+
+template <>
+__device__ __forceinline__ double eff_dot<double>(const MechDev& M, int row, const double* C)
+{
+    const int nS = M.nS, nM = M.nM, n2 = nS >> 1;
+    const double2* __restrict__ a = reinterpret_cast<const double2*>(M.effV64) + row;
+    const double2* c = reinterpret_cast<const double2*>(C);
+    double m0 = 0.0, m1 = 0.0;
+    for (int k = 0; k < n2; ++k) {
+        const double2 e = a[(int64_t)k * nM], x = c[k];
+        m0 += e.x * x.x;
+        m1 += e.y * x.y;
+    }
+    if (nS & 1) m0 += a[(int64_t)n2 * nM].x * C[nS - 1];
+    return m0 + m1;
+}
 
 // Shared words per warp: C [nS] and Omega [nR], padded to 4, sized for FP64
 // (the mixed-precision path evaluates f in FP32 for its RK stages and in FP64
@@ -146,39 +185,73 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
         if (i < nS) C[i] = C[i] * rho;
     }
     __syncwarp(mask);
-    const R* __restrict__ effT = TabW<R>::effT(M);
+    // permutation order: plain reactions, then third-body (efficiency row
+    // q - nP), then falloff (ordinal q - nF)
+    const int nP = nR - nM, nF = nR - M.nFO;
+    const uint32_t* __restrict__ rxw = M.rxw;
     for (int q = lane; q < nR; q += G) {
-        const Rxn rx = M.rxnp[q];
+        const uint32_t w = rxw[q];
         R v = (R)Kc[q];
-        if (rx.r0 >= 0) v *= C[rx.r0];
-        if (rx.r1 >= 0) v *= C[rx.r1];
-        if (rx.type != KIN_RXN_PLAIN) {
-            const R* a = effT + rx.row;
-            R m0 = R(0), m1 = R(0);
-            int k = 0;
-            for (; k + 1 < nS; k += 2) {
-                m0 += a[(int64_t)k * nM] * C[k];
-                m1 += a[(int64_t)(k + 1) * nM] * C[k + 1];
-            }
-            if (k < nS) m0 += a[(int64_t)k * nM] * C[k];
-            const R Mc = m0 + m1;
-            if (rx.type == KIN_RXN_THIRD_BODY) {
+        const int r0 = (int)(w & 0xffffu) - 1, r1 = (int)(w >> 16) - 1;
+        if (r0 >= 0) v *= C[r0];
+        if (r1 >= 0) v *= C[r1];
+        if (q >= nP) {
+            const R Mc = eff_dot<R>(M, q - nP, C);
+            if (q < nF) {
                 v *= Mc;
             } else {
-                const R Pr = (R)Kc[nR + rx.fo] * Mc;
+                const R Pr = (R)Kc[nR + (q - nF)] * Mc;
                 v *= Pr / (R(1) + Pr);
             }
         }
         OM[q] = v;
     }
     __syncwarp(mask);
+    const double invrho = (double)s * invCtot;
+    if constexpr (G == 32 && sizeof(R) == 4) {
+        if (M.seg_ent) {
+            // omega over equal chunks of the nonzeros (seg_tables.h); the
+            // partial sums land past Omega, in the FP32 half of the warp's
+            // words that only the FP64 evaluations use
+            float* P = reinterpret_cast<float*>(OM) + nR;
+            const uint32_t* __restrict__ ent = M.seg_ent + lane;
+            int slot = M.seg_slot0[lane];
+            float w = 0.0f;
+            const int K = M.seg_K;
+            for (int k = 0; k < K; ++k) {
+                const uint32_t e = ent[32 * k];
+                w = fmaf(__uint_as_float(e & SEG_NU_MASK), OM[e & SEG_POS_MASK], w);
+                if (e & SEG_FLUSH) {
+                    P[slot++] = w;
+                    w = 0.0f;
+                }
+            }
+            __syncwarp(mask);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int i = lane + 32 * r;
+                double o = 0.0;
+                if (i < nS) {
+                    const int pt = M.seg_part[i];
+                    if (pt >= 0) {
+                        const float* pp = P + (pt >> 8);
+                        float v = pp[0];
+                        for (int c = 1; c < (pt & 0xff); ++c) v += pp[c];
+                        o = (double)v * (M.W[i] * invrho);
+                    }
+                }
+                out[r] = o;
+            }
+            __syncwarp(mask);  // C, OM and P are rewritten by the next evaluation
+            return;
+        }
+    }
     // W_i omega_i over the species' row (W_i folded into its coefficients).
     // With 32 lanes per cell the row is read from the ELL copy, where the
     // lanes of a step read consecutive entries (one or two cache lines per
     // load instead of one line per lane); the entries and their order are
     // those of the species-major rows.
     const R* __restrict__ nuW = Tab<R>::nuW(M);
-    const double invrho = (double)s * invCtot;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int i = lane + G * r;
@@ -251,25 +324,19 @@ __device__ __forceinline__ void warp_feval_energy(const MechDev& M, double p, R*
         if (i < nS) C[i] = C[i] * rho;
     }
     __syncwarp(mask);
-    const R* __restrict__ effT = TabW<R>::effT(M);
+    const int nP = nR - nM, nF = nR - M.nFO;
+    const uint32_t* __restrict__ rxw = M.rxw;
     for (int q = lane; q < nR; q += G) {
-        const Rxn rx = M.rxnp[q];
+        const uint32_t w = rxw[q];
         const int j = M.rxn_perm[q];
         const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
         R v = Tab<R>::ex(a);
-        if (rx.r0 >= 0) v *= C[rx.r0];
-        if (rx.r1 >= 0) v *= C[rx.r1];
-        if (rx.type != KIN_RXN_PLAIN) {
-            const R* ea = effT + rx.row;
-            R m0 = R(0), m1 = R(0);
-            int k = 0;
-            for (; k + 1 < nS; k += 2) {
-                m0 += ea[(int64_t)k * nM] * C[k];
-                m1 += ea[(int64_t)(k + 1) * nM] * C[k + 1];
-            }
-            if (k < nS) m0 += ea[(int64_t)k * nM] * C[k];
-            const R Mc = m0 + m1;
-            if (rx.type == KIN_RXN_THIRD_BODY) {
+        const int r0 = (int)(w & 0xffffu) - 1, r1 = (int)(w >> 16) - 1;
+        if (r0 >= 0) v *= C[r0];
+        if (r1 >= 0) v *= C[r1];
+        if (q >= nP) {
+            const R Mc = eff_dot<R>(M, q - nP, C);
+            if (q < nF) {
                 v *= Mc;
             } else {
                 const double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
@@ -581,17 +648,18 @@ struct WarpRKC {
 
 // Register budget at 256 threads per block. OCC 0: 128 registers (no spills
 // for up to 4 vector slots; 16 resident warps per SM); OCC 1, for 2 or fewer
-// slots: 64 registers (32 warps per SM; some values spill to local memory),
-// or 80 (24 warps) with the energy equation, whose f holds more live values;
-// 128 for 4 and 8 slots. The isothermal f evaluation of these mechanisms
-// waits on L1 and shared-memory round trips, and more resident warps hide
-// more of that latency: on 53 species / 634 reactions, mixed precision, 32
-// warps per SM measured 195 K cells/s against 178 K at 24 (80 registers).
-// With the energy equation the same shape measured 72.1 K against 74.1 K at
-// 80 registers.
+// slots: 48 registers (40 warps per SM, about the most that the shared words
+// of a 53-species / 634-reaction cell leave room for; some values spill to
+// local memory), or 80 (24 warps) with the energy equation, whose f holds
+// more live values; 128 for 4 and 8 slots. The isothermal f evaluation of
+// these mechanisms waits on L1 and shared-memory round trips, and more
+// resident warps hide more of that latency: on 53 species / 634 reactions,
+// mixed precision, 198 K cells/s at 32 warps per SM (64 registers), 217 K at
+// 36 (56) and 237 K at 40 (48), against 178 K at 24 (80). With the energy
+// equation 74.1 K at 80 registers against 72.1 K at 64.
 template <int NR, int OCC, bool EN>
 struct WarpBounds {
-    static constexpr int min_blocks = NR == 8 ? (OCC ? 2 : 1) : (OCC && NR <= 2 ? (EN ? 3 : 4) : 2);
+    static constexpr int min_blocks = NR == 8 ? (OCC ? 2 : 1) : (OCC && NR <= 2 ? (EN ? 3 : 5) : 2);
 };
 
 // Pre-pass, one warp per cell (grid-stride over cells): the cell's rate
