@@ -87,11 +87,12 @@ HOST_ONLY = ("abi.cu", "no_alloc.cu", "peaks.cu")
 
 def kernel_hash() -> str:
     """Hash of the sources that define kernel code (device templates, their
-    instantiations and the generator of the run-time compiled f)."""
+    instantiations, the generator of the run-time compiled f, and the layout
+    of the warp f's gather tables)."""
     d = os.path.join(ROOT, "paper_1309_2710_gb300", "csrc")
     h = hashlib.sha1()
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")) and f not in HOST_ONLY:
+        if (f.endswith((".cu", ".cuh")) or f == "seg_tables.h") and f not in HOST_ONLY:
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
 

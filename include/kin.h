@@ -84,8 +84,8 @@ extern "C" {
                              reactions and species of f; the cell's concentrations and
                              rates of progress live in shared memory. staging is
                              ignored; for RKC, occupancy selects the register budget
-                             (KIN_OCC_HIGH: for up to 64 state components 64
-                             registers and 32 warps per SM, or 80 registers and 24
+                             (KIN_OCC_HIGH: for up to 64 state components 48
+                             registers and 40 warps per SM, or 80 registers and 24
                              warps with the energy equation); block_threads may be up
                              to 256 */
 #define KIN_WARP_MIN_REACTIONS 256
@@ -166,14 +166,15 @@ typedef struct {
     int32_t max_steps;     /* attempted steps per cell; <= 0 means 100000 */
     int32_t block_threads; /* threads per block, multiple of 32, <= 128 (<= 256 with
                               KIN_LAYOUT_WARP); 0 = library choice (128) */
-    int32_t blocks_per_sm; /* persistent blocks per SM; 0 = as many as fit (<= 512 threads per
-                              SM, 768 with KIN_OCC_HIGH) */
+    int32_t blocks_per_sm; /* persistent blocks per SM; 0 = as many as fit (lane layout:
+                              <= 512 threads per SM, 768 with KIN_OCC_HIGH) */
     int32_t staging;       /* KIN_STAGE_*: where f's per-lane arrays live. Shared staging
                               needs (n_species + n_reactions) [+ n_reactions + n_falloff
                               for SHARED_ALL] x block_threads elements of the rate type
                               per block; KIN_EUNSUPPORTED if that does not fit */
     int32_t occupancy;     /* KIN_OCC_DEFAULT: kernel built for up to 16 resident warps per
-                              SM; KIN_OCC_HIGH: built with a register cap for 24 */
+                              SM; KIN_OCC_HIGH: built with a register cap for 24 (the
+                              warp layout's caps are listed with KIN_LAYOUT_WARP) */
     int32_t sigma;         /* RKC spectral radius: KIN_SIGMA_GERSHGORIN (Gershgorin bound on a
                               finite-difference Jacobian, n_species f evaluations) or
                               KIN_SIGMA_POWER (nonlinear power method with warm start, the

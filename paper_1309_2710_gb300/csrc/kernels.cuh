@@ -375,6 +375,14 @@ constexpr double SIG_SQRT_U = 1.4901161193847656e-08;  // sqrt(2^-52)
 // over 4M log-uniform inputs on GB300 -> ~1e-12 after the step): enough for an
 // error norm and a step-size factor, which only need to reproduce the FP64
 // decisions. Outside the FP32 normal range the plain FP64 operation is used.
+// IEEE FP64 division and square root, and the FP64 power, kept out of line:
+// each library sequence is 2-9 KB of code, and one copy per kernel instead
+// of one per use keeps the hot loops' instructions in cache (the warp
+// layout's per-cell control has a dozen such uses). Same results as inline.
+static __device__ __noinline__ double ddiv(double a, double b) { return a / b; }
+static __device__ __noinline__ double dsqrt(double a) { return sqrt(a); }
+static __device__ __noinline__ double dpow(double a, double b) { return pow(a, b); }
+
 __device__ __forceinline__ bool f32_normal(double x)
 {
     const int e = (__double2hiint(x) >> 20) & 0x7ff;  // biased exponent (sign ignored)
@@ -385,7 +393,7 @@ __device__ __forceinline__ bool f32_normal(double x)
 // round trip, so no conversions on the FP64 pipe).
 __device__ __forceinline__ double rcp_newton(double x)
 {
-    if (!f32_normal(x)) return 1.0 / x;
+    if (!f32_normal(x)) return ddiv(1.0, x);
     double r0;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(x));
     return fma(r0, fma(-x, r0, 1.0), r0);
@@ -405,7 +413,7 @@ __device__ __forceinline__ double cbrt_newton(double a)
 // step, ample for a step-size factor).
 __device__ __forceinline__ double rpow5_newton(double x)
 {
-    if (!f32_normal(x)) return pow(x, -0.2);
+    if (!f32_normal(x)) return dpow(x, -0.2);
     const double y0 = (double)powf((float)x, -0.2f);
     const double y2 = y0 * y0;
     const double u = fma(-(x * y0), y2 * y2, 1.0);
@@ -415,7 +423,7 @@ __device__ __forceinline__ double rpow5_newton(double x)
 // x^(-1/6) for x > 0: the RKC controller's err^(-1/3) from x = err^2.
 __device__ __forceinline__ double rpow6_newton(double x)
 {
-    if (!f32_normal(x)) return pow(x, -1.0 / 6.0);
+    if (!f32_normal(x)) return dpow(x, -1.0 / 6.0);
     const double y0 = (double)powf((float)x, -1.0f / 6.0f);
     const double y2 = y0 * y0;
     const double u = fma(-(x * y2), y2 * y2, 1.0);
@@ -424,7 +432,7 @@ __device__ __forceinline__ double rpow6_newton(double x)
 
 __device__ __forceinline__ double rpow4_newton(double x)
 {
-    if (!f32_normal(x)) return pow(x, -0.25);
+    if (!f32_normal(x)) return dpow(x, -0.25);
     const double y0 = (double)powf((float)x, -0.25f);
     const double y2 = y0 * y0;
     const double u = fma(-(x * y2), y2, 1.0);

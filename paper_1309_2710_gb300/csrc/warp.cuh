@@ -189,6 +189,7 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
     // q - nP), then falloff (ordinal q - nF)
     const int nP = nR - nM, nF = nR - M.nFO;
     const uint32_t* __restrict__ rxw = M.rxw;
+#pragma unroll 1
     for (int q = lane; q < nR; q += G) {
         const uint32_t w = rxw[q];
         R v = (R)Kc[q];
@@ -445,38 +446,23 @@ struct WarpRKC {
         for (int r = 0; r < NR; ++r)
             if (valid(r)) {
                 const double sc = atol + rtol * fmax(fabs(a[r]), fabs(b[r]));
-                const double q = d[r] / sc;
+                const double q = ddiv(d[r], sc);
                 acc += q * q;
             }
-        return sqrt(warp_sum(acc) / nV);
+        return dsqrt(ddiv(warp_sum(acc), (double)nV));
     }
 
-    // Gershgorin bound on the finite-difference Jacobian at y (base = f(y) in FP64).
-    __device__ double gershgorin(const double (&base)[NR])
+    // FP64 f(y), the base of the spectral-radius differences: f0 in the FP64
+    // path; in the mixed-precision path w2, which the estimate evaluates first.
+    __device__ __forceinline__ double sig_base(int r) const
     {
-        double rs[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) rs[r] = 0.0;
-        for (int k = 0; k < nV; ++k) {
-            const int kr = k >> 5, kl = k & 31;
-            const double yk = __shfl_sync(0xffffffffu, reg_get(y, kr), kl);
-            const double eps = SIG_SQRT_U * fmax(fabs(yk), atol);
-#pragma unroll
-            for (int r = 0; r < NR; ++r) x[r] = (r == kr && lane == kl) ? yk + eps : y[r];
-            fs(x, fx);
-            const double ie = rcp_newton(eps);
-#pragma unroll
-            for (int r = 0; r < NR; ++r)
-                if (valid(r)) rs[r] += fabs((fx[r] - base[r]) * ie);
-        }
-        double m = 0.0;
-#pragma unroll
-        for (int r = 0; r < NR; ++r) m = fmax(m, rs[r]);
-        return warp_max(m);
+        if constexpr (sizeof(R) == 4) return w2[r];
+        else return f0[r];
     }
 
-    // Nonlinear power method warm-started from ev (see power_begin/power_post).
-    __device__ double power(const double (&base)[NR])
+    // Start of the nonlinear power method, warm-started from ev: scales ev to
+    // the difference length sqrt(u) |y| and returns that length.
+    __device__ double power_setup()
     {
         double yn = 0.0, vn = 0.0;
 #pragma unroll
@@ -484,57 +470,96 @@ struct WarpRKC {
             yn += y[r] * y[r];
             vn += ev[r] * ev[r];
         }
-        yn = sqrt(warp_sum(yn));
-        vn = sqrt(warp_sum(vn));
+        yn = dsqrt(warp_sum(yn));
+        vn = dsqrt(warp_sum(vn));
         const double dyn = yn > 0.0 ? SIG_SQRT_U * yn : SIG_SQRT_U;
         if (!(vn > 0.0) || !isfinite(vn)) {
 #pragma unroll
             for (int r = 0; r < NR; ++r) ev[r] = valid(r) ? 1.0 : 0.0;
-            vn = sqrt((double)nV);
+            vn = dsqrt((double)nV);
         }
-        const double sc0 = dyn / vn;
+        const double sc0 = ddiv(dyn, vn);
 #pragma unroll
         for (int r = 0; r < NR; ++r) ev[r] = ev[r] * sc0;
-        double sig = 0.0, prev = 0.0;
-        for (int k = 1; k <= 20; ++k) {
-#pragma unroll
-            for (int r = 0; r < NR; ++r) x[r] = y[r] + ev[r];
-            fs(x, fx);
-            double wn = 0.0;
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                fx[r] = fx[r] - base[r];
-                wn += fx[r] * fx[r];
-            }
-            wn = sqrt(warp_sum(wn));
-            sig = wn / dyn;
-            if (!(wn > 0.0) || !isfinite(wn)) break;
-            const double sc = dyn / wn;
-#pragma unroll
-            for (int r = 0; r < NR; ++r) ev[r] = fx[r] * sc;
-            if (k >= 2 && fabs(sig - prev) <= 0.01 * sig) break;
-            prev = sig;
-        }
-        return 1.2 * sig;
+        return dyn;
     }
 
-    // Spectral radius at y. The mixed-precision path first re-evaluates f(y)
-    // in FP64 into w2 (free between steps). `first` starts the power method
-    // from f(y).
+    // Spectral radius at y: the Gershgorin bound on the finite-difference
+    // Jacobian (one column per evaluation) or the nonlinear power method
+    // warm-started from ev (at most 20 products, stopping when two estimates
+    // agree to 1 %; returns 1.2 times the last), Section 2.3. The mixed-
+    // precision path first re-evaluates f(y) in FP64 into w2. `first` starts
+    // the power method from f(y). Every FP64 evaluation of the estimate goes
+    // through the one call of fs below, so the kernel holds one inlined copy
+    // of the FP64 f.
     __device__ double sigma(bool first)
     {
-        if constexpr (sizeof(R) == 4) {
-            fs(y, w2);
-            if (first)
+        constexpr bool MIX = sizeof(R) == 4;
+        const bool pw = L.sigma_method == KIN_SIGMA_POWER;
+        double rs[NR];
 #pragma unroll
-                for (int r = 0; r < NR; ++r) ev[r] = w2[r];
-            return L.sigma_method == KIN_SIGMA_POWER ? power(w2) : gershgorin(w2);
-        } else {
+        for (int r = 0; r < NR; ++r) rs[r] = 0.0;
+        double dyn = 0.0, sig = 0.0, prev = 0.0, eps = 0.0;
+        if constexpr (!MIX) {
             if (first)
 #pragma unroll
                 for (int r = 0; r < NR; ++r) ev[r] = f0[r];
-            return L.sigma_method == KIN_SIGMA_POWER ? power(f0) : gershgorin(f0);
+            if (pw) dyn = power_setup();
         }
+        for (int k = MIX ? -1 : 0;; ++k) {  // k = -1: the base f(y)
+            if (k < 0) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) x[r] = y[r];
+            } else if (pw) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) x[r] = y[r] + ev[r];
+            } else {  // Gershgorin column k
+                const int kr = k >> 5, kl = k & 31;
+                const double yk = __shfl_sync(0xffffffffu, reg_get(y, kr), kl);
+                eps = SIG_SQRT_U * fmax(fabs(yk), atol);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) x[r] = (r == kr && lane == kl) ? yk + eps : y[r];
+            }
+            fs(x, fx);
+            if (k < 0) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) w2[r] = fx[r];
+                if (first)
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) ev[r] = w2[r];
+                if (pw) dyn = power_setup();
+                continue;
+            }
+            if (pw) {
+                double wn = 0.0;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    fx[r] = fx[r] - sig_base(r);
+                    wn += fx[r] * fx[r];
+                }
+                wn = dsqrt(warp_sum(wn));
+                sig = ddiv(wn, dyn);
+                if (!(wn > 0.0) || !isfinite(wn)) break;
+                const double sc = ddiv(dyn, wn);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) ev[r] = fx[r] * sc;
+                if (k >= 1 && fabs(sig - prev) <= 0.01 * sig) break;
+                prev = sig;
+                if (k + 1 >= 20) break;
+            } else {
+                const double ie = rcp_newton(eps);
+#pragma unroll
+                for (int r = 0; r < NR; ++r)
+                    if (valid(r)) rs[r] += fabs((fx[r] - sig_base(r)) * ie);
+                if (k + 1 >= nV) {
+                    double m = 0.0;
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) m = fmax(m, rs[r]);
+                    return warp_max(m);
+                }
+            }
+        }
+        return 1.2 * sig;
     }
 
     __device__ __forceinline__ const double* coef(int s, int j) const
@@ -549,7 +574,7 @@ struct WarpRKC {
         double t = 0.0, hprev = 0.0, cprev = 0.0;
         int attempts = 0, since = 0;
         bool sigma_here = true, last_rej = false, have_prev = false;
-        const double invN = 1.0 / nV;
+        const double invN = ddiv(1.0, (double)nV);
         for (;;) {
             if (attempts >= L.max_steps) return KIN_CELL_MAXSTEPS;
             if (since >= 25 || (last_rej && !sigma_here)) {
@@ -565,13 +590,13 @@ struct WarpRKC {
                 hh = dt - t;
                 last = true;
             }
-            const double sr = floor(1.0 + sqrt(1.0 + 1.54 * hh * sig));
+            const double sr = floor(1.0 + dsqrt(1.0 + 1.54 * hh * sig));
             int s;
             if (sr < 2.0) {
                 s = 2;
             } else if (sr > (double)SMAX) {
                 s = SMAX;
-                hh = ((SMAX - 1.0) * (SMAX - 1.0) - 1.0) / (1.54 * sig);
+                hh = ddiv((SMAX - 1.0) * (SMAX - 1.0) - 1.0, 1.54 * sig);
                 last = false;
             } else {
                 s = (int)sr;
@@ -583,8 +608,9 @@ struct WarpRKC {
                 w2[r] = y[r];
                 w1[r] = y[r] + m1 * f0[r];
             }
-            for (int j = 2; j <= s; ++j) {
-                f(w1, fx);
+            for (int j = 2;; ++j) {
+                f(w1, fx);  // f(w_{j-1}); after the last stage, f(w_s)
+                if (j > s) break;
                 const double* c = coef(s, j);
                 const double mu = c[0], nu = c[1], mt = c[2] * hh, gt = c[3] * hh, c0 = c[4];
 #pragma unroll
@@ -594,7 +620,6 @@ struct WarpRKC {
                     w1[r] = wn;
                 }
             }
-            f(w1, fx);  // f(w_s)
             attempts++;
             double acc = 0.0;
 #pragma unroll
@@ -606,14 +631,16 @@ struct WarpRKC {
                     acc += q * q;
                 }
             // x = ||Delta||^2; z = x^(-1/6) = err^(-1/3) (see the lane kernel)
+            // (one evaluation of the power serves both branches)
             const double xe = warp_sum(acc) * invN;
+            const double z = (xe > 0.0 && isfinite(xe)) ? rpow6_newton(xe) : 0.0;
             if (xe <= 1.0) {
                 nacc++;
                 double fac, c3 = 0.0;
                 if (xe == 0.0) {
                     fac = 10.0;
                 } else {
-                    const double z = rpow6_newton(xe), z2 = z * z;
+                    const double z2 = z * z;
                     c3 = xe * (z2 * z2 * z);
                     if (have_prev && !last_rej && cprev > 0.0)
                         fac = 0.8 * hh * cprev * z2 * rcp_newton(hprev);
@@ -636,7 +663,7 @@ struct WarpRKC {
                 h = fac * hh;
             } else {
                 nrej++;
-                double fac = isfinite(xe) ? 0.8 * rpow6_newton(xe) : 0.1;
+                double fac = isfinite(xe) ? 0.8 * z : 0.1;
                 if (fac < 0.1) fac = 0.1;
                 last_rej = true;
                 h = fac * hh;
@@ -677,8 +704,8 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC, EN>::min_blocks) warp
         const InstDev& I = L.inst[ii];
         const int64_t c = g - L.start[ii];
         const double T = I.T[c], p = I.p[c];
-        W.Ctot = p * 1e-6 / (R_GAS * T);
-        W.invCtot = 1.0 / W.Ctot;
+        W.Ctot = ddiv(p * 1e-6, R_GAS * T);
+        W.invCtot = ddiv(1.0, W.Ctot);
         W.atol = I.atol;
         W.rtol = I.rtol;
         W.p = p;
@@ -726,7 +753,7 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC, EN>::min_blocks) warp
             if (!isfinite(sig)) {
                 st = KIN_CELL_NONFINITE;
             } else {
-                double h0 = sig > 0.0 ? 1.0 / sig : I.dt;
+                double h0 = sig > 0.0 ? ddiv(1.0, sig) : I.dt;
                 if (h0 > I.dt) h0 = I.dt;
 #pragma unroll
                 for (int r = 0; r < NR; ++r) W.x[r] = W.y[r] + h0 * W.f0[r];
@@ -735,7 +762,7 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC, EN>::min_blocks) warp
                 for (int r = 0; r < NR; ++r) W.x[r] = h0 * (W.fx[r] - W.f0[r]);  // Delta_0
                 const double e0 = W.rms(W.x, W.y, W.y);
                 if (!isfinite(e0)) h = 0.1 * h0;
-                else h = e0 > 0.0 ? 0.1 * h0 / sqrt(e0) : I.dt;
+                else h = e0 > 0.0 ? ddiv(0.1 * h0, dsqrt(e0)) : I.dt;
                 if (h > I.dt) h = I.dt;
                 if (h < 1e-20 * I.dt) st = KIN_CELL_HMIN;
             }
@@ -782,8 +809,8 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC, EN>::min_blocks) warp
             code = pre;  // decided by the pre-pass; Y stays as given
         } else {
             const double T = I.T[c], p = I.p[c];
-            W.Ctot = p * 1e-6 / (R_GAS * T);
-            W.invCtot = 1.0 / W.Ctot;
+            W.Ctot = ddiv(p * 1e-6, R_GAS * T);
+            W.invCtot = ddiv(1.0, W.Ctot);
             W.atol = I.atol;
             W.rtol = I.rtol;
             W.p = p;
@@ -971,8 +998,8 @@ __global__ void __launch_bounds__(256, NR == 8 ? 1 : 2) warp_rkck_kernel(const _
         const InstDev& I = L.inst[ii];
         const int64_t c = g - L.start[ii];
         const double T = I.T[c], p = I.p[c];
-        W.Ctot = p * 1e-6 / (R_GAS * T);
-        W.invCtot = 1.0 / W.Ctot;
+        W.Ctot = ddiv(p * 1e-6, R_GAS * T);
+        W.invCtot = ddiv(1.0, W.Ctot);
         W.atol = I.atol;
         W.rtol = I.rtol;
         W.p = p;
