@@ -345,14 +345,16 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
         return off;
     };
     std::vector<double> invW(nS);
-    std::vector<float> invW32(nS), nu32(cnu.begin(), cnu.end());
+    std::vector<float> invW32(nS), W32(nS), nu32(cnu.begin(), cnu.end());
     for (int i = 0; i < nS; ++i) {
         invW[i] = 1.0 / d->W[i];
         invW32[i] = (float)invW[i];
+        W32[i] = (float)d->W[i];
     }
     std::vector<float> eff32((size_t)nM * nS);
     for (size_t k = 0; k < eff32.size(); ++k) eff32[k] = (float)d->eff[k];
     const size_t oW = put(d->W, 8 * nS), oIW = put(invW.data(), 8 * nS), oIW32 = put(invW32.data(), 4 * nS);
+    const size_t oW32 = put(W32.data(), 4 * nS);
     const size_t oLA = put(d->lnA, 8 * nR), oB = put(d->beta, 8 * nR), oE = put(EaR.data(), 8 * nR);
     const size_t oLA0 = put(lnA0.data(), 8 * nR), oB0 = put(beta0.data(), 8 * nR), oE0 = put(Ea0R.data(), 8 * nR);
     const size_t oRx = put(rxn.data(), sizeof(Rxn) * nR);
@@ -500,6 +502,7 @@ int kin_create_mechanism(const kin_mech_desc* d, kin_mech** out)
     MechDev& M = m->dev;
     M.nS = nS; M.nR = nR; M.nM = nM; M.nFO = nFO; M.nnz = nnz;
     M.W = (const double*)(b + oW); M.invW = (const double*)(b + oIW); M.invW32 = (const float*)(b + oIW32);
+    M.W32 = (const float*)(b + oW32);
     M.lnA = (const double*)(b + oLA); M.beta = (const double*)(b + oB); M.EaR = (const double*)(b + oE);
     M.lnA0 = (const double*)(b + oLA0); M.beta0 = (const double*)(b + oB0); M.Ea0R = (const double*)(b + oE0);
     M.rxn = (const Rxn*)(b + oRx);

@@ -151,8 +151,8 @@ void emit_body(std::string& s, const kin_mech_desc* d, bool energy)
     const int nS = d->n_species, nR = d->n_reactions;
     if (energy) {
         appendf(s, "        const double T = x[%d];\n", nS);
-        s += "        const double lnT = log(T), invT = 1.0 / T;\n"
-             "        const double Ctot = p * 1e-6 * invT * (1.0 / R_GAS), invCtot = 1.0 / Ctot;\n";
+        s += "        const double lnT = log(T), invT = ddiv(1.0, T);\n"
+             "        const double Ctot = p * 1e-6 * invT * (1.0 / R_GAS), invCtot = ddiv(1.0, Ctot);\n";
     }
     // mixture: m_k = Y_k / W_k, S = sum m_k (two partial sums), rho = Ctot / S
     for (int i = 0; i < nS; ++i) appendf(s, "        const double m%d = x[%d] * %s;\n", i, i, lit(1.0 / d->W[i]).c_str());
@@ -231,7 +231,7 @@ void emit_body(std::string& s, const kin_mech_desc* d, bool energy)
                             exponent(d->lnA0[j], d->beta0[j], d->Ea0[j]).c_str());
                 else
                     appendf(s, "            const double Pr = KR[%d] * Mc;\n", fo);
-                s += "            q *= Pr / (1.0 + Pr);\n";
+                s += "            q *= ddiv(Pr, 1.0 + Pr);\n";
                 ++fo;
             }
             ++row;
@@ -256,7 +256,7 @@ void emit_body(std::string& s, const kin_mech_desc* d, bool energy)
                         cpW.c_str(), i);
             appendf(s, "        cpm = fma(x[%d], %s, cpm);\n", i, cpW.c_str());
         }
-        appendf(s, "        out[%d] = -hw * invrho / cpm;\n", nS);
+        appendf(s, "        out[%d] = ddiv(-hw * invrho, cpm);\n", nS);
     }
 }
 

@@ -29,6 +29,12 @@
 //    (state, stage accumulation, norm and control stay double).
 //  * No tensor cores: the stoichiometric contraction is sparse (about four
 //    nonzeros per reaction).
+//  * Code size: the integrator's loops over the state vector are not
+//    unrolled (#pragma unroll 1) and the FP64 division, square root and power
+//    are called out of line. A lane kernel holds every phase of the method,
+//    and unrolled copies of some thirty short loops had made it 150 KB of
+//    instructions; a smaller kernel waits less on instruction fetch (13
+//    species: 2.105 M against 2.093 M cells/s).
 #pragma once
 #ifndef __CUDACC_RTC__  // run-time compilation (generated f) brings its own definitions
 #include <cuda_runtime.h>
@@ -40,6 +46,22 @@
 #include "kin_dev.cuh"
 
 namespace kin {
+
+// IEEE FP64 division and square root, and the FP64 power, kept out of line:
+// each library sequence is 2-9 KB of code, and one copy per kernel instead
+// of one per use keeps the hot loops' instructions in cache (the warp
+// layout's per-cell control has a dozen such uses). Same results as inline.
+static __device__ __noinline__ double ddiv(double a, double b) { return a / b; }
+static __device__ __noinline__ double dsqrt(double a) { return sqrt(a); }
+static __device__ __noinline__ double dpow(double a, double b) { return pow(a, b); }
+// a / b in the rate type: the FP64 division out of line, FP32 inline.
+template <typename R>
+__device__ __forceinline__ R rdiv(R a, R b)
+{
+    if constexpr (sizeof(R) == 8) return ddiv(a, b);
+    else return a / b;
+}
+
 
 // ---------------------------------------------------------------- helpers --
 template <typename T>
@@ -86,7 +108,7 @@ struct Tab<float> {
 template <typename R>
 __device__ void rate_constants(const MechDev& M, double T, Lane<R> K, Lane<R> KR)
 {
-    const double lnT = log(T), invT = 1.0 / T;
+    const double lnT = log(T), invT = ddiv(1.0, T);
     for (int j = 0; j < M.nR; ++j) {
         const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
         K[j] = Tab<R>::ex(a);
@@ -150,7 +172,7 @@ __device__ void feval(const MechDev& M, double Ctot, double invCtot, Lane<KT> K,
                 q *= Mc;
             } else {
                 const R Pr = (R)KR[r.fo] * Mc;
-                q *= Pr / (R(1) + Pr);
+                q *= rdiv<R>(Pr, R(1) + Pr);
             }
         }
         OM[j] = q;
@@ -183,8 +205,8 @@ __device__ void feval_energy(const MechDev& M, double p, Lane<R> C, Lane<R> OM, 
 {
     const int nS = M.nS, nR = M.nR;
     const double T = x[nS];
-    const double lnT = log(T), invT = 1.0 / T;
-    const double Ctot = p * 1e-6 * invT * (1.0 / R_GAS), invCtot = 1.0 / Ctot;
+    const double lnT = log(T), invT = ddiv(1.0, T);
+    const double Ctot = p * 1e-6 * invT * (1.0 / R_GAS), invCtot = ddiv(1.0, Ctot);
     const R* __restrict__ invW = Tab<R>::invW(M);
     R S0 = R(0), S1 = R(0);
     int i = 0;
@@ -226,7 +248,7 @@ __device__ void feval_energy(const MechDev& M, double p, Lane<R> C, Lane<R> OM, 
             } else {
                 const double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
                 const R Pr = Tab<R>::ex(a0 - a) * Mc;
-                q *= Pr / (R(1) + Pr);
+                q *= rdiv<R>(Pr, R(1) + Pr);
             }
         }
         OM[j] = q;
@@ -249,7 +271,7 @@ __device__ void feval_energy(const MechDev& M, double p, Lane<R> C, Lane<R> OM, 
         hw += (M.Hf[sp] + M.cp[sp] * dT) * om;
         cpm += x[sp] * M.cpW[sp];
     }
-    out[nS] = -hw * invrho / cpm;
+    out[nS] = ddiv(-hw * invrho, cpm);
 }
 
 __device__ __forceinline__ int find_inst(const Launch& L, long long g)
@@ -345,12 +367,13 @@ __device__ __forceinline__ double rms(int n, double rtol, double atol, Lane<doub
                                       Lane<double> a, Lane<double> b)
 {
     double acc = 0.0;
+#pragma unroll 1
     for (int i = 0; i < n; ++i) {
         const double sc = atol + rtol * fmax(fabs(a[i]), fabs(b[i]));
-        const double r = d[i] / sc;
+        const double r = ddiv(d[i], sc);
         acc += r * r;
     }
-    return sqrt(acc / n);
+    return dsqrt(ddiv(acc, (double)n));
 }
 
 // ------------------------------------------------- power-method sigma ---
@@ -375,14 +398,6 @@ constexpr double SIG_SQRT_U = 1.4901161193847656e-08;  // sqrt(2^-52)
 // over 4M log-uniform inputs on GB300 -> ~1e-12 after the step): enough for an
 // error norm and a step-size factor, which only need to reproduce the FP64
 // decisions. Outside the FP32 normal range the plain FP64 operation is used.
-// IEEE FP64 division and square root, and the FP64 power, kept out of line:
-// each library sequence is 2-9 KB of code, and one copy per kernel instead
-// of one per use keeps the hot loops' instructions in cache (the warp
-// layout's per-cell control has a dozen such uses). Same results as inline.
-static __device__ __noinline__ double ddiv(double a, double b) { return a / b; }
-static __device__ __noinline__ double dsqrt(double a) { return sqrt(a); }
-static __device__ __noinline__ double dpow(double a, double b) { return pow(a, b); }
-
 __device__ __forceinline__ bool f32_normal(double x)
 {
     const int e = (__double2hiint(x) >> 20) & 0x7ff;  // biased exponent (sign ignored)
@@ -456,18 +471,21 @@ __device__ __forceinline__ void power_begin(int nS, Lane<double> Y, Lane<double>
                                             PowerState& P)
 {
     double yn = 0.0, vn = 0.0;
+#pragma unroll 1
     for (int i = 0; i < nS; ++i) {
         yn += Y[i] * Y[i];
         vn += EV[i] * EV[i];
     }
-    yn = sqrt(yn);
+    yn = dsqrt(yn);
     P.dyn = yn > 0.0 ? SIG_SQRT_U * yn : SIG_SQRT_U;
-    vn = sqrt(vn);
+    vn = dsqrt(vn);
     if (!(vn > 0.0) || !isfinite(vn)) {
+#pragma unroll 1
         for (int i = 0; i < nS; ++i) EV[i] = 1.0;
-        vn = sqrt((double)nS);
+        vn = dsqrt((double)nS);
     }
-    const double sc = P.dyn / vn;
+    const double sc = ddiv(P.dyn, vn);
+#pragma unroll 1
     for (int i = 0; i < nS; ++i) {
         EV[i] = EV[i] * sc;
         X[i] = Y[i] + EV[i];
@@ -484,19 +502,22 @@ __device__ __forceinline__ bool power_post(int nS, Lane<double> Y, Lane<double> 
                            Lane<double> X, Lane<double> FX, PowerState& P)
 {
     double wn = 0.0;
+#pragma unroll 1
     for (int i = 0; i < nS; ++i) {
         const double w = FX[i] - F0[i];
         FX[i] = w;
         wn += w * w;
     }
-    wn = sqrt(wn);
-    P.sig = wn / P.dyn;
+    wn = dsqrt(wn);
+    P.sig = ddiv(wn, P.dyn);
     if (!(wn > 0.0) || !isfinite(wn)) return true;
-    const double sc = P.dyn / wn;
+    const double sc = ddiv(P.dyn, wn);
+#pragma unroll 1
     for (int i = 0; i < nS; ++i) EV[i] = FX[i] * sc;
     if (P.k >= 2 && fabs(P.sig - P.prev) <= 0.01 * P.sig) return true;
     P.prev = P.sig;
     if (++P.k > 20) return true;
+#pragma unroll 1
     for (int i = 0; i < nS; ++i) X[i] = Y[i] + EV[i];
     return false;
 }
@@ -553,7 +574,7 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
         const InstDev& I = L.inst[ii];
         const int64_t c = g - L.start[ii];
         const double T = I.T[c], p = I.p[c];
-        const double Ctot = p * 1e-6 / (R_GAS * T), invCtot = 1.0 / Ctot;
+        const double Ctot = ddiv(p * 1e-6, R_GAS * T), invCtot = ddiv(1.0, Ctot);
         Lane<R> K = W.K(g), KR = W.KR(g);
         if constexpr (!EN) rate_constants<R>(M, T, K, KR);
         // f in the rate type, and f in FP64 for the spectral radius
@@ -571,6 +592,7 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
         };
         Lane<double> Y = W.V(V_Y), F0 = W.F0cell(g), X = W.V(V_X), FX = W.V(V_FX), RS = W.V(V_RS);
         bool ok = true;
+#pragma unroll 1
         for (int i = 0; i < n; ++i) {
             const double y = i < nS ? I.Y[(int64_t)i * I.ldY + c] : T;
             Y[i] = y;
@@ -578,6 +600,7 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
             RS[i] = 0.0;
         }
         frate(Y, F0);
+#pragma unroll 1
         for (int i = 0; i < n; ++i) ok &= isfinite(F0[i]);
         uint8_t st = ok ? 0 : KIN_CELL_NONFINITE;
         double sigma = 0.0, h = I.dt;
@@ -593,6 +616,7 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
         }
         if (METHOD == KIN_RKC && ok && L.sigma_method == KIN_SIGMA_POWER) {
             Lane<double> EV = W.EVcell(g);
+#pragma unroll 1
             for (int i = 0; i < n; ++i) EV[i] = B[i];  // first direction: f(y0)
             PowerState P;
             power_begin(n, Y, EV, X, P);
@@ -604,14 +628,17 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
             }
             sigma = 1.2 * P.sig;
         } else if (METHOD == KIN_RKC && ok) {
+#pragma unroll 1
             for (int k = 0; k < n; ++k) {  // Gershgorin columns
                 const double eps = SIG_SQRT_U * fmax(fabs(Y[k]), I.atol);
                 X[k] = Y[k] + eps;
                 fsig(X, FX);
-                const double ie = 1.0 / eps;
+                const double ie = ddiv(1.0, eps);
+#pragma unroll 1
                 for (int i = 0; i < n; ++i) RS[i] += fabs((FX[i] - B[i]) * ie);
                 X[k] = Y[k];
             }
+#pragma unroll 1
             for (int i = 0; i < n; ++i) sigma = fmax(sigma, RS[i]);
             nfe += n;
             nfs += n;
@@ -620,15 +647,17 @@ __global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ Launc
             if (!isfinite(sigma)) {
                 st = KIN_CELL_NONFINITE;
             } else {
-                double h0 = sigma > 0.0 ? 1.0 / sigma : I.dt;
+                double h0 = sigma > 0.0 ? ddiv(1.0, sigma) : I.dt;
                 if (h0 > I.dt) h0 = I.dt;
+#pragma unroll 1
                 for (int i = 0; i < n; ++i) X[i] = Y[i] + h0 * F0[i];
                 frate(X, FX);
                 nfe++;
+#pragma unroll 1
                 for (int i = 0; i < n; ++i) X[i] = h0 * (FX[i] - F0[i]);  // Delta_0
                 const double e0 = rms(n, I.rtol, I.atol, X, Y, Y);
                 if (!isfinite(e0)) h = 0.1 * h0;
-                else h = e0 > 0.0 ? 0.1 * h0 / sqrt(e0) : I.dt;
+                else h = e0 > 0.0 ? ddiv(0.1 * h0, dsqrt(e0)) : I.dt;
                 if (h > I.dt) h = I.dt;
                 if (h < 1e-20 * I.dt) st = KIN_CELL_HMIN;
             }
@@ -648,7 +677,7 @@ __device__ __forceinline__ int cost_bucket(const Launch& L, int64_t g)
 {
     if (L.cell_st[g] != 0) return 0;
     const int ii = find_inst(L, g);
-    const double r = L.inst[ii].dt / L.cell_h[g];
+    const double r = ddiv(L.inst[ii].dt, L.cell_h[g]);
     const int b = 1 + (int)(4.0f * log2f(1.0f + (float)r));
     return b < 1 ? 1 : (b > NBUCKET - 1 ? NBUCKET - 1 : b);
 }
@@ -733,8 +762,8 @@ struct Integrator {
             }
             const double T = I.T[S.cell], p = I.p[S.cell];
             S.p = p;
-            S.Ctot = p * 1e-6 / (R_GAS * T);
-            S.invCtot = 1.0 / S.Ctot;
+            S.Ctot = ddiv(p * 1e-6, R_GAS * T);
+            S.invCtot = ddiv(1.0, S.Ctot);
             if constexpr (!EN) {
                 // the cell's rate constants into the lane's (coalesced or shared) copy
                 K = W.Kl;
@@ -745,6 +774,7 @@ struct Integrator {
             }
             const int n = L.nV;
             Lane<double> Y = V(V_Y), F0 = V(V_F0), F0c = W.F0cell(g);
+#pragma unroll 1
             for (int k = 0; k < n; ++k) {
                 Y[k] = k < M.nS ? I.Y[(int64_t)k * I.ldY + S.cell] : T;
                 F0[k] = F0c[k];
@@ -752,12 +782,13 @@ struct Integrator {
             if (METHOD == KIN_RKC && L.sigma_method == KIN_SIGMA_POWER) {
                 // the pre-pass estimate's direction warm-starts the next one
                 Lane<double> EV = V(V_RS), EVc = W.EVcell(g);
+#pragma unroll 1
                 for (int k = 0; k < n; ++k) EV[k] = EVc[k];
             }
             S.dt = I.dt;
             S.rtol = I.rtol;
             S.atol = I.atol;
-            S.invN = 1.0 / n;
+            S.invN = ddiv(1.0, (double)n);
             S.t = 0.0;
             S.h = L.cell_h[g];
             S.sigma = L.cell_sig[g];
@@ -824,6 +855,7 @@ struct Integrator {
             return;
         }
         Lane<double> Y = V(V_Y), X = V(V_X), RS = V(V_RS);
+#pragma unroll 1
         for (int i = 0; i < L.nV; ++i) {
             X[i] = Y[i];
             RS[i] = 0.0;
@@ -841,6 +873,7 @@ struct Integrator {
     {
         Lane<double> Y = V(V_Y), X = V(V_X), RS = V(V_RS), FX = V(V_FX), F0 = V(V_BASE);
         const double ie = rcp_newton(S.eps);
+#pragma unroll 1
         for (int i = 0; i < L.nV; ++i) RS[i] += fabs((FX[i] - F0[i]) * ie);
         X[S.col] = Y[S.col];
         if (++S.col < L.nV) {
@@ -849,6 +882,7 @@ struct Integrator {
             return false;
         }
         double sg = 0.0;
+#pragma unroll 1
         for (int i = 0; i < L.nV; ++i) sg = fmax(sg, RS[i]);
         S.sigma = sg;
         S.nsig++;
@@ -878,13 +912,13 @@ struct Integrator {
             hh = S.dt - S.t;
             S.last = true;
         }
-        const double sr = floor(1.0 + sqrt(1.0 + 1.54 * hh * S.sigma));
+        const double sr = floor(1.0 + dsqrt(1.0 + 1.54 * hh * S.sigma));
         int s;
         if (sr < 2.0) {
             s = 2;
         } else if (sr > (double)SMAX) {
             s = SMAX;
-            hh = ((SMAX - 1.0) * (SMAX - 1.0) - 1.0) / (1.54 * S.sigma);
+            hh = ddiv((SMAX - 1.0) * (SMAX - 1.0) - 1.0, 1.54 * S.sigma);
             S.last = false;
         } else {
             s = (int)sr;
@@ -894,6 +928,7 @@ struct Integrator {
         // w_1 = y + mu~_1 h f_0 into slot A; w_0 = y stays in V_Y
         const double m1 = coef(s, 1)[2] * hh;
         Lane<double> Y = V(V_Y), F0 = V(V_F0), A = V(V_A);
+#pragma unroll 1
         for (int i = 0; i < L.nV; ++i) A[i] = Y[i] + m1 * F0[i];
         S.iw1 = V_A;
         S.iw2 = V_Y;
@@ -932,6 +967,7 @@ struct Integrator {
             Lane<double> Y = V(V_Y), F0 = V(V_F0), W1 = V(S.iw1), W2 = V(fin ? S.iw1 : S.iw2),
                          FJ = V(V_FX), WN = V(nw);
             double acc = 0.0;
+#pragma unroll 1
             for (int i = 0; i < L.nV; ++i) {
                 const double y = Y[i], w1 = W1[i];
                 const double v = c0 * y + mu * w1 + nu * W2[i] + mt * FJ[i] + gt * F0[i];
@@ -997,6 +1033,7 @@ struct Integrator {
                 else fac = 0.8 * z;
             }
             fac = fmin(10.0, fmax(0.1, fac));
+#pragma unroll 1
             for (int i = 0; i < L.nV; ++i) {
                 Y[i] = WS[i];
                 F0[i] = FX[i];
@@ -1029,6 +1066,7 @@ struct Integrator {
     __device__ void rkck_stage_point(LaneState& S, int st)
     {
         Lane<double> Y = V(V_Y), X = V(V_X);
+#pragma unroll 1
         for (int i = 0; i < L.nV; ++i) {
             double acc = 0.0;
             for (int l = 0; l < st; ++l) acc += CK_B[st][l] * V(ck_slot(l))[i];
@@ -1069,6 +1107,7 @@ struct Integrator {
         const double hh = S.hh;
         double errmax = 0.0;
         bool blown = false;  // a NaN component makes the estimate non-finite (a rejection)
+#pragma unroll 1
         for (int i = 0; i < L.nV; ++i) {
             double s5 = 0.0, e = 0.0;
             for (int l = 0; l < 6; ++l) {
@@ -1086,6 +1125,7 @@ struct Integrator {
         S.attempts++;
         if (errmax <= 1.0) {
             S.nacc++;
+#pragma unroll 1
             for (int i = 0; i < L.nV; ++i) Y[i] = X[i];
             if (S.last) {
                 S.t = S.dt;
@@ -1110,6 +1150,7 @@ struct Integrator {
     {
         Lane<double> a = V(v);
         bool ok = true;
+#pragma unroll 1
         for (int i = 0; i < L.nV; ++i) ok &= isfinite(a[i]);
         return ok;
     }

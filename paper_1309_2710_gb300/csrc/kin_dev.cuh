@@ -46,6 +46,7 @@ constexpr int ELL_SLOTS = (KIN_MAX_SPECIES + 31) / 32;
 struct MechDev {
     int nS, nR, nM, nFO, nnz;
     const double* W;       // [nS]
+    const float* W32;      // [nS]
     const double* invW;    // [nS]
     const float* invW32;   // [nS]
     const double* lnA;     // [nR]

@@ -159,10 +159,13 @@ __host__ __device__ __forceinline__ int warp_group_words(const MechDev& M)
 // arithmetic type R. Kc are the cell's rate constants (stored as KT) in
 // reaction-permutation order followed by k0/kinf per falloff ordinal (written
 // earlier in the same pre-pass kernel, so not read through the read-only
-// cache); C and OM are the warp's shared arrays.
+// cache); C and OM are the warp's shared arrays. Ctot and invCtot (the total
+// concentration p / (R T) and its reciprocal) come in the arithmetic type, so
+// that the FP32 evaluation's scalar work stays off the FP64 pipe: only the
+// state's conversions in and the rates' conversions out are FP64 operations.
 template <typename R, typename KT, int NR, int G = 32>
 __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C, R* OM,
-                                           double Ctot, double invCtot, const double (&x)[NR],
+                                           R Ctot, R invCtot, const double (&x)[NR],
                                            double (&out)[NR], int lane, unsigned mask = 0xffffffffu)
 {
     const int nS = M.nS, nR = M.nR, nM = M.nM;
@@ -178,7 +181,7 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
         }
     }
     s = group_sum<G>(s, mask);
-    const R rho = (R)Ctot * Tab<R>::inv(s);
+    const R rho = Ctot * Tab<R>::inv(s);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int i = lane + G * r;
@@ -202,13 +205,13 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
                 v *= Mc;
             } else {
                 const R Pr = (R)Kc[nR + (q - nF)] * Mc;
-                v *= Pr / (R(1) + Pr);
+                v *= rdiv<R>(Pr, R(1) + Pr);
             }
         }
         OM[q] = v;
     }
     __syncwarp(mask);
-    const double invrho = (double)s * invCtot;
+    const R invrho = s * invCtot;
     if constexpr (G == 32 && sizeof(R) == 4) {
         if (M.seg_ent) {
             // omega over equal chunks of the nonzeros (seg_tables.h); the
@@ -238,7 +241,7 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
                         const float* pp = P + (pt >> 8);
                         float v = pp[0];
                         for (int c = 1; c < (pt & 0xff); ++c) v += pp[c];
-                        o = (double)v * (M.W[i] * invrho);
+                        o = (double)(v * (M.W32[i] * invrho));
                     }
                 }
                 out[r] = o;
@@ -281,7 +284,7 @@ __device__ __forceinline__ void warp_feval(const MechDev& M, const KT* Kc, R* C,
                 }
                 if (e < e1) w0 += nuW[e] * OM[M.csrp_rxn[e]];
             }
-            o = (double)(w0 + w1) * invrho;
+            o = (double)((w0 + w1) * invrho);
         }
         out[r] = o;
     }
@@ -304,8 +307,8 @@ __device__ __forceinline__ void warp_feval_energy(const MechDev& M, double p, R*
 {
     const int nS = M.nS, nR = M.nR, nM = M.nM;
     const double T = __shfl_sync(mask, reg_get(x, nS / G), nS % G, G);
-    const double lnT = log(T), invT = 1.0 / T;
-    const double Ctot = p * 1e-6 * invT * (1.0 / R_GAS), invCtot = 1.0 / Ctot;
+    const double lnT = log(T), invT = ddiv(1.0, T);
+    const double Ctot = p * 1e-6 * invT * (1.0 / R_GAS), invCtot = ddiv(1.0, Ctot);
     const R* __restrict__ invW = Tab<R>::invW(M);
     R s = R(0);
 #pragma unroll
@@ -342,7 +345,7 @@ __device__ __forceinline__ void warp_feval_energy(const MechDev& M, double p, R*
             } else {
                 const double a0 = M.lnA0[j] + M.beta0[j] * lnT - M.Ea0R[j] * invT;
                 const R Pr = Tab<R>::ex(a0 - a) * Mc;
-                v *= Pr / (R(1) + Pr);
+                v *= rdiv<R>(Pr, R(1) + Pr);
             }
         }
         OM[q] = v;
@@ -373,7 +376,7 @@ __device__ __forceinline__ void warp_feval_energy(const MechDev& M, double p, R*
     }
     hw = group_sum<G>(hw, mask);
     cpm = group_sum<G>(cpm, mask);
-    const double dTdt = -hw * invrho / cpm;
+    const double dTdt = ddiv(-hw * invrho, cpm);
 #pragma unroll
     for (int r = 0; r < NR; ++r)
         if (lane + G * r == nS) out[r] = dTdt;
@@ -403,6 +406,7 @@ struct WarpRKC {
     const R* Kc;
     int lane, nV;  // nV: state length, nS + 1 with the energy equation
     double Ctot, invCtot, atol, rtol, p;
+    R CtotR, invCtotR;   // the same in the rate type
     int nfe, nsig, nfs;  // f evaluations, sigma estimates, f evaluations inside them
     double y[NR], f0[NR], w1[NR], w2[NR], fx[NR], x[NR], ev[NR];
 
@@ -420,7 +424,7 @@ struct WarpRKC {
     __device__ __forceinline__ void f(const double (&in)[NR], double (&o)[NR])
     {
         if constexpr (EN) warp_feval_energy<R, NR>(M, p, C, OM, in, o, lane);
-        else warp_feval<R, R, NR>(M, Kc, C, OM, Ctot, invCtot, in, o, lane);
+        else warp_feval<R, R, NR>(M, Kc, C, OM, CtotR, invCtotR, in, o, lane);
         nfe++;
     }
 
@@ -706,6 +710,8 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC, EN>::min_blocks) warp
         const double T = I.T[c], p = I.p[c];
         W.Ctot = ddiv(p * 1e-6, R_GAS * T);
         W.invCtot = ddiv(1.0, W.Ctot);
+        W.CtotR = (R)W.Ctot;
+        W.invCtotR = (R)W.invCtot;
         W.atol = I.atol;
         W.rtol = I.rtol;
         W.p = p;
@@ -718,7 +724,7 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC, EN>::min_blocks) warp
             // evaluations in the staged copy when there is one)
             R* kc = reinterpret_cast<R*>(L.cell_k) + g * nK;
             R* ks = W.Ks ? W.Ks : kc;
-            const double lnT = log(T), invT = 1.0 / T;
+            const double lnT = log(T), invT = ddiv(1.0, T);
             for (int q = lane; q < M.nR; q += 32) {
                 const int j = M.rxn_perm[q];
                 const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;
@@ -811,6 +817,8 @@ __global__ void __launch_bounds__(256, WarpBounds<NR, OCC, EN>::min_blocks) warp
             const double T = I.T[c], p = I.p[c];
             W.Ctot = ddiv(p * 1e-6, R_GAS * T);
             W.invCtot = ddiv(1.0, W.Ctot);
+            W.CtotR = (R)W.Ctot;
+            W.invCtotR = (R)W.invCtot;
             W.atol = I.atol;
             W.rtol = I.rtol;
             W.p = p;
@@ -884,6 +892,7 @@ struct WarpRKCK {
     int lane, nV;
     unsigned mask;  // the group's lanes
     double Ctot, invCtot, atol, rtol, p;
+    R CtotR, invCtotR;  // the same in the rate type
     int nfe;
     double y[NR], x[NR], kx[NR], k[6][NR];
 
@@ -902,7 +911,7 @@ struct WarpRKCK {
     __device__ __forceinline__ void f(const double (&in)[NR], double (&o)[NR])
     {
         if constexpr (EN) warp_feval_energy<R, NR, G>(M, p, C, OM, in, o, lane, mask);
-        else warp_feval<R, R, NR, G>(M, Kc, C, OM, Ctot, invCtot, in, o, lane, mask);
+        else warp_feval<R, R, NR, G>(M, Kc, C, OM, CtotR, invCtotR, in, o, lane, mask);
         nfe++;
     }
 
@@ -1000,6 +1009,8 @@ __global__ void __launch_bounds__(256, NR == 8 ? 1 : 2) warp_rkck_kernel(const _
         const double T = I.T[c], p = I.p[c];
         W.Ctot = ddiv(p * 1e-6, R_GAS * T);
         W.invCtot = ddiv(1.0, W.Ctot);
+        W.CtotR = (R)W.Ctot;
+        W.invCtotR = (R)W.invCtot;
         W.atol = I.atol;
         W.rtol = I.rtol;
         W.p = p;
@@ -1008,7 +1019,7 @@ __global__ void __launch_bounds__(256, NR == 8 ? 1 : 2) warp_rkck_kernel(const _
             // formed straight into the staged copy when there is one (the
             // previous cell's last f ended in a sync of the group)
             R* kc = W.Ks ? W.Ks : reinterpret_cast<R*>(L.cell_k) + g * nK;
-            const double lnT = log(T), invT = 1.0 / T;
+            const double lnT = log(T), invT = ddiv(1.0, T);
             for (int qq = lane; qq < M.nR; qq += G) {
                 const int j = M.rxn_perm[qq];
                 const double a = M.lnA[j] + M.beta[j] * lnT - M.EaR[j] * invT;

@@ -28,6 +28,7 @@ template <typename T> struct Lane {
 };
 template <typename R> struct Tab;
 template <> struct Tab<double> { static double inv(double a) { return 1.0 / a; } };
+inline double ddiv(double a, double b) { return a / b; }
 constexpr double R_GAS = 8.314462618, T_REF = 298.15;
 using std::exp;
 using std::fma;
