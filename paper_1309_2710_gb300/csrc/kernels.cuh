@@ -939,16 +939,73 @@ struct Integrator {
         return -1;
     }
 
+    // Weighted RMS norm (Eq. (E:rmsE)) of the error vectors of the lanes in
+    // the final phase, left in their free slot nw; returns the sum of squares
+    // on those lanes. The per-element work (weight, reciprocal, scaling) of
+    // all of them is spread over every lane that reaches this point with
+    // them, so that a warp whose lanes end their steps at different times
+    // runs it in ceil(k n / 32) rounds instead of n rounds with k lanes
+    // active. Each final-phase lane then adds its own squares in element
+    // order: the result is bit for bit that of the lane alone.
+    __device__ double final_norm(const LaneState& S, bool fin, int nw)
+    {
+        const unsigned mask = __activemask();
+        const unsigned fm = __ballot_sync(mask, fin);
+        if (fm == 0u) return 0.0;
+        const int lane = threadIdx.x & 31;
+        const int n = L.nV;
+        const int nact = __popc(mask);
+        const int rank = __popc(mask & ((1u << lane) - 1u));
+        const int items = __popc(fm) * n;
+        const int64_t ns = L.nslots;
+        const int64_t slot0 = W.slot - lane;  // the warp's lanes hold consecutive slots
+        for (int base = 0; base < items; base += nact) {
+            const int t = base + rank;
+            const bool live = t < items;
+            const int f = live ? t / n : 0;
+            unsigned m = fm;  // the f-th finishing lane
+            for (int c = 0; c < f; ++c) m &= m - 1u;
+            const int A = __ffs(m) - 1;
+            const int a_iw1 = __shfl_sync(mask, S.iw1, A);
+            const int a_nw = __shfl_sync(mask, nw, A);
+            const double a_atol = __shfl_sync(mask, S.atol, A);
+            const double a_rtol = __shfl_sync(mask, S.rtol, A);
+            if (live) {
+                const int i = t - f * n;
+                double* const va = L.vec + slot0 + A;
+                const double y = va[((int64_t)V_Y * n + i) * ns];
+                const double w1 = va[((int64_t)a_iw1 * n + i) * ns];
+                double* const pd = va + ((int64_t)a_nw * n + i) * ns;
+                const double sc = a_atol + a_rtol * fmax(fabs(y), fabs(w1));
+                *pd = *pd * rcp_newton(sc);
+            }
+        }
+        __syncwarp(mask);
+        double acc = 0.0;
+        if (fin) {
+            Lane<double> D = V(nw);
+#pragma unroll 1
+            for (int i = 0; i < n; ++i) {
+                const double r = D[i];
+                acc += r * r;
+            }
+        }
+        return acc;
+    }
+
     __device__ int rkc_post(LaneState& S)
     {
-        if (S.phase == PH_STAGE || S.phase == PH_FINAL) {
+        const bool fin = S.phase == PH_FINAL;
+        const bool sf = S.phase == PH_STAGE || fin;
+        int nw = 0;
+        if (sf) {
             // One pass serves both phases, so that lanes of a warp in either
             // share it instead of running two loops in turn. FX = f(w_{j-1}):
             //   stage j: w_j = (1-mu-nu) y + mu w_{j-1} + nu w_{j-2}
             //                  + mu~ h f_{j-1} + gamma~ h f_0;
             //   final:   Delta = 0.8 (y - w_s) + 0.4 h (f_0 + f_s), the same
-            //            five-term form (nu = 0), and its weighted RMS norm.
-            const bool fin = S.phase == PH_FINAL;
+            //            five-term form (nu = 0), into the free slot for
+            //            final_norm.
             double c0, mu, nu, mt, gt;
             if (fin) {
                 c0 = 0.8;
@@ -963,22 +1020,15 @@ struct Integrator {
                 gt = c[3] * S.hh;
                 c0 = c[4];
             }
-            const int nw = (S.iw1 == V_A) ? V_B : (S.iw1 == V_B ? V_C : V_A);
+            nw = (S.iw1 == V_A) ? V_B : (S.iw1 == V_B ? V_C : V_A);
             Lane<double> Y = V(V_Y), F0 = V(V_F0), W1 = V(S.iw1), W2 = V(fin ? S.iw1 : S.iw2),
                          FJ = V(V_FX), WN = V(nw);
-            double acc = 0.0;
 #pragma unroll 1
-            for (int i = 0; i < L.nV; ++i) {
-                const double y = Y[i], w1 = W1[i];
-                const double v = c0 * y + mu * w1 + nu * W2[i] + mt * FJ[i] + gt * F0[i];
-                if (fin) {
-                    const double sc = S.atol + S.rtol * fmax(fabs(y), fabs(w1));
-                    const double r = v * rcp_newton(sc);
-                    acc += r * r;
-                } else {
-                    WN[i] = v;
-                }
-            }
+            for (int i = 0; i < L.nV; ++i)
+                WN[i] = c0 * Y[i] + mu * W1[i] + nu * W2[i] + mt * FJ[i] + gt * F0[i];
+        }
+        const double acc = final_norm(S, fin, nw);
+        if (sf) {
             if (fin) return rkc_final(S, acc);
             S.iw2 = S.iw1;
             S.iw1 = nw;
