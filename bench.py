@@ -54,9 +54,9 @@ SM_MAX_MHZ = 2070.0
 # cells in the captured launch). A capture on fewer cells than the benchmarked
 # workload is scaled by the cell count.
 TRAFFIC = {
-    "1150e5bd0eb7": {
-        ("h2co_13sp_rkc", (32, 16, 0, 0, 1), "generated"): (3996238080 + 5508681728, 262144),
-        ("ch4_53sp_rkc_mixed", (256, 5, 0, 1, 2), "tables"): (354568704 + 1332684288, 65536),
+    "ceefb53687b8": {
+        ("h2co_13sp_rkc", (32, 16, 0, 0, 1), "generated"): (7350724352 + 13686305280, 262144),
+        ("ch4_53sp_rkc_mixed", (256, 5, 0, 1, 2), "tables"): (353488640 + 1337438464, 65536),
     },
 }
 
