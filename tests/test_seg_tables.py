@@ -197,3 +197,54 @@ def test_unsupported_forms_are_refused(lib):
     assert build(lib, 2, 2, ptr, np.array([0, 2], np.int32), np.array([1.0, -1.0])) is None
     # the ordinary form passes
     assert build(lib, 2, 2, ptr, pos, np.array([2.0, -1.0])) is not None
+
+
+def _rows_from(spec, nR):
+    """CSR arrays from a per-species list of (position, nu) entries."""
+    ptr, pos, val = [0], [], []
+    for row in spec:
+        for q, v in row:
+            pos.append(q)
+            val.append(v)
+        ptr.append(len(pos))
+    return np.array(ptr, np.int32), np.array(pos, np.int32), np.array(val, np.float64)
+
+
+def _edge_case(case):
+    rng = np.random.default_rng(11)
+    if case == "fewer_nonzeros_than_lanes":  # K = 1: most lanes only pad
+        return [[(0, 1.0)], [(1, -1.0), (2, 1.0)], [], [(3, 2.0)]], 4
+    if case == "one_row_over_many_lanes":  # a 250-entry row cut into 28 parts
+        return [[(j, 1.0) for j in range(250)], [(j, -1.0) for j in range(10)], [(5, 2.0)]], 300
+    if case == "empty_rows_between":
+        spec = []
+        for i in range(40):
+            spec.append([] if i % 3 else [(int(q), 1.0) for q in rng.choice(90, 7, replace=False)])
+        return spec, 90
+    # coefficients -2..2 and rows of very different lengths
+    spec = []
+    for i in range(37):
+        k = int(rng.integers(0, 60))
+        spec.append([(int(q), float(rng.choice([-2.0, -1.0, 1.0, 2.0]))) for q in rng.choice(500, k, replace=False)])
+    return spec, 500
+
+
+@pytest.mark.parametrize("case", ["fewer_nonzeros_than_lanes", "one_row_over_many_lanes", "empty_rows_between",
+                                  "mixed_lengths_and_coefficients"])
+def test_segmented_gather_edge_cases(lib, case):
+    spec, nR = _edge_case(case)
+    nS = len(spec)
+    ptr, pos, val = _rows_from(spec, nR)
+    t = build(lib, nS, nR, ptr, pos, val)
+    assert t is not None
+    K, nslots, ent, slot0, part = t
+    nnz = int(ptr[-1])
+    assert K == max(1, -(-nnz // 32))
+    assert nslots <= nS + 31
+    Om = np.random.default_rng(3).uniform(-1, 1, nR)
+    out, visited = replay(K, nslots, ent, slot0, part, Om, nS)
+    want = np.array([sum(v * Om[q] for q, v in row) for row in spec])
+    np.testing.assert_allclose(out, want, rtol=1e-12, atol=1e-12)
+    assert sorted((q, v) for _, _, q, v in visited) == sorted(zip(pos.tolist(), val.tolist()))
+    empty = np.diff(ptr) == 0
+    assert ((part < 0) == empty).all() and (out[empty] == 0).all()
