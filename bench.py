@@ -54,9 +54,9 @@ SM_MAX_MHZ = 2070.0
 # cells in the captured launch). A capture on fewer cells than the benchmarked
 # workload is scaled by the cell count.
 TRAFFIC = {
-    "ceefb53687b8": {
-        ("h2co_13sp_rkc", (32, 16, 0, 0, 1), "generated"): (7350724352 + 13686305280, 262144),
-        ("ch4_53sp_rkc_mixed", (256, 5, 0, 1, 2), "tables"): (353488640 + 1337438464, 65536),
+    "d4328964f870": {
+        ("h2co_13sp_rkc", (32, 16, 0, 0, 1), "generated"): (7332879872 + 13668991488, 262144),
+        ("ch4_53sp_rkc_mixed", (256, 5, 0, 1, 2), "tables"): (348273920 + 1347731968, 65536),
     },
 }
 

@@ -594,7 +594,16 @@ struct WarpRKC {
                 hh = dt - t;
                 last = true;
             }
-            const double sr = floor(1.0 + dsqrt(1.0 + 1.54 * hh * sig));
+            // The mixed-precision path takes the stage count's square root in
+            // FP32: s is an integer, which the FP32 root changes only where
+            // 1 + sqrt(1 + 1.54 h sigma) lies within FP32 rounding of an
+            // integer, and the FP64 root is a dozen instructions on the FP64
+            // pipe that all 32 lanes repeat.
+            double sr;
+            if constexpr (sizeof(R) == 4)
+                sr = (double)floorf(1.0f + sqrtf(1.0f + (float)(1.54 * hh * sig)));
+            else
+                sr = floor(1.0 + dsqrt(1.0 + 1.54 * hh * sig));
             int s;
             if (sr < 2.0) {
                 s = 2;
@@ -637,7 +646,15 @@ struct WarpRKC {
             // x = ||Delta||^2; z = x^(-1/6) = err^(-1/3) (see the lane kernel)
             // (one evaluation of the power serves both branches)
             const double xe = warp_sum(acc) * invN;
-            const double z = (xe > 0.0 && isfinite(xe)) ? rpow6_newton(xe) : 0.0;
+            // (the mixed-precision path keeps the FP32 power, within 4 ulp: a
+            // step-size factor, with the FP32 rates' precision)
+            double z = 0.0;
+            if (xe > 0.0 && isfinite(xe)) {
+                if constexpr (sizeof(R) == 4)
+                    z = f32_normal(xe) ? (double)powf((float)xe, -1.0f / 6.0f) : dpow(xe, -1.0 / 6.0);
+                else
+                    z = rpow6_newton(xe);
+            }
             if (xe <= 1.0) {
                 nacc++;
                 double fac, c3 = 0.0;
