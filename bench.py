@@ -171,7 +171,7 @@ def algorithmic_work(m, method, precision, sigma, stats, energy=False):
     return float(ops64), float(ops32), exact
 
 
-def survey_flops(m, method, precision, stats, energy=False):
+def contract_flops(m, method, precision, stats, energy=False):
     """Algorithmic flops of one call in the hot-path contract's count (an FMA
     is 2 flops), from the per-cell counters. Per f evaluation
     F = 4 nS + 2 nR + 2 nS nM + 6 nFO + 8 nR + 2 nS (mixture and
@@ -428,13 +428,13 @@ def rank_states(name, m, cells_per_rank, world, rank, order="random"):
 
 def roofline(m, method, prec, sigma, stats, energy, kernel_ms, pk, world=1):
     """The dominant launch against the binding arithmetic pipe, in two
-    counts: the hot-path contract's flops (FMA = 2; survey_flops) against
+    counts: the hot-path contract's flops (FMA = 2; contract_flops) against
     twice the measured FMA rate, and this build's lane operations (an FMA,
     add, multiply or divide is one; algorithmic_work) against the FMA rate.
     The FP64 and FP32 pipes run concurrently; the one with the larger work /
     peak binds."""
     ops64, ops32, exact = algorithmic_work(m, method, prec, sigma, stats, energy)
-    fl64, fl32 = survey_flops(m, method, prec, stats, energy)
+    fl64, fl32 = contract_flops(m, method, prec, stats, energy)
     if pk:
         f64, f32 = pk["fp64_fma_per_s"], pk["fp32_fma_per_s"]
         basis = ("measured: dependent-FMA probe (include/kin_peaks.h) on this GPU in this run, "

@@ -2,7 +2,7 @@
 import numpy as np
 
 # The FP64 target in the hot-path contract's metric, |dY| / max(|Y|, atol).
-SURVEY_TOL = 1e-8
+CONTRACT_TOL = 1e-8
 # Allowed multiple of the oracle's own rounding noise floor in that metric
 # (tests/oracle_variants.py). The CUDA path differs from the oracle in more
 # roundings at once than any one variant does (CUDA's exp, tree-ordered warp
@@ -42,7 +42,7 @@ def compare(Yg, Yo, st_g, st_o, sta_g, sta_o, atol, rtol, tol=1e-8, div_tol=None
 
     With `floor` (the oracle's rounding noise floor on the same cells, from
     tests.oracle_variants.reference), trace-identical cells must also meet
-    the contract's metric rel_err: at most max(SURVEY_TOL, FLOOR_K floor).
+    the contract's metric rel_err: at most max(CONTRACT_TOL, FLOOR_K floor).
     Returns a summary dict with both metrics.
     """
     div_tol = 10 * rtol if div_tol is None else div_tol
@@ -58,7 +58,7 @@ def compare(Yg, Yo, st_g, st_o, sta_g, sta_o, atol, rtol, tol=1e-8, div_tol=None
                max_err_atol_floor_same=float(rel_a[same].max()) if same.any() else 0.0)
     if floor is not None:
         out["noise_floor"] = float(floor)
-        out["atol_floor_bound"] = max(SURVEY_TOL, FLOOR_K * float(floor))
+        out["atol_floor_bound"] = max(CONTRACT_TOL, FLOOR_K * float(floor))
     assert out["max_err_same"] <= tol, out
     assert (~same).mean() <= max_div_frac, out
     assert out["max_err_divergent"] <= div_tol, out

@@ -118,7 +118,7 @@ def test_traffic_lookup(monkeypatch):
     assert bench.traffic_for("w", (32, 16, 0, 0, 1), "generated", 10) == (None, None)
 
 
-def test_survey_flops_by_hand():
+def test_contract_flops_by_hand():
     """The hot-path contract's flop count: per f evaluation
     F = 4 nS + 2 nR + 2 nS nM + 6 nFO + 8 nR + 2 nS; RKC adds 10 nS per
     stage, 14 nS per attempt, 2 nS^2 per spectral-radius estimate."""
@@ -126,24 +126,24 @@ def test_survey_flops_by_hand():
     F = 4 * 3 + 2 * 4 + 2 * 3 * 2 + 6 * 1 + 8 * 4 + 2 * 3
     assert F == 76
     st = stats([[40, 10, 1, 2, 6]])
-    f64, f32 = bench.survey_flops(m, synth.RKC, synth.FP64, st)
+    f64, f32 = bench.contract_flops(m, synth.RKC, synth.FP64, st)
     stages, att = 40 - 6 - 2, 11
     assert f32 == 0
     assert f64 == 34 * F + stages * 10 * 3 + att * 14 * 3 + 2 * 2 * 9 + 6 * F
     st = stats([[40, 10, 1, 2, 8]])
-    f64, f32 = bench.survey_flops(m, synth.RKC, synth.MIXED, st)
+    f64, f32 = bench.contract_flops(m, synth.RKC, synth.MIXED, st)
     rate = 40 - 8
     assert f32 == rate * (F - 2 * 3)
     assert f64 == rate * 2 * 3 + (rate - 2) * 10 * 3 + att * 14 * 3 + 2 * 2 * 9 + 8 * F
     st = stats([[60, 8, 2, 0, 0]])
-    f64, f32 = bench.survey_flops(m, synth.RKCK, synth.FP64, st)
+    f64, f32 = bench.contract_flops(m, synth.RKCK, synth.FP64, st)
     assert f64 == 60 * F + 10 * 60 * 3 and f32 == 0
 
 
-def test_survey_flops_per_evaluation_of_the_headline_mechanism():
+def test_contract_flops_per_evaluation_of_the_headline_mechanism():
     # 13 species, 54 reactions, 5 third-body reactions, no falloff: 748 flops
     m = synth.workload_mechanism("h2co_13sp_rkc")
-    assert bench.survey_flops(m, synth.RKCK, synth.FP64, stats([[1, 0, 0, 0, 0]]))[0] == 748
+    assert bench.contract_flops(m, synth.RKCK, synth.FP64, stats([[1, 0, 0, 0, 0]]))[0] == 748
 
 
 def test_launcher_runs_one_process_per_gpu():
